@@ -1,0 +1,387 @@
+#!/usr/bin/env python3
+"""Benchmark of the SVT track-fit hot path on GB300.
+
+One step = one batch of the scaled-up workload (3000 events; roads per event
+Poisson(64); hits per layer geometric with mean 3 capped at 8; 512 sectors)
+through unpack -> combine -> fit -> cut -> select -> format.  The fused
+persistent path is the headline; the plain per-stage path is timed beside it.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead: the paper ships no code, so the oracle is the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fits/sec"
+UNIT = "fits/s"
+# Integer operations one combination needs in the separable evaluation used by
+# the fused kernel: per chi row a two-word add, a funnel shift, a two-op clamp
+# and a multiply-add (6 x 3), plus the compare against the running best.
+OPS_PER_FIT = 19
+# int32 issue peak: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz
+N_SM, LANES_PER_SM, SM_MAX_GHZ = 152, 128, 2.07
+ALU_PEAK_TOPS = N_SM * LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12
+FIT_KERNEL_SRC = os.path.join(ROOT, "paper_1311_0380_gb300", "csrc", "svt_fused.cu")
+TRAFFIC_NOTE = os.path.join(ROOT, "profiles", "fit_persistent_scaled3000.md")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="svt", choices=["svt", "reference"])
+    ap.add_argument("--workload", default="scaled", choices=["scaled", "paper", "uneven", "small"])
+    ap.add_argument("--events", type=int, default=3000)
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--rows", type=int, default=0)
+    ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--bps", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def file_sha(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the fit kernel from the committed ncu summary,
+    or None when the summary is absent or the kernel source changed since."""
+    try:
+        text = open(TRAFFIC_NOTE).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+kernel_sha:\s*([0-9a-f]+)", text)
+    if not m or m.group(2) != file_sha(FIT_KERNEL_SRC):
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="svt_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def workload(args, rank):
+    from paper_1311_0380_gb300 import synth
+    spec = synth.SPECS[args.workload]
+    consts = synth.make_constants(spec.n_sectors)
+    # every rank fits its own batch (independent events): weak scaling
+    batch = synth.make_batch(spec, args.events, consts, seed=spec.seed + 7919 * rank)
+    return spec, consts, batch
+
+
+def percentile(xs, p):
+    return float(np.percentile(np.asarray(xs, np.float64), p)) if xs else None
+
+
+def cpu_baseline(spec, consts, batch, budget_s=12.0):
+    """The oracle as it stands (serial C), on a bounded sample of the batch."""
+    import oracle
+    cfg = oracle.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, spec.n_sectors)
+    fits_ev = batch.combinations(spec.max_comb)
+    # event prefix sized for about budget_s of serial work (~12 Mfits/s per core)
+    road_end = np.cumsum(batch.n_roads)
+    fits_cum = np.concatenate([[0], np.cumsum(fits_ev)])
+    target = budget_s * 12e6
+    n_ev = int(np.searchsorted(fits_cum[road_end], target)) + 1
+    n_ev = max(1, min(n_ev, batch.n_events))
+    n_words = int(batch.event_off[n_ev])
+    words = batch.words[:n_words]
+    off = batch.event_off[: n_ev + 1]
+    fits = int(fits_cum[road_end[n_ev - 1]])
+    t0 = time.perf_counter()
+    key, _ = oracle.run(words, off, consts.F, consts.q, cfg, omp=False)
+    dt = time.perf_counter() - t0
+    assert key == oracle.KEY_OK
+    return {"value": fits / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"first {n_ev} of {batch.n_events} events ({fits} fits), serial C oracle, one pass",
+            "seconds": round(dt, 3)}
+
+
+def run_reference(args, world, rank):
+    """--impl reference: the CPU oracle, timed step by step on a bounded sample."""
+    if rank != 0:
+        return
+    import oracle
+    spec, consts, batch = workload(args, 0)
+    cfg = oracle.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, spec.n_sectors)
+    # each step: a 30-event slice of the workload (about 1.1M fits for 'scaled')
+    step_events = max(1, min(30, batch.n_events))
+    ev_of_road = np.repeat(np.arange(batch.n_events), batch.n_roads)
+    fits_ev = np.bincount(ev_of_road, weights=batch.combinations(spec.max_comb),
+                          minlength=batch.n_events).astype(np.int64)
+    slices = []
+    for s in range(args.warmup + args.steps):
+        e0 = (s * step_events) % max(1, batch.n_events - step_events + 1)
+        e1 = e0 + step_events
+        w0, w1 = int(batch.event_off[e0]), int(batch.event_off[e1])
+        slices.append((batch.words[w0:w1], (batch.event_off[e0:e1 + 1] - batch.event_off[e0]),
+                       int(fits_ev[e0:e1].sum())))
+    for s in range(args.warmup):
+        oracle.run(slices[s][0], slices[s][1], consts.F, consts.q, cfg)
+    t0 = time.perf_counter()
+    fits = 0
+    for s in range(args.warmup, args.warmup + args.steps):
+        key, _ = oracle.run(slices[s][0], slices[s][1], consts.F, consts.q, cfg)
+        assert key == oracle.KEY_OK
+        fits += slices[s][2]
+    dt = time.perf_counter() - t0
+    value = fits / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}-{step_events}ev-slices", "events_per_step": step_events,
+                   "fits_per_step": fits / args.steps, "sectors": spec.n_sectors},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{step_events}-event slices of the {args.workload} workload per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    from paper_1311_0380_gb300 import api
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec, consts, batch = workload(args, rank)
+    cfg = api.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, spec.n_sectors)
+    dconst = api.DeviceConstants.from_numpy(consts.F, consts.q, cfg, dev)
+    n_words, n_events, R = len(batch.words), batch.n_events, batch.total_roads
+    sched = api.schedule(args.warps, args.bps, args.rows)
+    fused = api.FusedPath(n_words, n_events, R, dconst, sched, dev)
+    d_words = api.to_device_u32(batch.words, dev)
+    d_off = api.to_device_u64(batch.event_off, dev)
+    timer = api.FitTimer()
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)   # 256 MB > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- fused path, inputs resident in HBM
+    for _ in range(args.warmup):
+        fused.run(d_words, n_words, d_off, n_events, timer=timer)
+    torch.cuda.synchronize()
+    status, rec, counts = fused.result()
+    assert status == api.N.STATUS_OK, api.N.decode_status(status)
+    fits_per_step = int(counts[2])
+    passing = int(counts[3])
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    step_ms, fit_ms = [], []
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        for i in range(args.steps):
+            flush.fill_(i)
+            ev[i][0].record(stream)
+            fused.run(d_words, n_words, d_off, n_events, timer=timer)
+            ev[i][1].record(stream)
+            fit_ms.append(timer.fit_ms())
+        torch.cuda.synchronize()
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * fits_per_step * args.steps / (total_ms / 1e3)
+    clock_summary = clocks.summary()
+
+    # ---- roofline of the persistent fit kernel (ALU / issue bound)
+    fit_mean_s = statistics.mean(fit_ms) / 1e3
+    achieved = fits_per_step * OPS_PER_FIT / fit_mean_s / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                "frac": achieved / ALU_PEAK_TOPS, "traffic": recorded_traffic(),
+                "kernel": "k_fit_persistent", "ops_per_fit": OPS_PER_FIT,
+                "fit_kernel_ms": statistics.mean(fit_ms),
+                "peak_source": "152 SM x 128 int32 lanes x 2.07 GHz (issue bound)"}
+
+    # ---- end to end through host buffers (fused)
+    e2e = None
+    lat_fused = []
+    if not args.no_e2e:
+        runner = api.HostRunner(fused, stream)
+        h_words, h_off = api.HostRunner.pin_batch(batch.words, batch.event_off)
+        for _ in range(args.warmup):
+            runner.submit(h_words, h_off, R)
+            runner.wait()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        h2d = d2h = 0
+        for i in range(args.steps):
+            flush.fill_(i)
+            evs[i][0].record(stream)
+            h2d, d2h = runner.submit(h_words, h_off, R)
+            evs[i][1].record(stream)
+            st, out = runner.wait()
+        assert st == api.N.STATUS_OK
+        assert np.array_equal(out, rec)
+        lat_fused = [a.elapsed_time(b) * 1e3 for a, b in evs]   # us
+        e2e = {"value": fits_per_step / (statistics.mean(lat_fused) / 1e6), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "p50_us": percentile(lat_fused, 50), "p99_us": percentile(lat_fused, 99)}
+
+    # ---- plain per-stage path beside it
+    plain = None
+    if not args.no_plain:
+        pp = api.PlainPath(n_words, n_events, R, fits_per_step, dconst, dev)
+        for _ in range(args.warmup):
+            pp.run(d_words, n_words, d_off, n_events)
+        torch.cuda.synchronize()
+        pst, prec, _ = pp.result()
+        assert pst == api.N.STATUS_OK and np.array_equal(prec, rec), "plain path differs"
+        evp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for i in range(args.steps):
+            flush.fill_(i)
+            evp[i][0].record(stream)
+            pp.run(d_words, n_words, d_off, n_events)
+            evp[i][1].record(stream)
+        torch.cuda.synchronize()
+        pms = [a.elapsed_time(b) for a, b in evp]
+        plain = {"value": fits_per_step / (statistics.mean(pms) / 1e3), "unit": UNIT,
+                 "ms_per_step": statistics.mean(pms)}
+        if not args.no_e2e:
+            prun = api.HostRunner(pp, stream)
+            for _ in range(args.warmup):
+                prun.submit(h_words, h_off, R)
+                prun.wait()
+            lat = []
+            for i in range(args.steps):
+                flush.fill_(i)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                prun.submit(h_words, h_off, R)
+                b.record(stream)
+                prun.wait()
+                lat.append(a.elapsed_time(b) * 1e3)
+            plain["e2e_p50_us"] = percentile(lat, 50)
+            plain["e2e_p99_us"] = percentile(lat, 99)
+        del pp
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(spec, consts, batch)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}-{n_events}ev", "events": n_events, "roads": R,
+                       "fits_per_step": fits_per_step, "roads_passing": passing,
+                       "sectors": spec.n_sectors, "max_comb": spec.max_comb,
+                       "l2": "flushed between steps (256 MB write)",
+                       "schedule": {"warps": args.warps, "blocks_per_sm": args.bps, "rows": args.rows}},
+            "events_per_s": world * n_events * args.steps / (total_ms / 1e3),
+            "latency_us": {"p50": percentile([m * 1e3 for m in step_ms], 50),
+                           "p99": percentile([m * 1e3 for m in step_ms], 99)},
+            "e2e": e2e, "plain": plain, "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clock_summary,
+            "gpu_launches": api.FUSED_LAUNCHES_PER_RUN * args.steps,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

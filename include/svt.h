@@ -1,0 +1,275 @@
+/*
+ * svt.h -- C ABI of the GB300 (sm_103a) SVT linearised track-fit library.
+ *
+ * The method (Amerio et al., "Many-core applications to online track
+ * reconstruction in HEP experiments", Sec. 2): inside every road (a coarse
+ * track candidate), every combination of one hit per detector layer is fitted
+ * with a linearised fit, p_i = f_i . x + q_i, using integer multiply/add and
+ * constants looked up per road; the fit also yields a chi-square.  Sec. 2.1
+ * splits the code into three stages -- unpack the input words, compute all
+ * hit combinations of each road, fit each combination -- over three nested
+ * loops (events, roads, combinations).  This library adds the chi-square cut,
+ * the best combination per road and an output record.
+ *
+ * Fixed-point reading used throughout (the paper gives the form, not the
+ * widths):
+ *   x_l      unsigned 15-bit coordinate of the chosen hit of layer l (0..5),
+ *            0 for a layer without hits;
+ *   m        6-bit layer mask, bit l set iff layer l has at least one hit;
+ *   acc_k    = q[s][m][k] * 2^qshift + sum_l F[s][m][k][l] * x_l   (exact int64)
+ *   y_k      = floor(acc_k / 2^oshift)
+ *   p_k      = (int32) y_k for k = 0,1,2   (d0, phi, curvature)
+ *   chi2     = sum_{k=3..5} clamp(y_k, -32767, 32767)^2   (uint32)
+ *   pass     iff chi2 <= chi2_cut; per road keep the passing combination with
+ *            the smallest chi2, ties to the smallest combination index.
+ * Combination index c: mixed radix over layers, layer 0 most significant,
+ * layer 5 fastest, hits in order of appearance; n'_l = max(n_l, 1) and
+ * C = prod n'_l.  A road with C > max_comb evaluates c < max_comb only and is
+ * flagged OVERFLOW.  A road with fewer than min_layers layers hit is flagged
+ * BAD_PATTERN and not fitted.
+ *
+ * Input words (uint32, type in bits [31:30]):
+ *   event header (3): [29:12] event id, [11:0] number of roads (<= 4095)
+ *   road header  (2): [29:21] sector (< n_sectors <= 512), [20:0] road id
+ *   hit          (0): [29:27] layer (0..5), [26:15] reserved = 0, [14:0] coordinate
+ *   type 1 is invalid.  An event is its header followed by its roads; a road
+ *   is its header followed by its hits sorted by layer (at most 16 per layer).
+ *   event_off[n_events + 1] (uint64) gives each event's first word;
+ *   event_off[0] = 0, event_off[n_events] = n_words < 2^32.
+ *
+ * Output record, 6 x uint32 per road, roads in input order:
+ *   w0 = road id [20:0] | flags << 24   (PASS 1, OVERFLOW 2, BAD_PATTERN 4, NO_HITS 8)
+ *   w1 = best combination index (0xFFFFFFFF when nothing passes)
+ *   w2 = chi2 of the best combination (0 when nothing passes)
+ *   w3..w5 = p_0..p_2 as int32 bit patterns (0 when nothing passes)
+ *
+ * Constants: int16 F[n_sectors][64][6][6] (F[s][m][k][l]) and
+ * q[n_sectors][64][6], row-major, little endian.
+ *
+ * Conventions for every entry point below:
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; h_* are host
+ *     pointers; the library never allocates, frees or keeps device memory
+ *     except where a function says otherwise (the serving loop).
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     only enqueue work and return; nothing is synchronised unless stated.
+ *   - The return value is a host-side status: SVT_OK, SVT_ERR_BAD_ARG for an
+ *     argument the host can reject (null pointer, size over a limit, config
+ *     out of range, workspace too small) or SVT_ERR_CUDA when a launch fails.
+ *   - Problems found in the DATA are reported on the device in d_status, one
+ *     uint64: UINT64_MAX when all is well, else (word_index << 8) | code, the
+ *     smallest such key over all violated rules.  The outputs of a batch whose
+ *     status is not UINT64_MAX are unspecified.  svt_unpack and svt_run reset
+ *     d_status; the later plain stages read it, do no work when it already
+ *     holds an error, and only ever lower it.
+ */
+#ifndef SVT_H
+#define SVT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes (host return values and the low 8 bits of d_status) ---- */
+#define SVT_OK 0
+#define SVT_ERR_BAD_ARG 1         /* bad argument; on the device: bad event offsets (word 0) */
+#define SVT_ERR_BAD_TYPE 2        /* word type not allowed at this position            */
+#define SVT_ERR_BAD_RESERVED 3    /* hit word with reserved bits set                    */
+#define SVT_ERR_BAD_LAYER 4       /* hit layer > 5                                      */
+#define SVT_ERR_UNSORTED 5        /* hit layer lower than the previous hit's            */
+#define SVT_ERR_TOO_MANY_HITS 6   /* 17th hit of one layer in a road                    */
+#define SVT_ERR_BAD_SECTOR 7      /* road sector >= n_sectors                           */
+#define SVT_ERR_NROADS_MISMATCH 8 /* event header's road count differs from its roads   */
+#define SVT_ERR_OOM 9             /* a caller-sized buffer is too small                 */
+#define SVT_ERR_BAD_CONFIG 10     /* svt_config out of range                            */
+#define SVT_ERR_TIMEOUT 11        /* a bounded device wait gave up                      */
+#define SVT_ERR_CUDA 20           /* a CUDA call failed (host return value only)        */
+
+#define SVT_STATUS_OK UINT64_MAX
+
+/* ---- output flags (bits [31:24] of record word 0) ---- */
+#define SVT_FLAG_PASS 1u
+#define SVT_FLAG_OVERFLOW 2u
+#define SVT_FLAG_BAD_PATTERN 4u
+#define SVT_FLAG_NO_HITS 8u
+
+/* Fit configuration.  Limits (else SVT_ERR_BAD_CONFIG): 9 <= oshift <= 31,
+ * qshift <= 24, max_comb >= 1, min_layers <= 6, 1 <= n_sectors <= 512.
+ * These limits keep |y_k| < 2^31 for every int16/uint15 input. */
+typedef struct {
+    uint32_t oshift;
+    uint32_t qshift;
+    uint32_t chi2_cut;
+    uint32_t max_comb;
+    uint32_t min_layers;
+    uint32_t n_sectors;
+} svt_config;
+
+/* Best combination of one road, as produced by svt_select (24 bytes). */
+typedef struct {
+    uint32_t flags;   /* SVT_FLAG_* */
+    uint32_t comb;    /* best combination index, 0xFFFFFFFF if none passes */
+    uint32_t chi2;
+    int32_t p[3];
+} svt_best;
+
+/* Schedule of the persistent fit kernel.  Zero fields take the defaults.
+ *   warps_per_block  warps of one persistent block (1..16, default 8)
+ *   blocks_per_sm    persistent blocks per SM (default 2)
+ *   rows_per_item    rows of the (prefix x suffix) combination grid handled
+ *                    by one warp work item (1..64, default 16) */
+typedef struct {
+    uint32_t warps_per_block;
+    uint32_t blocks_per_sm;
+    uint32_t rows_per_item;
+    uint32_t reserved;
+} svt_schedule;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int svt_version(void);
+
+/* Number of CUDA devices visible and the SM count of `device` (0 on error). */
+int svt_device_sm_count(int device);
+
+/* ======================================================================
+ * Plain path: one call per stage, one or more launches each, every
+ * intermediate materialised in caller memory (the per-stage structure of the
+ * paper's Sec. 2.1: unpack, combine, fit; then select and format).
+ * ====================================================================== */
+
+/* Workspace bytes svt_unpack needs for up to n_words words. */
+size_t svt_unpack_workspace_size(uint64_t n_words);
+
+/*
+ * svt_unpack -- stage 1 of Sec. 2.1: unpack the input words into per-road
+ * arrays and validate them.
+ *   d_words[n_words], d_event_off[n_events+1]  input (see the word format)
+ *   n_sectors      sectors of the constant table (road headers must be below)
+ *   road_cap       capacity of the road arrays
+ *   d_road_word[road_cap]   out: word index of each road header, input order
+ *   d_road_nhit[road_cap]   out: hits per layer, 5 bits each: n_l = (v >> 5l) & 31
+ *   d_event_road[n_events+1] out: index of each event's first road; the last
+ *                           entry is the road count R
+ *   d_n_roads[1]   out: R (uint64)
+ *   d_status[1]    out: reset, then the validation key (see above); R > road_cap
+ *                  gives SVT_ERR_OOM at the first header that does not fit
+ *   d_workspace    svt_unpack_workspace_size(n_words) bytes
+ */
+int svt_unpack(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_off,
+               uint64_t n_events, uint32_t n_sectors, uint64_t road_cap, uint32_t *d_road_word,
+               uint32_t *d_road_nhit, uint32_t *d_event_road, uint64_t *d_n_roads,
+               uint64_t *d_status, void *d_workspace, size_t workspace_bytes, void *stream);
+
+/* Workspace bytes svt_combine needs for up to road_cap roads. */
+size_t svt_combine_workspace_size(uint64_t road_cap);
+
+/*
+ * svt_combine -- stage 2 of Sec. 2.1: all combinations of one hit per layer
+ * in every road, written out one record per combination.
+ *   d_road_nhit, d_n_roads, road_cap   from svt_unpack
+ *   cfg            host pointer to the fit configuration
+ *   comb_cap       capacity of the combination arrays
+ *   d_road_flags[road_cap]  out: OVERFLOW / BAD_PATTERN / NO_HITS per road
+ *   d_comb_off[road_cap+1]  out: first combination of each road (uint64);
+ *                           road r owns [d_comb_off[r], d_comb_off[r+1])
+ *   d_comb_road[comb_cap]   out: road of each combination
+ *   d_comb_hits[comb_cap]   out: hit index per layer, 4 bits each (layer l at
+ *                           bits [4l+3:4l]); combinations of a road in
+ *                           increasing index c
+ *   d_n_combs[1]   out: total combinations (uint64)
+ *   d_status       lowered to (0 << 8 | SVT_ERR_OOM) when the total exceeds comb_cap
+ */
+int svt_combine(const uint32_t *d_road_nhit, const uint64_t *d_n_roads, uint64_t road_cap,
+                const svt_config *cfg, uint64_t comb_cap, uint32_t *d_road_flags,
+                uint64_t *d_comb_off, uint32_t *d_comb_road, uint32_t *d_comb_hits,
+                uint64_t *d_n_combs, uint64_t *d_status, void *d_workspace,
+                size_t workspace_bytes, void *stream);
+
+/*
+ * svt_fit -- stage 3 of Sec. 2.1: the linearised fit of every combination
+ * (one thread per combination).
+ *   d_words                       the input words (coordinates are read there)
+ *   d_road_word, d_road_nhit      from svt_unpack
+ *   d_comb_road, d_comb_hits, d_n_combs, comb_cap   from svt_combine
+ *   d_F, d_q       constant table (int16, layout above), cfg->n_sectors sectors
+ *   d_fit_chi2[comb_cap]    out: chi2 of each combination
+ *   d_fit_par[3*comb_cap]   out: p_k of combination j at d_fit_par[k*comb_cap + j]
+ */
+int svt_fit(const uint32_t *d_words, const uint32_t *d_road_word, const uint32_t *d_road_nhit,
+            const uint32_t *d_comb_road, const uint32_t *d_comb_hits, const uint64_t *d_n_combs,
+            uint64_t comb_cap, const int16_t *d_F, const int16_t *d_q, const svt_config *cfg,
+            uint32_t *d_fit_chi2, int32_t *d_fit_par, const uint64_t *d_status, void *stream);
+
+/*
+ * svt_select -- chi-square cut and best combination per road (one warp per
+ * road, shuffle argmin).
+ *   d_fit_chi2, d_fit_par, comb_cap   from svt_fit
+ *   d_comb_off, d_road_flags          from svt_combine
+ *   d_best[road_cap]       out: per-road best (svt_best)
+ */
+int svt_select(const uint32_t *d_fit_chi2, const int32_t *d_fit_par, uint64_t comb_cap,
+               const uint64_t *d_comb_off, const uint32_t *d_road_flags,
+               const uint64_t *d_n_roads, uint64_t road_cap, const svt_config *cfg,
+               svt_best *d_best, const uint64_t *d_status, void *stream);
+
+/*
+ * svt_format -- pack each road's result into the 6-word output record.
+ *   d_best, d_n_roads, road_cap   from svt_select / svt_unpack
+ *   d_words, d_road_word          to read each road id from its header
+ *   d_out[6*road_cap]             out: records in input road order
+ */
+int svt_format(const svt_best *d_best, const uint32_t *d_words, const uint32_t *d_road_word,
+               const uint64_t *d_n_roads, uint64_t road_cap, uint32_t *d_out,
+               const uint64_t *d_status, void *stream);
+
+/* ======================================================================
+ * Kernel timer: a pair of CUDA events that svt_run records, on its stream,
+ * right before and right after its persistent fit kernel.  The timer is a
+ * host object; create/destroy are the only calls that allocate (two events).
+ * ====================================================================== */
+typedef struct svt_timer_s *svt_timer;
+int svt_timer_create(svt_timer *out);
+int svt_timer_destroy(svt_timer timer);
+/* Milliseconds of the last timed fit kernel; waits for its end event. */
+int svt_timer_fit_ms(svt_timer timer, float *ms);
+
+/* ======================================================================
+ * Fused path: unpack, combine, fit, cut, select and format of a whole batch
+ * of uneven events, with the fit, cut, select and format in one persistent
+ * kernel (dynamic work queue over warp-sized work items).
+ * ====================================================================== */
+
+/* Workspace bytes svt_run needs for batches of up to max_words words and
+ * max_events events with up to road_cap roads.  sched may be NULL. */
+size_t svt_run_workspace_size(uint64_t max_words, uint64_t max_events, uint64_t road_cap,
+                              const svt_schedule *sched);
+
+/*
+ * svt_run -- the whole hot path of one batch.
+ *   d_words[n_words], d_event_off[n_events+1]  input
+ *   d_F, d_q, cfg      constant table and configuration
+ *   road_cap           capacity of d_out (roads)
+ *   d_out[6*road_cap]  out: one record per road, input order
+ *   d_event_road[n_events+1]  out (may be NULL): first road of each event, then R
+ *   d_counts[4]        out (may be NULL): R, work items, total evaluated
+ *                      combinations, roads that passed
+ *   d_status[1]        out: reset, then the validation key
+ *   d_workspace        svt_run_workspace_size(n_words, n_events, road_cap, sched)
+ *                      bytes, 256-byte aligned
+ *   sched              schedule (NULL = defaults)
+ *   timer              NULL, or a timer that records the fit kernel's events
+ * Host-side limits: n_words < 2^32, n_events < 2^31, road_cap < 2^31.
+ */
+int svt_run(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_off,
+            uint64_t n_events, const int16_t *d_F, const int16_t *d_q, const svt_config *cfg,
+            uint64_t road_cap, uint32_t *d_out, uint32_t *d_event_road, uint64_t *d_counts,
+            uint64_t *d_status, void *d_workspace, size_t workspace_bytes,
+            const svt_schedule *sched, svt_timer timer, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SVT_H */

@@ -1,0 +1,115 @@
+"""ctypes binding of ``libsvt.so`` (the C ABI in include/svt.h).
+
+Argument marshalling only: every function here forwards to the CUDA library
+and raises when it reports a host-side error.  There is no CPU fallback: if
+the library is missing the import of the binding fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsvt.so")
+
+SVT_OK = 0
+ERRORS = {
+    1: "BAD_ARG", 2: "BAD_TYPE", 3: "BAD_RESERVED", 4: "BAD_LAYER", 5: "UNSORTED",
+    6: "TOO_MANY_HITS", 7: "BAD_SECTOR", 8: "NROADS_MISMATCH", 9: "OOM", 10: "BAD_CONFIG",
+    11: "TIMEOUT", 20: "CUDA",
+}
+STATUS_OK = (1 << 64) - 1
+FLAG_PASS, FLAG_OVERFLOW, FLAG_BAD_PATTERN, FLAG_NO_HITS = 1, 2, 4, 8
+
+
+class SvtError(RuntimeError):
+    pass
+
+
+class SvtConfig(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in
+                ("oshift", "qshift", "chi2_cut", "max_comb", "min_layers", "n_sectors")]
+
+
+class SvtSchedule(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in
+                ("warps_per_block", "blocks_per_sm", "rows_per_item", "reserved")]
+
+
+class SvtBest(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_uint32), ("comb", ctypes.c_uint32), ("chi2", ctypes.c_uint32),
+                ("p", ctypes.c_int32 * 3)]
+
+
+_vp = ctypes.c_void_p
+_u64 = ctypes.c_uint64
+_u32 = ctypes.c_uint32
+_sz = ctypes.c_size_t
+_cfgp = ctypes.POINTER(SvtConfig)
+_schp = ctypes.POINTER(SvtSchedule)
+
+# name -> (restype, argtypes); mirrors include/svt.h
+SIGNATURES = {
+    "svt_version": (ctypes.c_int, []),
+    "svt_device_sm_count": (ctypes.c_int, [ctypes.c_int]),
+    "svt_unpack_workspace_size": (_sz, [_u64]),
+    "svt_unpack": (ctypes.c_int, [_vp, _u64, _vp, _u64, _u32, _u64, _vp, _vp, _vp, _vp, _vp, _vp,
+                                  _sz, _vp]),
+    "svt_combine_workspace_size": (_sz, [_u64]),
+    "svt_combine": (ctypes.c_int, [_vp, _vp, _u64, _cfgp, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
+                                   _sz, _vp]),
+    "svt_fit": (ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _u64, _vp, _vp, _cfgp, _vp, _vp, _vp,
+                               _vp]),
+    "svt_select": (ctypes.c_int, [_vp, _vp, _u64, _vp, _vp, _vp, _u64, _cfgp, _vp, _vp, _vp]),
+    "svt_format": (ctypes.c_int, [_vp, _vp, _vp, _vp, _u64, _vp, _vp, _vp]),
+    "svt_run_workspace_size": (_sz, [_u64, _u64, _u64, _schp]),
+    "svt_run": (ctypes.c_int, [_vp, _u64, _vp, _u64, _vp, _vp, _cfgp, _u64, _vp, _vp, _vp, _vp,
+                               _vp, _sz, _schp, _vp, _vp]),
+    "svt_timer_create": (ctypes.c_int, [ctypes.POINTER(_vp)]),
+    "svt_timer_destroy": (ctypes.c_int, [_vp]),
+    "svt_timer_fit_ms": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load():
+    """Load libsvt.so (building it first when nvcc is available)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            from . import build as _build
+            try:
+                _build.build()
+            except Exception as e:  # noqa: BLE001
+                raise ImportError(f"libsvt.so is missing and could not be built: {e}") from e
+        else:
+            from . import build as _build
+            try:
+                _build.build()   # rebuild when sources are newer
+            except RuntimeError:
+                pass
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return _lib
+
+
+def check(rc: int, what: str):
+    if rc != SVT_OK:
+        raise SvtError(f"{what} failed: {ERRORS.get(rc, rc)}")
+
+
+def decode_status(key: int):
+    """(word_index, error name) of a device status key, or None when OK."""
+    key = int(key) & STATUS_OK
+    if key == STATUS_OK:
+        return None
+    return key >> 8, ERRORS.get(key & 0xFF, key & 0xFF)

@@ -1,0 +1,313 @@
+// svt_abi.cu -- the extern "C" entry points of include/svt.h: argument checks,
+// workspace carving and the launch sequence of each call.
+#include <mutex>
+
+#include "svt_kernels.cuh"
+
+namespace svt {
+size_t scan_u64_tile_count(uint64_t cap);
+}
+
+using namespace svt;
+
+namespace {
+
+constexpr int MAX_DEVICES = 64;
+int g_sm_count[MAX_DEVICES];
+std::once_flag g_sm_once[MAX_DEVICES];
+
+int sm_count_of(int dev) {
+    if (dev < 0 || dev >= MAX_DEVICES) return 0;
+    std::call_once(g_sm_once[dev], [dev] {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n = 0;
+        g_sm_count[dev] = n;
+    });
+    return g_sm_count[dev];
+}
+
+int current_sm_count() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    return sm_count_of(dev);
+}
+
+bool config_ok(const svt_config *c) {
+    if (!c) return false;
+    if (c->oshift < 9 || c->oshift > 31) return false;
+    if (c->qshift > 24) return false;
+    if (c->max_comb < 1) return false;
+    if (c->min_layers > 6) return false;
+    if (c->n_sectors < 1 || c->n_sectors > 512) return false;
+    return true;
+}
+
+svt_schedule resolve(const svt_schedule *s) {
+    svt_schedule r{8, 2, 16, 0};
+    if (s) {
+        if (s->warps_per_block) r.warps_per_block = s->warps_per_block;
+        if (s->blocks_per_sm) r.blocks_per_sm = s->blocks_per_sm;
+        if (s->rows_per_item) r.rows_per_item = s->rows_per_item;
+    }
+    return r;
+}
+
+bool schedule_ok(const svt_schedule &s) {
+    return s.warps_per_block >= 1 && s.warps_per_block <= 16 && s.blocks_per_sm >= 1 &&
+           s.blocks_per_sm <= 32 && s.rows_per_item >= 1 && s.rows_per_item <= 64;
+}
+
+int tile_grid() {
+    int sms = current_sm_count();
+    return (sms > 0 ? sms : 1) * 8;
+}
+
+int launch_status() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SVT_OK : SVT_ERR_CUDA;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Workspace layout of svt_unpack.
+struct UnpackWs {
+    Dims *dims;
+    uint32_t *tile_roads;
+    size_t bytes;
+};
+UnpackWs carve_unpack(void *base, uint64_t max_words) {
+    Carver c(base);
+    UnpackWs w;
+    w.dims = c.take<Dims>(1);
+    w.tile_roads = c.take<uint32_t>(n_tiles(max_words) + 1);
+    w.bytes = c.size();
+    return w;
+}
+
+// Workspace layout of svt_run.
+struct RunWs {
+    Dims *dims;
+    uint32_t *tile_roads, *tile_items;
+    uint32_t *road_word, *road_nhit, *road_items, *road_item_off, *road_pending;
+    unsigned long long *road_best;
+    uint32_t *event_road;
+    uint32_t *item_counter;
+    uint64_t *counts;
+    size_t bytes;
+};
+RunWs carve_run(void *base, uint64_t max_words, uint64_t max_events, uint64_t road_cap) {
+    Carver c(base);
+    RunWs w;
+    const uint64_t T = n_tiles(max_words);
+    w.dims = c.take<Dims>(1);
+    w.counts = c.take<uint64_t>(4);
+    w.item_counter = c.take<uint32_t>(1);
+    w.tile_roads = c.take<uint32_t>(T + 1);
+    w.tile_items = c.take<uint32_t>(T + 1);
+    w.road_word = c.take<uint32_t>(road_cap);
+    w.road_nhit = c.take<uint32_t>(road_cap);
+    w.road_items = c.take<uint32_t>(road_cap);
+    w.road_item_off = c.take<uint32_t>(road_cap + 1);
+    w.road_pending = c.take<uint32_t>(road_cap);
+    w.road_best = c.take<unsigned long long>(road_cap);
+    w.event_road = c.take<uint32_t>(max_events + 1);
+    w.bytes = c.size();
+    return w;
+}
+
+}  // namespace
+
+struct svt_timer_s {
+    cudaEvent_t start, end;
+    bool recorded;
+};
+
+extern "C" {
+
+int svt_timer_create(svt_timer *out) {
+    if (!out) return SVT_ERR_BAD_ARG;
+    svt_timer t = new svt_timer_s();
+    if (cudaEventCreate(&t->start) != cudaSuccess || cudaEventCreate(&t->end) != cudaSuccess) {
+        delete t;
+        return SVT_ERR_CUDA;
+    }
+    t->recorded = false;
+    *out = t;
+    return SVT_OK;
+}
+
+int svt_timer_destroy(svt_timer t) {
+    if (!t) return SVT_ERR_BAD_ARG;
+    cudaEventDestroy(t->start);
+    cudaEventDestroy(t->end);
+    delete t;
+    return SVT_OK;
+}
+
+int svt_timer_fit_ms(svt_timer t, float *ms) {
+    if (!t || !ms || !t->recorded) return SVT_ERR_BAD_ARG;
+    if (cudaEventSynchronize(t->end) != cudaSuccess) return SVT_ERR_CUDA;
+    return cudaEventElapsedTime(ms, t->start, t->end) == cudaSuccess ? SVT_OK : SVT_ERR_CUDA;
+}
+
+int svt_version(void) { return 10000; }
+
+int svt_device_sm_count(int device) { return sm_count_of(device); }
+
+size_t svt_unpack_workspace_size(uint64_t n_words) { return carve_unpack(nullptr, n_words).bytes; }
+
+int svt_unpack(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_off,
+               uint64_t n_events, uint32_t n_sectors, uint64_t road_cap, uint32_t *d_road_word,
+               uint32_t *d_road_nhit, uint32_t *d_event_road, uint64_t *d_n_roads,
+               uint64_t *d_status, void *d_workspace, size_t workspace_bytes, void *stream) {
+    if (!d_event_off || !d_event_road || !d_n_roads || !d_status || !d_workspace)
+        return SVT_ERR_BAD_ARG;
+    if (n_words > 0 && (!d_words || !aligned16(d_words))) return SVT_ERR_BAD_ARG;
+    if (road_cap > 0 && (!d_road_word || !d_road_nhit)) return SVT_ERR_BAD_ARG;
+    if (n_words >= (1ull << 32) || n_events >= (1ull << 31) || road_cap >= (1ull << 32))
+        return SVT_ERR_BAD_ARG;
+    if (n_sectors < 1 || n_sectors > 512) return SVT_ERR_BAD_ARG;
+    UnpackWs w = carve_unpack(d_workspace, n_words);
+    if (workspace_bytes < w.bytes) return SVT_ERR_BAD_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *status = (unsigned long long *)d_status;
+    const int grid = tile_grid();
+    svt_config cfg{15, 15, 0, 1, 0, n_sectors};
+    launch_set_dims(w.dims, n_words, n_events, status, d_n_roads, 1, st);
+    launch_unpack_count(d_words, d_event_off, w.dims, n_words, n_sectors, w.tile_roads, status,
+                        grid, st);
+    launch_scan_tiles(w.tile_roads, w.dims, nullptr, d_n_roads, d_event_road, status, st);
+    launch_unpack_roads(d_words, d_event_off, w.dims, n_words, w.tile_roads, road_cap, d_road_word,
+                        d_road_nhit, d_event_road, cfg, 0, nullptr, nullptr, nullptr, status, grid,
+                        st);
+    launch_unpack_events(d_words, d_event_off, w.dims, n_events, d_event_road, status, grid, st);
+    return launch_status();
+}
+
+size_t svt_combine_workspace_size(uint64_t road_cap) {
+    return align_up(scan_u64_tile_count(road_cap + 1) * sizeof(uint64_t), 256);
+}
+
+int svt_combine(const uint32_t *d_road_nhit, const uint64_t *d_n_roads, uint64_t road_cap,
+                const svt_config *cfg, uint64_t comb_cap, uint32_t *d_road_flags,
+                uint64_t *d_comb_off, uint32_t *d_comb_road, uint32_t *d_comb_hits,
+                uint64_t *d_n_combs, uint64_t *d_status, void *d_workspace,
+                size_t workspace_bytes, void *stream) {
+    if (!config_ok(cfg)) return SVT_ERR_BAD_CONFIG;
+    if (!d_n_roads || !d_comb_off || !d_n_combs || !d_status || !d_workspace) return SVT_ERR_BAD_ARG;
+    if (road_cap > 0 && (!d_road_nhit || !d_road_flags)) return SVT_ERR_BAD_ARG;
+    if (comb_cap > 0 && (!d_comb_road || !d_comb_hits)) return SVT_ERR_BAD_ARG;
+    if (road_cap >= (1ull << 32)) return SVT_ERR_BAD_ARG;
+    if (workspace_bytes < svt_combine_workspace_size(road_cap)) return SVT_ERR_BAD_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int grid = tile_grid();
+    unsigned long long *status = (unsigned long long *)d_status;
+    launch_combine_count(d_road_nhit, d_n_roads, road_cap, *cfg, d_road_flags, d_comb_off, status,
+                         grid, st);
+    launch_scan_u64(d_comb_off, d_n_roads, road_cap, (uint64_t *)d_workspace, d_n_combs, status,
+                    grid, st);
+    launch_combine_write(d_road_nhit, d_n_roads, road_cap, d_comb_off, comb_cap, d_comb_road,
+                         d_comb_hits, status, grid, st);
+    return launch_status();
+}
+
+int svt_fit(const uint32_t *d_words, const uint32_t *d_road_word, const uint32_t *d_road_nhit,
+            const uint32_t *d_comb_road, const uint32_t *d_comb_hits, const uint64_t *d_n_combs,
+            uint64_t comb_cap, const int16_t *d_F, const int16_t *d_q, const svt_config *cfg,
+            uint32_t *d_fit_chi2, int32_t *d_fit_par, const uint64_t *d_status, void *stream) {
+    if (!config_ok(cfg)) return SVT_ERR_BAD_CONFIG;
+    if (!d_n_combs || !d_F || !d_q || !d_status) return SVT_ERR_BAD_ARG;
+    if (comb_cap > 0 && (!d_words || !d_road_word || !d_road_nhit || !d_comb_road ||
+                         !d_comb_hits || !d_fit_chi2 || !d_fit_par))
+        return SVT_ERR_BAD_ARG;
+    launch_fit_plain(d_words, d_road_word, d_road_nhit, d_comb_road, d_comb_hits, d_n_combs,
+                     comb_cap, d_F, d_q, *cfg, d_fit_chi2, d_fit_par,
+                     (const unsigned long long *)d_status, current_sm_count() * 16,
+                     (cudaStream_t)stream);
+    return launch_status();
+}
+
+int svt_select(const uint32_t *d_fit_chi2, const int32_t *d_fit_par, uint64_t comb_cap,
+               const uint64_t *d_comb_off, const uint32_t *d_road_flags,
+               const uint64_t *d_n_roads, uint64_t road_cap, const svt_config *cfg,
+               svt_best *d_best, const uint64_t *d_status, void *stream) {
+    if (!config_ok(cfg)) return SVT_ERR_BAD_CONFIG;
+    if (!d_comb_off || !d_n_roads || !d_status) return SVT_ERR_BAD_ARG;
+    if (road_cap > 0 && (!d_road_flags || !d_best)) return SVT_ERR_BAD_ARG;
+    if (comb_cap > 0 && (!d_fit_chi2 || !d_fit_par)) return SVT_ERR_BAD_ARG;
+    launch_select(d_fit_chi2, d_fit_par, comb_cap, d_comb_off, d_road_flags, d_n_roads, road_cap,
+                  *cfg, d_best, (const unsigned long long *)d_status, current_sm_count() * 16,
+                  (cudaStream_t)stream);
+    return launch_status();
+}
+
+int svt_format(const svt_best *d_best, const uint32_t *d_words, const uint32_t *d_road_word,
+               const uint64_t *d_n_roads, uint64_t road_cap, uint32_t *d_out,
+               const uint64_t *d_status, void *stream) {
+    if (!d_n_roads || !d_status) return SVT_ERR_BAD_ARG;
+    if (road_cap > 0 && (!d_best || !d_words || !d_road_word || !d_out)) return SVT_ERR_BAD_ARG;
+    launch_format(d_best, d_words, d_road_word, d_n_roads, road_cap, d_out,
+                  (const unsigned long long *)d_status, current_sm_count() * 8,
+                  (cudaStream_t)stream);
+    return launch_status();
+}
+
+size_t svt_run_workspace_size(uint64_t max_words, uint64_t max_events, uint64_t road_cap,
+                              const svt_schedule *sched) {
+    (void)sched;
+    return carve_run(nullptr, max_words, max_events, road_cap).bytes;
+}
+
+int svt_run(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_off,
+            uint64_t n_events, const int16_t *d_F, const int16_t *d_q, const svt_config *cfg,
+            uint64_t road_cap, uint32_t *d_out, uint32_t *d_event_road, uint64_t *d_counts,
+            uint64_t *d_status, void *d_workspace, size_t workspace_bytes,
+            const svt_schedule *sched, svt_timer timer, void *stream) {
+    if (!config_ok(cfg)) return SVT_ERR_BAD_CONFIG;
+    const svt_schedule sc = resolve(sched);
+    if (!schedule_ok(sc)) return SVT_ERR_BAD_ARG;
+    if (!d_event_off || !d_F || !d_q || !d_status || !d_workspace) return SVT_ERR_BAD_ARG;
+    if (n_words > 0 && (!d_words || !aligned16(d_words))) return SVT_ERR_BAD_ARG;
+    if (road_cap > 0 && !d_out) return SVT_ERR_BAD_ARG;
+    if (n_words >= (1ull << 32) || n_events >= (1ull << 31) || road_cap >= (1ull << 31))
+        return SVT_ERR_BAD_ARG;
+    if ((uintptr_t)d_workspace & 255u) return SVT_ERR_BAD_ARG;
+    RunWs w = carve_run(d_workspace, n_words, n_events, road_cap);
+    if (workspace_bytes < w.bytes) return SVT_ERR_BAD_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *status = (unsigned long long *)d_status;
+    uint64_t *counts = d_counts ? d_counts : w.counts;
+    uint32_t *event_road = d_event_road ? d_event_road : w.event_road;
+    const int grid = tile_grid();
+    const int sms = current_sm_count();
+    if (sms <= 0) return SVT_ERR_CUDA;
+    int occ = fit_persistent_blocks_per_sm((int)sc.warps_per_block, sc.rows_per_item);
+    if (occ <= 0) return SVT_ERR_CUDA;
+    int bps = (int)sc.blocks_per_sm < occ ? (int)sc.blocks_per_sm : occ;
+
+    launch_set_dims(w.dims, n_words, n_events, status, counts, 4, st);
+    launch_unpack_count(d_words, d_event_off, w.dims, n_words, cfg->n_sectors, w.tile_roads, status,
+                        grid, st);
+    launch_scan_tiles(w.tile_roads, w.dims, nullptr, counts + 0, event_road, status, st);
+    launch_unpack_roads(d_words, d_event_off, w.dims, n_words, w.tile_roads, road_cap, w.road_word,
+                        w.road_nhit, event_road, *cfg, sc.rows_per_item, w.road_items,
+                        w.tile_items, counts, status, grid, st);
+    launch_unpack_events(d_words, d_event_off, w.dims, n_events, event_road, status, grid, st);
+    launch_scan_tiles(w.tile_items, w.dims, nullptr, counts + 1, nullptr, status, st);
+    launch_items(d_words, w.road_word, w.road_nhit, road_cap, w.dims, n_words, w.tile_roads,
+                 w.tile_items, w.road_items, w.road_item_off, w.road_best, w.road_pending, d_out,
+                 w.item_counter, status, grid, st);
+    if (timer && cudaEventRecord(timer->start, st) != cudaSuccess) return SVT_ERR_CUDA;
+    if (launch_fit_persistent(d_words, w.road_word, w.road_nhit, w.road_item_off, counts + 0,
+                              road_cap, counts + 1, d_F, d_q, *cfg, sc.rows_per_item, w.road_best,
+                              w.road_pending, d_out, w.item_counter, counts, status,
+                              (int)sc.warps_per_block, sms * bps, st) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    if (timer) {
+        if (cudaEventRecord(timer->end, st) != cudaSuccess) return SVT_ERR_CUDA;
+        timer->recorded = true;
+    }
+    return launch_status();
+}
+
+}  // extern "C"

@@ -1,0 +1,96 @@
+// svt_kernels.cuh -- declarations of the kernels and launch helpers that the
+// C-ABI layer (svt_abi.cu) strings together.
+#pragma once
+
+#include "svt_internal.cuh"
+
+namespace svt {
+
+// Device-side view of a batch's sizes.  Every pipeline kernel reads the sizes
+// through this so that one captured launch sequence serves batches of any
+// size up to its capacities.
+struct Dims {
+    uint64_t n_words;
+    uint64_t n_events;
+};
+
+// ---- unpack (svt_unpack.cu) --------------------------------------------------
+// K1: per-word validation (rules V2..V7, V9) and road headers per tile.
+void launch_unpack_count(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
+                         uint64_t max_words, uint32_t n_sectors, uint32_t *tile_roads,
+                         unsigned long long *status, int grid, cudaStream_t st);
+// Exclusive scan, in place, of a[0..n) where n = *n_dev, or the number of
+// word tiles when n_dev is NULL; writes the total to a[n] and, when given, to
+// *total64 and to event_road[n_events].  A total of 2^32 or more lowers the
+// status to (0, OOM).
+void launch_scan_tiles(uint32_t *a, const Dims *dims, const uint64_t *n_dev, uint64_t *total64,
+                       uint32_t *event_road, unsigned long long *status, cudaStream_t st);
+// K2: road extraction: road_word, road_nhit, rule V8, event_road of events
+// starting in each tile; with rows_per_item > 0 also the work items of each
+// road (road_items) and per tile (tile_items), and the evaluated
+// combinations (counts[2]).
+void launch_unpack_roads(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
+                         uint64_t max_words, const uint32_t *tile_roads, uint64_t road_cap,
+                         uint32_t *road_word, uint32_t *road_nhit, uint32_t *event_road,
+                         const svt_config cfg, uint32_t rows_per_item, uint32_t *road_items,
+                         uint32_t *tile_items, uint64_t *counts, unsigned long long *status,
+                         int grid, cudaStream_t st);
+// Per-event rules: offsets, V1, V10.
+void launch_unpack_events(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
+                          uint64_t max_events, const uint32_t *event_road,
+                          unsigned long long *status, int grid, cudaStream_t st);
+
+// ---- fused path (svt_fused.cu) -------------------------------------------------
+// K3: per-road item offsets (road_item_off[R] = total), road slots
+// (road_best = UINT64_MAX, road_pending = items), records of roads that are
+// not fitted; zeroes *item_counter.
+void launch_items(const uint32_t *words, const uint32_t *road_word, const uint32_t *road_nhit,
+                  uint64_t road_cap, const Dims *dims,
+                  uint64_t max_words, const uint32_t *tile_roads, const uint32_t *tile_items,
+                  const uint32_t *road_items, uint32_t *road_item_off,
+                  unsigned long long *road_best, uint32_t *road_pending, uint32_t *out,
+                  uint32_t *item_counter, unsigned long long *status, int grid,
+                  cudaStream_t st);
+cudaError_t launch_fit_persistent(const uint32_t *words, const uint32_t *road_word,
+                                  const uint32_t *road_nhit, const uint32_t *road_item_off,
+                                  const uint64_t *n_roads, uint64_t road_cap,
+                                  const uint64_t *total_items, const int16_t *F,
+                                  const int16_t *q, const svt_config cfg, uint32_t rows_per_item,
+                                  unsigned long long *road_best, uint32_t *road_pending,
+                                  uint32_t *out, uint32_t *item_counter, uint64_t *counts,
+                                  unsigned long long *status, int warps_per_block, int grid,
+                                  cudaStream_t st);
+// K4: the persistent fit; n_roads and total_items are device counters.
+int fit_persistent_blocks_per_sm(int warps_per_block, uint32_t rows_per_item);
+size_t fit_smem_bytes(int warps_per_block);
+
+// ---- plain path (svt_plain.cu) --------------------------------------------------
+// Every plain-path kernel returns at once when *status already holds an error.
+void launch_combine_count(const uint32_t *road_nhit, const uint64_t *n_roads, uint64_t road_cap,
+                          const svt_config cfg, uint32_t *road_flags, uint64_t *comb_cnt,
+                          const unsigned long long *status, int grid, cudaStream_t st);
+void launch_scan_u64(uint64_t *a, const uint64_t *n_dev, uint64_t cap, uint64_t *tile_sums,
+                     uint64_t *total, const unsigned long long *status, int grid, cudaStream_t st);
+void launch_combine_write(const uint32_t *road_nhit, const uint64_t *n_roads, uint64_t road_cap,
+                          const uint64_t *comb_off, uint64_t comb_cap, uint32_t *comb_road,
+                          uint32_t *comb_hits, unsigned long long *status, int grid,
+                          cudaStream_t st);
+void launch_fit_plain(const uint32_t *words, const uint32_t *road_word, const uint32_t *road_nhit,
+                      const uint32_t *comb_road, const uint32_t *comb_hits,
+                      const uint64_t *n_combs, uint64_t comb_cap, const int16_t *F,
+                      const int16_t *q, const svt_config cfg, uint32_t *fit_chi2,
+                      int32_t *fit_par, const unsigned long long *status, int grid,
+                      cudaStream_t st);
+void launch_select(const uint32_t *fit_chi2, const int32_t *fit_par, uint64_t comb_cap,
+                   const uint64_t *comb_off, const uint32_t *road_flags, const uint64_t *n_roads,
+                   uint64_t road_cap, const svt_config cfg, svt_best *best,
+                   const unsigned long long *status, int grid, cudaStream_t st);
+void launch_format(const svt_best *best, const uint32_t *words, const uint32_t *road_word,
+                   const uint64_t *n_roads, uint64_t road_cap, uint32_t *out,
+                   const unsigned long long *status, int grid, cudaStream_t st);
+
+// shared by both paths
+void launch_set_dims(Dims *dims, uint64_t n_words, uint64_t n_events,
+                     unsigned long long *status, uint64_t *counts, int n_counts, cudaStream_t st);
+
+}  // namespace svt

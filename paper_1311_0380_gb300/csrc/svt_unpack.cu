@@ -1,0 +1,323 @@
+// svt_unpack.cu -- stage 1 of the paper's Sec. 2.1 ("unpacking of input data
+// and filling of all the necessary data structures") for GB300.
+//
+// The batch is cut into tiles of 2048 words.  K1 validates every word against
+// its left neighbour (rules V2..V7, V9 of include/svt.h's format) and counts
+// road headers per tile; a single-block scan turns the counts into each
+// tile's first road index; K2 then gives every road header its global index
+// (block scan), records where it sits, walks its hits (rule V8, hits per
+// layer) and, for the fused path, sizes its work; a per-event kernel checks
+// the offsets and rules V1 and V10.  Loads are vectorised (2 x 16 B per
+// thread, coalesced across the warp).
+#include "svt_kernels.cuh"
+
+namespace svt {
+
+namespace {
+
+__device__ __forceinline__ void load8(const uint32_t *__restrict__ words, uint64_t base,
+                                      uint64_t n_words, uint32_t (&w)[TILE_PER_THREAD]) {
+    if (base + TILE_PER_THREAD <= n_words) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(words + base);
+        uint4 a = __ldg(p), b = __ldg(p + 1);
+        w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+        w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+    } else {
+#pragma unroll
+        for (int j = 0; j < TILE_PER_THREAD; ++j)
+            w[j] = (base + j < n_words) ? __ldg(words + base + j) : 0u;
+    }
+}
+
+// first index e in [0, n) with off[e] >= v (off assumed non-decreasing)
+__device__ __forceinline__ uint64_t lower_bound64(const uint64_t *__restrict__ off, uint64_t n,
+                                                  uint64_t v) {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        uint64_t mid = lo + (hi - lo) / 2;
+        if (__ldg(off + mid) < v)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ bool is_event_start(const uint64_t *__restrict__ off, uint64_t n,
+                                               uint64_t i) {
+    uint64_t e = lower_bound64(off, n, i);
+    return e < n && __ldg(off + e) == i;
+}
+
+__global__ void k_set_dims(Dims *dims, uint64_t n_words, uint64_t n_events,
+                           unsigned long long *status, uint64_t *counts, int n_counts) {
+    if (threadIdx.x == 0) {
+        if (dims) {
+            dims->n_words = n_words;
+            dims->n_events = n_events;
+        }
+        if (status) *status = ~0ull;
+    }
+    if (counts && (int)threadIdx.x < n_counts) counts[threadIdx.x] = 0;
+}
+
+__global__ void __launch_bounds__(TILE_THREADS)
+    k_unpack_count(const uint32_t *__restrict__ words, const uint64_t *__restrict__ event_off,
+                   const Dims *__restrict__ dims, uint32_t n_sectors, uint32_t *tile_roads,
+                   unsigned long long *status) {
+    __shared__ uint32_t red[TILE_THREADS / 32 + 1];
+    const uint64_t n_words = dims->n_words, n_events = dims->n_events;
+    const uint64_t T = n_tiles(n_words);
+    for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
+        const uint64_t base = t * TILE_WORDS + (uint64_t)threadIdx.x * TILE_PER_THREAD;
+        uint32_t w[TILE_PER_THREAD];
+        load8(words, base, n_words, w);
+        uint32_t prev = __shfl_up_sync(0xffffffffu, w[TILE_PER_THREAD - 1], 1);
+        if ((threadIdx.x & 31) == 0) prev = (base > 0 && base - 1 < n_words) ? __ldg(words + base - 1) : 0u;
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int j = 0; j < TILE_PER_THREAD; ++j) {
+            const uint64_t i = base + j;
+            if (i >= n_words) break;
+            const uint32_t x = w[j];
+            const uint32_t p = (j == 0) ? prev : w[j - 1];
+            const uint32_t ty = w_type(x);
+            if (ty == TYPE_ROAD) {
+                cnt += 1;
+                if (rd_sector(x) >= n_sectors) report(status, i, SVT_ERR_BAD_SECTOR);     // V9
+            } else if (ty == TYPE_BAD) {
+                report(status, i, SVT_ERR_BAD_TYPE);                                    // V3
+            } else if (ty == TYPE_EVENT) {
+                if (!is_event_start(event_off, n_events, i))
+                    report(status, i, SVT_ERR_BAD_TYPE);                                // V2
+            } else {
+                // V4 and V7 also fire on an event's first word, where V1 already
+                // reports the same word with the smallest code, so the key is unchanged.
+                if (i > 0 && w_type(p) == TYPE_EVENT) report(status, i, SVT_ERR_BAD_TYPE);   // V4
+                if (hit_reserved(x) != 0) report(status, i, SVT_ERR_BAD_RESERVED);           // V5
+                if (hit_layer(x) > 5) report(status, i, SVT_ERR_BAD_LAYER);                  // V6
+                if (i > 0 && w_type(p) == TYPE_HIT && hit_layer(p) > hit_layer(x))
+                    report(status, i, SVT_ERR_UNSORTED);                                     // V7
+            }
+        }
+        uint32_t total;
+        block_exclusive_scan<uint32_t>(cnt, red, &total);
+        if (threadIdx.x == 0) tile_roads[t] = total;
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+    k_scan_tiles(uint32_t *a, const Dims *__restrict__ dims, const uint64_t *n_dev,
+                 uint64_t *total64, uint32_t *event_road, unsigned long long *status) {
+    __shared__ uint32_t sm[33];
+    const uint64_t n = n_dev ? *n_dev : n_tiles(dims->n_words);
+    uint64_t carry = 0;
+    for (uint64_t c0 = 0; c0 < n; c0 += 4096) {
+        const uint64_t i0 = c0 + (uint64_t)threadIdx.x * 4;
+        uint32_t v[4], s = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = (i0 + k < n) ? a[i0 + k] : 0u;
+            s += v[k];
+        }
+        uint32_t tot;
+        uint32_t ex = block_exclusive_scan<uint32_t>(s, sm, &tot);
+        uint64_t run = carry + ex;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k < n) a[i0 + k] = (uint32_t)run;
+            run += v[k];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        a[n] = (uint32_t)carry;
+        if (carry > 0xFFFFFFFFull) report(status, 0, SVT_ERR_OOM);
+        if (total64) *total64 = carry;
+        if (event_road) event_road[dims->n_events] = (uint32_t)carry;
+    }
+}
+
+// Work items of one road for the fused fit: rows of the (prefix x suffix)
+// grid, rows_per_item rows per item.
+__device__ __forceinline__ uint32_t road_items_of(uint32_t packed, const svt_config &cfg,
+                                                  uint32_t rows_per_item, uint32_t *n_eval_out) {
+    RoadShape s = road_shape(packed);
+    if (s.n_layers_hit < cfg.min_layers) {
+        *n_eval_out = 0;
+        return 0;
+    }
+    uint32_t C = (uint32_t)s.C;
+    uint32_t C_eval = C > cfg.max_comb ? cfg.max_comb : C;
+    uint32_t split, NB;
+    road_split(s, split, NB);
+    uint32_t NA = (C_eval + NB - 1) / NB;
+    *n_eval_out = C_eval;
+    return (NA + rows_per_item - 1) / rows_per_item;
+}
+
+__global__ void __launch_bounds__(TILE_THREADS)
+    k_unpack_roads(const uint32_t *__restrict__ words, const uint64_t *__restrict__ event_off,
+                   const Dims *__restrict__ dims, const uint32_t *__restrict__ tile_roads,
+                   uint64_t road_cap, uint32_t *road_word, uint32_t *road_nhit,
+                   uint32_t *event_road, const svt_config cfg, uint32_t rows_per_item,
+                   uint32_t *road_items, uint32_t *tile_items, uint64_t *counts,
+                   unsigned long long *status) {
+    __shared__ uint32_t red[TILE_THREADS / 32 + 1];
+    __shared__ unsigned long long red64[TILE_THREADS / 32 + 1];
+    __shared__ uint32_t pre[TILE_WORDS];
+    __shared__ uint64_t ev_range[2];
+    const uint64_t n_words = dims->n_words, n_events = dims->n_events;
+    const uint64_t T = n_tiles(n_words);
+    for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
+        const uint64_t tile_start = t * TILE_WORDS;
+        const uint64_t tile_end = min(tile_start + TILE_WORDS, n_words);
+        const uint64_t base = tile_start + (uint64_t)threadIdx.x * TILE_PER_THREAD;
+        if (threadIdx.x == 0) {
+            ev_range[0] = lower_bound64(event_off, n_events, tile_start);
+            ev_range[1] = lower_bound64(event_off, n_events, tile_end);
+        }
+        uint32_t w[TILE_PER_THREAD];
+        load8(words, base, n_words, w);
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int j = 0; j < TILE_PER_THREAD; ++j)
+            cnt += (base + j < n_words && w_type(w[j]) == TYPE_ROAD) ? 1u : 0u;
+        uint32_t total;
+        const uint32_t ex = block_exclusive_scan<uint32_t>(cnt, red, &total);
+        const uint64_t tile_base = tile_roads[t];
+        uint32_t run = ex;
+        uint32_t items_sum = 0;
+        unsigned long long comb_sum = 0;
+#pragma unroll
+        for (int j = 0; j < TILE_PER_THREAD; ++j) {
+            const uint64_t i = base + j;
+            pre[threadIdx.x * TILE_PER_THREAD + j] = run;
+            if (i >= n_words || w_type(w[j]) != TYPE_ROAD) continue;
+            const uint64_t r = tile_base + run;
+            run += 1;
+            if (r >= road_cap) {
+                report(status, i, SVT_ERR_OOM);
+                continue;
+            }
+            road_word[r] = (uint32_t)i;
+            // walk the hit run that follows the header (rule V8 and hits per layer)
+            unsigned long long cnt8 = 0;
+            for (uint64_t k = i + 1; k < n_words; ++k) {
+                const uint32_t x = __ldg(words + k);
+                if (w_type(x) != TYPE_HIT) break;
+                const uint32_t l = hit_layer(x);
+                uint32_t c = (uint32_t)(cnt8 >> (8 * l)) & 0xFFu;
+                if (c < 32) {
+                    cnt8 += 1ull << (8 * l);
+                    if (c + 1 == MAX_HITS + 1) report(status, k, SVT_ERR_TOO_MANY_HITS);
+                }
+            }
+            uint32_t packed = 0;
+#pragma unroll
+            for (int l = 0; l < N_LAYERS; ++l) {
+                uint32_t c = (uint32_t)(cnt8 >> (8 * l)) & 0xFFu;
+                packed |= (c > MAX_HITS ? (uint32_t)MAX_HITS : c) << (5 * l);
+            }
+            road_nhit[r] = packed;
+            if (rows_per_item) {
+                uint32_t n_eval;
+                uint32_t it = road_items_of(packed, cfg, rows_per_item, &n_eval);
+                road_items[r] = it;
+                items_sum += it;
+                comb_sum += n_eval;
+            }
+        }
+        __syncthreads();
+        // first road of every event that starts inside this tile
+        const uint64_t e_lo = ev_range[0], e_hi = ev_range[1];
+        for (uint64_t e = e_lo + threadIdx.x; e < e_hi; e += TILE_THREADS) {
+            const uint64_t s = __ldg(event_off + e);
+            if (s >= tile_start && s < tile_end)
+                event_road[e] = (uint32_t)(tile_base + pre[s - tile_start]);
+        }
+        if (rows_per_item) {
+            uint32_t it_total;
+            block_exclusive_scan<uint32_t>(items_sum, red, &it_total);
+            unsigned long long c_total;
+            block_exclusive_scan<unsigned long long>(comb_sum, red64, &c_total);
+            if (threadIdx.x == 0) {
+                tile_items[t] = it_total;
+                if (counts && c_total) atomicAdd((unsigned long long *)(counts + 2), c_total);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_unpack_events(const uint32_t *__restrict__ words,
+                                const uint64_t *__restrict__ event_off,
+                                const Dims *__restrict__ dims,
+                                const uint32_t *__restrict__ event_road,
+                                unsigned long long *status) {
+    const uint64_t n_words = dims->n_words, n_events = dims->n_events;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid == 0) {
+        if (__ldg(event_off) != 0 || __ldg(event_off + n_events) != n_words)
+            report(status, 0, SVT_ERR_BAD_ARG);
+    }
+    for (uint64_t e = tid; e < n_events; e += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t s = __ldg(event_off + e), s1 = __ldg(event_off + e + 1);
+        if (s1 <= s || s >= n_words) {
+            report(status, 0, SVT_ERR_BAD_ARG);
+            continue;
+        }
+        const uint32_t h = __ldg(words + s);
+        if (w_type(h) != TYPE_EVENT) {
+            report(status, s, SVT_ERR_BAD_TYPE);                                   // V1
+        } else if (ev_nroads(h) != event_road[e + 1] - event_road[e]) {
+            report(status, s, SVT_ERR_NROADS_MISMATCH);                            // V10
+        }
+    }
+}
+
+}  // namespace
+
+void launch_set_dims(Dims *dims, uint64_t n_words, uint64_t n_events, unsigned long long *status,
+                     uint64_t *counts, int n_counts, cudaStream_t st) {
+    k_set_dims<<<1, 32, 0, st>>>(dims, n_words, n_events, status, counts, n_counts);
+}
+
+void launch_unpack_count(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
+                         uint64_t max_words, uint32_t n_sectors, uint32_t *tile_roads,
+                         unsigned long long *status, int grid, cudaStream_t st) {
+    uint64_t T = n_tiles(max_words);
+    int g = (int)(T < (uint64_t)grid ? T : (uint64_t)grid);
+    if (g > 0) k_unpack_count<<<g, TILE_THREADS, 0, st>>>(words, event_off, dims, n_sectors, tile_roads, status);
+}
+
+void launch_scan_tiles(uint32_t *a, const Dims *dims, const uint64_t *n_dev, uint64_t *total64,
+                       uint32_t *event_road, unsigned long long *status, cudaStream_t st) {
+    k_scan_tiles<<<1, 1024, 0, st>>>(a, dims, n_dev, total64, event_road, status);
+}
+
+void launch_unpack_roads(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
+                         uint64_t max_words, const uint32_t *tile_roads, uint64_t road_cap,
+                         uint32_t *road_word, uint32_t *road_nhit, uint32_t *event_road,
+                         const svt_config cfg, uint32_t rows_per_item, uint32_t *road_items,
+                         uint32_t *tile_items, uint64_t *counts, unsigned long long *status,
+                         int grid, cudaStream_t st) {
+    uint64_t T = n_tiles(max_words);
+    int g = (int)(T < (uint64_t)grid ? T : (uint64_t)grid);
+    if (g > 0)
+        k_unpack_roads<<<g, TILE_THREADS, 0, st>>>(words, event_off, dims, tile_roads, road_cap,
+                                                   road_word, road_nhit, event_road, cfg,
+                                                   rows_per_item, road_items, tile_items, counts,
+                                                   status);
+}
+
+void launch_unpack_events(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
+                          uint64_t max_events, const uint32_t *event_road,
+                          unsigned long long *status, int grid, cudaStream_t st) {
+    uint64_t blocks = (max_events + 255) / 256;
+    if (blocks < 1) blocks = 1;
+    int g = (int)(blocks < (uint64_t)grid ? blocks : (uint64_t)grid);
+    k_unpack_events<<<g, 256, 0, st>>>(words, event_off, dims, event_road, status);
+}
+
+}  // namespace svt

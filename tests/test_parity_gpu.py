@@ -1,0 +1,244 @@
+"""Bit-exact parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Every case runs the same seeded batch through libsvt.so and through the
+oracle and compares the status key and every output word.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1311_0380_gb300 import synth
+from svt_testlib import assert_same, batch_for, cfg_pair, gpu_run, oracle_run
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1311_0380_gb300 import api
+    api.svt_version()   # loads libsvt.so or fails loudly
+
+
+CONSTS = {}
+
+
+def consts_for(S):
+    if S not in CONSTS:
+        CONSTS[S] = synth.make_constants(S)
+    return CONSTS[S]
+
+
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_small_batch(path):
+    spec, consts, b = batch_for("small", 100, consts_for(64))
+    cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb, n_sectors=64)
+    key, rec = oracle_run(b.words, b.event_off, consts.F, consts.q, ocfg)
+    st, got, _ = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, path)
+    assert_same(st, got, key, rec, "small/" + path)
+    assert np.any(rec[:, 0] >> 24 & 1) and not np.all(rec[:, 0] >> 24 & 1)
+
+
+@pytest.mark.parametrize("n_events", [1, 10, 100, 1000, 3000])
+def test_scaled_batch_fused(n_events):
+    spec, consts, b = batch_for("scaled", n_events, consts_for(512))
+    cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb)
+    key, rec = oracle_run(b.words, b.event_off, consts.F, consts.q, ocfg)
+    st, got, counts = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "fused")
+    assert_same(st, got, key, rec, f"scaled{n_events}")
+    assert counts[0] == b.total_roads
+    assert counts[2] == b.combinations(spec.max_comb).sum()
+    assert counts[3] == int(np.sum(rec[:, 0] >> 24 & 1))
+
+
+@pytest.mark.parametrize("n_events", [1, 100, 1000])
+def test_scaled_batch_plain(n_events):
+    spec, consts, b = batch_for("scaled", n_events, consts_for(512))
+    cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb)
+    key, rec = oracle_run(b.words, b.event_off, consts.F, consts.q, ocfg)
+    n_comb = int(b.combinations(spec.max_comb).sum())
+    st, got, _ = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "plain", comb_cap=n_comb)
+    assert_same(st, got, key, rec, f"plain{n_events}")
+
+
+def test_paper_shape_3000_events():
+    # 2048 combinations per event, 3000 events: the paper's largest sample
+    spec, consts, b = batch_for("paper", 3000, consts_for(512))
+    assert int(b.combinations().sum()) == 2048 * 3000
+    cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb)
+    key, rec = oracle_run(b.words, b.event_off, consts.F, consts.q, ocfg)
+    for path in ("fused", "plain"):
+        st, got, _ = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, path,
+                             comb_cap=2048 * 3000)
+        assert_same(st, got, key, rec, "paper/" + path)
+
+
+def test_uneven_batch_capped():
+    spec, consts, b = batch_for("uneven", 48, consts_for(512))
+    cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb)
+    key, rec = oracle_run(b.words, b.event_off, consts.F, consts.q, ocfg)
+    st, got, _ = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "fused")
+    assert_same(st, got, key, rec, "uneven")
+    assert np.mean(rec[:, 0] >> 24 & oracle.F_OVERFLOW > 0) > 0.5
+
+
+@pytest.mark.parametrize("sched", [(1, 1, 1), (4, 3, 7), (16, 1, 64), (8, 4, 32), (2, 8, 2)])
+def test_schedules_give_identical_results(sched):
+    from paper_1311_0380_gb300 import api
+    spec, consts, b = batch_for("scaled", 60, consts_for(512))
+    cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb)
+    key, rec = oracle_run(b.words, b.event_off, consts.F, consts.q, ocfg)
+    st, got, _ = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "fused",
+                         sched=api.schedule(*sched))
+    assert_same(st, got, key, rec, f"sched{sched}")
+
+
+# ----------------------------------------------------------------------------- edge cases
+def words_of(events):
+    """events: list of (event_id, [(sector, road_id, [(layer, coord), ...]), ...])"""
+    words, off = [], [0]
+    for eid, roads in events:
+        words.append(int(synth.event_word(eid, len(roads))))
+        for sec, rid, hits in roads:
+            words.append(int(synth.road_word(sec, rid)))
+            words.extend(int(synth.hit_word(l, c)) for l, c in sorted(hits, key=lambda h: h[0]))
+        off.append(len(words))
+    return np.array(words, np.uint32), np.array(off, np.uint64)
+
+
+def random_consts(S, seed, scale=32768):
+    rng = np.random.default_rng(seed)
+    F = rng.integers(-scale, scale, (S, 64, 6, 6)).astype(np.int16)
+    q = rng.integers(-scale, scale, (S, 64, 6)).astype(np.int16)
+    return F, q
+
+
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_empty_batch_and_events_without_roads(path):
+    F, q = random_consts(4, 1)
+    cfg, ocfg = cfg_pair(n_sectors=4)
+    w = np.zeros(0, np.uint32)
+    off = np.zeros(1, np.uint64)
+    st, got, _ = gpu_run(w, off, F, q, cfg, path)
+    assert st == oracle.KEY_OK
+    w, off = words_of([(1, []), (2, []), (3, [])])
+    key, rec = oracle_run(w, off, F, q, ocfg)
+    st, got, _ = gpu_run(w, off, F, q, cfg, path)
+    assert_same(st, got, key, rec, "no roads")
+
+
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_missing_layers_patterns_and_no_hits(path):
+    rng = np.random.default_rng(3)
+    F, q = random_consts(8, 2, scale=3000)
+    roads = []
+    for rid in range(300):
+        n = rng.integers(0, 4, 6)
+        if rid % 50 == 0:
+            n[:] = 0
+        hits = [(l, int(rng.integers(0, 32768))) for l in range(6) for _ in range(n[l])]
+        roads.append((int(rng.integers(0, 8)), rid, hits))
+    events = [(e, roads[e * 30:(e + 1) * 30]) for e in range(10)]
+    w, off = words_of(events)
+    for min_layers in (0, 3, 5, 6):
+        cfg, ocfg = cfg_pair(chi2_cut=200000000, max_comb=50, min_layers=min_layers, n_sectors=8)
+        key, rec = oracle_run(w, off, F, q, ocfg)
+        st, got, _ = gpu_run(w, off, F, q, cfg, path, comb_cap=300 * 64)
+        assert_same(st, got, key, rec, f"min_layers{min_layers}")
+
+
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_ties_and_extreme_constants(path):
+    rng = np.random.default_rng(4)
+    S = 2
+    F, q = random_consts(S, 5)
+    F[:, :, 3:, :] = rng.integers(-2, 3, (S, 64, 3, 6))      # tiny chi rows: many equal chi2
+    roads = []
+    for rid in range(400):
+        n = rng.integers(1, 5, 6)
+        base = int(rng.integers(0, 32768))
+        hits = [(l, base if rng.random() < 0.6 else int(rng.integers(0, 32768)))
+                for l in range(6) for _ in range(n[l])]
+        roads.append((int(rng.integers(0, S)), rid, hits))
+    w, off = words_of([(e, roads[e * 40:(e + 1) * 40]) for e in range(10)])
+    for cut in (0, 5, 1000, 0xFFFFFFFF):
+        for oshift, qshift in ((15, 15), (9, 0), (31, 24), (12, 20)):
+            cfg, ocfg = cfg_pair(oshift, qshift, cut, 300, 5, S)
+            key, rec = oracle_run(w, off, F, q, ocfg)
+            st, got, _ = gpu_run(w, off, F, q, cfg, path, comb_cap=400 * 300)
+            assert_same(st, got, key, rec, f"cut{cut} os{oshift} qs{qshift}")
+
+
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_maximum_hits_per_layer(path):
+    # 16 hits in every layer: 16^6 combinations, capped
+    rng = np.random.default_rng(6)
+    F, q = random_consts(1, 7, scale=20000)
+    roads = [(0, rid, [(l, int(rng.integers(0, 32768))) for l in range(6) for _ in range(16)])
+             for rid in range(6)]
+    w, off = words_of([(0, roads)])
+    for cap in (1, 31, 33, 4096, 70000):
+        cfg, ocfg = cfg_pair(max_comb=cap, n_sectors=1, chi2_cut=0xFFFFFFFF)
+        key, rec = oracle_run(w, off, F, q, ocfg)
+        st, got, _ = gpu_run(w, off, F, q, cfg, path, comb_cap=6 * cap)
+        assert_same(st, got, key, rec, f"cap{cap}")
+        assert np.all(rec[:, 0] >> 24 & oracle.F_OVERFLOW)
+
+
+def test_uncapped_giant_road_fused():
+    # one road of 16^5 * 8 = 8.4M combinations next to small ones
+    rng = np.random.default_rng(8)
+    F, q = random_consts(1, 9, scale=20000)
+    big = (0, 1, [(l, int(rng.integers(0, 32768))) for l in range(6) for _ in range(16 if l else 8)])
+    small = [(0, 2 + i, [(l, int(rng.integers(0, 32768))) for l in range(6)]) for i in range(5)]
+    w, off = words_of([(0, small[:2] + [big] + small[2:])])
+    cfg, ocfg = cfg_pair(max_comb=1 << 24, n_sectors=1, chi2_cut=0xFFFFFFFF)
+    key, rec = oracle_run(w, off, F, q, ocfg)
+    st, got, _ = gpu_run(w, off, F, q, cfg, "fused")
+    assert_same(st, got, key, rec, "giant")
+
+
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_validation_cases_match_oracle(path):
+    from test_oracle_pins import tokens_to_words
+    data = json.load(open(os.path.join(GOLDEN, "validation_cases.json")))
+    F, q = random_consts(64, 10)
+    for case in data["cases"]:
+        w = tokens_to_words(case["words"])
+        off = np.array(case["offsets"], np.uint64)
+        cfg, ocfg = cfg_pair(n_sectors=case["n_sectors"], min_layers=0)
+        key = oracle.validate(w, off, case["n_sectors"])
+        if key == oracle.KEY_OK:
+            key, rec = oracle_run(w, off, F, q, ocfg)
+        else:
+            rec = None
+        st, got, _ = gpu_run(w, off, F, q, cfg, path, road_cap=len(w) + 1)
+        assert_same(st, got, key, rec, case["name"])
+
+
+def test_random_corruptions_match_oracle():
+    rng = np.random.default_rng(11)
+    spec, consts, b = batch_for("small", 30, consts_for(64))
+    cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb, n_sectors=64)
+    for trial in range(40):
+        w = b.words.copy()
+        for _ in range(int(rng.integers(1, 4))):
+            i = int(rng.integers(0, len(w)))
+            w[i] ^= np.uint32(1) << np.uint32(int(rng.integers(0, 32)))
+        key = oracle.validate(w, b.event_off, 64)
+        rec = oracle_run(w, b.event_off, consts.F, consts.q, ocfg)[1] if key == oracle.KEY_OK else None
+        st, got, _ = gpu_run(w, b.event_off, consts.F, consts.q, cfg, "fused", road_cap=len(w))
+        assert_same(st, got, key, rec, f"corrupt{trial}")
+
+
+def test_road_capacity_overflow_is_reported():
+    spec, consts, b = batch_for("small", 5, consts_for(64))
+    cfg, _ = cfg_pair(n_sectors=64)
+    st, _, _ = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "fused", road_cap=7)
+    assert st & 0xFF == 9
