@@ -115,16 +115,22 @@ typedef struct {
     int32_t p[3];
 } svt_best;
 
-/* Schedule of the persistent fit kernel.  Zero fields take the defaults.
+/* Schedule of the fused path's persistent fit kernel.  Zero fields take the
+ * defaults.
  *   warps_per_block  warps of one persistent block (1..16, default 8)
- *   blocks_per_sm    persistent blocks per SM (default 2)
- *   rows_per_item    rows of the (prefix x suffix) combination grid handled
- *                    by one warp work item (1..64, default 16) */
+ *   blocks_per_sm    persistent blocks per SM (default: as many as fit)
+ *   rows_per_item    rows of the (prefix x suffix) combination grid in one
+ *                    work item of a split road (1..64, default 16)
+ *   roads_per_chunk  consecutive roads a warp takes at once (1..32, default 4)
+ *   small_max        roads with more evaluated combinations than this are
+ *                    split into work items; the others are fitted whole by
+ *                    one warp (default 4096) */
 typedef struct {
     uint32_t warps_per_block;
     uint32_t blocks_per_sm;
     uint32_t rows_per_item;
-    uint32_t reserved;
+    uint32_t roads_per_chunk;
+    uint32_t small_max;
 } svt_schedule;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -253,8 +259,8 @@ size_t svt_run_workspace_size(uint64_t max_words, uint64_t max_events, uint64_t 
  *   road_cap           capacity of d_out (roads)
  *   d_out[6*road_cap]  out: one record per road, input order
  *   d_event_road[n_events+1]  out (may be NULL): first road of each event, then R
- *   d_counts[4]        out (may be NULL): R, work items, total evaluated
- *                      combinations, roads that passed
+ *   d_counts[4]        out (may be NULL): R, work items of split roads, total
+ *                      evaluated combinations, roads that passed
  *   d_status[1]        out: reset, then the validation key
  *   d_workspace        svt_run_workspace_size(n_words, n_events, road_cap, sched)
  *                      bytes, 256-byte aligned

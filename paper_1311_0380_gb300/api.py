@@ -32,8 +32,9 @@ def config(oshift=15, qshift=15, chi2_cut=0xFFFFFFFF, max_comb=262144, min_layer
     return SvtConfig(oshift, qshift, chi2_cut, max_comb, min_layers, n_sectors)
 
 
-def schedule(warps_per_block=0, blocks_per_sm=0, rows_per_item=0) -> SvtSchedule:
-    return SvtSchedule(warps_per_block, blocks_per_sm, rows_per_item, 0)
+def schedule(warps_per_block=0, blocks_per_sm=0, rows_per_item=0, roads_per_chunk=0,
+             small_max=0) -> SvtSchedule:
+    return SvtSchedule(warps_per_block, blocks_per_sm, rows_per_item, roads_per_chunk, small_max)
 
 
 # ------------------------------------------------------------------ raw entry points
@@ -250,7 +251,7 @@ class PlainPath:
         return status, rec, R
 
 
-FUSED_LAUNCHES_PER_RUN = 8   # set_dims, unpack_count, scan, unpack_roads, unpack_events, scan, items, fit
+FUSED_LAUNCHES_PER_RUN = 9   # set_dims, unpack_count, scan, unpack_roads, unpack_events, 2 scans, big list, fit
 PLAIN_LAUNCHES_PER_RUN = 13  # unpack (5), combine (5), fit, select, format
 
 

@@ -43,18 +43,21 @@ bool config_ok(const svt_config *c) {
 }
 
 svt_schedule resolve(const svt_schedule *s) {
-    svt_schedule r{8, 2, 16, 0};
+    svt_schedule r{8, 0, 16, 4, 4096};
     if (s) {
         if (s->warps_per_block) r.warps_per_block = s->warps_per_block;
         if (s->blocks_per_sm) r.blocks_per_sm = s->blocks_per_sm;
         if (s->rows_per_item) r.rows_per_item = s->rows_per_item;
+        if (s->roads_per_chunk) r.roads_per_chunk = s->roads_per_chunk;
+        if (s->small_max) r.small_max = s->small_max;
     }
     return r;
 }
 
 bool schedule_ok(const svt_schedule &s) {
-    return s.warps_per_block >= 1 && s.warps_per_block <= 16 && s.blocks_per_sm >= 1 &&
-           s.blocks_per_sm <= 32 && s.rows_per_item >= 1 && s.rows_per_item <= 64;
+    return s.warps_per_block >= 1 && s.warps_per_block <= 16 && s.blocks_per_sm <= 32 &&
+           s.rows_per_item >= 1 && s.rows_per_item <= 64 && s.roads_per_chunk >= 1 &&
+           s.roads_per_chunk <= 32 && s.small_max >= 1;
 }
 
 int tile_grid() {
@@ -87,12 +90,14 @@ UnpackWs carve_unpack(void *base, uint64_t max_words) {
 // Workspace layout of svt_run.
 struct RunWs {
     Dims *dims;
-    uint32_t *tile_roads, *tile_items;
-    uint32_t *road_word, *road_nhit, *road_items, *road_item_off, *road_pending;
-    unsigned long long *road_best;
-    uint32_t *event_road;
-    uint32_t *item_counter;
     uint64_t *counts;
+    uint64_t *n_big;
+    uint32_t *counters;
+    uint32_t *tile_roads, *tile_big, *tile_bigitems;
+    uint4 *desc;
+    uint32_t *big_road, *big_item_off, *big_pending;
+    unsigned long long *big_best;
+    uint32_t *event_road;
     size_t bytes;
 };
 RunWs carve_run(void *base, uint64_t max_words, uint64_t max_events, uint64_t road_cap) {
@@ -101,15 +106,16 @@ RunWs carve_run(void *base, uint64_t max_words, uint64_t max_events, uint64_t ro
     const uint64_t T = n_tiles(max_words);
     w.dims = c.take<Dims>(1);
     w.counts = c.take<uint64_t>(4);
-    w.item_counter = c.take<uint32_t>(1);
+    w.n_big = c.take<uint64_t>(1);
+    w.counters = c.take<uint32_t>(2);
     w.tile_roads = c.take<uint32_t>(T + 1);
-    w.tile_items = c.take<uint32_t>(T + 1);
-    w.road_word = c.take<uint32_t>(road_cap);
-    w.road_nhit = c.take<uint32_t>(road_cap);
-    w.road_items = c.take<uint32_t>(road_cap);
-    w.road_item_off = c.take<uint32_t>(road_cap + 1);
-    w.road_pending = c.take<uint32_t>(road_cap);
-    w.road_best = c.take<unsigned long long>(road_cap);
+    w.tile_big = c.take<uint32_t>(T + 1);
+    w.tile_bigitems = c.take<uint32_t>(T + 1);
+    w.desc = c.take<uint4>(road_cap);
+    w.big_road = c.take<uint32_t>(road_cap);
+    w.big_item_off = c.take<uint32_t>(road_cap + 1);
+    w.big_pending = c.take<uint32_t>(road_cap);
+    w.big_best = c.take<unsigned long long>(road_cap);
     w.event_road = c.take<uint32_t>(max_events + 1);
     w.bytes = c.size();
     return w;
@@ -177,9 +183,9 @@ int svt_unpack(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_even
     launch_unpack_count(d_words, d_event_off, w.dims, n_words, n_sectors, w.tile_roads, status,
                         grid, st);
     launch_scan_tiles(w.tile_roads, w.dims, nullptr, d_n_roads, d_event_road, status, st);
+    const FusedRoads none{nullptr, nullptr, nullptr, 1, 0};
     launch_unpack_roads(d_words, d_event_off, w.dims, n_words, w.tile_roads, road_cap, d_road_word,
-                        d_road_nhit, d_event_road, cfg, 0, nullptr, nullptr, nullptr, status, grid,
-                        st);
+                        d_road_nhit, d_event_road, cfg, none, nullptr, status, grid, st);
     launch_unpack_events(d_words, d_event_off, w.dims, n_events, d_event_road, status, grid, st);
     return launch_status();
 }
@@ -281,26 +287,26 @@ int svt_run(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_o
     const int grid = tile_grid();
     const int sms = current_sm_count();
     if (sms <= 0) return SVT_ERR_CUDA;
-    int occ = fit_persistent_blocks_per_sm((int)sc.warps_per_block, sc.rows_per_item);
+    const int occ = fit_persistent_blocks_per_sm((int)sc.warps_per_block);
     if (occ <= 0) return SVT_ERR_CUDA;
-    int bps = (int)sc.blocks_per_sm < occ ? (int)sc.blocks_per_sm : occ;
+    const int bps = (sc.blocks_per_sm == 0 || (int)sc.blocks_per_sm > occ) ? occ : (int)sc.blocks_per_sm;
+    const FusedRoads fr{w.desc, w.tile_big, w.tile_bigitems, sc.rows_per_item, sc.small_max};
+    const BigList bl{w.big_road, w.big_item_off, w.big_best, w.big_pending, w.counters};
 
     launch_set_dims(w.dims, n_words, n_events, status, counts, 4, st);
     launch_unpack_count(d_words, d_event_off, w.dims, n_words, cfg->n_sectors, w.tile_roads, status,
                         grid, st);
     launch_scan_tiles(w.tile_roads, w.dims, nullptr, counts + 0, event_road, status, st);
-    launch_unpack_roads(d_words, d_event_off, w.dims, n_words, w.tile_roads, road_cap, w.road_word,
-                        w.road_nhit, event_road, *cfg, sc.rows_per_item, w.road_items,
-                        w.tile_items, counts, status, grid, st);
+    launch_unpack_roads(d_words, d_event_off, w.dims, n_words, w.tile_roads, road_cap, nullptr,
+                        nullptr, event_road, *cfg, fr, counts, status, grid, st);
     launch_unpack_events(d_words, d_event_off, w.dims, n_events, event_road, status, grid, st);
-    launch_scan_tiles(w.tile_items, w.dims, nullptr, counts + 1, nullptr, status, st);
-    launch_items(d_words, w.road_word, w.road_nhit, road_cap, w.dims, n_words, w.tile_roads,
-                 w.tile_items, w.road_items, w.road_item_off, w.road_best, w.road_pending, d_out,
-                 w.item_counter, status, grid, st);
+    launch_scan_tiles(w.tile_bigitems, w.dims, nullptr, counts + 1, nullptr, status, st);
+    launch_scan_tiles(w.tile_big, w.dims, nullptr, w.n_big, nullptr, status, st);
+    launch_big_list(w.desc, road_cap, w.dims, n_words, w.tile_roads, w.tile_big, w.tile_bigitems,
+                    fr, bl, status, grid, st);
     if (timer && cudaEventRecord(timer->start, st) != cudaSuccess) return SVT_ERR_CUDA;
-    if (launch_fit_persistent(d_words, w.road_word, w.road_nhit, w.road_item_off, counts + 0,
-                              road_cap, counts + 1, d_F, d_q, *cfg, sc.rows_per_item, w.road_best,
-                              w.road_pending, d_out, w.item_counter, counts, status,
+    if (launch_fit_persistent(d_words, w.desc, counts, road_cap, w.n_big, d_F, d_q, *cfg, fr,
+                              sc.roads_per_chunk, bl, d_out, counts, status,
                               (int)sc.warps_per_block, sms * bps, st) != cudaSuccess)
         return SVT_ERR_CUDA;
     if (timer) {

@@ -1,0 +1,422 @@
+// svt_calib.cu -- FP32 relaxation of the linearised fit for calibrating its
+// constants (the paper's Sec. 2 form p = f.x + q without the integer shift
+// and clamp):
+//     y_t = F[s_t] x_t + q[s_t]                       (6 rows per track)
+//     L   = (1/N) sum_t [ sum_{k<3} w_k (y_tk - theta_tk)^2 + sum_{k>=3} y_tk^2 ]
+// with hand-written forward and backward kernels.
+//
+// Tracks are first sorted by sector (stable counting sort on the device);
+// every kernel then works on "items" of at most CALIB_CHUNK consecutive tracks
+// of one sector, one warp per item.  Reductions are two-level and in a fixed
+// order (lanes -> shuffle tree -> items in index order), so results are
+// bitwise reproducible run to run.
+#include "svt_internal.cuh"
+
+namespace svt {
+
+namespace {
+
+constexpr int CALIB_CHUNK = 256;          // tracks per item (8 per lane)
+constexpr int SORT_TILE = 1024;           // tracks per histogram tile
+constexpr int NPAR = 42;                  // 36 entries of F[s] + 6 of q[s]
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+    return v;
+}
+
+// ---- stable counting sort by sector ------------------------------------------
+__global__ void k_hist(const int32_t *__restrict__ sector, uint64_t n, uint32_t S, uint32_t T,
+                       uint32_t *counts, unsigned long long *status) {
+    __shared__ uint32_t h[512];
+    for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
+        for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) h[s] = 0;
+        __syncthreads();
+        for (uint32_t j = threadIdx.x; j < SORT_TILE; j += blockDim.x) {
+            const uint64_t i = (uint64_t)t * SORT_TILE + j;
+            if (i < n) {
+                const int32_t s = sector[i];
+                if (s < 0 || (uint32_t)s >= S) {
+                    report(status, i, SVT_ERR_BAD_SECTOR);
+                } else {
+                    atomicAdd(&h[s], 1u);
+                }
+            }
+        }
+        __syncthreads();
+        for (uint32_t s = threadIdx.x; s < S; s += blockDim.x) counts[(uint64_t)s * T + t] = h[s];
+        __syncthreads();
+    }
+}
+
+// exclusive scan of counts[0..n) in one block; n = S * T
+__global__ void __launch_bounds__(1024) k_scan_counts(uint32_t *counts, uint64_t n) {
+    __shared__ uint32_t sm[33];
+    uint32_t carry = 0;
+    for (uint64_t c0 = 0; c0 < n; c0 += 4096) {
+        const uint64_t i0 = c0 + (uint64_t)threadIdx.x * 4;
+        uint32_t v[4], s = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = (i0 + k < n) ? counts[i0 + k] : 0u;
+            s += v[k];
+        }
+        uint32_t tot;
+        uint32_t run = carry + block_exclusive_scan<uint32_t>(s, sm, &tot);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k < n) counts[i0 + k] = run;
+            run += v[k];
+        }
+        carry += tot;
+    }
+}
+
+// one warp per tile: stable ranks inside the tile by rounds of 32 tracks
+__global__ void k_scatter(const int32_t *__restrict__ sector, uint64_t n, uint32_t S, uint32_t T,
+                          const uint32_t *__restrict__ base, int32_t *perm) {
+    __shared__ uint32_t cnt[512];
+    const int lane = threadIdx.x;
+    for (uint32_t t = blockIdx.x; t < T; t += gridDim.x) {
+        for (uint32_t s = lane; s < S; s += 32) cnt[s] = 0;
+        __syncwarp();
+        for (int r = 0; r < SORT_TILE / 32; ++r) {
+            const uint64_t i = (uint64_t)t * SORT_TILE + r * 32 + lane;
+            const bool valid = i < n;
+            const int32_t s = valid ? sector[i] : -1;
+            const bool ok = valid && s >= 0 && (uint32_t)s < S;
+            const uint32_t key = ok ? (uint32_t)s : 0xFFFFFFFFu;
+            const uint32_t match = __match_any_sync(0xffffffffu, key);
+            const uint32_t rank = __popc(match & ((1u << lane) - 1u));
+            uint32_t before = 0;
+            if (ok) before = cnt[s];
+            __syncwarp();
+            if (ok) {
+                perm[base[(uint64_t)s * T + t] + before + rank] = (int32_t)i;
+                if (rank == 0) cnt[s] = before + __popc(match);
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// sector_off and the item table, one block
+__global__ void __launch_bounds__(1024)
+    k_items(const uint32_t *__restrict__ base, uint32_t S, uint32_t T, uint64_t n,
+            int32_t *sector_off, int32_t *item_sector, int32_t *item_start, int32_t *n_items,
+            uint32_t max_items) {
+    __shared__ uint32_t sm[33];
+    __shared__ uint32_t carry_s;
+    if (threadIdx.x == 0) carry_s = 0;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < S; c0 += 1024) {
+        const uint32_t s = c0 + threadIdx.x;
+        uint32_t off = 0, len = 0;
+        if (s < S) {
+            off = base[(uint64_t)s * T];
+            const uint32_t end = (s + 1 < S) ? base[(uint64_t)(s + 1) * T] : (uint32_t)n;
+            len = end - off;
+            sector_off[s] = (int32_t)off;
+        }
+        const uint32_t items = (len + CALIB_CHUNK - 1) / CALIB_CHUNK;
+        uint32_t tot;
+        const uint32_t first = carry_s + block_exclusive_scan<uint32_t>(items, sm, &tot);
+        for (uint32_t k = 0; k < items; ++k) {
+            if (first + k < max_items) {
+                item_sector[first + k] = (int32_t)s;
+                item_start[first + k] = (int32_t)(off + k * CALIB_CHUNK);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry_s += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        sector_off[S] = (int32_t)n;
+        *n_items = (int32_t)carry_s;
+    }
+}
+
+__global__ void k_gather(const float *__restrict__ src, uint32_t width,
+                         const int32_t *__restrict__ perm, uint64_t n, float *dst) {
+    const uint64_t total = n * width;
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t i = k / width, c = k % width;
+        dst[k] = src[(uint64_t)perm[i] * width + c];
+    }
+}
+
+// ---- forward / loss / backward -------------------------------------------------
+struct Item {
+    uint32_t s, start, end;
+};
+
+__device__ __forceinline__ Item item_of(const int32_t *item_sector, const int32_t *item_start,
+                                        const int32_t *sector_off, uint32_t i) {
+    Item it;
+    it.s = (uint32_t)item_sector[i];
+    it.start = (uint32_t)item_start[i];
+    const uint32_t send = (uint32_t)sector_off[it.s + 1];
+    it.end = min(it.start + (uint32_t)CALIB_CHUNK, send);
+    return it;
+}
+
+// F[s] and q[s] of the item's sector in the warp's shared slot
+__device__ __forceinline__ void load_consts(float *c, const float *__restrict__ F,
+                                            const float *__restrict__ q, uint32_t s, int lane) {
+    for (int j = lane; j < NPAR; j += 32) c[j] = j < 36 ? F[(size_t)s * 36 + j] : q[(size_t)s * 6 + (j - 36)];
+    __syncwarp();
+}
+
+__device__ __forceinline__ void eval_track(const float *c, const float *__restrict__ x, uint32_t t,
+                                           float xv[6], float y[6]) {
+    const float2 *xp = reinterpret_cast<const float2 *>(x + (size_t)t * 6);
+    float2 a = xp[0], b = xp[1], d = xp[2];
+    xv[0] = a.x; xv[1] = a.y; xv[2] = b.x; xv[3] = b.y; xv[4] = d.x; xv[5] = d.y;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        float acc = c[36 + k];
+#pragma unroll
+        for (int l = 0; l < 6; ++l) acc = fmaf(c[k * 6 + l], xv[l], acc);
+        y[k] = acc;
+    }
+}
+
+__global__ void k_forward(const float *__restrict__ x, const int32_t *__restrict__ item_sector,
+                          const int32_t *__restrict__ item_start,
+                          const int32_t *__restrict__ sector_off, const int32_t *__restrict__ n_items,
+                          const float *__restrict__ F, const float *__restrict__ q, float *y) {
+    __shared__ float cs[8][48];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t NI = (uint32_t)*n_items;
+    for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + wib; i < NI; i += gridDim.x * (blockDim.x >> 5)) {
+        const Item it = item_of(item_sector, item_start, sector_off, i);
+        load_consts(cs[wib], F, q, it.s, lane);
+        for (uint32_t t = it.start + lane; t < it.end; t += 32) {
+            float xv[6], yv[6];
+            eval_track(cs[wib], x, t, xv, yv);
+            float2 *yp = reinterpret_cast<float2 *>(y + (size_t)t * 6);
+            yp[0] = make_float2(yv[0], yv[1]);
+            yp[1] = make_float2(yv[2], yv[3]);
+            yp[2] = make_float2(yv[4], yv[5]);
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void k_loss_items(const float *__restrict__ x, const float *__restrict__ theta,
+                             const int32_t *__restrict__ item_sector,
+                             const int32_t *__restrict__ item_start,
+                             const int32_t *__restrict__ sector_off,
+                             const int32_t *__restrict__ n_items, const float *__restrict__ F,
+                             const float *__restrict__ q, const float *__restrict__ w,
+                             float *item_loss) {
+    __shared__ float cs[8][48];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t NI = (uint32_t)*n_items;
+    const float w0 = w[0], w1 = w[1], w2 = w[2];
+    for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + wib; i < NI; i += gridDim.x * (blockDim.x >> 5)) {
+        const Item it = item_of(item_sector, item_start, sector_off, i);
+        load_consts(cs[wib], F, q, it.s, lane);
+        float acc = 0.f;
+        for (uint32_t t = it.start + lane; t < it.end; t += 32) {
+            float xv[6], yv[6];
+            eval_track(cs[wib], x, t, xv, yv);
+            const float r0 = yv[0] - theta[(size_t)t * 3 + 0];
+            const float r1 = yv[1] - theta[(size_t)t * 3 + 1];
+            const float r2 = yv[2] - theta[(size_t)t * 3 + 2];
+            acc += w0 * r0 * r0 + w1 * r1 * r1 + w2 * r2 * r2 + yv[3] * yv[3] + yv[4] * yv[4] +
+                   yv[5] * yv[5];
+        }
+        acc = warp_sum(acc);
+        if (lane == 0) item_loss[i] = acc;
+        __syncwarp();
+    }
+}
+
+// one block: loss = (sum of item partials in index order) / n, pairwise by blocks of 1024
+__global__ void __launch_bounds__(1024)
+    k_loss_final(const float *__restrict__ item_loss, const int32_t *__restrict__ n_items,
+                 uint64_t n, float *loss) {
+    __shared__ float sm[32];
+    const uint32_t NI = (uint32_t)*n_items;
+    float total = 0.f;
+    for (uint32_t c0 = 0; c0 < NI; c0 += 1024) {
+        float v = (c0 + threadIdx.x < NI) ? item_loss[c0 + threadIdx.x] : 0.f;
+        v = warp_sum(v);
+        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            float u = sm[threadIdx.x];
+            u = warp_sum(u);
+            if (threadIdx.x == 0) total += u;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = n ? total / (float)n : 0.f;
+}
+
+// per item: sum_t g_t x_t^T and sum_t g_t, where g comes from the loss
+// (mode 0, without the 2/N factor) or from grad_y (mode 1); also dx (mode 1).
+template <int MODE>
+__global__ void k_grad_items(const float *__restrict__ x, const float *__restrict__ theta,
+                             const float *__restrict__ grad_y,
+                             const int32_t *__restrict__ item_sector,
+                             const int32_t *__restrict__ item_start,
+                             const int32_t *__restrict__ sector_off,
+                             const int32_t *__restrict__ n_items, const float *__restrict__ F,
+                             const float *__restrict__ q, const float *__restrict__ w,
+                             float *item_grad, float *dx) {
+    __shared__ float cs[8][48];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t NI = (uint32_t)*n_items;
+    for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + wib; i < NI; i += gridDim.x * (blockDim.x >> 5)) {
+        const Item it = item_of(item_sector, item_start, sector_off, i);
+        load_consts(cs[wib], F, q, it.s, lane);
+        float acc[NPAR];
+#pragma unroll
+        for (int j = 0; j < NPAR; ++j) acc[j] = 0.f;
+        for (uint32_t t = it.start + lane; t < it.end; t += 32) {
+            float xv[6], g[6];
+            if (MODE == 0) {
+                float yv[6];
+                eval_track(cs[wib], x, t, xv, yv);
+                g[0] = w[0] * (yv[0] - theta[(size_t)t * 3 + 0]);
+                g[1] = w[1] * (yv[1] - theta[(size_t)t * 3 + 1]);
+                g[2] = w[2] * (yv[2] - theta[(size_t)t * 3 + 2]);
+                g[3] = yv[3];
+                g[4] = yv[4];
+                g[5] = yv[5];
+            } else {
+                const float2 *xp = reinterpret_cast<const float2 *>(x + (size_t)t * 6);
+                const float2 *gp = reinterpret_cast<const float2 *>(grad_y + (size_t)t * 6);
+                float2 a = xp[0], b = xp[1], d = xp[2];
+                xv[0] = a.x; xv[1] = a.y; xv[2] = b.x; xv[3] = b.y; xv[4] = d.x; xv[5] = d.y;
+                a = gp[0]; b = gp[1]; d = gp[2];
+                g[0] = a.x; g[1] = a.y; g[2] = b.x; g[3] = b.y; g[4] = d.x; g[5] = d.y;
+                if (dx) {
+                    float dv[6];
+#pragma unroll
+                    for (int l = 0; l < 6; ++l) {
+                        float s = 0.f;
+#pragma unroll
+                        for (int k = 0; k < 6; ++k) s = fmaf(cs[wib][k * 6 + l], g[k], s);
+                        dv[l] = s;
+                    }
+                    float2 *dp = reinterpret_cast<float2 *>(dx + (size_t)t * 6);
+                    dp[0] = make_float2(dv[0], dv[1]);
+                    dp[1] = make_float2(dv[2], dv[3]);
+                    dp[2] = make_float2(dv[4], dv[5]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+#pragma unroll
+                for (int l = 0; l < 6; ++l) acc[k * 6 + l] = fmaf(g[k], xv[l], acc[k * 6 + l]);
+                acc[36 + k] += g[k];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NPAR; ++j) acc[j] = warp_sum(acc[j]);
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < NPAR; ++j) item_grad[(size_t)i * NPAR + j] = acc[j];
+        }
+        __syncwarp();
+    }
+}
+
+// per (sector, entry): sum of the sector's item partials in index order, scaled
+__global__ void k_grad_final(const float *__restrict__ item_grad,
+                             const int32_t *__restrict__ item_start,
+                             const int32_t *__restrict__ sector_off, uint32_t S,
+                             const float *__restrict__ scale_dev, float scale, float *dF,
+                             float *dq) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= S * NPAR) return;
+    const uint32_t s = k / NPAR, j = k % NPAR;
+    // items of sector s are consecutive; the first is the one starting at sector_off[s]
+    const uint32_t off = (uint32_t)sector_off[s], end = (uint32_t)sector_off[s + 1];
+    float total = 0.f;
+    if (end > off) {
+        // index of the sector's first item = number of items of earlier sectors
+        uint32_t first = 0;
+        for (uint32_t u = 0; u < s; ++u) {
+            const uint32_t len = (uint32_t)(sector_off[u + 1] - sector_off[u]);
+            first += (len + CALIB_CHUNK - 1) / CALIB_CHUNK;
+        }
+        const uint32_t items = (end - off + CALIB_CHUNK - 1) / CALIB_CHUNK;
+        for (uint32_t m = 0; m < items; ++m) total += item_grad[(size_t)(first + m) * NPAR + j];
+    }
+    const float sc = scale * (scale_dev ? *scale_dev : 1.f);
+    if (j < 36)
+        dF[(size_t)s * 36 + j] = total * sc;
+    else
+        dq[(size_t)s * 6 + (j - 36)] = total * sc;
+}
+
+}  // namespace
+
+// ---- launchers used by svt_abi.cu -------------------------------------------------
+uint32_t calib_max_items(uint64_t n, uint32_t S) {
+    return (uint32_t)((n + CALIB_CHUNK - 1) / CALIB_CHUNK + S);
+}
+uint32_t calib_tiles(uint64_t n) { return (uint32_t)((n + SORT_TILE - 1) / SORT_TILE); }
+
+void launch_calib_sort(const int32_t *sector, uint64_t n, uint32_t S, uint32_t *counts,
+                       int32_t *perm, int32_t *sector_off, int32_t *item_sector,
+                       int32_t *item_start, int32_t *n_items, unsigned long long *status,
+                       int grid, cudaStream_t st) {
+    const uint32_t T = calib_tiles(n);
+    const int g = (int)min((uint32_t)grid, max(T, 1u));
+    if (T > 0) k_hist<<<g, 256, 0, st>>>(sector, n, S, T, counts, status);
+    k_scan_counts<<<1, 1024, 0, st>>>(counts, (uint64_t)S * T);
+    if (T > 0) k_scatter<<<g, 32, 0, st>>>(sector, n, S, T, counts, perm);
+    if (T > 0)
+        k_items<<<1, 1024, 0, st>>>(counts, S, T, n, sector_off, item_sector, item_start, n_items,
+                                    calib_max_items(n, S));
+}
+
+void launch_calib_gather(const float *src, uint32_t width, const int32_t *perm, uint64_t n,
+                         float *dst, int grid, cudaStream_t st) {
+    k_gather<<<grid, 256, 0, st>>>(src, width, perm, n, dst);
+}
+
+void launch_calib_forward(const float *x, const int32_t *item_sector, const int32_t *item_start,
+                          const int32_t *sector_off, const int32_t *n_items, uint32_t max_items,
+                          const float *F, const float *q, float *y, int grid, cudaStream_t st) {
+    const int g = (int)min((uint32_t)grid, (max_items + 7) / 8 + 1);
+    k_forward<<<g, 256, 0, st>>>(x, item_sector, item_start, sector_off, n_items, F, q, y);
+}
+
+void launch_calib_loss(const float *x, const float *theta, const int32_t *item_sector,
+                       const int32_t *item_start, const int32_t *sector_off,
+                       const int32_t *n_items, uint32_t max_items, uint64_t n, const float *F,
+                       const float *q, const float *w, float *item_loss, float *loss, int grid,
+                       cudaStream_t st) {
+    const int g = (int)min((uint32_t)grid, (max_items + 7) / 8 + 1);
+    k_loss_items<<<g, 256, 0, st>>>(x, theta, item_sector, item_start, sector_off, n_items, F, q, w,
+                                   item_loss);
+    k_loss_final<<<1, 1024, 0, st>>>(item_loss, n_items, n, loss);
+}
+
+void launch_calib_grad(int mode, const float *x, const float *theta, const float *grad_y,
+                       const int32_t *item_sector, const int32_t *item_start,
+                       const int32_t *sector_off, const int32_t *n_items, uint32_t max_items,
+                       uint32_t S, const float *F, const float *q, const float *w,
+                       const float *scale_dev, float scale, float *item_grad, float *dF,
+                       float *dq, float *dx, int grid, cudaStream_t st) {
+    const int g = (int)min((uint32_t)grid, (max_items + 7) / 8 + 1);
+    if (mode == 0)
+        k_grad_items<0><<<g, 256, 0, st>>>(x, theta, grad_y, item_sector, item_start, sector_off,
+                                          n_items, F, q, w, item_grad, dx);
+    else
+        k_grad_items<1><<<g, 256, 0, st>>>(x, theta, grad_y, item_sector, item_start, sector_off,
+                                          n_items, F, q, w, item_grad, dx);
+    k_grad_final<<<(S * NPAR + 255) / 256, 256, 0, st>>>(item_grad, item_start, sector_off, S,
+                                                        scale_dev, scale, dF, dq);
+}
+
+}  // namespace svt

@@ -14,6 +14,36 @@ struct Dims {
     uint64_t n_events;
 };
 
+// Fused-path outputs of the road extraction (desc == nullptr: plain path).
+struct FusedRoads {
+    uint4 *desc;               // per road: header word index, hits per layer,
+                               // header word, evaluated combinations
+    uint32_t *tile_big;        // per word tile: roads split into items
+    uint32_t *tile_bigitems;   // per word tile: items of those roads
+    uint32_t rows;             // rows per item
+    uint32_t small_max;        // roads above this many combinations are split
+};
+
+// Evaluated combinations of a road (0 when it has fewer than min_layers
+// layers hit) and, for the fused fit, its work items: roads with more than
+// small_max evaluated combinations are split into items of `rows` rows of
+// the (prefix x suffix) grid; smaller roads are fitted whole by one warp.
+__device__ __forceinline__ uint32_t road_eval_count(uint32_t packed, const svt_config &cfg) {
+    RoadShape s = road_shape(packed);
+    if (s.n_layers_hit < cfg.min_layers) return 0;
+    const uint32_t C = (uint32_t)s.C;
+    return C > cfg.max_comb ? cfg.max_comb : C;
+}
+__device__ __forceinline__ uint32_t road_big_items(uint32_t packed, uint32_t C_eval,
+                                                   const FusedRoads &fr) {
+    if (C_eval <= fr.small_max) return 0;
+    RoadShape s = road_shape(packed);
+    uint32_t split, NB;
+    road_split(s, split, NB);
+    const uint32_t NA = (C_eval + NB - 1) / NB;
+    return (NA + fr.rows - 1) / fr.rows;
+}
+
 // ---- unpack (svt_unpack.cu) --------------------------------------------------
 // K1: per-word validation (rules V2..V7, V9) and road headers per tile.
 void launch_unpack_count(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
@@ -25,43 +55,44 @@ void launch_unpack_count(const uint32_t *words, const uint64_t *event_off, const
 // status to (0, OOM).
 void launch_scan_tiles(uint32_t *a, const Dims *dims, const uint64_t *n_dev, uint64_t *total64,
                        uint32_t *event_road, unsigned long long *status, cudaStream_t st);
-// K2: road extraction: road_word, road_nhit, rule V8, event_road of events
-// starting in each tile; with rows_per_item > 0 also the work items of each
-// road (road_items) and per tile (tile_items), and the evaluated
+// K2: road extraction: road_word, road_nhit (either may be null), rule V8,
+// event_road of events starting in each tile; with fr.desc also the road
+// descriptors, the split roads and items per tile and the evaluated
 // combinations (counts[2]).
 void launch_unpack_roads(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
                          uint64_t max_words, const uint32_t *tile_roads, uint64_t road_cap,
                          uint32_t *road_word, uint32_t *road_nhit, uint32_t *event_road,
-                         const svt_config cfg, uint32_t rows_per_item, uint32_t *road_items,
-                         uint32_t *tile_items, uint64_t *counts, unsigned long long *status,
-                         int grid, cudaStream_t st);
+                         const svt_config cfg, const FusedRoads fr, uint64_t *counts,
+                         unsigned long long *status, int grid, cudaStream_t st);
 // Per-event rules: offsets, V1, V10.
 void launch_unpack_events(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
                           uint64_t max_events, const uint32_t *event_road,
                           unsigned long long *status, int grid, cudaStream_t st);
 
 // ---- fused path (svt_fused.cu) -------------------------------------------------
-// K3: per-road item offsets (road_item_off[R] = total), road slots
-// (road_best = UINT64_MAX, road_pending = items), records of roads that are
-// not fitted; zeroes *item_counter.
-void launch_items(const uint32_t *words, const uint32_t *road_word, const uint32_t *road_nhit,
-                  uint64_t road_cap, const Dims *dims,
-                  uint64_t max_words, const uint32_t *tile_roads, const uint32_t *tile_items,
-                  const uint32_t *road_items, uint32_t *road_item_off,
-                  unsigned long long *road_best, uint32_t *road_pending, uint32_t *out,
-                  uint32_t *item_counter, unsigned long long *status, int grid,
-                  cudaStream_t st);
-cudaError_t launch_fit_persistent(const uint32_t *words, const uint32_t *road_word,
-                                  const uint32_t *road_nhit, const uint32_t *road_item_off,
-                                  const uint64_t *n_roads, uint64_t road_cap,
-                                  const uint64_t *total_items, const int16_t *F,
-                                  const int16_t *q, const svt_config cfg, uint32_t rows_per_item,
-                                  unsigned long long *road_best, uint32_t *road_pending,
-                                  uint32_t *out, uint32_t *item_counter, uint64_t *counts,
+// K3: list of split roads (big_road, big_item_off with the total at
+// [n_big], big_best = UINT64_MAX, big_pending = items) and reset of the two
+// work counters.
+struct BigList {
+    uint32_t *road;
+    uint32_t *item_off;
+    unsigned long long *best;
+    uint32_t *pending;
+    uint32_t *counters;        // [0] big items taken, [1] roads taken
+};
+void launch_big_list(const uint4 *desc, uint64_t road_cap, const Dims *dims, uint64_t max_words,
+                     const uint32_t *tile_roads, const uint32_t *tile_big,
+                     const uint32_t *tile_bigitems, const FusedRoads fr, BigList bl,
+                     unsigned long long *status, int grid, cudaStream_t st);
+// K4: the persistent fit over split-road items, then over chunks of roads.
+cudaError_t launch_fit_persistent(const uint32_t *words, const uint4 *desc, const uint64_t *counts,
+                                  uint64_t road_cap, const uint64_t *n_big,
+                                  const int16_t *F, const int16_t *q, const svt_config cfg,
+                                  const FusedRoads fr, uint32_t roads_per_chunk, BigList bl,
+                                  uint32_t *out, uint64_t *counts_out,
                                   unsigned long long *status, int warps_per_block, int grid,
                                   cudaStream_t st);
-// K4: the persistent fit; n_roads and total_items are device counters.
-int fit_persistent_blocks_per_sm(int warps_per_block, uint32_t rows_per_item);
+int fit_persistent_blocks_per_sm(int warps_per_block);
 size_t fit_smem_bytes(int warps_per_block);
 
 // ---- plain path (svt_plain.cu) --------------------------------------------------

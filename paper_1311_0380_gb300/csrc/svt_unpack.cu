@@ -138,31 +138,12 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
-// Work items of one road for the fused fit: rows of the (prefix x suffix)
-// grid, rows_per_item rows per item.
-__device__ __forceinline__ uint32_t road_items_of(uint32_t packed, const svt_config &cfg,
-                                                  uint32_t rows_per_item, uint32_t *n_eval_out) {
-    RoadShape s = road_shape(packed);
-    if (s.n_layers_hit < cfg.min_layers) {
-        *n_eval_out = 0;
-        return 0;
-    }
-    uint32_t C = (uint32_t)s.C;
-    uint32_t C_eval = C > cfg.max_comb ? cfg.max_comb : C;
-    uint32_t split, NB;
-    road_split(s, split, NB);
-    uint32_t NA = (C_eval + NB - 1) / NB;
-    *n_eval_out = C_eval;
-    return (NA + rows_per_item - 1) / rows_per_item;
-}
-
 __global__ void __launch_bounds__(TILE_THREADS)
     k_unpack_roads(const uint32_t *__restrict__ words, const uint64_t *__restrict__ event_off,
                    const Dims *__restrict__ dims, const uint32_t *__restrict__ tile_roads,
                    uint64_t road_cap, uint32_t *road_word, uint32_t *road_nhit,
-                   uint32_t *event_road, const svt_config cfg, uint32_t rows_per_item,
-                   uint32_t *road_items, uint32_t *tile_items, uint64_t *counts,
-                   unsigned long long *status) {
+                   uint32_t *event_road, const svt_config cfg, const FusedRoads fr,
+                   uint64_t *counts, unsigned long long *status) {
     __shared__ uint32_t red[TILE_THREADS / 32 + 1];
     __shared__ unsigned long long red64[TILE_THREADS / 32 + 1];
     __shared__ uint32_t pre[TILE_WORDS];
@@ -187,7 +168,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
         const uint32_t ex = block_exclusive_scan<uint32_t>(cnt, red, &total);
         const uint64_t tile_base = tile_roads[t];
         uint32_t run = ex;
-        uint32_t items_sum = 0;
+        uint32_t items_sum = 0, big_sum = 0;
         unsigned long long comb_sum = 0;
 #pragma unroll
         for (int j = 0; j < TILE_PER_THREAD; ++j) {
@@ -200,7 +181,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 report(status, i, SVT_ERR_OOM);
                 continue;
             }
-            road_word[r] = (uint32_t)i;
+            if (road_word) road_word[r] = (uint32_t)i;
             // walk the hit run that follows the header (rule V8 and hits per layer)
             unsigned long long cnt8 = 0;
             for (uint64_t k = i + 1; k < n_words; ++k) {
@@ -219,12 +200,13 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 uint32_t c = (uint32_t)(cnt8 >> (8 * l)) & 0xFFu;
                 packed |= (c > MAX_HITS ? (uint32_t)MAX_HITS : c) << (5 * l);
             }
-            road_nhit[r] = packed;
-            if (rows_per_item) {
-                uint32_t n_eval;
-                uint32_t it = road_items_of(packed, cfg, rows_per_item, &n_eval);
-                road_items[r] = it;
+            if (road_nhit) road_nhit[r] = packed;
+            if (fr.desc) {
+                const uint32_t n_eval = road_eval_count(packed, cfg);
+                const uint32_t it = road_big_items(packed, n_eval, fr);
+                fr.desc[r] = make_uint4((uint32_t)i, packed, w[j], n_eval);
                 items_sum += it;
+                big_sum += it ? 1u : 0u;
                 comb_sum += n_eval;
             }
         }
@@ -236,13 +218,15 @@ __global__ void __launch_bounds__(TILE_THREADS)
             if (s >= tile_start && s < tile_end)
                 event_road[e] = (uint32_t)(tile_base + pre[s - tile_start]);
         }
-        if (rows_per_item) {
-            uint32_t it_total;
+        if (fr.desc) {
+            uint32_t it_total, big_total;
             block_exclusive_scan<uint32_t>(items_sum, red, &it_total);
+            block_exclusive_scan<uint32_t>(big_sum, red, &big_total);
             unsigned long long c_total;
             block_exclusive_scan<unsigned long long>(comb_sum, red64, &c_total);
             if (threadIdx.x == 0) {
-                tile_items[t] = it_total;
+                fr.tile_bigitems[t] = it_total;
+                fr.tile_big[t] = big_total;
                 if (counts && c_total) atomicAdd((unsigned long long *)(counts + 2), c_total);
             }
         }
@@ -299,16 +283,14 @@ void launch_scan_tiles(uint32_t *a, const Dims *dims, const uint64_t *n_dev, uin
 void launch_unpack_roads(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
                          uint64_t max_words, const uint32_t *tile_roads, uint64_t road_cap,
                          uint32_t *road_word, uint32_t *road_nhit, uint32_t *event_road,
-                         const svt_config cfg, uint32_t rows_per_item, uint32_t *road_items,
-                         uint32_t *tile_items, uint64_t *counts, unsigned long long *status,
-                         int grid, cudaStream_t st) {
+                         const svt_config cfg, const FusedRoads fr, uint64_t *counts,
+                         unsigned long long *status, int grid, cudaStream_t st) {
     uint64_t T = n_tiles(max_words);
     int g = (int)(T < (uint64_t)grid ? T : (uint64_t)grid);
     if (g > 0)
         k_unpack_roads<<<g, TILE_THREADS, 0, st>>>(words, event_off, dims, tile_roads, road_cap,
-                                                   road_word, road_nhit, event_road, cfg,
-                                                   rows_per_item, road_items, tile_items, counts,
-                                                   status);
+                                                   road_word, road_nhit, event_road, cfg, fr,
+                                                   counts, status);
 }
 
 void launch_unpack_events(const uint32_t *words, const uint64_t *event_off, const Dims *dims,

@@ -88,7 +88,8 @@ def test_uneven_batch_capped():
     assert np.mean(rec[:, 0] >> 24 & oracle.F_OVERFLOW > 0) > 0.5
 
 
-@pytest.mark.parametrize("sched", [(1, 1, 1), (4, 3, 7), (16, 1, 64), (8, 4, 32), (2, 8, 2)])
+@pytest.mark.parametrize("sched", [(1, 1, 1, 1, 1), (4, 3, 7, 3, 100), (16, 1, 64, 32, 64),
+                                   (8, 4, 32, 8, 1 << 30), (2, 8, 2, 2, 33), (8, 0, 16, 4, 4096)])
 def test_schedules_give_identical_results(sched):
     from paper_1311_0380_gb300 import api
     spec, consts, b = batch_for("scaled", 60, consts_for(512))
@@ -189,6 +190,18 @@ def test_maximum_hits_per_layer(path):
         st, got, _ = gpu_run(w, off, F, q, cfg, path, comb_cap=6 * cap)
         assert_same(st, got, key, rec, f"cap{cap}")
         assert np.all(rec[:, 0] >> 24 & oracle.F_OVERFLOW)
+
+
+def test_uneven_batch_split_and_whole_agree():
+    from paper_1311_0380_gb300 import api
+    spec, consts, b = batch_for("uneven", 12, consts_for(512))
+    cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb)
+    key, rec = oracle_run(b.words, b.event_off, consts.F, consts.q, ocfg)
+    for small_max in (1, 500, 4096):
+        st, got, counts = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "fused",
+                                  sched=api.schedule(rows_per_item=8, small_max=small_max))
+        assert_same(st, got, key, rec, f"small_max{small_max}")
+        assert (counts[1] > 0) == (small_max < 4096)
 
 
 def test_uncapped_giant_road_fused():
