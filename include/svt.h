@@ -274,6 +274,60 @@ int svt_run(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_o
             uint64_t *d_status, void *d_workspace, size_t workspace_bytes,
             const svt_schedule *sched, svt_timer timer, void *stream);
 
+/* ======================================================================
+ * FP32 calibration relaxation.  The fit of Sec. 2 without the integer shift
+ * and clamp, per track t of sector s:
+ *     y_t = F[s] x_t + q[s]        (F: float [S][6][6], q: float [S][6])
+ *     L   = (1/N) sum_t [ sum_{k<3} w_k (y_tk - theta_tk)^2 + sum_{k>=3} y_tk^2 ]
+ * with hand-written forward and backward kernels, for calibrating fit
+ * constants on tracks whose true parameters theta are known.  Tracks are
+ * used in sector order: svt_calib_index sorts them (stable counting sort on
+ * the device) and svt_calib_gather permutes per-track arrays.  All sums run
+ * in a fixed order, so repeated calls give identical bits.
+ * Layouts: x float [N][6], theta float [N][3], w float [3], y float [N][6].
+ * ====================================================================== */
+
+/* Bytes of the sector index of n tracks in n_sectors sectors. */
+size_t svt_calib_index_size(uint64_t n_tracks, uint32_t n_sectors);
+
+/* Sector index: d_perm[i] = original index of the i-th track in sector order
+ * (stable).  d_status: reset, then (track << 8 | SVT_ERR_BAD_SECTOR) of the
+ * first track whose sector is outside [0, n_sectors).  n_tracks < 2^31,
+ * n_sectors <= 512. */
+int svt_calib_index(const int32_t *d_sector, uint64_t n_tracks, uint32_t n_sectors, void *d_index,
+                    size_t index_bytes, int32_t *d_perm, uint64_t *d_status, void *stream);
+
+/* d_dst[i][c] = d_src[d_perm[i]][c] for c < width. */
+int svt_calib_gather(const float *d_src, uint32_t width, const int32_t *d_perm, uint64_t n,
+                     float *d_dst, void *stream);
+
+/* Workspace bytes of the loss and backward calls. */
+size_t svt_calib_workspace_size(uint64_t n_tracks, uint32_t n_sectors);
+
+/* y = F[s] x + q[s] for sector-ordered tracks. */
+int svt_calib_forward(const float *d_x, uint64_t n_tracks, uint32_t n_sectors,
+                      const void *d_index, const float *d_F, const float *d_q, float *d_y,
+                      void *stream);
+
+/* d_loss[0] = L for sector-ordered tracks. */
+int svt_calib_loss(const float *d_x, const float *d_theta, const float *d_w, uint64_t n_tracks,
+                   uint32_t n_sectors, const void *d_index, const float *d_F, const float *d_q,
+                   float *d_loss, void *d_workspace, size_t workspace_bytes, void *stream);
+
+/* d_dF = g dL/dF, d_dq = g dL/dq with g = *d_grad_loss (NULL: g = 1). */
+int svt_calib_loss_backward(const float *d_x, const float *d_theta, const float *d_w,
+                            uint64_t n_tracks, uint32_t n_sectors, const void *d_index,
+                            const float *d_F, const float *d_q, const float *d_grad_loss,
+                            float *d_dF, float *d_dq, void *d_workspace, size_t workspace_bytes,
+                            void *stream);
+
+/* Backward of y = F[s] x + q[s] from d_grad_y [N][6]: d_dF[s] = sum_t g_t x_t^T,
+ * d_dq[s] = sum_t g_t and, when d_dx is not NULL, d_dx_t = F[s]^T g_t. */
+int svt_calib_backward(const float *d_x, const float *d_grad_y, uint64_t n_tracks,
+                       uint32_t n_sectors, const void *d_index, const float *d_F, float *d_dF,
+                       float *d_dq, float *d_dx, void *d_workspace, size_t workspace_bytes,
+                       void *stream);
+
 #ifdef __cplusplus
 }
 #endif

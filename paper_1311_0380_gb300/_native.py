@@ -70,6 +70,16 @@ SIGNATURES = {
     "svt_timer_create": (ctypes.c_int, [ctypes.POINTER(_vp)]),
     "svt_timer_destroy": (ctypes.c_int, [_vp]),
     "svt_timer_fit_ms": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)]),
+    "svt_calib_index_size": (_sz, [_u64, _u32]),
+    "svt_calib_index": (ctypes.c_int, [_vp, _u64, _u32, _vp, _sz, _vp, _vp, _vp]),
+    "svt_calib_gather": (ctypes.c_int, [_vp, _u32, _vp, _u64, _vp, _vp]),
+    "svt_calib_workspace_size": (_sz, [_u64, _u32]),
+    "svt_calib_forward": (ctypes.c_int, [_vp, _u64, _u32, _vp, _vp, _vp, _vp, _vp]),
+    "svt_calib_loss": (ctypes.c_int, [_vp, _vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "svt_calib_loss_backward": (ctypes.c_int, [_vp, _vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _vp,
+                                               _vp, _vp, _sz, _vp]),
+    "svt_calib_backward": (ctypes.c_int, [_vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
+                                          _vp]),
 }
 
 _lib = None

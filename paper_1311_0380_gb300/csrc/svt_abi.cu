@@ -121,6 +121,41 @@ RunWs carve_run(void *base, uint64_t max_words, uint64_t max_events, uint64_t ro
     return w;
 }
 
+// Sector index of the calibration tracks.
+struct CalibIndex {
+    uint32_t *counts;
+    int32_t *sector_off, *sector_item, *item_sector, *item_start, *n_items;
+    uint32_t max_items;
+    size_t bytes;
+};
+CalibIndex carve_calib_index(const void *base, uint64_t n, uint32_t S) {
+    Carver c(const_cast<void *>(base));
+    CalibIndex x;
+    x.max_items = calib_max_items(n, S);
+    x.counts = c.take<uint32_t>((size_t)S * calib_tiles(n) + 1);
+    x.sector_off = c.take<int32_t>(S + 1);
+    x.sector_item = c.take<int32_t>(S + 1);
+    x.item_sector = c.take<int32_t>(x.max_items);
+    x.item_start = c.take<int32_t>(x.max_items);
+    x.n_items = c.take<int32_t>(1);
+    x.bytes = c.size();
+    return x;
+}
+struct CalibWs {
+    float *item_loss, *item_grad;
+    size_t bytes;
+};
+CalibWs carve_calib_ws(void *base, uint64_t n, uint32_t S) {
+    Carver c(base);
+    CalibWs w;
+    const uint32_t mi = calib_max_items(n, S);
+    w.item_loss = c.take<float>(mi);
+    w.item_grad = c.take<float>((size_t)mi * 42);
+    w.bytes = c.size();
+    return w;
+}
+bool calib_sizes_ok(uint64_t n, uint32_t S) { return n < (1ull << 31) && S >= 1 && S <= 512; }
+
 }  // namespace
 
 struct svt_timer_s {
@@ -313,6 +348,108 @@ int svt_run(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_o
         if (cudaEventRecord(timer->end, st) != cudaSuccess) return SVT_ERR_CUDA;
         timer->recorded = true;
     }
+    return launch_status();
+}
+
+size_t svt_calib_index_size(uint64_t n_tracks, uint32_t n_sectors) {
+    return carve_calib_index(nullptr, n_tracks, n_sectors).bytes;
+}
+
+int svt_calib_index(const int32_t *d_sector, uint64_t n_tracks, uint32_t n_sectors, void *d_index,
+                    size_t index_bytes, int32_t *d_perm, uint64_t *d_status, void *stream) {
+    if (!calib_sizes_ok(n_tracks, n_sectors) || !d_index || !d_status) return SVT_ERR_BAD_ARG;
+    if (n_tracks > 0 && (!d_sector || !d_perm)) return SVT_ERR_BAD_ARG;
+    CalibIndex x = carve_calib_index(d_index, n_tracks, n_sectors);
+    if (index_bytes < x.bytes) return SVT_ERR_BAD_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *status = (unsigned long long *)d_status;
+    launch_set_dims(nullptr, 0, 0, status, nullptr, 0, st);
+    if (cudaMemsetAsync(x.sector_off, 0, sizeof(int32_t) * (n_sectors + 1), st) != cudaSuccess ||
+        cudaMemsetAsync(x.sector_item, 0, sizeof(int32_t) * (n_sectors + 1), st) != cudaSuccess ||
+        cudaMemsetAsync(x.n_items, 0, sizeof(int32_t), st) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    launch_calib_sort(d_sector, n_tracks, n_sectors, x.counts, d_perm, x.sector_off,
+                      x.sector_item, x.item_sector, x.item_start, x.n_items, status, tile_grid(),
+                      st);
+    return launch_status();
+}
+
+int svt_calib_gather(const float *d_src, uint32_t width, const int32_t *d_perm, uint64_t n,
+                     float *d_dst, void *stream) {
+    if (n == 0) return SVT_OK;
+    if (!d_src || !d_perm || !d_dst || width == 0 || width > 64 || n >= (1ull << 31))
+        return SVT_ERR_BAD_ARG;
+    launch_calib_gather(d_src, width, d_perm, n, d_dst, tile_grid(), (cudaStream_t)stream);
+    return launch_status();
+}
+
+size_t svt_calib_workspace_size(uint64_t n_tracks, uint32_t n_sectors) {
+    return carve_calib_ws(nullptr, n_tracks, n_sectors).bytes;
+}
+
+int svt_calib_forward(const float *d_x, uint64_t n_tracks, uint32_t n_sectors,
+                      const void *d_index, const float *d_F, const float *d_q, float *d_y,
+                      void *stream) {
+    if (!calib_sizes_ok(n_tracks, n_sectors) || !d_index || !d_F || !d_q) return SVT_ERR_BAD_ARG;
+    if (n_tracks == 0) return SVT_OK;
+    if (!d_x || !d_y || ((uintptr_t)d_x & 7u) || ((uintptr_t)d_y & 7u)) return SVT_ERR_BAD_ARG;
+    CalibIndex x = carve_calib_index(d_index, n_tracks, n_sectors);
+    launch_calib_forward(d_x, x.item_sector, x.item_start, x.sector_off, x.n_items, x.max_items,
+                         d_F, d_q, d_y, tile_grid(), (cudaStream_t)stream);
+    return launch_status();
+}
+
+int svt_calib_loss(const float *d_x, const float *d_theta, const float *d_w, uint64_t n_tracks,
+                   uint32_t n_sectors, const void *d_index, const float *d_F, const float *d_q,
+                   float *d_loss, void *d_workspace, size_t workspace_bytes, void *stream) {
+    if (!calib_sizes_ok(n_tracks, n_sectors) || !d_index || !d_F || !d_q || !d_w || !d_loss ||
+        !d_workspace)
+        return SVT_ERR_BAD_ARG;
+    if (n_tracks > 0 && (!d_x || !d_theta || ((uintptr_t)d_x & 7u))) return SVT_ERR_BAD_ARG;
+    CalibWs w = carve_calib_ws(d_workspace, n_tracks, n_sectors);
+    if (workspace_bytes < w.bytes) return SVT_ERR_BAD_ARG;
+    CalibIndex x = carve_calib_index(d_index, n_tracks, n_sectors);
+    launch_calib_loss(d_x, d_theta, x.item_sector, x.item_start, x.sector_off, x.n_items,
+                      x.max_items, n_tracks, d_F, d_q, d_w, w.item_loss, d_loss, tile_grid(),
+                      (cudaStream_t)stream);
+    return launch_status();
+}
+
+int svt_calib_loss_backward(const float *d_x, const float *d_theta, const float *d_w,
+                            uint64_t n_tracks, uint32_t n_sectors, const void *d_index,
+                            const float *d_F, const float *d_q, const float *d_grad_loss,
+                            float *d_dF, float *d_dq, void *d_workspace, size_t workspace_bytes,
+                            void *stream) {
+    if (!calib_sizes_ok(n_tracks, n_sectors) || !d_index || !d_F || !d_q || !d_w || !d_dF ||
+        !d_dq || !d_workspace)
+        return SVT_ERR_BAD_ARG;
+    if (n_tracks > 0 && (!d_x || !d_theta || ((uintptr_t)d_x & 7u))) return SVT_ERR_BAD_ARG;
+    CalibWs w = carve_calib_ws(d_workspace, n_tracks, n_sectors);
+    if (workspace_bytes < w.bytes) return SVT_ERR_BAD_ARG;
+    CalibIndex x = carve_calib_index(d_index, n_tracks, n_sectors);
+    const float scale = n_tracks ? 2.0f / (float)n_tracks : 0.f;
+    launch_calib_grad(0, d_x, d_theta, nullptr, x.item_sector, x.item_start, x.sector_off,
+                      x.sector_item, x.n_items, x.max_items, n_sectors, d_F, d_q, d_w, d_grad_loss, scale,
+                      w.item_grad, d_dF, d_dq, nullptr, tile_grid(), (cudaStream_t)stream);
+    return launch_status();
+}
+
+int svt_calib_backward(const float *d_x, const float *d_grad_y, uint64_t n_tracks,
+                       uint32_t n_sectors, const void *d_index, const float *d_F, float *d_dF,
+                       float *d_dq, float *d_dx, void *d_workspace, size_t workspace_bytes,
+                       void *stream) {
+    if (!calib_sizes_ok(n_tracks, n_sectors) || !d_index || !d_F || !d_dF || !d_dq ||
+        !d_workspace)
+        return SVT_ERR_BAD_ARG;
+    if (n_tracks > 0 && (!d_x || !d_grad_y || ((uintptr_t)d_x & 7u) || ((uintptr_t)d_grad_y & 7u) ||
+                         ((uintptr_t)d_dx & 7u)))
+        return SVT_ERR_BAD_ARG;
+    CalibWs w = carve_calib_ws(d_workspace, n_tracks, n_sectors);
+    if (workspace_bytes < w.bytes) return SVT_ERR_BAD_ARG;
+    CalibIndex x = carve_calib_index(d_index, n_tracks, n_sectors);
+    launch_calib_grad(1, d_x, nullptr, d_grad_y, x.item_sector, x.item_start, x.sector_off,
+                      x.sector_item, x.n_items, x.max_items, n_sectors, d_F, nullptr, nullptr, nullptr, 1.0f,
+                      w.item_grad, d_dF, d_dq, d_dx, tile_grid(), (cudaStream_t)stream);
     return launch_status();
 }
 

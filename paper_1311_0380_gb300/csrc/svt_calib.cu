@@ -104,8 +104,8 @@ __global__ void k_scatter(const int32_t *__restrict__ sector, uint64_t n, uint32
 // sector_off and the item table, one block
 __global__ void __launch_bounds__(1024)
     k_items(const uint32_t *__restrict__ base, uint32_t S, uint32_t T, uint64_t n,
-            int32_t *sector_off, int32_t *item_sector, int32_t *item_start, int32_t *n_items,
-            uint32_t max_items) {
+            int32_t *sector_off, int32_t *sector_item, int32_t *item_sector, int32_t *item_start,
+            int32_t *n_items, uint32_t max_items) {
     __shared__ uint32_t sm[33];
     __shared__ uint32_t carry_s;
     if (threadIdx.x == 0) carry_s = 0;
@@ -122,6 +122,7 @@ __global__ void __launch_bounds__(1024)
         const uint32_t items = (len + CALIB_CHUNK - 1) / CALIB_CHUNK;
         uint32_t tot;
         const uint32_t first = carry_s + block_exclusive_scan<uint32_t>(items, sm, &tot);
+        if (s < S) sector_item[s] = (int32_t)first;
         for (uint32_t k = 0; k < items; ++k) {
             if (first + k < max_items) {
                 item_sector[first + k] = (int32_t)s;
@@ -134,6 +135,7 @@ __global__ void __launch_bounds__(1024)
     }
     if (threadIdx.x == 0) {
         sector_off[S] = (int32_t)n;
+        sector_item[S] = (int32_t)carry_s;
         *n_items = (int32_t)carry_s;
     }
 }
@@ -330,26 +332,15 @@ __global__ void k_grad_items(const float *__restrict__ x, const float *__restric
 
 // per (sector, entry): sum of the sector's item partials in index order, scaled
 __global__ void k_grad_final(const float *__restrict__ item_grad,
-                             const int32_t *__restrict__ item_start,
-                             const int32_t *__restrict__ sector_off, uint32_t S,
+                             const int32_t *__restrict__ sector_item, uint32_t S,
                              const float *__restrict__ scale_dev, float scale, float *dF,
                              float *dq) {
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= S * NPAR) return;
     const uint32_t s = k / NPAR, j = k % NPAR;
-    // items of sector s are consecutive; the first is the one starting at sector_off[s]
-    const uint32_t off = (uint32_t)sector_off[s], end = (uint32_t)sector_off[s + 1];
+    const uint32_t first = (uint32_t)sector_item[s], last = (uint32_t)sector_item[s + 1];
     float total = 0.f;
-    if (end > off) {
-        // index of the sector's first item = number of items of earlier sectors
-        uint32_t first = 0;
-        for (uint32_t u = 0; u < s; ++u) {
-            const uint32_t len = (uint32_t)(sector_off[u + 1] - sector_off[u]);
-            first += (len + CALIB_CHUNK - 1) / CALIB_CHUNK;
-        }
-        const uint32_t items = (end - off + CALIB_CHUNK - 1) / CALIB_CHUNK;
-        for (uint32_t m = 0; m < items; ++m) total += item_grad[(size_t)(first + m) * NPAR + j];
-    }
+    for (uint32_t m = first; m < last; ++m) total += item_grad[(size_t)m * NPAR + j];
     const float sc = scale * (scale_dev ? *scale_dev : 1.f);
     if (j < 36)
         dF[(size_t)s * 36 + j] = total * sc;
@@ -366,17 +357,17 @@ uint32_t calib_max_items(uint64_t n, uint32_t S) {
 uint32_t calib_tiles(uint64_t n) { return (uint32_t)((n + SORT_TILE - 1) / SORT_TILE); }
 
 void launch_calib_sort(const int32_t *sector, uint64_t n, uint32_t S, uint32_t *counts,
-                       int32_t *perm, int32_t *sector_off, int32_t *item_sector,
-                       int32_t *item_start, int32_t *n_items, unsigned long long *status,
-                       int grid, cudaStream_t st) {
+                       int32_t *perm, int32_t *sector_off, int32_t *sector_item,
+                       int32_t *item_sector, int32_t *item_start, int32_t *n_items,
+                       unsigned long long *status, int grid, cudaStream_t st) {
     const uint32_t T = calib_tiles(n);
     const int g = (int)min((uint32_t)grid, max(T, 1u));
     if (T > 0) k_hist<<<g, 256, 0, st>>>(sector, n, S, T, counts, status);
     k_scan_counts<<<1, 1024, 0, st>>>(counts, (uint64_t)S * T);
     if (T > 0) k_scatter<<<g, 32, 0, st>>>(sector, n, S, T, counts, perm);
     if (T > 0)
-        k_items<<<1, 1024, 0, st>>>(counts, S, T, n, sector_off, item_sector, item_start, n_items,
-                                    calib_max_items(n, S));
+        k_items<<<1, 1024, 0, st>>>(counts, S, T, n, sector_off, sector_item, item_sector,
+                                    item_start, n_items, calib_max_items(n, S));
 }
 
 void launch_calib_gather(const float *src, uint32_t width, const int32_t *perm, uint64_t n,
@@ -404,10 +395,11 @@ void launch_calib_loss(const float *x, const float *theta, const int32_t *item_s
 
 void launch_calib_grad(int mode, const float *x, const float *theta, const float *grad_y,
                        const int32_t *item_sector, const int32_t *item_start,
-                       const int32_t *sector_off, const int32_t *n_items, uint32_t max_items,
-                       uint32_t S, const float *F, const float *q, const float *w,
-                       const float *scale_dev, float scale, float *item_grad, float *dF,
-                       float *dq, float *dx, int grid, cudaStream_t st) {
+                       const int32_t *sector_off, const int32_t *sector_item,
+                       const int32_t *n_items, uint32_t max_items, uint32_t S, const float *F,
+                       const float *q, const float *w, const float *scale_dev, float scale,
+                       float *item_grad, float *dF, float *dq, float *dx, int grid,
+                       cudaStream_t st) {
     const int g = (int)min((uint32_t)grid, (max_items + 7) / 8 + 1);
     if (mode == 0)
         k_grad_items<0><<<g, 256, 0, st>>>(x, theta, grad_y, item_sector, item_start, sector_off,
@@ -415,8 +407,8 @@ void launch_calib_grad(int mode, const float *x, const float *theta, const float
     else
         k_grad_items<1><<<g, 256, 0, st>>>(x, theta, grad_y, item_sector, item_start, sector_off,
                                           n_items, F, q, w, item_grad, dx);
-    k_grad_final<<<(S * NPAR + 255) / 256, 256, 0, st>>>(item_grad, item_start, sector_off, S,
-                                                        scale_dev, scale, dF, dq);
+    k_grad_final<<<(S * NPAR + 255) / 256, 256, 0, st>>>(item_grad, sector_item, S, scale_dev,
+                                                        scale, dF, dq);
 }
 
 }  // namespace svt

@@ -32,18 +32,19 @@ namespace {
 
 constexpr int ROWS_MAX = 64;
 
+// All accumulator terms are kept multiplied by 2^(32 - oshift): the high word
+// of a 64-bit sum of such terms is then exactly floor(sum / 2^oshift).
 struct WarpSmem {
-    int32_t T[N_LAYERS * MAX_HITS * 3];   // chi-row terms F[3+k][l] * x, [l][i][k]
+    long long T[N_LAYERS * MAX_HITS * 3]; // chi-row terms F[3+k][l] * x * 2^(32-oshift), [l][i][k]
+    longlong2 S[32][2];                   // suffix sums below the top suffix layer, [b'](3 rows)
+    longlong2 A[ROWS_MAX][2];             // prefix sums incl. q, per row: (A3, A4), (A5, -)
     int32_t cF[18];                       // F[3+k][l] at k*6+l
     int32_t cq[3];
     int32_t pad[3];
-    longlong2 A[ROWS_MAX][2];             // (A3, A4), (A5, -)
-};
-
-struct RoadCtx {
-    RoadShape s;
-    uint32_t split, NB, NA, C_eval;
-    SmallDiv dv[N_LAYERS];
+    SmallDiv dv[N_LAYERS];                // exact division by n'_l
+    uint32_t n[N_LAYERS];                 // n'_l = max(n_l, 1)
+    // road geometry (warp-uniform): c = a * NB + b, b = i_top * NBp + b'
+    uint32_t split, NB, NA, C_eval, NBp, d_hi, d_lo, total_hits;
 };
 
 // K3: the list of split roads
@@ -117,18 +118,39 @@ __device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
 
 __device__ __forceinline__ int32_t clamp_chi(int32_t y) { return max(min(y, 32767), -32767); }
 
-// Constants of the chi rows and per-hit terms of road D in the warp's slot.
+// Constants of the chi rows, per-hit terms and suffix table of road D in the
+// warp's slot.
 __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restrict__ words,
                                            const uint4 D, const int16_t *__restrict__ F,
-                                           const int16_t *__restrict__ q, RoadCtx &ctx, int lane) {
+                                           const int16_t *__restrict__ q, uint32_t sh, int lane) {
     const uint32_t packed = D.y;
-    ctx.s = road_shape(packed);
-    ctx.C_eval = D.w;
-    road_split(ctx.s, ctx.split, ctx.NB);
-    ctx.NA = (ctx.C_eval + ctx.NB - 1) / ctx.NB;
+    if (lane == 0) {
+        const RoadShape rs = road_shape(packed);
+        uint32_t split, NB;
+        road_split(rs, split, NB);
+        uint32_t ntop = 1;
 #pragma unroll
-    for (int l = 0; l < N_LAYERS; ++l) ctx.dv[l] = make_div(ctx.s.n[l]);
-    const size_t cs = (size_t)rd_sector(D.z) * 64 + ctx.s.mask;
+        for (int l = 0; l < N_LAYERS; ++l)
+            if ((uint32_t)l == split) ntop = rs.n[l];
+        const uint32_t NBp = NB / ntop;
+        sm.split = split;
+        sm.NB = NB;
+        sm.C_eval = D.w;
+        sm.NA = (D.w + NB - 1) / NB;
+        sm.NBp = NBp;
+        sm.d_hi = 32u / NBp;
+        sm.d_lo = 32u - (32u / NBp) * NBp;
+        sm.total_hits = rs.total_hits;
+    }
+    if (lane < N_LAYERS) {
+        const uint32_t nl = nhit_of(packed, lane);
+        sm.n[lane] = nl ? nl : 1u;
+        sm.dv[lane] = make_div(nl ? nl : 1u);
+    }
+    uint32_t mask = 0;
+#pragma unroll
+    for (int l = 0; l < N_LAYERS; ++l) mask |= nhit_of(packed, l) ? (1u << l) : 0u;
+    const size_t cs = (size_t)rd_sector(D.z) * 64 + mask;
     if (lane < 18) sm.cF[lane] = __ldg(F + cs * 36 + 18 + lane);
     else if (lane < 21) sm.cq[lane - 18] = __ldg(q + cs * 6 + 3 + (lane - 18));
     // layers without hits contribute x = 0
@@ -138,7 +160,8 @@ __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restr
         sm.T[(lane * MAX_HITS) * 3 + 2] = 0;
     }
     __syncwarp();
-    for (uint32_t h = lane; h < ctx.s.total_hits; h += 32) {
+    const uint32_t total_hits = sm.total_hits;
+    for (uint32_t h = lane; h < total_hits; h += 32) {
         const uint32_t x = __ldg(words + D.x + 1 + h);
         const uint32_t l = hit_layer(x);
         uint32_t i = h;
@@ -146,27 +169,48 @@ __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restr
         for (int ll = 0; ll < N_LAYERS; ++ll)
             if ((uint32_t)ll < l) i -= nhit_of(packed, ll);
         const int32_t xc = (int32_t)hit_coord(x);
-        int32_t *t = sm.T + (l * MAX_HITS + i) * 3;
-        t[0] = sm.cF[0 * 6 + l] * xc;
-        t[1] = sm.cF[1 * 6 + l] * xc;
-        t[2] = sm.cF[2 * 6 + l] * xc;
+        long long *t = sm.T + (l * MAX_HITS + i) * 3;
+        t[0] = (long long)(sm.cF[0 * 6 + l] * xc) << sh;
+        t[1] = (long long)(sm.cF[1 * 6 + l] * xc) << sh;
+        t[2] = (long long)(sm.cF[2 * 6 + l] * xc) << sh;
+    }
+    __syncwarp();
+    // S[b'] = sum over the suffix layers below the top one, b' < NBp (< 32)
+    const uint32_t split = sm.split;
+    if ((uint32_t)lane < sm.NBp) {
+        uint32_t rem = lane;
+        long long S3 = 0, S4 = 0, S5 = 0;
+#pragma unroll
+        for (int l = N_LAYERS - 1; l >= 1; --l) {
+            if ((uint32_t)l > split) {
+                const uint32_t qd = div_small(rem, sm.dv[l]);
+                const uint32_t i = rem - qd * sm.n[l];
+                rem = qd;
+                const long long *t = sm.T + (l * MAX_HITS + i) * 3;
+                S3 += t[0];
+                S4 += t[1];
+                S5 += t[2];
+            }
+        }
+        sm.S[lane][0] = make_longlong2(S3, S4);
+        sm.S[lane][1] = make_longlong2(S5, 0);
     }
     __syncwarp();
 }
 
-__device__ __forceinline__ void build_row(WarpSmem &sm, const RoadCtx &ctx, uint32_t a,
-                                          uint32_t slot, uint32_t qshift) {
+__device__ __forceinline__ void build_row(WarpSmem &sm, uint32_t split, uint32_t a,
+                                          uint32_t slot, uint32_t qsh) {
     uint32_t rem = a;
-    long long A3 = (long long)sm.cq[0] * (1ll << qshift);
-    long long A4 = (long long)sm.cq[1] * (1ll << qshift);
-    long long A5 = (long long)sm.cq[2] * (1ll << qshift);
+    long long A3 = (long long)sm.cq[0] << qsh;
+    long long A4 = (long long)sm.cq[1] << qsh;
+    long long A5 = (long long)sm.cq[2] << qsh;
 #pragma unroll
     for (int l = N_LAYERS - 1; l >= 0; --l) {
-        if ((uint32_t)l < ctx.split) {
-            const uint32_t qd = div_small(rem, ctx.dv[l]);
-            const uint32_t i = rem - qd * ctx.s.n[l];
+        if ((uint32_t)l < split) {
+            const uint32_t qd = div_small(rem, sm.dv[l]);
+            const uint32_t i = rem - qd * sm.n[l];
             rem = qd;
-            const int32_t *t = sm.T + (l * MAX_HITS + i) * 3;
+            const long long *t = sm.T + (l * MAX_HITS + i) * 3;
             A3 += t[0];
             A4 += t[1];
             A5 += t[2];
@@ -176,59 +220,74 @@ __device__ __forceinline__ void build_row(WarpSmem &sm, const RoadCtx &ctx, uint
     sm.A[slot][1] = make_longlong2(A5, 0);
 }
 
-// Best (chi2 << 32 | c) over rows [a_lo, a_hi) of the road, reduced over the warp.
-__device__ unsigned long long eval_rows(WarpSmem &sm, const RoadCtx &ctx, uint32_t a_lo,
-                                        uint32_t a_hi, uint32_t os, uint32_t qshift,
-                                        uint32_t init_chi, int lane) {
+__device__ __forceinline__ int32_t hi_word(long long v) {
+    return (int32_t)((unsigned long long)v >> 32);
+}
+
+// Best (chi2 << 32 | c) over rows [a_lo, a_hi) of the road, reduced over the
+// warp.  NOCLAMP (valid when chi2_cut < 32767^2): the squares are summed
+// unclamped in 64 bits; any combination with a chi component of magnitude
+// 32767 or more then exceeds the cut under both readings, and below that the
+// clamp is the identity, so pass/fail, chi2 of passing combinations and the
+// argmin are unchanged.
+template <bool NOCLAMP>
+__device__ __forceinline__ unsigned long long eval_rows(WarpSmem &sm, uint32_t a_lo,
+                                                        uint32_t a_hi, uint32_t qsh,
+                                                        uint32_t init_chi, int lane) {
     unsigned long long best = ~0ull;
-    const uint32_t NB = ctx.NB, NA = ctx.NA, C_eval = ctx.C_eval;
+    const uint32_t NB = sm.NB, NA = sm.NA, C_eval = sm.C_eval, NBp = sm.NBp;
+    const uint32_t top = sm.split, d_lo = sm.d_lo, d_hi = sm.d_hi;
+    const uint32_t is0 = (uint32_t)lane / NBp, bp0 = (uint32_t)lane - is0 * NBp;
     for (uint32_t ac = a_lo; ac < a_hi; ac += ROWS_MAX) {
         const uint32_t ae = min(ac + (uint32_t)ROWS_MAX, a_hi);
-        if (ac + lane < ae) build_row(sm, ctx, ac + lane, lane, qshift);
-        if (ac + lane + 32 < ae) build_row(sm, ctx, ac + lane + 32, lane + 32, qshift);
+        if (ac + lane < ae) build_row(sm, top, ac + lane, lane, qsh);
+        if (ac + lane + 32 < ae) build_row(sm, top, ac + lane + 32, lane + 32, qsh);
         __syncwarp();
+        uint32_t is = is0, bp = bp0;   // column b = is * NBp + bp
         for (uint32_t b0 = 0; b0 < NB; b0 += 32) {
-            const uint32_t b = b0 + lane;
-            long long B3 = 0, B4 = 0, B5 = 0;
-            {
-                uint32_t rem = b;
-#pragma unroll
-                for (int l = N_LAYERS - 1; l >= 0; --l) {
-                    if ((uint32_t)l >= ctx.split) {
-                        const uint32_t qd = div_small(rem, ctx.dv[l]);
-                        const uint32_t i = rem - qd * ctx.s.n[l];
-                        rem = qd;
-                        const int32_t *t = sm.T + (l * MAX_HITS + i) * 3;
-                        B3 += t[0];
-                        B4 += t[1];
-                        B5 += t[2];
+            const uint32_t b = b0 + (uint32_t)lane;
+            if (b < NB) {
+                const long long *t = sm.T + (top * MAX_HITS + is) * 3;
+                const longlong2 s01 = sm.S[bp][0], s2 = sm.S[bp][1];
+                const long long B3 = t[0] + s01.x, B4 = t[1] + s01.y, B5 = t[2] + s2.x;
+                uint32_t a_end = ae;
+                if (ae == NA && (NA - 1) * NB + b >= C_eval) a_end = ae - 1;
+                uint32_t bchi = init_chi, ba = 0;
+                const longlong2 *Ap = &sm.A[0][0];
+#pragma unroll 4
+                for (uint32_t a = ac; a < a_end; ++a, Ap += 2) {
+                    const longlong2 v01 = Ap[0];
+                    const longlong2 v2 = Ap[1];
+                    const int32_t y3 = hi_word(v01.x + B3);
+                    const int32_t y4 = hi_word(v01.y + B4);
+                    const int32_t y5 = hi_word(v2.x + B5);
+                    if (NOCLAMP) {
+                        unsigned long long v = (unsigned long long)((long long)y3 * y3);
+                        v += (unsigned long long)((long long)y4 * y4);
+                        v += (unsigned long long)((long long)y5 * y5);
+                        if (v < (unsigned long long)bchi) {
+                            bchi = (uint32_t)v;
+                            ba = a;
+                        }
+                    } else {
+                        const int32_t c3 = clamp_chi(y3), c4 = clamp_chi(y4), c5 = clamp_chi(y5);
+                        const uint32_t chi2 = (uint32_t)(c3 * c3) + (uint32_t)(c4 * c4) + (uint32_t)(c5 * c5);
+                        if (chi2 < bchi) {
+                            bchi = chi2;
+                            ba = a;
+                        }
                     }
                 }
-            }
-            uint32_t a_end = ae;
-            if (b >= NB)
-                a_end = ac;
-            else if (ae == NA && (NA - 1) * NB + b >= C_eval)
-                a_end = ae - 1;
-            uint32_t bchi = init_chi, bc = 0;
-            uint32_t c = ac * NB + b;
-            const longlong2 *Ap = &sm.A[0][0];
-            for (uint32_t a = ac; a < a_end; ++a, c += NB, Ap += 2) {
-                const longlong2 v01 = Ap[0];
-                const longlong2 v2 = Ap[1];
-                const long long s3 = v01.x + B3, s4 = v01.y + B4, s5 = v2.x + B5;
-                const int32_t y3 = clamp_chi((int32_t)__funnelshift_r((uint32_t)s3, (uint32_t)(s3 >> 32), os));
-                const int32_t y4 = clamp_chi((int32_t)__funnelshift_r((uint32_t)s4, (uint32_t)(s4 >> 32), os));
-                const int32_t y5 = clamp_chi((int32_t)__funnelshift_r((uint32_t)s5, (uint32_t)(s5 >> 32), os));
-                const uint32_t chi2 = (uint32_t)(y3 * y3) + (uint32_t)(y4 * y4) + (uint32_t)(y5 * y5);
-                if (chi2 < bchi) {
-                    bchi = chi2;
-                    bc = c;
+                if (bchi != init_chi) {
+                    const unsigned long long key = ((unsigned long long)bchi << 32) | (ba * NB + b);
+                    best = key < best ? key : best;
                 }
             }
-            if (bchi != init_chi) {
-                const unsigned long long key = ((unsigned long long)bchi << 32) | bc;
-                best = key < best ? key : best;
+            bp += d_lo;
+            is += d_hi;
+            if (bp >= NBp) {
+                bp -= NBp;
+                is += 1;
             }
         }
         __syncwarp();
@@ -237,7 +296,7 @@ __device__ unsigned long long eval_rows(WarpSmem &sm, const RoadCtx &ctx, uint32
 }
 
 // Record of a road from its best key (all lanes call; lanes 0..2 recompute p).
-__device__ void format_road(const uint32_t *__restrict__ words, const uint4 D,
+__device__ __forceinline__ void format_road(const uint32_t *__restrict__ words, const uint4 D,
                             const int16_t *__restrict__ F, const int16_t *__restrict__ q,
                             const svt_config &cfg, unsigned long long best, uint32_t *o,
                             uint64_t *counts, int lane) {
@@ -287,7 +346,8 @@ __device__ void format_road(const uint32_t *__restrict__ words, const uint4 D,
 }
 
 // K4: persistent fit / cut / select / format
-__global__ void k_fit_persistent(const uint32_t *__restrict__ words,
+template <bool NOCLAMP>
+__global__ void __launch_bounds__(256, 4) k_fit_persistent(const uint32_t *__restrict__ words,
                                  const uint4 *__restrict__ desc,
                                  const uint64_t *__restrict__ counts_in, uint64_t road_cap,
                                  const uint64_t *__restrict__ n_big_p,
@@ -306,9 +366,8 @@ __global__ void k_fit_persistent(const uint32_t *__restrict__ words,
     if (n_items64 > 0xFFFFFFFFull) return;
     const uint32_t n_items = (uint32_t)n_items64;
     const uint32_t n_big = (uint32_t)*n_big_p;
-    const uint32_t os = cfg.oshift, qs = cfg.qshift;
+    const uint32_t sh = 32u - cfg.oshift, qsh = cfg.qshift + sh;
     const uint32_t init_chi = cfg.chi2_cut == 0xFFFFFFFFu ? 0xFFFFFFFFu : cfg.chi2_cut + 1u;
-    RoadCtx ctx;
 
     // phase 1: items of split roads
     for (;;) {
@@ -320,10 +379,10 @@ __global__ void k_fit_persistent(const uint32_t *__restrict__ words,
         const uint32_t r = __ldg(bl.road + j);
         const uint32_t k = it - __ldg(bl.item_off + j);
         const uint4 D = __ldg(desc + r);
-        road_setup(sm, words, D, F, q, ctx, lane);
+        road_setup(sm, words, D, F, q, sh, lane);
         const uint32_t a_lo = k * fr.rows;
-        const uint32_t a_hi = min(a_lo + fr.rows, ctx.NA);
-        const unsigned long long best = eval_rows(sm, ctx, a_lo, a_hi, os, qs, init_chi, lane);
+        const uint32_t a_hi = min(a_lo + fr.rows, sm.NA);
+        const unsigned long long best = eval_rows<NOCLAMP>(sm, a_lo, a_hi, qsh, init_chi, lane);
         uint32_t last = 0;
         if (lane == 0) {
             if (best != ~0ull) atomicMin(bl.best + j, best);
@@ -357,8 +416,8 @@ __global__ void k_fit_persistent(const uint32_t *__restrict__ words,
             if (D.w > fr.small_max) continue;   // split road: done in phase 1
             unsigned long long best = ~0ull;
             if (D.w > 0) {
-                road_setup(sm, words, D, F, q, ctx, lane);
-                best = eval_rows(sm, ctx, 0, ctx.NA, os, qs, init_chi, lane);
+                road_setup(sm, words, D, F, q, sh, lane);
+                best = eval_rows<NOCLAMP>(sm, 0, sm.NA, qsh, init_chi, lane);
             }
             format_road(words, D, F, q, cfg, best, out + (size_t)(c0 + jj) * 6, counts, lane);
             __syncwarp();
@@ -382,13 +441,16 @@ void launch_big_list(const uint4 *desc, uint64_t road_cap, const Dims *dims, uin
 size_t fit_smem_bytes(int warps_per_block) { return sizeof(WarpSmem) * (size_t)warps_per_block; }
 
 int fit_persistent_blocks_per_sm(int warps_per_block) {
-    int n = 0;
+    int n = 0, n2 = 0;
     size_t smem = fit_smem_bytes(warps_per_block);
-    cudaFuncSetAttribute(k_fit_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit_persistent, warps_per_block * 32,
-                                                      smem) != cudaSuccess)
+    cudaFuncSetAttribute(k_fit_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_fit_persistent<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit_persistent<true>, warps_per_block * 32,
+                                                      smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_fit_persistent<false>,
+                                                      warps_per_block * 32, smem) != cudaSuccess)
         return 0;
-    return n;
+    return n < n2 ? n : n2;
 }
 
 cudaError_t launch_fit_persistent(const uint32_t *words, const uint4 *desc, const uint64_t *counts,
@@ -398,9 +460,14 @@ cudaError_t launch_fit_persistent(const uint32_t *words, const uint4 *desc, cons
                                   uint64_t *counts_out, unsigned long long *status,
                                   int warps_per_block, int grid, cudaStream_t st) {
     size_t smem = fit_smem_bytes(warps_per_block);
-    k_fit_persistent<<<grid, warps_per_block * 32, smem, st>>>(
-        words, desc, counts, road_cap, n_big, F, q, cfg, fr, roads_per_chunk, bl, out, counts_out,
-        status);
+    if (cfg.chi2_cut < 32767u * 32767u)
+        k_fit_persistent<true><<<grid, warps_per_block * 32, smem, st>>>(
+            words, desc, counts, road_cap, n_big, F, q, cfg, fr, roads_per_chunk, bl, out,
+            counts_out, status);
+    else
+        k_fit_persistent<false><<<grid, warps_per_block * 32, smem, st>>>(
+            words, desc, counts, road_cap, n_big, F, q, cfg, fr, roads_per_chunk, bl, out,
+            counts_out, status);
     return cudaGetLastError();
 }
 

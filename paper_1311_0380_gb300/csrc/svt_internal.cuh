@@ -131,14 +131,16 @@ __device__ __forceinline__ RoadShape road_shape(uint32_t packed) {
 // row; roads with fewer than 32 combinations put everything in the suffix.
 __device__ __forceinline__ void road_split(const RoadShape &s, uint32_t &split, uint32_t &NB) {
     uint32_t nb = 1;
+    bool found = false;
     split = 0;
     NB = (uint32_t)s.C;
+#pragma unroll
     for (int l = N_LAYERS - 1; l >= 0; --l) {
         nb *= s.n[l];
-        if (nb >= 32) {
+        if (!found && nb >= 32) {
             split = (uint32_t)l;
             NB = nb;
-            return;
+            found = true;
         }
     }
 }

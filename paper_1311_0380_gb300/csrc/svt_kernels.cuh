@@ -120,6 +120,31 @@ void launch_format(const svt_best *best, const uint32_t *words, const uint32_t *
                    const uint64_t *n_roads, uint64_t road_cap, uint32_t *out,
                    const unsigned long long *status, int grid, cudaStream_t st);
 
+// ---- calibration (svt_calib.cu) ------------------------------------------------
+uint32_t calib_max_items(uint64_t n, uint32_t S);
+uint32_t calib_tiles(uint64_t n);
+void launch_calib_sort(const int32_t *sector, uint64_t n, uint32_t S, uint32_t *counts,
+                       int32_t *perm, int32_t *sector_off, int32_t *sector_item,
+                       int32_t *item_sector, int32_t *item_start, int32_t *n_items,
+                       unsigned long long *status, int grid, cudaStream_t st);
+void launch_calib_gather(const float *src, uint32_t width, const int32_t *perm, uint64_t n,
+                         float *dst, int grid, cudaStream_t st);
+void launch_calib_forward(const float *x, const int32_t *item_sector, const int32_t *item_start,
+                          const int32_t *sector_off, const int32_t *n_items, uint32_t max_items,
+                          const float *F, const float *q, float *y, int grid, cudaStream_t st);
+void launch_calib_loss(const float *x, const float *theta, const int32_t *item_sector,
+                       const int32_t *item_start, const int32_t *sector_off,
+                       const int32_t *n_items, uint32_t max_items, uint64_t n, const float *F,
+                       const float *q, const float *w, float *item_loss, float *loss, int grid,
+                       cudaStream_t st);
+void launch_calib_grad(int mode, const float *x, const float *theta, const float *grad_y,
+                       const int32_t *item_sector, const int32_t *item_start,
+                       const int32_t *sector_off, const int32_t *sector_item,
+                       const int32_t *n_items, uint32_t max_items, uint32_t S, const float *F,
+                       const float *q, const float *w, const float *scale_dev, float scale,
+                       float *item_grad, float *dF, float *dq, float *dx, int grid,
+                       cudaStream_t st);
+
 // shared by both paths
 void launch_set_dims(Dims *dims, uint64_t n_words, uint64_t n_events,
                      unsigned long long *status, uint64_t *counts, int n_counts, cudaStream_t st);

@@ -1,0 +1,140 @@
+"""FP32 calibration kernels (forward, loss, hand-written backward) against the
+FP64 CPU reference in oracle/calib.py: analytic gradient and central finite
+differences, relative error 1e-4; the integer table is not involved."""
+import numpy as np
+import pytest
+
+from oracle import calib as ref
+from paper_1311_0380_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def make(n, S, seed):
+    consts = synth.make_constants(S)
+    return synth.make_calib(n, consts, seed=seed)
+
+
+def rel_err(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def check_grad(dF, dq, rF, rq):
+    assert rel_err(dF, rF) <= REL, rel_err(dF, rF)
+    assert rel_err(dq, rq) <= REL, rel_err(dq, rq)
+    for got, want in ((dF, rF), (dq, rq)):
+        big = np.abs(want) > 1e-3 * np.abs(want).max()
+        err = np.abs(got[big] - want[big]) / np.abs(want[big])
+        assert err.max() <= REL, err.max()
+
+
+@pytest.mark.parametrize("n,S", [(2000, 4), (20000, 64), (1 << 20, 512)])
+def test_loss_and_gradient_match_fp64(n, S):
+    import torch
+    from paper_1311_0380_gb300 import calib
+    cs = make(n, S, seed=n + S)
+    data = calib.CalibData(cs.x, cs.sector, cs.theta, S, cs.weight)
+    F = torch.tensor(cs.F0, device="cuda", requires_grad=True)
+    q = torch.tensor(cs.q0, device="cuda", requires_grad=True)
+    loss = calib.calib_loss(F, q, data)
+    loss.backward()
+    L64 = ref.loss(cs.x, cs.sector, cs.theta, cs.weight, cs.F0, cs.q0)
+    assert abs(loss.item() - L64) <= REL * abs(L64)
+    rF, rq = ref.grad(cs.x, cs.sector, cs.theta, cs.weight, cs.F0, cs.q0)
+    check_grad(F.grad.cpu().numpy(), q.grad.cpu().numpy(), rF, rq)
+
+
+def test_gradient_matches_fp64_finite_differences():
+    import torch
+    from paper_1311_0380_gb300 import calib
+    S = 4
+    cs = make(4000, S, seed=5)
+    data = calib.CalibData(cs.x, cs.sector, cs.theta, S, cs.weight)
+    F = torch.tensor(cs.F0, device="cuda", requires_grad=True)
+    q = torch.tensor(cs.q0, device="cuda", requires_grad=True)
+    calib.calib_loss(F, q, data).backward()
+    rng = np.random.default_rng(1)
+    entries = [("F", *map(int, rng.integers(0, [S, 6, 6]))) for _ in range(40)]
+    entries += [("q", *map(int, rng.integers(0, [S, 6]))) for _ in range(16)]
+    fd = ref.fd_grad(cs.x, cs.sector, cs.theta, cs.weight, cs.F0, cs.q0, entries)
+    gF, gq = F.grad.cpu().numpy(), q.grad.cpu().numpy()
+    got = np.array([gF[e[1:]] if e[0] == "F" else gq[e[1:]] for e in entries])
+    scale = np.abs(fd).max()
+    big = np.abs(fd) > 1e-3 * scale
+    assert np.max(np.abs(got[big] - fd[big]) / np.abs(fd[big])) <= REL
+
+
+def test_forward_and_general_backward():
+    import torch
+    from paper_1311_0380_gb300 import calib
+    S = 16
+    cs = make(30000, S, seed=7)
+    data = calib.CalibData(cs.x, cs.sector, cs.theta, S, cs.weight)
+    perm = data.perm.cpu().numpy()
+    F = torch.tensor(cs.F0, device="cuda", requires_grad=True)
+    q = torch.tensor(cs.q0, device="cuda", requires_grad=True)
+    y = calib.fit_fp32(F, q, data)
+    y64 = ref.forward(cs.x, cs.sector, cs.F0, cs.q0)[perm]
+    scale = np.abs(cs.F0).sum(axis=2).max() * 32768
+    assert np.max(np.abs(y.detach().cpu().numpy() - y64)) <= 1e-6 * scale
+    # sorted order really is by sector, stable
+    s_sorted = cs.sector[perm]
+    assert np.all(np.diff(s_sorted) >= 0)
+    for s in range(S):
+        idx = perm[s_sorted == s]
+        assert np.all(np.diff(idx) > 0)
+    gy = torch.randn_like(y)
+    (y * gy).sum().backward()
+    g = gy.cpu().numpy().astype(np.float64)
+    x = cs.x[perm].astype(np.float64)
+    rF = np.zeros((S, 6, 6))
+    rq = np.zeros((S, 6))
+    np.add.at(rF, s_sorted, g[:, :, None] * x[:, None, :])
+    np.add.at(rq, s_sorted, g)
+    check_grad(F.grad.cpu().numpy(), q.grad.cpu().numpy(), rF, rq)
+
+
+def test_results_are_bitwise_reproducible():
+    import torch
+    from paper_1311_0380_gb300 import calib
+    S = 32
+    cs = make(50000, S, seed=9)
+    out = []
+    for _ in range(2):
+        data = calib.CalibData(cs.x, cs.sector, cs.theta, S, cs.weight)
+        F = torch.tensor(cs.F0, device="cuda", requires_grad=True)
+        q = torch.tensor(cs.q0, device="cuda", requires_grad=True)
+        loss = calib.calib_loss(F, q, data)
+        loss.backward()
+        out.append((loss.item(), F.grad.cpu().numpy().copy(), q.grad.cpu().numpy().copy()))
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
+
+
+def test_calibration_descent_reduces_loss():
+    import torch
+    from paper_1311_0380_gb300 import calib
+    S = 8
+    cs = make(40000, S, seed=11)
+    data = calib.CalibData(cs.x, cs.sector, cs.theta, S, cs.weight)
+    F = torch.tensor(cs.F0, device="cuda", requires_grad=True)
+    q = torch.tensor(cs.q0, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([F, q], lr=1e-4)
+    first = None
+    for _ in range(60):
+        opt.zero_grad()
+        loss = calib.calib_loss(F, q, data)
+        if first is None:
+            first = loss.item()
+        loss.backward()
+        opt.step()
+    assert calib.calib_loss(F, q, data).item() < 0.7 * first
