@@ -274,6 +274,35 @@ int svt_run(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_o
             uint64_t *d_status, void *d_workspace, size_t workspace_bytes,
             const svt_schedule *sched, svt_timer timer, void *stream);
 
+/*
+ * svt_run_sized -- svt_run with the batch sizes read on the device:
+ * d_sizes[2] = {n_words, n_events} (device memory), at most max_words /
+ * max_events, the capacities every buffer and the workspace are sized for
+ * (svt_run_workspace_size(max_words, max_events, road_cap, sched)).  Sizes
+ * above the capacities give status (0 << 8 | SVT_ERR_BAD_ARG) and no work.
+ * This is the form a CUDA graph captures once and replays for every batch.
+ */
+int svt_run_sized(const uint32_t *d_words, uint64_t max_words, const uint64_t *d_event_off,
+                  uint64_t max_events, const uint64_t *d_sizes, const int16_t *d_F,
+                  const int16_t *d_q, const svt_config *cfg, uint64_t road_cap, uint32_t *d_out,
+                  uint32_t *d_event_road, uint64_t *d_counts, uint64_t *d_status,
+                  void *d_workspace, size_t workspace_bytes, const svt_schedule *sched,
+                  void *stream);
+
+/* CUDA graph of svt_run_sized's launch sequence, captured once on a private
+ * stream (same arguments).  svt_graph_launch replays it on `stream`; every
+ * replay reads the then-current device contents of d_sizes, d_words and
+ * d_event_off.  create/destroy allocate and free the graph objects. */
+typedef struct svt_graph_s *svt_graph;
+int svt_graph_create(const uint32_t *d_words, uint64_t max_words, const uint64_t *d_event_off,
+                     uint64_t max_events, const uint64_t *d_sizes, const int16_t *d_F,
+                     const int16_t *d_q, const svt_config *cfg, uint64_t road_cap,
+                     uint32_t *d_out, uint32_t *d_event_road, uint64_t *d_counts,
+                     uint64_t *d_status, void *d_workspace, size_t workspace_bytes,
+                     const svt_schedule *sched, svt_graph *out);
+int svt_graph_launch(svt_graph graph, void *stream);
+int svt_graph_destroy(svt_graph graph);
+
 /* ======================================================================
  * FP32 calibration relaxation.  The fit of Sec. 2 without the integer shift
  * and clamp, per track t of sector s:

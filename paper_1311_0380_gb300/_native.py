@@ -67,6 +67,12 @@ SIGNATURES = {
     "svt_run_workspace_size": (_sz, [_u64, _u64, _u64, _schp]),
     "svt_run": (ctypes.c_int, [_vp, _u64, _vp, _u64, _vp, _vp, _cfgp, _u64, _vp, _vp, _vp, _vp,
                                _vp, _sz, _schp, _vp, _vp]),
+    "svt_run_sized": (ctypes.c_int, [_vp, _u64, _vp, _u64, _vp, _vp, _vp, _cfgp, _u64, _vp, _vp,
+                                     _vp, _vp, _vp, _sz, _schp, _vp]),
+    "svt_graph_create": (ctypes.c_int, [_vp, _u64, _vp, _u64, _vp, _vp, _vp, _cfgp, _u64, _vp,
+                                        _vp, _vp, _vp, _vp, _sz, _schp, ctypes.POINTER(_vp)]),
+    "svt_graph_launch": (ctypes.c_int, [_vp, _vp]),
+    "svt_graph_destroy": (ctypes.c_int, [_vp]),
     "svt_timer_create": (ctypes.c_int, [ctypes.POINTER(_vp)]),
     "svt_timer_destroy": (ctypes.c_int, [_vp]),
     "svt_timer_fit_ms": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)]),

@@ -299,11 +299,18 @@ size_t svt_run_workspace_size(uint64_t max_words, uint64_t max_events, uint64_t 
     return carve_run(nullptr, max_words, max_events, road_cap).bytes;
 }
 
-int svt_run(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_off,
-            uint64_t n_events, const int16_t *d_F, const int16_t *d_q, const svt_config *cfg,
-            uint64_t road_cap, uint32_t *d_out, uint32_t *d_event_road, uint64_t *d_counts,
-            uint64_t *d_status, void *d_workspace, size_t workspace_bytes,
-            const svt_schedule *sched, svt_timer timer, void *stream) {
+}  // extern "C"
+
+namespace {
+
+// The fused launch sequence.  With d_sizes the batch sizes are read on the
+// device (capacities n_words / n_events), which lets one captured graph serve
+// batches of any size up to its capacities.
+int run_impl(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_off,
+             uint64_t n_events, const uint64_t *d_sizes, const int16_t *d_F, const int16_t *d_q,
+             const svt_config *cfg, uint64_t road_cap, uint32_t *d_out, uint32_t *d_event_road,
+             uint64_t *d_counts, uint64_t *d_status, void *d_workspace, size_t workspace_bytes,
+             const svt_schedule *sched, svt_timer timer, cudaStream_t st) {
     if (!config_ok(cfg)) return SVT_ERR_BAD_CONFIG;
     const svt_schedule sc = resolve(sched);
     if (!schedule_ok(sc)) return SVT_ERR_BAD_ARG;
@@ -315,7 +322,6 @@ int svt_run(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_o
     if ((uintptr_t)d_workspace & 255u) return SVT_ERR_BAD_ARG;
     RunWs w = carve_run(d_workspace, n_words, n_events, road_cap);
     if (workspace_bytes < w.bytes) return SVT_ERR_BAD_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
     unsigned long long *status = (unsigned long long *)d_status;
     uint64_t *counts = d_counts ? d_counts : w.counts;
     uint32_t *event_road = d_event_road ? d_event_road : w.event_road;
@@ -328,7 +334,7 @@ int svt_run(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_o
     const FusedRoads fr{w.desc, w.tile_big, w.tile_bigitems, sc.rows_per_item, sc.small_max};
     const BigList bl{w.big_road, w.big_item_off, w.big_best, w.big_pending, w.counters};
 
-    launch_set_dims(w.dims, n_words, n_events, status, counts, 4, st);
+    launch_set_dims(w.dims, n_words, n_events, status, counts, 4, st, d_sizes);
     launch_unpack_count(d_words, d_event_off, w.dims, n_words, cfg->n_sectors, w.tile_roads, status,
                         grid, st);
     launch_scan_tiles(w.tile_roads, w.dims, nullptr, counts + 0, event_road, status, st);
@@ -349,6 +355,86 @@ int svt_run(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_o
         timer->recorded = true;
     }
     return launch_status();
+}
+
+}  // namespace
+
+struct svt_graph_s {
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+};
+
+extern "C" {
+
+int svt_run(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_off,
+            uint64_t n_events, const int16_t *d_F, const int16_t *d_q, const svt_config *cfg,
+            uint64_t road_cap, uint32_t *d_out, uint32_t *d_event_road, uint64_t *d_counts,
+            uint64_t *d_status, void *d_workspace, size_t workspace_bytes,
+            const svt_schedule *sched, svt_timer timer, void *stream) {
+    return run_impl(d_words, n_words, d_event_off, n_events, nullptr, d_F, d_q, cfg, road_cap,
+                    d_out, d_event_road, d_counts, d_status, d_workspace, workspace_bytes, sched,
+                    timer, (cudaStream_t)stream);
+}
+
+int svt_run_sized(const uint32_t *d_words, uint64_t max_words, const uint64_t *d_event_off,
+                  uint64_t max_events, const uint64_t *d_sizes, const int16_t *d_F,
+                  const int16_t *d_q, const svt_config *cfg, uint64_t road_cap, uint32_t *d_out,
+                  uint32_t *d_event_road, uint64_t *d_counts, uint64_t *d_status,
+                  void *d_workspace, size_t workspace_bytes, const svt_schedule *sched,
+                  void *stream) {
+    if (!d_sizes) return SVT_ERR_BAD_ARG;
+    return run_impl(d_words, max_words, d_event_off, max_events, d_sizes, d_F, d_q, cfg, road_cap,
+                    d_out, d_event_road, d_counts, d_status, d_workspace, workspace_bytes, sched,
+                    nullptr, (cudaStream_t)stream);
+}
+
+int svt_graph_create(const uint32_t *d_words, uint64_t max_words, const uint64_t *d_event_off,
+                     uint64_t max_events, const uint64_t *d_sizes, const int16_t *d_F,
+                     const int16_t *d_q, const svt_config *cfg, uint64_t road_cap,
+                     uint32_t *d_out, uint32_t *d_event_road, uint64_t *d_counts,
+                     uint64_t *d_status, void *d_workspace, size_t workspace_bytes,
+                     const svt_schedule *sched, svt_graph *out) {
+    if (!out || !d_sizes) return SVT_ERR_BAD_ARG;
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return SVT_ERR_CUDA;
+    int rc = SVT_OK;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return SVT_ERR_CUDA;
+    }
+    rc = run_impl(d_words, max_words, d_event_off, max_events, d_sizes, d_F, d_q, cfg, road_cap,
+                  d_out, d_event_road, d_counts, d_status, d_workspace, workspace_bytes, sched,
+                  nullptr, cs);
+    cudaError_t ce = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (rc != SVT_OK || ce != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc != SVT_OK ? rc : SVT_ERR_CUDA;
+    }
+    svt_graph h = new svt_graph_s();
+    h->graph = g;
+    if (cudaGraphInstantiate(&h->exec, g, 0) != cudaSuccess) {
+        cudaGraphDestroy(g);
+        delete h;
+        return SVT_ERR_CUDA;
+    }
+    *out = h;
+    return SVT_OK;
+}
+
+int svt_graph_launch(svt_graph g, void *stream) {
+    if (!g) return SVT_ERR_BAD_ARG;
+    return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? SVT_OK : SVT_ERR_CUDA;
+}
+
+int svt_graph_destroy(svt_graph g) {
+    if (!g) return SVT_ERR_BAD_ARG;
+    cudaGraphExecDestroy(g->exec);
+    cudaGraphDestroy(g->graph);
+    delete g;
+    return SVT_OK;
 }
 
 size_t svt_calib_index_size(uint64_t n_tracks, uint32_t n_sectors) {

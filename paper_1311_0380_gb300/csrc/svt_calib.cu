@@ -165,10 +165,16 @@ __device__ __forceinline__ Item item_of(const int32_t *item_sector, const int32_
     return it;
 }
 
-// F[s] and q[s] of the item's sector in the warp's shared slot
+// F[s] and q[s] of the item's sector in the warp's shared slot (q may be null
+// where only F is needed: the offsets then read as 0)
 __device__ __forceinline__ void load_consts(float *c, const float *__restrict__ F,
                                             const float *__restrict__ q, uint32_t s, int lane) {
-    for (int j = lane; j < NPAR; j += 32) c[j] = j < 36 ? F[(size_t)s * 36 + j] : q[(size_t)s * 6 + (j - 36)];
+    for (int j = lane; j < NPAR; j += 32) {
+        if (j < 36)
+            c[j] = F[(size_t)s * 36 + j];
+        else
+            c[j] = q ? q[(size_t)s * 6 + (j - 36)] : 0.f;
+    }
     __syncwarp();
 }
 

@@ -146,7 +146,10 @@ void launch_calib_grad(int mode, const float *x, const float *theta, const float
                        cudaStream_t st);
 
 // shared by both paths
+// Sets the batch sizes (from `sizes` on the device when given, bounded by
+// n_words / n_events), resets the status and zeroes counts[0..n_counts).
 void launch_set_dims(Dims *dims, uint64_t n_words, uint64_t n_events,
-                     unsigned long long *status, uint64_t *counts, int n_counts, cudaStream_t st);
+                     unsigned long long *status, uint64_t *counts, int n_counts, cudaStream_t st,
+                     const uint64_t *sizes = nullptr);
 
 }  // namespace svt

@@ -49,14 +49,25 @@ __device__ __forceinline__ bool is_event_start(const uint64_t *__restrict__ off,
     return e < n && __ldg(off + e) == i;
 }
 
+// Batch sizes for the launch sequence: the given values, or -- when `sizes`
+// is set -- the device-resident pair {n_words, n_events}, which must not
+// exceed the capacities the sequence was sized for (else BAD_ARG, empty batch).
 __global__ void k_set_dims(Dims *dims, uint64_t n_words, uint64_t n_events,
-                           unsigned long long *status, uint64_t *counts, int n_counts) {
+                           const uint64_t *sizes, unsigned long long *status, uint64_t *counts,
+                           int n_counts) {
     if (threadIdx.x == 0) {
+        bool bad = false;
+        if (sizes) {
+            const uint64_t w = sizes[0], e = sizes[1];
+            bad = w > n_words || e > n_events;
+            n_words = bad ? 0 : w;
+            n_events = bad ? 0 : e;
+        }
         if (dims) {
             dims->n_words = n_words;
             dims->n_events = n_events;
         }
-        if (status) *status = ~0ull;
+        if (status) *status = bad ? (unsigned long long)SVT_ERR_BAD_ARG : ~0ull;
     }
     if (counts && (int)threadIdx.x < n_counts) counts[threadIdx.x] = 0;
 }
@@ -263,8 +274,8 @@ __global__ void k_unpack_events(const uint32_t *__restrict__ words,
 }  // namespace
 
 void launch_set_dims(Dims *dims, uint64_t n_words, uint64_t n_events, unsigned long long *status,
-                     uint64_t *counts, int n_counts, cudaStream_t st) {
-    k_set_dims<<<1, 32, 0, st>>>(dims, n_words, n_events, status, counts, n_counts);
+                     uint64_t *counts, int n_counts, cudaStream_t st, const uint64_t *sizes) {
+    k_set_dims<<<1, 32, 0, st>>>(dims, n_words, n_events, sizes, status, counts, n_counts);
 }
 
 void launch_unpack_count(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
