@@ -347,7 +347,7 @@ __device__ __forceinline__ void format_road(const uint32_t *__restrict__ words, 
 
 // K4: persistent fit / cut / select / format
 template <bool NOCLAMP>
-__global__ void __launch_bounds__(256, 4) k_fit_persistent(const uint32_t *__restrict__ words,
+__global__ void __launch_bounds__(512, 2) k_fit_persistent(const uint32_t *__restrict__ words,
                                  const uint4 *__restrict__ desc,
                                  const uint64_t *__restrict__ counts_in, uint64_t road_cap,
                                  const uint64_t *__restrict__ n_big_p,
