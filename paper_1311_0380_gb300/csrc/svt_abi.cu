@@ -94,7 +94,7 @@ struct RunWs {
     uint64_t *n_big;
     uint32_t *counters;
     uint32_t *tile_roads, *tile_big, *tile_bigitems;
-    uint4 *desc;
+    RoadDesc *desc;
     uint32_t *big_road, *big_item_off, *big_pending;
     unsigned long long *big_best;
     uint32_t *event_road;
@@ -111,7 +111,7 @@ RunWs carve_run(void *base, uint64_t max_words, uint64_t max_events, uint64_t ro
     w.tile_roads = c.take<uint32_t>(T + 1);
     w.tile_big = c.take<uint32_t>(T + 1);
     w.tile_bigitems = c.take<uint32_t>(T + 1);
-    w.desc = c.take<uint4>(road_cap);
+    w.desc = c.take<RoadDesc>(road_cap);
     w.big_road = c.take<uint32_t>(road_cap);
     w.big_item_off = c.take<uint32_t>(road_cap + 1);
     w.big_pending = c.take<uint32_t>(road_cap);

@@ -38,18 +38,16 @@ struct WarpSmem {
     long long T[N_LAYERS * MAX_HITS * 3]; // chi-row terms F[3+k][l] * x * 2^(32-oshift), [l][i][k]
     longlong2 S[32][2];                   // suffix sums below the top suffix layer, [b'](3 rows)
     longlong2 A[ROWS_MAX][2];             // prefix sums incl. q, per row: (A3, A4), (A5, -)
-    int32_t cF[18];                       // F[3+k][l] at k*6+l
-    int32_t cq[3];
-    int32_t pad[3];
-    SmallDiv dv[N_LAYERS];                // exact division by n'_l
+    uint32_t x[N_LAYERS * MAX_HITS];      // hit coordinates [l][i] (x = 0 for an empty layer)
+    int32_t F[36];                        // F[s][m][k][l] at k*6+l
+    int32_t q[6];
     uint32_t n[N_LAYERS];                 // n'_l = max(n_l, 1)
-    // road geometry (warp-uniform): c = a * NB + b, b = i_top * NBp + b'
-    uint32_t split, NB, NA, C_eval, NBp, d_hi, d_lo, total_hits;
+    uint32_t m[N_LAYERS];                 // division magic of n'_l
 };
 
 // K3: the list of split roads
 __global__ void __launch_bounds__(TILE_THREADS)
-    k_big_list(const uint4 *__restrict__ desc, uint64_t road_cap, const Dims *__restrict__ dims,
+    k_big_list(const RoadDesc *__restrict__ desc, uint64_t road_cap, const Dims *__restrict__ dims,
                const uint32_t *__restrict__ tile_roads, const uint32_t *__restrict__ tile_big,
                const uint32_t *__restrict__ tile_bigitems, const FusedRoads fr, BigList bl,
                unsigned long long *status) {
@@ -68,10 +66,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
 #pragma unroll
         for (int j = 0; j < TILE_PER_THREAD; ++j) {
             it[j] = 0;
-            if (rb + j < r1) {
-                const uint4 d = desc[rb + j];
-                it[j] = road_big_items(d.y, d.w, fr);
-            }
+            if (rb + j < r1) it[j] = road_big_items(desc[rb + j], fr);
             n_it += it[j];
             n_big += it[j] ? 1u : 0u;
         }
@@ -118,73 +113,85 @@ __device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
 
 __device__ __forceinline__ int32_t clamp_chi(int32_t y) { return max(min(y, 32767), -32767); }
 
-// Constants of the chi rows, per-hit terms and suffix table of road D in the
-// warp's slot.
+// Road geometry unpacked from its descriptor (warp-uniform values).
+struct Geo {
+    uint32_t split, NBp, NB, NA, C_eval, mask, total_hits;
+};
+__device__ __forceinline__ Geo geo_of(const RoadDesc &D) {
+    Geo g;
+    const uint32_t w = D.b.x;
+    g.split = w & 7u;
+    g.NBp = (w >> 3) & 31u;
+    g.mask = (w >> 13) & 63u;
+    g.total_hits = (w >> 19) & 127u;
+    g.NB = D.b.y;
+    g.NA = D.b.z;
+    g.C_eval = D.a.w;
+    return g;
+}
+
+// Constants, hit coordinates, per-hit chi terms and the suffix table of road D
+// in the warp's slot.  Global loads are issued before any shared-memory work.
 __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restrict__ words,
-                                           const uint4 D, const int16_t *__restrict__ F,
+                                           const RoadDesc &D, const Geo &g,
+                                           const int16_t *__restrict__ F,
                                            const int16_t *__restrict__ q, uint32_t sh, int lane) {
-    const uint32_t packed = D.y;
-    if (lane == 0) {
-        const RoadShape rs = road_shape(packed);
-        uint32_t split, NB;
-        road_split(rs, split, NB);
-        uint32_t ntop = 1;
+    const uint32_t rw = D.a.x, packed = D.a.y;
+    const size_t cs = (size_t)rd_sector(D.a.z) * 64 + g.mask;
+    const int32_t f0 = __ldg(F + cs * 36 + lane);
+    int32_t f1 = 0;
+    if (lane < 4) f1 = __ldg(F + cs * 36 + 32 + lane);
+    else if (lane < 10) f1 = __ldg(q + cs * 6 + (lane - 4));
+    uint32_t hv[3];
 #pragma unroll
-        for (int l = 0; l < N_LAYERS; ++l)
-            if ((uint32_t)l == split) ntop = rs.n[l];
-        const uint32_t NBp = NB / ntop;
-        sm.split = split;
-        sm.NB = NB;
-        sm.C_eval = D.w;
-        sm.NA = (D.w + NB - 1) / NB;
-        sm.NBp = NBp;
-        sm.d_hi = 32u / NBp;
-        sm.d_lo = 32u - (32u / NBp) * NBp;
-        sm.total_hits = rs.total_hits;
+    for (int j = 0; j < 3; ++j) {
+        const uint32_t h = (uint32_t)lane + 32u * j;
+        hv[j] = h < g.total_hits ? __ldg(words + rw + 1 + h) : 0u;
     }
+    sm.F[lane] = f0;
+    if (lane < 4) sm.F[32 + lane] = f1;
+    else if (lane < 10) sm.q[lane - 4] = f1;
     if (lane < N_LAYERS) {
         const uint32_t nl = nhit_of(packed, lane);
-        sm.n[lane] = nl ? nl : 1u;
-        sm.dv[lane] = make_div(nl ? nl : 1u);
-    }
-    uint32_t mask = 0;
-#pragma unroll
-    for (int l = 0; l < N_LAYERS; ++l) mask |= nhit_of(packed, l) ? (1u << l) : 0u;
-    const size_t cs = (size_t)rd_sector(D.z) * 64 + mask;
-    if (lane < 18) sm.cF[lane] = __ldg(F + cs * 36 + 18 + lane);
-    else if (lane < 21) sm.cq[lane - 18] = __ldg(q + cs * 6 + 3 + (lane - 18));
-    // layers without hits contribute x = 0
-    if (lane < N_LAYERS && nhit_of(packed, lane) == 0) {
-        sm.T[(lane * MAX_HITS) * 3 + 0] = 0;
-        sm.T[(lane * MAX_HITS) * 3 + 1] = 0;
-        sm.T[(lane * MAX_HITS) * 3 + 2] = 0;
+        const uint32_t np = nl ? nl : 1u;
+        sm.n[lane] = np;
+        sm.m[lane] = kDivMagic[np];
+        if (nl == 0) {   // a layer without hits contributes x = 0
+            sm.x[lane * MAX_HITS] = 0;
+            sm.T[(lane * MAX_HITS) * 3 + 0] = 0;
+            sm.T[(lane * MAX_HITS) * 3 + 1] = 0;
+            sm.T[(lane * MAX_HITS) * 3 + 2] = 0;
+        }
     }
     __syncwarp();
-    const uint32_t total_hits = sm.total_hits;
-    for (uint32_t h = lane; h < total_hits; h += 32) {
-        const uint32_t x = __ldg(words + D.x + 1 + h);
-        const uint32_t l = hit_layer(x);
-        uint32_t i = h;
 #pragma unroll
-        for (int ll = 0; ll < N_LAYERS; ++ll)
-            if ((uint32_t)ll < l) i -= nhit_of(packed, ll);
-        const int32_t xc = (int32_t)hit_coord(x);
-        long long *t = sm.T + (l * MAX_HITS + i) * 3;
-        t[0] = (long long)(sm.cF[0 * 6 + l] * xc) << sh;
-        t[1] = (long long)(sm.cF[1 * 6 + l] * xc) << sh;
-        t[2] = (long long)(sm.cF[2 * 6 + l] * xc) << sh;
+    for (int j = 0; j < 3; ++j) {
+        const uint32_t h = (uint32_t)lane + 32u * j;
+        if (h < g.total_hits) {
+            const uint32_t l = hit_layer(hv[j]);
+            uint32_t i = h;
+#pragma unroll
+            for (int ll = 0; ll < N_LAYERS; ++ll)
+                if ((uint32_t)ll < l) i -= nhit_of(packed, ll);
+            const uint32_t xc = hit_coord(hv[j]);
+            sm.x[l * MAX_HITS + i] = xc;
+            long long *t = sm.T + (l * MAX_HITS + i) * 3;
+            t[0] = (long long)(sm.F[18 + l] * (int32_t)xc) << sh;
+            t[1] = (long long)(sm.F[24 + l] * (int32_t)xc) << sh;
+            t[2] = (long long)(sm.F[30 + l] * (int32_t)xc) << sh;
+        }
     }
     __syncwarp();
     // S[b'] = sum over the suffix layers below the top one, b' < NBp (< 32)
-    const uint32_t split = sm.split;
-    if ((uint32_t)lane < sm.NBp) {
+    if ((uint32_t)lane < g.NBp) {
         uint32_t rem = lane;
         long long S3 = 0, S4 = 0, S5 = 0;
 #pragma unroll
         for (int l = N_LAYERS - 1; l >= 1; --l) {
-            if ((uint32_t)l > split) {
-                const uint32_t qd = div_small(rem, sm.dv[l]);
-                const uint32_t i = rem - qd * sm.n[l];
+            if ((uint32_t)l > g.split) {
+                const uint32_t nl = sm.n[l];
+                const uint32_t qd = div_by(rem, nl, sm.m[l]);
+                const uint32_t i = rem - qd * nl;
                 rem = qd;
                 const long long *t = sm.T + (l * MAX_HITS + i) * 3;
                 S3 += t[0];
@@ -201,14 +208,15 @@ __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restr
 __device__ __forceinline__ void build_row(WarpSmem &sm, uint32_t split, uint32_t a,
                                           uint32_t slot, uint32_t qsh) {
     uint32_t rem = a;
-    long long A3 = (long long)sm.cq[0] << qsh;
-    long long A4 = (long long)sm.cq[1] << qsh;
-    long long A5 = (long long)sm.cq[2] << qsh;
+    long long A3 = (long long)sm.q[3] << qsh;
+    long long A4 = (long long)sm.q[4] << qsh;
+    long long A5 = (long long)sm.q[5] << qsh;
 #pragma unroll
     for (int l = N_LAYERS - 1; l >= 0; --l) {
         if ((uint32_t)l < split) {
-            const uint32_t qd = div_small(rem, sm.dv[l]);
-            const uint32_t i = rem - qd * sm.n[l];
+            const uint32_t nl = sm.n[l];
+            const uint32_t qd = div_by(rem, nl, sm.m[l]);
+            const uint32_t i = rem - qd * nl;
             rem = qd;
             const long long *t = sm.T + (l * MAX_HITS + i) * 3;
             A3 += t[0];
@@ -224,20 +232,23 @@ __device__ __forceinline__ int32_t hi_word(long long v) {
     return (int32_t)((unsigned long long)v >> 32);
 }
 
-// Best (chi2 << 32 | c) over rows [a_lo, a_hi) of the road, reduced over the
-// warp.  NOCLAMP (valid when chi2_cut < 32767^2): the squares are summed
-// unclamped in 64 bits; any combination with a chi component of magnitude
-// 32767 or more then exceeds the cut under both readings, and below that the
-// clamp is the identity, so pass/fail, chi2 of passing combinations and the
-// argmin are unchanged.
+// Best key over rows [a_lo, a_hi) of the road, reduced over the warp.  The key
+// is (chi2 << 32) | (row << 9) | column; since columns < NB < 512 its low word
+// orders exactly like the combination index c = row * NB + column.
+// NOCLAMP (valid when chi2_cut < 32767^2): the squares are summed unclamped in
+// 64 bits; any combination with a chi component of magnitude 32767 or more
+// then exceeds the cut under both readings, and below that the clamp is the
+// identity, so pass/fail, chi2 of passing combinations and the argmin are
+// unchanged.
 template <bool NOCLAMP>
-__device__ __forceinline__ unsigned long long eval_rows(WarpSmem &sm, uint32_t a_lo,
+__device__ __forceinline__ unsigned long long eval_rows(WarpSmem &sm, const Geo &g, uint32_t a_lo,
                                                         uint32_t a_hi, uint32_t qsh,
                                                         uint32_t init_chi, int lane) {
     unsigned long long best = ~0ull;
-    const uint32_t NB = sm.NB, NA = sm.NA, C_eval = sm.C_eval, NBp = sm.NBp;
-    const uint32_t top = sm.split, d_lo = sm.d_lo, d_hi = sm.d_hi;
-    const uint32_t is0 = (uint32_t)lane / NBp, bp0 = (uint32_t)lane - is0 * NBp;
+    const uint32_t NB = g.NB, NA = g.NA, C_eval = g.C_eval, NBp = g.NBp, top = g.split;
+    const uint32_t mp = kDivMagic[NBp];
+    const uint32_t d_hi = div_by(32u, NBp, mp), d_lo = 32u - d_hi * NBp;
+    const uint32_t is0 = div_by((uint32_t)lane, NBp, mp), bp0 = (uint32_t)lane - is0 * NBp;
     for (uint32_t ac = a_lo; ac < a_hi; ac += ROWS_MAX) {
         const uint32_t ae = min(ac + (uint32_t)ROWS_MAX, a_hi);
         if (ac + lane < ae) build_row(sm, top, ac + lane, lane, qsh);
@@ -279,7 +290,7 @@ __device__ __forceinline__ unsigned long long eval_rows(WarpSmem &sm, uint32_t a
                     }
                 }
                 if (bchi != init_chi) {
-                    const unsigned long long key = ((unsigned long long)bchi << 32) | (ba * NB + b);
+                    const unsigned long long key = ((unsigned long long)bchi << 32) | (ba << 9) | b;
                     best = key < best ? key : best;
                 }
             }
@@ -295,39 +306,32 @@ __device__ __forceinline__ unsigned long long eval_rows(WarpSmem &sm, uint32_t a
     return warp_min64(best);
 }
 
-// Record of a road from its best key (all lanes call; lanes 0..2 recompute p).
-__device__ __forceinline__ void format_road(const uint32_t *__restrict__ words, const uint4 D,
-                            const int16_t *__restrict__ F, const int16_t *__restrict__ q,
-                            const svt_config &cfg, unsigned long long best, uint32_t *o,
-                            uint64_t *counts, int lane) {
-    const uint32_t packed = D.y;
-    const RoadShape s = road_shape(packed);
+// Record of a road from its best key (all lanes call; lanes 0..2 recompute the
+// parameters from the warp's slot, which still holds this road).
+__device__ __forceinline__ void format_road(WarpSmem &sm, const RoadDesc &D, const Geo &g,
+                                            const svt_config &cfg, unsigned long long best,
+                                            uint32_t *o, uint64_t *counts, int lane) {
+    const uint32_t geo = D.b.x;
     const bool pass = best != ~0ull;
     uint32_t flags = 0;
-    if (s.total_hits == 0) flags |= SVT_FLAG_NO_HITS;
-    if (s.n_layers_hit < cfg.min_layers)
-        flags |= SVT_FLAG_BAD_PATTERN;
-    else if (s.C > cfg.max_comb)
-        flags |= SVT_FLAG_OVERFLOW;
+    if (g.total_hits == 0) flags |= SVT_FLAG_NO_HITS;
+    if (geo & (1u << 27)) flags |= SVT_FLAG_BAD_PATTERN;
+    if (geo & (1u << 26)) flags |= SVT_FLAG_OVERFLOW;
     if (pass) flags |= SVT_FLAG_PASS;
+    const uint32_t low = (uint32_t)best;
+    const uint32_t row = low >> 9, col = low & 511u;
     int32_t p = 0;
-    const uint32_t c = (uint32_t)best;
     if (pass && lane < 3) {
-        uint32_t rem = c, idx[N_LAYERS];
+        long long acc = (long long)sm.q[lane] * (1ll << cfg.qshift);
+        uint32_t rem = col;
 #pragma unroll
         for (int l = N_LAYERS - 1; l >= 0; --l) {
-            idx[l] = rem % s.n[l];
-            rem /= s.n[l];
-        }
-        const size_t cs = (size_t)rd_sector(D.z) * 64 + s.mask;
-        long long acc = (long long)__ldg(q + cs * 6 + lane) * (1ll << cfg.qshift);
-        uint32_t hoff = D.x + 1;
-#pragma unroll
-        for (int l = 0; l < N_LAYERS; ++l) {
-            const uint32_t nl = nhit_of(packed, l);
-            const uint32_t x = nl ? hit_coord(__ldg(words + hoff + idx[l])) : 0u;
-            acc += (long long)__ldg(F + cs * 36 + lane * 6 + l) * (long long)x;
-            hoff += nl;
+            if ((uint32_t)l + 1u == g.split) rem = row;   // the prefix layers take the row
+            const uint32_t nl = sm.n[l];
+            const uint32_t qd = div_by(rem, nl, sm.m[l]);
+            const uint32_t i = rem - qd * nl;
+            rem = qd;
+            acc += (long long)sm.F[lane * 6 + l] * (long long)sm.x[l * MAX_HITS + i];
         }
         p = (int32_t)(acc >> cfg.oshift);   // arithmetic shift: floor
     }
@@ -335,8 +339,8 @@ __device__ __forceinline__ void format_road(const uint32_t *__restrict__ words, 
     const int32_t p1 = __shfl_sync(0xffffffffu, p, 1);
     const int32_t p2 = __shfl_sync(0xffffffffu, p, 2);
     if (lane == 0) {
-        o[0] = rd_id(D.z) | (flags << 24);
-        o[1] = pass ? c : 0xFFFFFFFFu;
+        o[0] = rd_id(D.a.z) | (flags << 24);
+        o[1] = pass ? row * g.NB + col : 0xFFFFFFFFu;
         o[2] = pass ? (uint32_t)(best >> 32) : 0u;
         o[3] = (uint32_t)p0;
         o[4] = (uint32_t)p1;
@@ -347,14 +351,13 @@ __device__ __forceinline__ void format_road(const uint32_t *__restrict__ words, 
 
 // K4: persistent fit / cut / select / format
 template <bool NOCLAMP>
-__global__ void __launch_bounds__(512, 2) k_fit_persistent(const uint32_t *__restrict__ words,
-                                 const uint4 *__restrict__ desc,
-                                 const uint64_t *__restrict__ counts_in, uint64_t road_cap,
-                                 const uint64_t *__restrict__ n_big_p,
-                                 const int16_t *__restrict__ F, const int16_t *__restrict__ q,
-                                 const svt_config cfg, const FusedRoads fr,
-                                 uint32_t roads_per_chunk, BigList bl, uint32_t *out,
-                                 uint64_t *counts, unsigned long long *status) {
+__global__ void __launch_bounds__(512, 2)
+    k_fit_persistent(const uint32_t *__restrict__ words, const RoadDesc *__restrict__ desc,
+                     const uint64_t *__restrict__ counts_in, uint64_t road_cap,
+                     const uint64_t *__restrict__ n_big_p, const int16_t *__restrict__ F,
+                     const int16_t *__restrict__ q, const svt_config cfg, const FusedRoads fr,
+                     uint32_t roads_per_chunk, BigList bl, uint32_t *out, uint64_t *counts,
+                     unsigned long long *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
@@ -378,11 +381,14 @@ __global__ void __launch_bounds__(512, 2) k_fit_persistent(const uint32_t *__res
         const uint32_t j = find_slot(bl.item_off, n_big, it, lane);
         const uint32_t r = __ldg(bl.road + j);
         const uint32_t k = it - __ldg(bl.item_off + j);
-        const uint4 D = __ldg(desc + r);
-        road_setup(sm, words, D, F, q, sh, lane);
+        RoadDesc D;
+        D.a = __ldg(&desc[r].a);
+        D.b = __ldg(&desc[r].b);
+        const Geo g = geo_of(D);
+        road_setup(sm, words, D, g, F, q, sh, lane);
         const uint32_t a_lo = k * fr.rows;
-        const uint32_t a_hi = min(a_lo + fr.rows, sm.NA);
-        const unsigned long long best = eval_rows<NOCLAMP>(sm, a_lo, a_hi, qsh, init_chi, lane);
+        const uint32_t a_hi = min(a_lo + fr.rows, g.NA);
+        const unsigned long long best = eval_rows<NOCLAMP>(sm, g, a_lo, a_hi, qsh, init_chi, lane);
         uint32_t last = 0;
         if (lane == 0) {
             if (best != ~0ull) atomicMin(bl.best + j, best);
@@ -393,7 +399,7 @@ __global__ void __launch_bounds__(512, 2) k_fit_persistent(const uint32_t *__res
         if (last) {
             __threadfence();
             const unsigned long long fb = __ldcg(bl.best + j);
-            format_road(words, D, F, q, cfg, fb, out + (size_t)r * 6, counts, lane);
+            format_road(sm, D, g, cfg, fb, out + (size_t)r * 6, counts, lane);
         }
         __syncwarp();
     }
@@ -405,21 +411,29 @@ __global__ void __launch_bounds__(512, 2) k_fit_persistent(const uint32_t *__res
         c0 = __shfl_sync(0xffffffffu, c0, 0);
         if (c0 >= R) break;
         const uint32_t n = min(roads_per_chunk, R - c0);
-        uint4 d = make_uint4(0, 0, 0, 0);
-        if ((uint32_t)lane < n) d = __ldg(desc + c0 + lane);
+        uint4 da = make_uint4(0, 0, 0, 0), db = make_uint4(0, 0, 0, 0);
+        if ((uint32_t)lane < n) {
+            da = __ldg(&desc[c0 + lane].a);
+            db = __ldg(&desc[c0 + lane].b);
+        }
         for (uint32_t jj = 0; jj < n; ++jj) {
-            uint4 D;
-            D.x = __shfl_sync(0xffffffffu, d.x, jj);
-            D.y = __shfl_sync(0xffffffffu, d.y, jj);
-            D.z = __shfl_sync(0xffffffffu, d.z, jj);
-            D.w = __shfl_sync(0xffffffffu, d.w, jj);
-            if (D.w > fr.small_max) continue;   // split road: done in phase 1
+            RoadDesc D;
+            D.a.x = __shfl_sync(0xffffffffu, da.x, jj);
+            D.a.y = __shfl_sync(0xffffffffu, da.y, jj);
+            D.a.z = __shfl_sync(0xffffffffu, da.z, jj);
+            D.a.w = __shfl_sync(0xffffffffu, da.w, jj);
+            D.b.x = __shfl_sync(0xffffffffu, db.x, jj);
+            D.b.y = __shfl_sync(0xffffffffu, db.y, jj);
+            D.b.z = __shfl_sync(0xffffffffu, db.z, jj);
+            D.b.w = 0;
+            if (D.a.w > fr.small_max) continue;   // split road: done in phase 1
+            const Geo g = geo_of(D);
             unsigned long long best = ~0ull;
-            if (D.w > 0) {
-                road_setup(sm, words, D, F, q, sh, lane);
-                best = eval_rows<NOCLAMP>(sm, 0, sm.NA, qsh, init_chi, lane);
+            if (g.C_eval > 0) {
+                road_setup(sm, words, D, g, F, q, sh, lane);
+                best = eval_rows<NOCLAMP>(sm, g, 0, g.NA, qsh, init_chi, lane);
             }
-            format_road(words, D, F, q, cfg, best, out + (size_t)(c0 + jj) * 6, counts, lane);
+            format_road(sm, D, g, cfg, best, out + (size_t)(c0 + jj) * 6, counts, lane);
             __syncwarp();
         }
     }
@@ -427,7 +441,7 @@ __global__ void __launch_bounds__(512, 2) k_fit_persistent(const uint32_t *__res
 
 }  // namespace
 
-void launch_big_list(const uint4 *desc, uint64_t road_cap, const Dims *dims, uint64_t max_words,
+void launch_big_list(const RoadDesc *desc, uint64_t road_cap, const Dims *dims, uint64_t max_words,
                      const uint32_t *tile_roads, const uint32_t *tile_big,
                      const uint32_t *tile_bigitems, const FusedRoads fr, BigList bl,
                      unsigned long long *status, int grid, cudaStream_t st) {
@@ -453,7 +467,7 @@ int fit_persistent_blocks_per_sm(int warps_per_block) {
     return n < n2 ? n : n2;
 }
 
-cudaError_t launch_fit_persistent(const uint32_t *words, const uint4 *desc, const uint64_t *counts,
+cudaError_t launch_fit_persistent(const uint32_t *words, const RoadDesc *desc, const uint64_t *counts,
                                   uint64_t road_cap, const uint64_t *n_big, const int16_t *F,
                                   const int16_t *q, const svt_config cfg, const FusedRoads fr,
                                   uint32_t roads_per_chunk, BigList bl, uint32_t *out,

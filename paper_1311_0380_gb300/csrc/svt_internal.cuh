@@ -95,6 +95,17 @@ __host__ __device__ __forceinline__ SmallDiv make_div(uint32_t d) {
 __device__ __forceinline__ uint32_t div_small(uint32_t x, SmallDiv v) {
     return v.d <= 1 ? x : __umulhi(x, v.m);
 }
+// m = ceil(2^32 / d) for d = 2..32 (0 for d < 2): x / d = umulhi(x, m) for
+// x < 2^24 when d <= 16, and for x <= 64 when d <= 32.
+static __device__ __constant__ uint32_t kDivMagic[33] = {
+    0u, 0u, 2147483648u, 1431655766u, 1073741824u, 858993460u, 715827883u, 613566757u,
+    536870912u, 477218589u, 429496730u, 390451573u, 357913942u, 330382100u, 306783379u,
+    286331154u, 268435456u, 252645136u, 238609295u, 226050911u, 214748365u, 204522253u,
+    195225787u, 186737709u, 178956971u, 171798692u, 165191050u, 159072863u, 153391690u,
+    148102321u, 143165577u, 138547333u, 134217728u};
+__device__ __forceinline__ uint32_t div_by(uint32_t x, uint32_t d, uint32_t m) {
+    return d <= 1 ? x : __umulhi(x, m);
+}
 
 // ---- combination geometry of a road ----------------------------------------
 // All quantities derived from the per-layer hit counts.

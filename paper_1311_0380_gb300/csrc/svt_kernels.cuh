@@ -14,34 +14,55 @@ struct Dims {
     uint64_t n_events;
 };
 
+// Per-road descriptor of the fused path (32 bytes), built once by the road
+// extraction:
+//   a = {header word index, hits per layer (5 bits each), header word,
+//        evaluated combinations C_eval}
+//   b = {geo, NB, NA, 0} with the split c = a_row * NB + b_col (see road_split),
+//       NA = ceil(C_eval / NB) rows, and geo bits [2:0] split, [7:3] NBp (columns
+//       below the top suffix layer, NB = ntop * NBp), [12:8] ntop, [18:13] layer
+//       mask, [25:19] total hits, [26] OVERFLOW, [27] BAD_PATTERN.
+struct RoadDesc {
+    uint4 a, b;
+};
+__device__ __forceinline__ RoadDesc make_road_desc(uint32_t rw, uint32_t packed, uint32_t hw,
+                                                   const svt_config &cfg) {
+    const RoadShape s = road_shape(packed);
+    const bool bad = s.n_layers_hit < cfg.min_layers;
+    const uint32_t C = (uint32_t)s.C;
+    const uint32_t C_eval = bad ? 0u : (C > cfg.max_comb ? cfg.max_comb : C);
+    uint32_t split, NB;
+    road_split(s, split, NB);
+    uint32_t NBp = 1, ntop = 1;
+#pragma unroll
+    for (int l = 0; l < N_LAYERS; ++l) {
+        if ((uint32_t)l > split) NBp *= s.n[l];
+        if ((uint32_t)l == split) ntop = s.n[l];
+    }
+    const uint32_t NA = C_eval ? (C_eval + NB - 1) / NB : 0u;
+    const uint32_t geo = split | (NBp << 3) | (ntop << 8) | (s.mask << 13) | (s.total_hits << 19) |
+                         ((!bad && C > cfg.max_comb) ? (1u << 26) : 0u) | (bad ? (1u << 27) : 0u);
+    RoadDesc d;
+    d.a = make_uint4(rw, packed, hw, C_eval);
+    d.b = make_uint4(geo, NB, NA, 0u);
+    return d;
+}
+
 // Fused-path outputs of the road extraction (desc == nullptr: plain path).
 struct FusedRoads {
-    uint4 *desc;               // per road: header word index, hits per layer,
-                               // header word, evaluated combinations
+    RoadDesc *desc;            // per road
     uint32_t *tile_big;        // per word tile: roads split into items
     uint32_t *tile_bigitems;   // per word tile: items of those roads
     uint32_t rows;             // rows per item
     uint32_t small_max;        // roads above this many combinations are split
 };
 
-// Evaluated combinations of a road (0 when it has fewer than min_layers
-// layers hit) and, for the fused fit, its work items: roads with more than
-// small_max evaluated combinations are split into items of `rows` rows of
-// the (prefix x suffix) grid; smaller roads are fitted whole by one warp.
-__device__ __forceinline__ uint32_t road_eval_count(uint32_t packed, const svt_config &cfg) {
-    RoadShape s = road_shape(packed);
-    if (s.n_layers_hit < cfg.min_layers) return 0;
-    const uint32_t C = (uint32_t)s.C;
-    return C > cfg.max_comb ? cfg.max_comb : C;
-}
-__device__ __forceinline__ uint32_t road_big_items(uint32_t packed, uint32_t C_eval,
-                                                   const FusedRoads &fr) {
-    if (C_eval <= fr.small_max) return 0;
-    RoadShape s = road_shape(packed);
-    uint32_t split, NB;
-    road_split(s, split, NB);
-    const uint32_t NA = (C_eval + NB - 1) / NB;
-    return (NA + fr.rows - 1) / fr.rows;
+// Work items of a road for the fused fit: roads with more than small_max
+// evaluated combinations are split into items of `rows` rows of the
+// (prefix x suffix) grid; smaller roads are fitted whole by one warp.
+__device__ __forceinline__ uint32_t road_big_items(const RoadDesc &d, const FusedRoads &fr) {
+    if (d.a.w <= fr.small_max) return 0;
+    return (d.b.z + fr.rows - 1) / fr.rows;
 }
 
 // ---- unpack (svt_unpack.cu) --------------------------------------------------
@@ -80,12 +101,12 @@ struct BigList {
     uint32_t *pending;
     uint32_t *counters;        // [0] big items taken, [1] roads taken
 };
-void launch_big_list(const uint4 *desc, uint64_t road_cap, const Dims *dims, uint64_t max_words,
+void launch_big_list(const RoadDesc *desc, uint64_t road_cap, const Dims *dims, uint64_t max_words,
                      const uint32_t *tile_roads, const uint32_t *tile_big,
                      const uint32_t *tile_bigitems, const FusedRoads fr, BigList bl,
                      unsigned long long *status, int grid, cudaStream_t st);
 // K4: the persistent fit over split-road items, then over chunks of roads.
-cudaError_t launch_fit_persistent(const uint32_t *words, const uint4 *desc, const uint64_t *counts,
+cudaError_t launch_fit_persistent(const uint32_t *words, const RoadDesc *desc, const uint64_t *counts,
                                   uint64_t road_cap, const uint64_t *n_big,
                                   const int16_t *F, const int16_t *q, const svt_config cfg,
                                   const FusedRoads fr, uint32_t roads_per_chunk, BigList bl,

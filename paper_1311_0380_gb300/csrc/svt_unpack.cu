@@ -213,12 +213,12 @@ __global__ void __launch_bounds__(TILE_THREADS)
             }
             if (road_nhit) road_nhit[r] = packed;
             if (fr.desc) {
-                const uint32_t n_eval = road_eval_count(packed, cfg);
-                const uint32_t it = road_big_items(packed, n_eval, fr);
-                fr.desc[r] = make_uint4((uint32_t)i, packed, w[j], n_eval);
+                const RoadDesc d = make_road_desc((uint32_t)i, packed, w[j], cfg);
+                const uint32_t it = road_big_items(d, fr);
+                fr.desc[r] = d;
                 items_sum += it;
                 big_sum += it ? 1u : 0u;
-                comb_sum += n_eval;
+                comb_sum += d.a.w;
             }
         }
         __syncthreads();
