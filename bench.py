@@ -52,6 +52,7 @@ def parse_args():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--rows", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--bps", type=int, default=0)
@@ -179,6 +180,47 @@ def cpu_baseline(spec, consts, batch, budget_s=12.0):
     return {"value": fits / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {n_ev} of {batch.n_events} events ({fits} fits), serial C oracle, one pass",
             "seconds": round(dt, 3)}
+
+
+def serving(dev):
+    """Poisson arrivals of events shaped like the uneven workload (roads
+    log-uniform in 1..2048, 1-16 hits per layer, 4096 combinations per road at
+    most) at 30 kHz and 300 kHz through the continuous-batching server
+    (fused path, 4 slots, CUDA graphs), and the plain per-stage path served one
+    batch at a time at 30 kHz beside it.  Latency = submission to completion,
+    H2D and D2H included."""
+    from paper_1311_0380_gb300 import api, serve, synth
+    consts = synth.make_constants(512)
+    pool_b = synth.make_batch("uneven", 1024, consts, seed=synth.BASE_SEED + 4)
+    fits_ev = np.bincount(np.repeat(np.arange(pool_b.n_events), pool_b.n_roads),
+                          weights=pool_b.combinations(4096), minlength=pool_b.n_events)
+    pool = serve.pinned_pool(pool_b.words)
+    cfg = api.config(15, 15, consts.chi2_cut_99, 4096, 5, 512)
+    dc = api.DeviceConstants.from_numpy(consts.F, consts.q, cfg, dev)
+    out = {"events": "uneven-shaped, pool of 1024 distinct events cycled",
+           "mean_words_per_event": float(len(pool_b.words) / pool_b.n_events),
+           "mean_fits_per_event": float(fits_ev.mean())}
+
+    def run(srv, rate, n):
+        lat, wall = srv.bench_poisson(pool, pool_b.event_off, rate, n, seed=7)
+        ok = lat != np.uint64(2 ** 64 - 1)
+        us = lat[ok].astype(np.float64) / 1e3
+        fits = float(sum(fits_ev[i % pool_b.n_events] for i in range(n)))
+        return {"rate_hz": rate, "events": n, "failed": int((~ok).sum()),
+                "p50_us": float(np.percentile(us, 50)), "p99_us": float(np.percentile(us, 99)),
+                "p999_us": float(np.percentile(us, 99.9)), "events_per_s": n / wall,
+                "fits_per_s": fits / wall, "wall_s": wall}
+
+    srv = serve.Server(dc, n_slots=4, max_words=1 << 22, max_events=256, max_roads=1 << 17)
+    out["fused_graph_4slots"] = [run(srv, 30e3, 30000), run(srv, 300e3, 100000)]
+    st = srv.stats()
+    out["fused_graph_4slots_stats"] = {k: st[k] for k in ("batches", "h2d_bytes", "d2h_bytes")}
+    srv.close()
+    plain = serve.Server(dc, n_slots=1, max_words=1 << 20, max_events=64, max_roads=1 << 14,
+                         mode=1, max_combs=(1 << 14) * 4096)
+    out["plain_per_batch"] = [run(plain, 30e3, 300)]
+    plain.close()
+    return out
 
 
 def run_reference(args, world, rank):
@@ -356,6 +398,10 @@ def main():
             plain["e2e_p99_us"] = percentile(lat, 99)
         del pp
 
+    serve_out = None
+    if rank == 0 and not args.no_serve:
+        serve_out = serving(dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(spec, consts, batch)
@@ -374,6 +420,7 @@ def main():
             "latency_us": {"p50": percentile([m * 1e3 for m in step_ms], 50),
                            "p99": percentile([m * 1e3 for m in step_ms], 99)},
             "e2e": e2e, "plain": plain, "roofline": roofline, "cpu_baseline": cpu,
+            "serving": serve_out,
             "clocks": clock_summary,
             "gpu_launches": api.FUSED_LAUNCHES_PER_RUN * args.steps,
         }

@@ -304,6 +304,79 @@ int svt_graph_launch(svt_graph graph, void *stream);
 int svt_graph_destroy(svt_graph graph);
 
 /* ======================================================================
+ * Serving loop (the single-GPU form of the paper's trigger-node loop,
+ * Sec. 3 and Sec. 4.2: data in -> GPU -> data out), with continuous
+ * batching.  Events are submitted by reference -- a pointer to the event's
+ * words (its header first) in PINNED host memory that stays valid until the
+ * event's result is delivered.  A dispatcher thread admits queued events into
+ * free device slots (each slot holds a batch of at most max_words words,
+ * max_events events and max_roads roads: this is the device-memory budget),
+ * copies each contiguous run of event words with one H2D copy, replays the
+ * slot's captured CUDA graph of svt_run_sized and copies the records back,
+ * each slot on its own stream, so batches overlap on the device.  A batch
+ * whose status reports a data error is re-run event by event, so a corrupt
+ * event fails alone.  The library allocates no device or pinned memory here:
+ * the caller passes both (svt_server_sizes).  Results carry the latency from
+ * submission to the moment the dispatcher sees the batch complete.
+ * ====================================================================== */
+typedef struct {
+    uint32_t n_slots;            /* batches in flight, 1..16 */
+    uint32_t mode;               /* 0: fused path, one captured graph per slot;
+                                    1: plain per-stage path (svt_unpack .. svt_format) */
+    uint64_t max_words;          /* per batch */
+    uint64_t max_events;         /* per batch */
+    uint64_t max_roads;          /* per batch */
+    uint64_t max_combs;          /* per batch, mode 1 only (combination records) */
+    uint64_t device_budget;      /* bytes; 0 = no limit (else create fails with OOM) */
+    uint64_t max_queued_words;   /* admission queue bound; 0 = unbounded */
+} svt_server_config;
+
+typedef struct {
+    uint64_t tag;                /* as submitted */
+    uint64_t status;             /* SVT_STATUS_OK or the event's error key */
+    uint32_t n_roads;
+    uint32_t reserved;
+    uint64_t latency_ns;         /* submission -> completion seen */
+    int64_t t_arrive_ns;         /* steady-clock submission time */
+} svt_event_result;
+
+typedef struct {
+    uint64_t batches, events_done, events_failed, retried_batches, rejected, queued;
+    uint64_t h2d_bytes, d2h_bytes;
+} svt_server_stats;
+
+typedef struct svt_server_s *svt_server;
+
+/* Device workspace and pinned host bytes a server with this config needs. */
+int svt_server_sizes(const svt_server_config *cfg, const svt_schedule *sched,
+                     size_t *device_bytes, size_t *pinned_bytes);
+/* Creates the slots (streams, events, one captured graph each) and starts the
+ * dispatcher thread.  d_F, d_q, fit stay owned by the caller and must outlive
+ * the server.  d_workspace and h_pinned must be 256-byte aligned. */
+int svt_server_create(const svt_server_config *cfg, const int16_t *d_F, const int16_t *d_q,
+                      const svt_config *fit, const svt_schedule *sched, void *d_workspace,
+                      size_t workspace_bytes, void *h_pinned, size_t pinned_bytes,
+                      svt_server *out);
+/* Queues one event (thread safe).  h_records (may be NULL) receives the
+ * event's records (6 x uint32 per road) before its result is delivered.
+ * SVT_ERR_OOM: the event can never fit a slot, or the queue bound is reached. */
+int svt_server_submit(svt_server server, const uint32_t *h_words, uint32_t n_words, uint64_t tag,
+                      uint32_t *h_records);
+/* Takes up to max_results delivered results; waits up to wait_us for one. */
+int svt_server_poll(svt_server server, svt_event_result *out, uint32_t max_results,
+                    uint32_t *n_out, uint32_t wait_us);
+int svt_server_stats_get(svt_server server, svt_server_stats *out);
+/* Stops the dispatcher after the batches in flight; undelivered events are dropped. */
+int svt_server_destroy(svt_server server);
+/* Poisson arrivals at rate_hz of n_events events taken in turn from a pool
+ * (words h_pool in pinned memory, pool_off[n_pool + 1] word offsets);
+ * lat_ns[i] = latency of event i (UINT64_MAX if it failed); *wall_s = time
+ * from the first arrival to the last completion. */
+int svt_server_bench_poisson(svt_server server, const uint32_t *h_pool, const uint64_t *pool_off,
+                             uint32_t n_pool, double rate_hz, uint64_t n_events, uint64_t seed,
+                             uint64_t *lat_ns, double *wall_s);
+
+/* ======================================================================
  * FP32 calibration relaxation.  The fit of Sec. 2 without the integer shift
  * and clamp, per track t of sector s:
  *     y_t = F[s] x_t + q[s]        (F: float [S][6][6], q: float [S][6])

@@ -38,6 +38,25 @@ class SvtSchedule(ctypes.Structure):
                  "small_max")]
 
 
+class SvtServerConfig(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_uint32), ("mode", ctypes.c_uint32),
+                ("max_words", ctypes.c_uint64), ("max_events", ctypes.c_uint64),
+                ("max_roads", ctypes.c_uint64), ("max_combs", ctypes.c_uint64),
+                ("device_budget", ctypes.c_uint64), ("max_queued_words", ctypes.c_uint64)]
+
+
+class SvtEventResult(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_uint64), ("n_roads", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("latency_ns", ctypes.c_uint64),
+                ("t_arrive_ns", ctypes.c_int64)]
+
+
+class SvtServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in
+                ("batches", "events_done", "events_failed", "retried_batches", "rejected", "queued",
+                 "h2d_bytes", "d2h_bytes")]
+
+
 class SvtBest(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("comb", ctypes.c_uint32), ("chi2", ctypes.c_uint32),
                 ("p", ctypes.c_int32 * 3)]
@@ -76,6 +95,17 @@ SIGNATURES = {
     "svt_timer_create": (ctypes.c_int, [ctypes.POINTER(_vp)]),
     "svt_timer_destroy": (ctypes.c_int, [_vp]),
     "svt_timer_fit_ms": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)]),
+    "svt_server_sizes": (ctypes.c_int, [ctypes.POINTER(SvtServerConfig), _schp,
+                                        ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
+    "svt_server_create": (ctypes.c_int, [ctypes.POINTER(SvtServerConfig), _vp, _vp, _cfgp, _schp,
+                                         _vp, _sz, _vp, _sz, ctypes.POINTER(_vp)]),
+    "svt_server_submit": (ctypes.c_int, [_vp, _vp, _u32, _u64, _vp]),
+    "svt_server_poll": (ctypes.c_int, [_vp, ctypes.POINTER(SvtEventResult), _u32,
+                                       ctypes.POINTER(_u32), _u32]),
+    "svt_server_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(SvtServerStats)]),
+    "svt_server_destroy": (ctypes.c_int, [_vp]),
+    "svt_server_bench_poisson": (ctypes.c_int, [_vp, _vp, _vp, _u32, ctypes.c_double, _u64, _u64,
+                                                _vp, ctypes.POINTER(ctypes.c_double)]),
     "svt_calib_index_size": (_sz, [_u64, _u32]),
     "svt_calib_index": (ctypes.c_int, [_vp, _u64, _u32, _vp, _sz, _vp, _vp, _vp]),
     "svt_calib_gather": (ctypes.c_int, [_vp, _u32, _vp, _u64, _vp, _vp]),

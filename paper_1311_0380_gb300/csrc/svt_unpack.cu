@@ -155,9 +155,11 @@ __global__ void __launch_bounds__(TILE_THREADS)
                    uint64_t road_cap, uint32_t *road_word, uint32_t *road_nhit,
                    uint32_t *event_road, const svt_config cfg, const FusedRoads fr,
                    uint64_t *counts, unsigned long long *status) {
+    constexpr int HALO = 100;   // covers the hits of a valid road that starts in the tile
     __shared__ uint32_t red[TILE_THREADS / 32 + 1];
     __shared__ unsigned long long red64[TILE_THREADS / 32 + 1];
     __shared__ uint32_t pre[TILE_WORDS];
+    __shared__ uint32_t sw[TILE_WORDS + HALO];
     __shared__ uint64_t ev_range[2];
     const uint64_t n_words = dims->n_words, n_events = dims->n_events;
     const uint64_t T = n_tiles(n_words);
@@ -173,8 +175,14 @@ __global__ void __launch_bounds__(TILE_THREADS)
         load8(words, base, n_words, w);
         uint32_t cnt = 0;
 #pragma unroll
-        for (int j = 0; j < TILE_PER_THREAD; ++j)
+        for (int j = 0; j < TILE_PER_THREAD; ++j) {
             cnt += (base + j < n_words && w_type(w[j]) == TYPE_ROAD) ? 1u : 0u;
+            sw[threadIdx.x * TILE_PER_THREAD + j] = w[j];
+        }
+        if (threadIdx.x < HALO) {
+            const uint64_t k = tile_start + TILE_WORDS + threadIdx.x;
+            sw[TILE_WORDS + threadIdx.x] = k < n_words ? __ldg(words + k) : 0xFFFFFFFFu;
+        }
         uint32_t total;
         const uint32_t ex = block_exclusive_scan<uint32_t>(cnt, red, &total);
         const uint64_t tile_base = tile_roads[t];
@@ -196,7 +204,8 @@ __global__ void __launch_bounds__(TILE_THREADS)
             // walk the hit run that follows the header (rule V8 and hits per layer)
             unsigned long long cnt8 = 0;
             for (uint64_t k = i + 1; k < n_words; ++k) {
-                const uint32_t x = __ldg(words + k);
+                const uint64_t ks = k - tile_start;
+                const uint32_t x = ks < (uint64_t)(TILE_WORDS + HALO) ? sw[ks] : __ldg(words + k);
                 if (w_type(x) != TYPE_HIT) break;
                 const uint32_t l = hit_layer(x);
                 uint32_t c = (uint32_t)(cnt8 >> (8 * l)) & 0xFFu;
