@@ -30,12 +30,15 @@ if ROOT not in sys.path:
 
 METRIC = "fits/sec"
 UNIT = "fits/s"
-# Integer operations one combination needs in the separable evaluation used by
-# the fused kernel: per chi row a two-word add, a funnel shift, a two-op clamp
-# and a multiply-add (6 x 3), plus the compare against the running best.
-OPS_PER_FIT = 19
-# int32 issue peak: 152 SMs x 4 schedulers x 32 lanes x 2.07 GHz
+# Algorithmic integer operations per fitted combination in the direct form of
+# the fit: 36 multiply-adds, 6 offset adds, 6 shifts, 3 clamps, 3 squares,
+# 2 adds and 1 compare.  The fused kernel shares partial sums between
+# combinations and executes fewer, so its fraction of this peak can pass 1.
+OPS_PER_FIT = 57
+# int32 peak: 152 SMs x 128 int32 lanes (ALU and FMA pipes, 64 each) x 2.07 GHz
 N_SM, LANES_PER_SM, SM_MAX_GHZ = 152, 128, 2.07
+# plain-path fit kernel: 8 B of combination record read, 16 B of results written
+PLAIN_BYTES_PER_FIT = 24
 ALU_PEAK_TOPS = N_SM * LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12
 FIT_KERNEL_SRC = os.path.join(ROOT, "paper_1311_0380_gb300", "csrc", "svt_fused.cu")
 TRAFFIC_NOTE = os.path.join(ROOT, "profiles", "fit_persistent_scaled3000.md")
@@ -152,6 +155,13 @@ def workload(args, rank):
     # every rank fits its own batch (independent events): weak scaling
     batch = synth.make_batch(spec, args.events, consts, seed=spec.seed + 7919 * rank)
     return spec, consts, batch
+
+
+def measured_hbm_peak():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0   # fallback figure of the profiling recipe
 
 
 def percentile(xs, p):
@@ -333,7 +343,7 @@ def main():
                 "frac": achieved / ALU_PEAK_TOPS, "traffic": recorded_traffic(),
                 "kernel": "k_fit_persistent", "ops_per_fit": OPS_PER_FIT,
                 "fit_kernel_ms": statistics.mean(fit_ms),
-                "peak_source": "152 SM x 128 int32 lanes x 2.07 GHz (issue bound)"}
+                "peak_source": "derived: 152 SM x 128 int32 lanes x 2.07 GHz"}
 
     # ---- end to end through host buffers (fused)
     e2e = None
@@ -371,15 +381,26 @@ def main():
         assert pst == api.N.STATUS_OK and np.array_equal(prec, rec), "plain path differs"
         evp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
+        evf = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
         for i in range(args.steps):
             flush.fill_(i)
             evp[i][0].record(stream)
-            pp.run(d_words, n_words, d_off, n_events)
+            pp.run(d_words, n_words, d_off, n_events, fit_events=evf[i])
             evp[i][1].record(stream)
         torch.cuda.synchronize()
         pms = [a.elapsed_time(b) for a, b in evp]
+        fms = statistics.mean(a.elapsed_time(b) for a, b in evf) / 1e3
+        hbm_peak = measured_hbm_peak()
+        achieved_gbs = fits_per_step * PLAIN_BYTES_PER_FIT / fms / 1e9
         plain = {"value": fits_per_step / (statistics.mean(pms) / 1e3), "unit": UNIT,
-                 "ms_per_step": statistics.mean(pms)}
+                 "ms_per_step": statistics.mean(pms),
+                 "roofline_fit": {"bound": "hbm", "kernel": "k_fit_plain",
+                                  "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                                  "frac": achieved_gbs / hbm_peak,
+                                  "bytes_per_fit": PLAIN_BYTES_PER_FIT,
+                                  "fit_kernel_ms": fms * 1e3,
+                                  "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}}
         if not args.no_e2e:
             prun = api.HostRunner(pp, stream)
             for _ in range(args.warmup):

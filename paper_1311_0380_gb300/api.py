@@ -228,7 +228,9 @@ class PlainPath:
         self.best = torch.empty(rc * 6, dtype=torch.int32, device=d)
         self.out = torch.empty(rc * 6, dtype=torch.int32, device=d)
 
-    def run(self, words, n_words, event_off, n_events, stream=None):
+    def run(self, words, n_words, event_off, n_events, stream=None, fit_events=None):
+        """All five stages; fit_events = (start, end) torch events recorded
+        around the fit stage on the same stream."""
         c = self.consts
         svt_unpack(words, n_words, event_off, n_events, c.cfg.n_sectors, self.road_cap,
                    self.road_word, self.road_nhit, self.event_road, self.n_roads, self.status,
@@ -236,9 +238,13 @@ class PlainPath:
         svt_combine(self.road_nhit, self.n_roads, self.road_cap, c.cfg, self.comb_cap,
                     self.road_flags, self.comb_off, self.comb_road, self.comb_hits, self.n_combs,
                     self.status, self.ws_combine, stream)
+        if fit_events is not None:
+            fit_events[0].record(stream if stream is not None else torch.cuda.current_stream())
         svt_fit(words, self.road_word, self.road_nhit, self.comb_road, self.comb_hits,
                 self.n_combs, self.comb_cap, c.F, c.q, c.cfg, self.fit_chi2, self.fit_par,
                 self.status, stream)
+        if fit_events is not None:
+            fit_events[1].record(stream if stream is not None else torch.cuda.current_stream())
         svt_select(self.fit_chi2, self.fit_par, self.comb_cap, self.comb_off, self.road_flags,
                    self.n_roads, self.road_cap, c.cfg, self.best, self.status, stream)
         svt_format(self.best, words, self.road_word, self.n_roads, self.road_cap, self.out,
