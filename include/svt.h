@@ -304,6 +304,35 @@ int svt_graph_launch(svt_graph graph, void *stream);
 int svt_graph_destroy(svt_graph graph);
 
 /* ======================================================================
+ * svt_run without a workspace argument.  The paper has no counterpart: this
+ * is for callers of this library that cannot allocate device memory at all
+ * -- a front-end process that only receives device pointers from whatever
+ * owns the GPU, a real-time loop whose rules forbid allocating (with its
+ * latency and failure modes) once data taking has started, or a host program
+ * linked without a device allocator of its own.
+ *
+ * The scratch is one fixed array inside the library, SVT_NOALLOC_SCRATCH_BYTES
+ * (32 MiB) on every GPU that loads the library, held until the process exits.
+ * A batch whose svt_run_workspace_size(n_words, n_events, road_cap, sched)
+ * exceeds it is refused with SVT_ERR_OOM before anything is enqueued (32 MiB
+ * covers, e.g., a 3000-event batch of 3.5 million words and 190 thousand
+ * roads).  The first call on a device looks up the array's device address;
+ * make that first call before any stream capture.  Every call on a device
+ * shares the array and it keeps the last call's contents; each call
+ * re-initialises everything it reads, but calls whose work overlaps on the
+ * GPU (different streams, or different host threads) race on it: issue them
+ * on one stream or otherwise one after another.  Nothing is allocated or
+ * freed.  Arguments and results are those of svt_run.
+ * ====================================================================== */
+#define SVT_NOALLOC_SCRATCH_BYTES ((size_t)32 << 20)
+size_t svt_run_noalloc_scratch_bytes(void);
+int svt_run_noalloc(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_off,
+                    uint64_t n_events, const int16_t *d_F, const int16_t *d_q,
+                    const svt_config *cfg, uint64_t road_cap, uint32_t *d_out,
+                    uint32_t *d_event_road, uint64_t *d_counts, uint64_t *d_status,
+                    const svt_schedule *sched, void *stream);
+
+/* ======================================================================
  * Serving loop (the single-GPU form of the paper's trigger-node loop,
  * Sec. 3 and Sec. 4.2: data in -> GPU -> data out), with continuous
  * batching.  Events are submitted by reference -- a pointer to the event's

@@ -92,6 +92,9 @@ SIGNATURES = {
                                         _vp, _vp, _vp, _vp, _sz, _schp, ctypes.POINTER(_vp)]),
     "svt_graph_launch": (ctypes.c_int, [_vp, _vp]),
     "svt_graph_destroy": (ctypes.c_int, [_vp]),
+    "svt_run_noalloc_scratch_bytes": (_sz, []),
+    "svt_run_noalloc": (ctypes.c_int, [_vp, _u64, _vp, _u64, _vp, _vp, _cfgp, _u64, _vp, _vp, _vp,
+                                       _vp, _schp, _vp]),
     "svt_timer_create": (ctypes.c_int, [ctypes.POINTER(_vp)]),
     "svt_timer_destroy": (ctypes.c_int, [_vp]),
     "svt_timer_fit_ms": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_float)]),

@@ -104,6 +104,18 @@ def svt_run(words, n_words, event_off, n_events, F, q, cfg, road_cap, out, event
                              _stream(stream)), "svt_run")
 
 
+def svt_run_noalloc(words, n_words, event_off, n_events, F, q, cfg, road_cap, out, event_road,
+                    counts, status, sched=None, stream=None):
+    """svt_run for callers that cannot allocate device memory: the scratch is
+    a fixed array inside libsvt.so (svt_run_noalloc_scratch_bytes() per GPU),
+    shared by every call on that GPU, so calls must not overlap on the device."""
+    N.check(N.load().svt_run_noalloc(_p(words), n_words, _p(event_off), n_events, _p(F), _p(q),
+                                     ctypes.byref(cfg), road_cap, _p(out), _p(event_road),
+                                     _p(counts), _p(status),
+                                     ctypes.byref(sched) if sched is not None else None,
+                                     _stream(stream)), "svt_run_noalloc")
+
+
 class FitTimer:
     """CUDA events recorded by svt_run around its persistent fit kernel."""
 
