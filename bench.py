@@ -56,6 +56,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--no-tune", action="store_true", help="use the default schedule")
     ap.add_argument("--rows", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--bps", type=int, default=0)
@@ -298,6 +299,13 @@ def main():
     timer = api.FitTimer()
     flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)   # 256 MB > 129 MB L2
     stream = torch.cuda.current_stream()
+    tuned = None
+    if not args.no_tune and not (args.warps or args.rows or args.bps):
+        from paper_1311_0380_gb300 import autotune
+        sch, tms = autotune.tuned_schedule(fused, d_words, n_words, d_off, n_events, cache=None)
+        fused.sched = sch
+        tuned = {f: getattr(sch, f) for f, _ in api.SvtSchedule._fields_}
+        tuned["tuning_ms_per_run"] = tms
 
     def barrier():
         if world > 1:
@@ -436,7 +444,9 @@ def main():
                        "fits_per_step": fits_per_step, "roads_passing": passing,
                        "sectors": spec.n_sectors, "max_comb": spec.max_comb,
                        "l2": "flushed between steps (256 MB write)",
-                       "schedule": {"warps": args.warps, "blocks_per_sm": args.bps, "rows": args.rows}},
+                       "schedule": tuned if tuned else {"warps": args.warps,
+                                                        "blocks_per_sm": args.bps,
+                                                        "rows": args.rows}},
             "events_per_s": world * n_events * args.steps / (total_ms / 1e3),
             "latency_us": {"p50": percentile([m * 1e3 for m in step_ms], 50),
                            "p99": percentile([m * 1e3 for m in step_ms], 99)},

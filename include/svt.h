@@ -289,6 +289,20 @@ int svt_run_sized(const uint32_t *d_words, uint64_t max_words, const uint64_t *d
                   void *d_workspace, size_t workspace_bytes, const svt_schedule *sched,
                   void *stream);
 
+/* Schedule autotuner: runs svt_run on one device-resident batch for every
+ * schedule of {4, 8, 16} warps per block x {8, 16, 32, 64} rows per item x
+ * {1, 2, 4, 8} roads per chunk x {1024, 4096, 16384} small_max (blocks per SM
+ * as many as fit), one warm-up and `reps` timed runs each (CUDA events on
+ * `stream`), and returns the fastest schedule and its mean time per run.
+ * Synchronises the stream.  Buffers as for svt_run; on return d_out and
+ * d_status hold a valid result of the batch (every schedule gives the same
+ * bits). */
+int svt_autotune(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_off,
+                 uint64_t n_events, const int16_t *d_F, const int16_t *d_q, const svt_config *cfg,
+                 uint64_t road_cap, uint32_t *d_out, uint64_t *d_status, void *d_workspace,
+                 size_t workspace_bytes, uint32_t reps, svt_schedule *best, float *best_ms,
+                 void *stream);
+
 /* CUDA graph of svt_run_sized's launch sequence, captured once on a private
  * stream (same arguments).  svt_graph_launch replays it on `stream`; every
  * replay reads the then-current device contents of d_sizes, d_words and

@@ -90,6 +90,8 @@ SIGNATURES = {
                                      _vp, _vp, _vp, _sz, _schp, _vp]),
     "svt_graph_create": (ctypes.c_int, [_vp, _u64, _vp, _u64, _vp, _vp, _vp, _cfgp, _u64, _vp,
                                         _vp, _vp, _vp, _vp, _sz, _schp, ctypes.POINTER(_vp)]),
+    "svt_autotune": (ctypes.c_int, [_vp, _u64, _vp, _u64, _vp, _vp, _cfgp, _u64, _vp, _vp, _vp,
+                                    _sz, _u32, _schp, ctypes.POINTER(ctypes.c_float), _vp]),
     "svt_graph_launch": (ctypes.c_int, [_vp, _vp]),
     "svt_graph_destroy": (ctypes.c_int, [_vp]),
     "svt_run_noalloc_scratch_bytes": (_sz, []),

@@ -424,6 +424,64 @@ int svt_graph_create(const uint32_t *d_words, uint64_t max_words, const uint64_t
     return SVT_OK;
 }
 
+int svt_autotune(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_off,
+                 uint64_t n_events, const int16_t *d_F, const int16_t *d_q, const svt_config *cfg,
+                 uint64_t road_cap, uint32_t *d_out, uint64_t *d_status, void *d_workspace,
+                 size_t workspace_bytes, uint32_t reps, svt_schedule *best, float *best_ms,
+                 void *stream) {
+    if (!best || !best_ms || reps < 1 || reps > 100) return SVT_ERR_BAD_ARG;
+    static const uint32_t kWarps[] = {4, 8, 16};
+    static const uint32_t kRows[] = {8, 16, 32, 64};
+    static const uint32_t kChunk[] = {1, 2, 4, 8};
+    static const uint32_t kSmall[] = {1024, 4096, 16384};
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return SVT_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return SVT_ERR_CUDA;
+    }
+    float best_t = 3.4e38f;
+    svt_schedule best_s{0, 0, 0, 0, 0};
+    int rc = SVT_OK;
+    for (uint32_t w : kWarps)
+        for (uint32_t r : kRows)
+            for (uint32_t c : kChunk)
+                for (uint32_t m : kSmall) {
+                    const svt_schedule sc{w, 0, r, c, m};
+                    rc = svt_run(d_words, n_words, d_event_off, n_events, d_F, d_q, cfg, road_cap,
+                                 d_out, nullptr, nullptr, d_status, d_workspace, workspace_bytes,
+                                 &sc, nullptr, stream);   // warm-up
+                    if (rc != SVT_OK) goto done;
+                    if (cudaEventRecord(e0, st) != cudaSuccess) { rc = SVT_ERR_CUDA; goto done; }
+                    for (uint32_t k = 0; k < reps; ++k) {
+                        rc = svt_run(d_words, n_words, d_event_off, n_events, d_F, d_q, cfg,
+                                     road_cap, d_out, nullptr, nullptr, d_status, d_workspace,
+                                     workspace_bytes, &sc, nullptr, stream);
+                        if (rc != SVT_OK) goto done;
+                    }
+                    if (cudaEventRecord(e1, st) != cudaSuccess ||
+                        cudaEventSynchronize(e1) != cudaSuccess) {
+                        rc = SVT_ERR_CUDA;
+                        goto done;
+                    }
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms /= (float)reps;
+                    if (ms < best_t) {
+                        best_t = ms;
+                        best_s = sc;
+                    }
+                }
+done:
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SVT_OK) return rc;
+    *best = best_s;
+    *best_ms = best_t;
+    return SVT_OK;
+}
+
 int svt_graph_launch(svt_graph g, void *stream) {
     if (!g) return SVT_ERR_BAD_ARG;
     return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? SVT_OK : SVT_ERR_CUDA;

@@ -29,24 +29,26 @@ __device__ __forceinline__ void load8(const uint32_t *__restrict__ words, uint64
     }
 }
 
-// first index e in [0, n) with off[e] >= v (off assumed non-decreasing)
-__device__ __forceinline__ uint64_t lower_bound64(const uint64_t *__restrict__ off, uint64_t n,
-                                                  uint64_t v) {
+// First index e in [0, n) with off[e] >= v (off assumed non-decreasing),
+// searched cooperatively by a warp (every lane gets the result): 32 probes per
+// round, so log32(n) dependent loads instead of log2(n).
+__device__ __forceinline__ uint64_t warp_lower_bound64(const uint64_t *__restrict__ off,
+                                                       uint64_t n, uint64_t v, int lane) {
     uint64_t lo = 0, hi = n;
-    while (lo < hi) {
-        uint64_t mid = lo + (hi - lo) / 2;
-        if (__ldg(off + mid) < v)
-            lo = mid + 1;
-        else
-            hi = mid;
+    while (hi > lo) {
+        const uint64_t step = (hi - lo + 31) / 32;
+        const uint64_t p = lo + (uint64_t)lane * step;
+        const bool lt = p < hi && __ldg(off + p) < v;
+        const uint32_t k = __popc(__ballot_sync(0xffffffffu, lt));
+        if (k == 0) {
+            hi = lo;
+        } else {
+            const uint64_t pk = lo + (uint64_t)(k - 1) * step;
+            hi = min(pk + step, hi);
+            lo = pk + 1;
+        }
     }
     return lo;
-}
-
-__device__ __forceinline__ bool is_event_start(const uint64_t *__restrict__ off, uint64_t n,
-                                               uint64_t i) {
-    uint64_t e = lower_bound64(off, n, i);
-    return e < n && __ldg(off + e) == i;
 }
 
 // Batch sizes for the launch sequence: the given values, or -- when `sizes`
@@ -99,8 +101,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
             } else if (ty == TYPE_BAD) {
                 report(status, i, SVT_ERR_BAD_TYPE);                                    // V3
             } else if (ty == TYPE_EVENT) {
-                if (!is_event_start(event_off, n_events, i))
-                    report(status, i, SVT_ERR_BAD_TYPE);                                // V2
+                // V2 (an event header must start an event) is checked below by the warp
             } else {
                 // V4 and V7 also fire on an event's first word, where V1 already
                 // reports the same word with the smallest code, so the key is unchanged.
@@ -109,6 +110,20 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 if (hit_layer(x) > 5) report(status, i, SVT_ERR_BAD_LAYER);                  // V6
                 if (i > 0 && w_type(p) == TYPE_HIT && hit_layer(p) > hit_layer(x))
                     report(status, i, SVT_ERR_UNSORTED);                                     // V7
+            }
+        }
+        // V2: every event-header word must sit at an event offset
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int j = 0; j < TILE_PER_THREAD; ++j) {
+            uint32_t bal = __ballot_sync(0xffffffffu, base + j < n_words && w_type(w[j]) == TYPE_EVENT);
+            while (bal) {
+                const int src = __ffs(bal) - 1;
+                const uint64_t i = __shfl_sync(0xffffffffu, base + j, src);
+                const uint64_t e = warp_lower_bound64(event_off, n_events, i, lane);
+                const bool start = e < n_events && __ldg(event_off + e) == i;
+                if (lane == src && !start) report(status, i, SVT_ERR_BAD_TYPE);
+                bal &= bal - 1;
             }
         }
         uint32_t total;
@@ -167,9 +182,13 @@ __global__ void __launch_bounds__(TILE_THREADS)
         const uint64_t tile_start = t * TILE_WORDS;
         const uint64_t tile_end = min(tile_start + TILE_WORDS, n_words);
         const uint64_t base = tile_start + (uint64_t)threadIdx.x * TILE_PER_THREAD;
-        if (threadIdx.x == 0) {
-            ev_range[0] = lower_bound64(event_off, n_events, tile_start);
-            ev_range[1] = lower_bound64(event_off, n_events, tile_end);
+        if (threadIdx.x < 32) {
+            const uint64_t lo = warp_lower_bound64(event_off, n_events, tile_start, threadIdx.x);
+            const uint64_t hi = warp_lower_bound64(event_off, n_events, tile_end, threadIdx.x);
+            if (threadIdx.x == 0) {
+                ev_range[0] = lo;
+                ev_range[1] = hi;
+            }
         }
         uint32_t w[TILE_PER_THREAD];
         load8(words, base, n_words, w);
