@@ -79,8 +79,10 @@ def test_autotuner_picks_a_schedule_that_stays_bit_exact(tmp_path):
     cache = str(tmp_path / "sched.json")
     sch, ms = autotune.tuned_schedule(fp, dw, len(b.words), de, b.n_events, cache=cache, reps=1)
     assert ms > 0 and sch.warps_per_block in (4, 8, 16) and sch.rows_per_item in (8, 16, 32, 64)
-    st, got, _ = fp.result()
-    assert st == key and np.array_equal(got, rec)       # the tuner's last run is a valid result
+    # the tuner's last run leaves a valid result (it passes no counts buffer)
+    st = int(api.u64(fp.status)[0])
+    got = api.u32(fp.out[: b.total_roads * 6]).reshape(-1, 6)
+    assert st == key and np.array_equal(got, rec)
     fp.sched = sch
     fp.run(dw, len(b.words), de, b.n_events)
     torch.cuda.synchronize()
