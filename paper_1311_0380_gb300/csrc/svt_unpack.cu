@@ -164,23 +164,40 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
+// K2, data-parallel per tile:
+//  * the tile is staged in shared memory with 16 words before it and 100
+//    after it (a valid road has at most 96 hits, so a road that starts in the
+//    tile ends in the staged range);
+//  * a block scan gives every road header its index; each hit word adds one to
+//    its road's counter of its layer (shared-memory atomics, 8 bits per
+//    layer);
+//  * rule V8 is checked per word on the staged window: a hit whose 16
+//    predecessors are hits of the same layer is the 17th (or later) of a
+//    contiguous block.  For the smallest status key this matches counting
+//    over the run: the first out-of-order hit of a run is an UNSORTED word
+//    that precedes any later, non-contiguous 17th hit;
+//  * one thread per road then writes the road's outputs.
 __global__ void __launch_bounds__(TILE_THREADS)
     k_unpack_roads(const uint32_t *__restrict__ words, const uint64_t *__restrict__ event_off,
                    const Dims *__restrict__ dims, const uint32_t *__restrict__ tile_roads,
                    uint64_t road_cap, uint32_t *road_word, uint32_t *road_nhit,
                    uint32_t *event_road, const svt_config cfg, const FusedRoads fr,
                    uint64_t *counts, unsigned long long *status) {
-    constexpr int HALO = 100;   // covers the hits of a valid road that starts in the tile
+    constexpr int FRONT = 16, BACK = 100;
+    constexpr uint32_t SENTINEL = 0xC0000000u;   // an event-header word: ends every run
     __shared__ uint32_t red[TILE_THREADS / 32 + 1];
     __shared__ unsigned long long red64[TILE_THREADS / 32 + 1];
-    __shared__ uint32_t pre[TILE_WORDS];
-    __shared__ uint32_t sw[TILE_WORDS + HALO];
+    __shared__ uint32_t sw[FRONT + TILE_WORDS + BACK];
+    __shared__ unsigned long long cnt[TILE_WORDS];    // per road of the tile: 8 bits per layer
+    __shared__ uint16_t hdr_pos[TILE_WORDS];          // tile position of each road header
     __shared__ uint64_t ev_range[2];
+    __shared__ int last_nonhit;
     const uint64_t n_words = dims->n_words, n_events = dims->n_events;
     const uint64_t T = n_tiles(n_words);
     for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
         const uint64_t tile_start = t * TILE_WORDS;
         const uint64_t tile_end = min(tile_start + TILE_WORDS, n_words);
+        const int tile_len = (int)(tile_end - tile_start);
         const uint64_t base = tile_start + (uint64_t)threadIdx.x * TILE_PER_THREAD;
         if (threadIdx.x < 32) {
             const uint64_t lo = warp_lower_bound64(event_off, n_events, tile_start, threadIdx.x);
@@ -188,60 +205,118 @@ __global__ void __launch_bounds__(TILE_THREADS)
             if (threadIdx.x == 0) {
                 ev_range[0] = lo;
                 ev_range[1] = hi;
+                last_nonhit = -1;
             }
         }
         uint32_t w[TILE_PER_THREAD];
         load8(words, base, n_words, w);
-        uint32_t cnt = 0;
+        uint32_t nh = 0;
 #pragma unroll
         for (int j = 0; j < TILE_PER_THREAD; ++j) {
-            cnt += (base + j < n_words && w_type(w[j]) == TYPE_ROAD) ? 1u : 0u;
-            sw[threadIdx.x * TILE_PER_THREAD + j] = w[j];
+            const int p = threadIdx.x * TILE_PER_THREAD + j;
+            const bool in = p < tile_len;
+            sw[FRONT + p] = in ? w[j] : SENTINEL;
+            nh += (in && w_type(w[j]) == TYPE_ROAD) ? 1u : 0u;
         }
-        if (threadIdx.x < HALO) {
-            const uint64_t k = tile_start + TILE_WORDS + threadIdx.x;
-            sw[TILE_WORDS + threadIdx.x] = k < n_words ? __ldg(words + k) : 0xFFFFFFFFu;
+        if (threadIdx.x < FRONT) {
+            const int64_t k = (int64_t)tile_start - FRONT + threadIdx.x;
+            sw[threadIdx.x] = k >= 0 ? __ldg(words + k) : SENTINEL;
         }
-        uint32_t total;
-        const uint32_t ex = block_exclusive_scan<uint32_t>(cnt, red, &total);
+        if (threadIdx.x < BACK) {
+            const uint64_t k = tile_end + threadIdx.x;
+            sw[FRONT + TILE_WORDS + threadIdx.x] = k < n_words ? __ldg(words + k) : SENTINEL;
+        }
+        uint32_t n_roads_tile;
+        const uint32_t ex = block_exclusive_scan<uint32_t>(nh, red, &n_roads_tile);   // syncs
         const uint64_t tile_base = tile_roads[t];
-        uint32_t run = ex;
-        uint32_t items_sum = 0, big_sum = 0;
-        unsigned long long comb_sum = 0;
+        // road headers: positions; counters cleared
+        {
+            uint32_t r = ex;
 #pragma unroll
-        for (int j = 0; j < TILE_PER_THREAD; ++j) {
-            const uint64_t i = base + j;
-            pre[threadIdx.x * TILE_PER_THREAD + j] = run;
-            if (i >= n_words || w_type(w[j]) != TYPE_ROAD) continue;
-            const uint64_t r = tile_base + run;
-            run += 1;
-            if (r >= road_cap) {
-                report(status, i, SVT_ERR_OOM);
-                continue;
-            }
-            if (road_word) road_word[r] = (uint32_t)i;
-            // walk the hit run that follows the header (rule V8 and hits per layer)
-            unsigned long long cnt8 = 0;
-            for (uint64_t k = i + 1; k < n_words; ++k) {
-                const uint64_t ks = k - tile_start;
-                const uint32_t x = ks < (uint64_t)(TILE_WORDS + HALO) ? sw[ks] : __ldg(words + k);
-                if (w_type(x) != TYPE_HIT) break;
-                const uint32_t l = hit_layer(x);
-                uint32_t c = (uint32_t)(cnt8 >> (8 * l)) & 0xFFu;
-                if (c < 32) {
-                    cnt8 += 1ull << (8 * l);
-                    if (c + 1 == MAX_HITS + 1) report(status, k, SVT_ERR_TOO_MANY_HITS);
+            for (int j = 0; j < TILE_PER_THREAD; ++j) {
+                const int p = threadIdx.x * TILE_PER_THREAD + j;
+                if (p < tile_len && w_type(w[j]) == TYPE_ROAD) {
+                    hdr_pos[r] = (uint16_t)p;
+                    cnt[r] = 0ull;
+                    r += 1;
                 }
             }
+        }
+        __syncthreads();
+        // hits: count into their road, check V8, note the tile's last non-hit word
+        {
+            int r = (int)ex - 1;   // local road of the latest header before this thread's words
+            int my_last_nonhit = -1;
+#pragma unroll
+            for (int j = 0; j < TILE_PER_THREAD; ++j) {
+                const int p = threadIdx.x * TILE_PER_THREAD + j;
+                if (p >= tile_len) break;
+                const uint32_t x = w[j];
+                const uint32_t ty = w_type(x);
+                if (ty == TYPE_ROAD) r += 1;
+                if (ty != TYPE_HIT) {
+                    my_last_nonhit = p;
+                    continue;
+                }
+                const uint32_t l = hit_layer(x);
+                if (r >= 0) atomicAdd(&cnt[r], 1ull << (8 * l));
+                bool run16 = true;   // the 16 words before p are hits of layer l
+#pragma unroll
+                for (int d = 1; d <= 16; ++d) {
+                    const uint32_t y = sw[FRONT + p - d];
+                    run16 = run16 && w_type(y) == TYPE_HIT && hit_layer(y) == l;
+                }
+                if (run16) report(status, tile_start + p, SVT_ERR_TOO_MANY_HITS);
+            }
+            if (my_last_nonhit >= 0) atomicMax(&last_nonhit, my_last_nonhit);
+        }
+        __syncthreads();
+        // hits after the tile that continue the tile's last road
+        if (n_roads_tile > 0 && last_nonhit == (int)hdr_pos[n_roads_tile - 1]) {
+            const int r = (int)n_roads_tile - 1;
+            if (threadIdx.x < 32) {
+                // length of the run of hit words at the start of the back halo
+                int run = 0;
+                for (int c0 = 0; c0 < BACK; c0 += 32) {
+                    const int h = c0 + threadIdx.x;
+                    const bool hit = h < BACK && w_type(sw[FRONT + tile_len + h]) == TYPE_HIT &&
+                                     tile_len + h < FRONT + TILE_WORDS + BACK - FRONT;
+                    const uint32_t nb = __ballot_sync(0xffffffffu, !hit);
+                    if (nb) {
+                        run = c0 + __ffs(nb) - 1;
+                        break;
+                    }
+                    run = c0 + 32;
+                }
+                run = min(run, BACK);
+                for (int h = threadIdx.x; h < run; h += 32) {
+                    const uint32_t l = hit_layer(sw[FRONT + tile_len + h]);
+                    atomicAdd(&cnt[r], 1ull << (8 * l));
+                }
+            }
+        }
+        __syncthreads();
+        // one thread per road of the tile
+        uint32_t items_sum = 0, big_sum = 0;
+        unsigned long long comb_sum = 0;
+        for (uint32_t rl = threadIdx.x; rl < n_roads_tile; rl += TILE_THREADS) {
+            const uint64_t r = tile_base + rl;
+            const int p = hdr_pos[rl];
+            if (r >= road_cap) {
+                report(status, tile_start + p, SVT_ERR_OOM);
+                continue;
+            }
+            const unsigned long long c8 = cnt[rl];
             uint32_t packed = 0;
 #pragma unroll
             for (int l = 0; l < N_LAYERS; ++l) {
-                uint32_t c = (uint32_t)(cnt8 >> (8 * l)) & 0xFFu;
+                const uint32_t c = (uint32_t)(c8 >> (8 * l)) & 0xFFu;
                 packed |= (c > MAX_HITS ? (uint32_t)MAX_HITS : c) << (5 * l);
             }
+            if (road_word) road_word[r] = (uint32_t)(tile_start + p);
             if (road_nhit) road_nhit[r] = packed;
             if (fr.desc) {
-                const RoadDesc d = make_road_desc((uint32_t)i, packed, w[j], cfg);
+                const RoadDesc d = make_road_desc((uint32_t)(tile_start + p), packed, sw[FRONT + p], cfg);
                 const uint32_t it = road_big_items(d, fr);
                 fr.desc[r] = d;
                 items_sum += it;
@@ -249,13 +324,21 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 comb_sum += d.a.w;
             }
         }
-        __syncthreads();
-        // first road of every event that starts inside this tile
+        // first road of every event that starts inside this tile: the number
+        // of road headers before the event's first word
         const uint64_t e_lo = ev_range[0], e_hi = ev_range[1];
         for (uint64_t e = e_lo + threadIdx.x; e < e_hi; e += TILE_THREADS) {
-            const uint64_t s = __ldg(event_off + e);
-            if (s >= tile_start && s < tile_end)
-                event_road[e] = (uint32_t)(tile_base + pre[s - tile_start]);
+            const uint64_t s0 = __ldg(event_off + e);
+            if (s0 >= tile_start && s0 < tile_end) {
+                // roads of the tile whose header lies before s0 (hdr_pos is increasing)
+                const int ps = (int)(s0 - tile_start);
+                uint32_t lo = 0, hi = n_roads_tile;
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if ((int)hdr_pos[mid] < ps) lo = mid + 1; else hi = mid;
+                }
+                event_road[e] = (uint32_t)(tile_base + lo);
+            }
         }
         if (fr.desc) {
             uint32_t it_total, big_total;
