@@ -169,8 +169,9 @@ __global__ void __launch_bounds__(1024)
 //    after it (a valid road has at most 96 hits, so a road that starts in the
 //    tile ends in the staged range);
 //  * a block scan gives every road header its index; each hit word adds one to
-//    its road's counter of its layer (shared-memory atomics, 8 bits per
-//    layer);
+//    its road's counter of its layer (shared-memory atomics on the packed
+//    5-bits-per-layer word; a field can only overflow with more than 31 hits of
+//    one layer, which rule V8 already rejects);
 //  * rule V8 is checked per word on the staged window: a hit whose 16
 //    predecessors are hits of the same layer is the 17th (or later) of a
 //    contiguous block.  For the smallest status key this matches counting
@@ -188,7 +189,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
     __shared__ uint32_t red[TILE_THREADS / 32 + 1];
     __shared__ unsigned long long red64[TILE_THREADS / 32 + 1];
     __shared__ uint32_t sw[FRONT + TILE_WORDS + BACK];
-    __shared__ unsigned long long cnt[TILE_WORDS];    // per road of the tile: 8 bits per layer
+    __shared__ uint32_t cnt[TILE_WORDS];              // per road of the tile: 5 bits per layer
     __shared__ uint16_t hdr_pos[TILE_WORDS];          // tile position of each road header
     __shared__ uint64_t ev_range[2];
     __shared__ int last_nonhit;
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 const int p = threadIdx.x * TILE_PER_THREAD + j;
                 if (p < tile_len && w_type(w[j]) == TYPE_ROAD) {
                     hdr_pos[r] = (uint16_t)p;
-                    cnt[r] = 0ull;
+                    cnt[r] = 0u;
                     r += 1;
                 }
             }
@@ -259,14 +260,19 @@ __global__ void __launch_bounds__(TILE_THREADS)
                     continue;
                 }
                 const uint32_t l = hit_layer(x);
-                if (r >= 0) atomicAdd(&cnt[r], 1ull << (8 * l));
-                bool run16 = true;   // the 16 words before p are hits of layer l
+                if (r >= 0) atomicAdd(&cnt[r], 1u << (5 * l));
+                // the 16 words before p are hits of layer l (checked in full only
+                // when the 16th one back is)
+                const uint32_t y16 = sw[FRONT + p - 16];
+                if (w_type(y16) == TYPE_HIT && hit_layer(y16) == l) {
+                    bool run16 = true;
 #pragma unroll
-                for (int d = 1; d <= 16; ++d) {
-                    const uint32_t y = sw[FRONT + p - d];
-                    run16 = run16 && w_type(y) == TYPE_HIT && hit_layer(y) == l;
+                    for (int d = 1; d < 16; ++d) {
+                        const uint32_t y = sw[FRONT + p - d];
+                        run16 = run16 && w_type(y) == TYPE_HIT && hit_layer(y) == l;
+                    }
+                    if (run16) report(status, tile_start + p, SVT_ERR_TOO_MANY_HITS);
                 }
-                if (run16) report(status, tile_start + p, SVT_ERR_TOO_MANY_HITS);
             }
             if (my_last_nonhit >= 0) atomicMax(&last_nonhit, my_last_nonhit);
         }
@@ -291,7 +297,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 run = min(run, BACK);
                 for (int h = threadIdx.x; h < run; h += 32) {
                     const uint32_t l = hit_layer(sw[FRONT + tile_len + h]);
-                    atomicAdd(&cnt[r], 1ull << (8 * l));
+                    atomicAdd(&cnt[r], 1u << (5 * l));
                 }
             }
         }
@@ -306,13 +312,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 report(status, tile_start + p, SVT_ERR_OOM);
                 continue;
             }
-            const unsigned long long c8 = cnt[rl];
-            uint32_t packed = 0;
-#pragma unroll
-            for (int l = 0; l < N_LAYERS; ++l) {
-                const uint32_t c = (uint32_t)(c8 >> (8 * l)) & 0xFFu;
-                packed |= (c > MAX_HITS ? (uint32_t)MAX_HITS : c) << (5 * l);
-            }
+            const uint32_t packed = cnt[rl];
             if (road_word) road_word[r] = (uint32_t)(tile_start + p);
             if (road_nhit) road_nhit[r] = packed;
             if (fr.desc) {
