@@ -63,16 +63,41 @@ def parse_args():
     return ap.parse_args()
 
 
-def dist_setup(args):
+def dist_setup(args, backend=None):
+    """One process per GPU, as launched by torchrun: rank, world size and
+    local rank come from the environment.  The reference arm runs on host
+    cores only, so it joins over gloo."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch
         import torch.distributed as dist
-        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend is None:
+            gpu = torch.cuda.is_available() and args.impl != "reference"
+            backend = "nccl" if gpu else "gloo"
         dist.init_process_group(backend=backend)
     return world, rank, local
+
+
+def dist_teardown(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def reduce_over_ranks(world, ms, units, device="cpu"):
+    """Whole-job figures: the slowest rank's time and the sum of every rank's
+    units (each rank fits its own batch, so their fit counts differ)."""
+    if world == 1:
+        return float(ms), [int(u) for u in units]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([int(x) for x in units], dtype=torch.int64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), [int(x) for x in u.tolist()]
 
 
 def file_sha(path):
@@ -282,6 +307,7 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+        dist_teardown(world)
         return
     import torch
     from paper_1311_0380_gb300 import api
@@ -335,13 +361,9 @@ def main():
         torch.cuda.synchronize()
     barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * fits_per_step * args.steps / (total_ms / 1e3)
+    total_ms, (job_fits, job_events) = reduce_over_ranks(
+        world, sum(step_ms), [fits_per_step * args.steps, n_events * args.steps], dev)
+    value = job_fits / (total_ms / 1e3)
     clock_summary = clocks.summary()
 
     # ---- roofline of the persistent fit kernel (ALU / issue bound)
@@ -365,6 +387,7 @@ def main():
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
         h2d = d2h = 0
+        barrier()
         for i in range(args.steps):
             flush.fill_(i)
             evs[i][0].record(stream)
@@ -374,7 +397,10 @@ def main():
         assert st == api.N.STATUS_OK
         assert np.array_equal(out, rec)
         lat_fused = [a.elapsed_time(b) * 1e3 for a, b in evs]   # us
-        e2e = {"value": fits_per_step / (statistics.mean(lat_fused) / 1e6), "unit": UNIT,
+        barrier()
+        e2e_ms, (e2e_fits,) = reduce_over_ranks(world, sum(lat_fused) / 1e3,
+                                                [fits_per_step * args.steps], dev)
+        e2e = {"value": e2e_fits / (e2e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "p50_us": percentile(lat_fused, 50), "p99_us": percentile(lat_fused, 99)}
 
@@ -442,12 +468,13 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": f"{args.workload}-{n_events}ev", "events": n_events, "roads": R,
                        "fits_per_step": fits_per_step, "roads_passing": passing,
+                       "job_fits_per_step": job_fits // args.steps,
                        "sectors": spec.n_sectors, "max_comb": spec.max_comb,
                        "l2": "flushed between steps (256 MB write)",
                        "schedule": tuned if tuned else {"warps": args.warps,
                                                         "blocks_per_sm": args.bps,
                                                         "rows": args.rows}},
-            "events_per_s": world * n_events * args.steps / (total_ms / 1e3),
+            "events_per_s": job_events / (total_ms / 1e3),
             "latency_us": {"p50": percentile([m * 1e3 for m in step_ms], 50),
                            "p99": percentile([m * 1e3 for m in step_ms], 99)},
             "e2e": e2e, "plain": plain, "roofline": roofline, "cpu_baseline": cpu,
@@ -456,9 +483,7 @@ def main():
             "gpu_launches": api.FUSED_LAUNCHES_PER_RUN * args.steps,
         }
         print(json.dumps(line))
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    dist_teardown(world)
 
 
 if __name__ == "__main__":
