@@ -235,12 +235,13 @@ __device__ __forceinline__ int32_t hi_word(long long v) {
 // Best key over rows [a_lo, a_hi) of the road, reduced over the warp.  The key
 // is (chi2 << 32) | (row << 9) | column; since columns < NB < 512 its low word
 // orders exactly like the combination index c = row * NB + column.
-// NOCLAMP (valid when chi2_cut < 32767^2): the squares are summed unclamped in
-// 64 bits; any combination with a chi component of magnitude 32767 or more
-// then exceeds the cut under both readings, and below that the clamp is the
-// identity, so pass/fail, chi2 of passing combinations and the argmin are
-// unchanged.
-template <bool NOCLAMP>
+// GUARDED (valid when chi2_cut < 32767^2): a combination with a chi component
+// of magnitude 32767 or more cannot pass, clamped or not.  One range test keeps
+// only combinations with -32768 <= y_k <= 32767 for all three components; for
+// those the sum of the squares is below 3 * 2^30 < 2^32 and is formed exactly
+// in 32 bits, and the clamp changes no square that could still pass.
+// Pass/fail, chi2 of passing combinations and the argmin are unchanged.
+template <bool GUARDED>
 __device__ __forceinline__ unsigned long long eval_rows(WarpSmem &sm, const Geo &g, uint32_t a_lo,
                                                         uint32_t a_hi, uint32_t qsh,
                                                         uint32_t init_chi, int lane) {
@@ -260,7 +261,11 @@ __device__ __forceinline__ unsigned long long eval_rows(WarpSmem &sm, const Geo 
             if (b < NB) {
                 const long long *t = sm.T + (top * MAX_HITS + is) * 3;
                 const longlong2 s01 = sm.S[bp][0], s2 = sm.S[bp][1];
-                const long long B3 = t[0] + s01.x, B4 = t[1] + s01.y, B5 = t[2] + s2.x;
+                // GUARDED: the column terms carry +32768 in the high word, so the
+                // inner loop sees g_k = y_k + 32768 (mod 2^32) directly
+                const long long bias = GUARDED ? (32768LL << 32) : 0LL;
+                const long long B3 = t[0] + s01.x + bias, B4 = t[1] + s01.y + bias,
+                                B5 = t[2] + s2.x + bias;
                 uint32_t a_end = ae;
                 if (ae == NA && (NA - 1) * NB + b >= C_eval) a_end = ae - 1;
                 uint32_t bchi = init_chi, ba = 0;
@@ -272,12 +277,16 @@ __device__ __forceinline__ unsigned long long eval_rows(WarpSmem &sm, const Geo 
                     const int32_t y3 = hi_word(v01.x + B3);
                     const int32_t y4 = hi_word(v01.y + B4);
                     const int32_t y5 = hi_word(v2.x + B5);
-                    if (NOCLAMP) {
-                        unsigned long long v = (unsigned long long)((long long)y3 * y3);
-                        v += (unsigned long long)((long long)y4 * y4);
-                        v += (unsigned long long)((long long)y5 * y5);
-                        if (v < (unsigned long long)bchi) {
-                            bchi = (uint32_t)v;
+                    if (GUARDED) {
+                        const uint32_t g3 = (uint32_t)y3, g4 = (uint32_t)y4, g5 = (uint32_t)y5;
+                        // g_k < 2^16 for all three <=> -32768 <= y_k <= 32767; then
+                        // sum (g_k - 32768)^2 = sum g_k^2 - 2^16 sum g_k + 3 * 2^30
+                        // holds exactly in 32-bit arithmetic
+                        const uint32_t range = g3 | g4 | g5;
+                        const uint32_t chi2 = g3 * g3 + g4 * g4 + g5 * g5 + (3u << 30) -
+                                              ((g3 + g4 + g5) << 16);
+                        if (range < 65536u && chi2 < bchi) {
+                            bchi = chi2;
                             ba = a;
                         }
                     } else {
@@ -350,7 +359,7 @@ __device__ __forceinline__ void format_road(WarpSmem &sm, const RoadDesc &D, con
 }
 
 // K4: persistent fit / cut / select / format
-template <bool NOCLAMP>
+template <bool GUARDED>
 __global__ void __launch_bounds__(512, 2)
     k_fit_persistent(const uint32_t *__restrict__ words, const RoadDesc *__restrict__ desc,
                      const uint64_t *__restrict__ counts_in, uint64_t road_cap,
@@ -388,7 +397,7 @@ __global__ void __launch_bounds__(512, 2)
         road_setup(sm, words, D, g, F, q, sh, lane);
         const uint32_t a_lo = k * fr.rows;
         const uint32_t a_hi = min(a_lo + fr.rows, g.NA);
-        const unsigned long long best = eval_rows<NOCLAMP>(sm, g, a_lo, a_hi, qsh, init_chi, lane);
+        const unsigned long long best = eval_rows<GUARDED>(sm, g, a_lo, a_hi, qsh, init_chi, lane);
         uint32_t last = 0;
         if (lane == 0) {
             if (best != ~0ull) atomicMin(bl.best + j, best);
@@ -431,7 +440,7 @@ __global__ void __launch_bounds__(512, 2)
             unsigned long long best = ~0ull;
             if (g.C_eval > 0) {
                 road_setup(sm, words, D, g, F, q, sh, lane);
-                best = eval_rows<NOCLAMP>(sm, g, 0, g.NA, qsh, init_chi, lane);
+                best = eval_rows<GUARDED>(sm, g, 0, g.NA, qsh, init_chi, lane);
             }
             format_road(sm, D, g, cfg, best, out + (size_t)(c0 + jj) * 6, counts, lane);
             __syncwarp();

@@ -169,11 +169,45 @@ def test_ties_and_extreme_constants(path):
         roads.append((int(rng.integers(0, S)), rid, hits))
     w, off = words_of([(e, roads[e * 40:(e + 1) * 40]) for e in range(10)])
     for cut in (0, 5, 1000, 0xFFFFFFFF):
-        for oshift, qshift in ((15, 15), (9, 0), (31, 24), (12, 20)):
+        for oshift, qshift in ((15, 15), (9, 0), (9, 24), (31, 24), (12, 20)):
             cfg, ocfg = cfg_pair(oshift, qshift, cut, 300, 5, S)
             key, rec = oracle_run(w, off, F, q, ocfg)
             st, got, _ = gpu_run(w, off, F, q, cfg, path, comb_cap=400 * 300)
             assert_same(st, got, key, rec, f"cut{cut} os{oshift} qs{qshift}")
+
+
+@pytest.mark.parametrize("path", ["fused", "plain"])
+def test_chi_components_at_the_clamp_boundary(path):
+    """chi components straddling +-32767 / +-32768 (the clamp of Eq. 2's
+    chi-square), with cuts just below, at and above 32767^2: the range test of
+    the small-cut kernels and the clamped sum of the large-cut kernels both
+    agree with the oracle's clamped reading, ties included."""
+    rng = np.random.default_rng(11)
+    S = 2
+    F = np.zeros((S, 64, 6, 6), np.int16)
+    q = np.zeros((S, 64, 6), np.int16)
+    F[:, :, :3, :] = rng.integers(-2000, 2000, (S, 64, 3, 6))
+    # oshift = qshift = 15: y_k = q_k + floor(sum_l F_kl x_l / 2^15), x_l < 2^15
+    F[0, :, 3, :] = rng.integers(0, 3, (64, 6))      # y_3 in [32764, 32776)
+    q[0, :, 3] = 32764
+    F[1, :, 3, :] = -rng.integers(0, 3, (64, 6))     # y_3 in (-32776, -32764]
+    q[1, :, 3] = -32764
+    F[:, :, 4:, :] = rng.integers(-1, 2, (S, 64, 2, 6))   # y_4, y_5 in [-6, 6)
+    roads = []
+    for rid in range(600):
+        n = rng.integers(1, 4, 6)
+        hits = [(l, int(rng.integers(0, 32768))) for l in range(6) for _ in range(n[l])]
+        roads.append((rid % S, rid, hits))
+    w, off = words_of([(e, roads[e * 50:(e + 1) * 50]) for e in range(12)])
+    c = 32767 * 32767
+    n_pass = []
+    for cut in (c - 70000, c - 1, c, c + 100, 0xFFFFFFFF):
+        cfg, ocfg = cfg_pair(15, 15, cut, 729, 6, S)
+        key, rec = oracle_run(w, off, F, q, ocfg)
+        n_pass.append(int(np.count_nonzero(rec[:, 0] & (1 << 24))))
+        st, got, _ = gpu_run(w, off, F, q, cfg, path, comb_cap=600 * 729)
+        assert_same(st, got, key, rec, f"cut {cut}")
+    assert 0 < n_pass[0] < n_pass[1] < n_pass[2] < n_pass[3]   # each cut decides roads
 
 
 @pytest.mark.parametrize("path", ["fused", "plain"])
