@@ -113,6 +113,7 @@ __device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
 
 __device__ __forceinline__ int32_t clamp_chi(int32_t y) { return max(min(y, 32767), -32767); }
 
+
 // Road geometry unpacked from its descriptor (warp-uniform values).
 struct Geo {
     uint32_t split, NBp, NB, NA, C_eval, mask, total_hits;
@@ -316,10 +317,11 @@ __device__ __forceinline__ unsigned long long eval_rows(WarpSmem &sm, const Geo 
 }
 
 // Record of a road from its best key (all lanes call; lanes 0..2 recompute the
-// parameters from the warp's slot, which still holds this road).
-__device__ __forceinline__ void format_road(WarpSmem &sm, const RoadDesc &D, const Geo &g,
+// parameters from the warp's slot, which still holds this road; lanes 0..5
+// store one word each).  Returns whether the road passed.
+__device__ __forceinline__ bool format_road(WarpSmem &sm, const RoadDesc &D, const Geo &g,
                                             const svt_config &cfg, unsigned long long best,
-                                            uint32_t *o, uint64_t *counts, int lane) {
+                                            uint32_t *o, int lane) {
     const uint32_t geo = D.b.x;
     const bool pass = best != ~0ull;
     uint32_t flags = 0;
@@ -344,18 +346,13 @@ __device__ __forceinline__ void format_road(WarpSmem &sm, const RoadDesc &D, con
         }
         p = (int32_t)(acc >> cfg.oshift);   // arithmetic shift: floor
     }
-    const int32_t p0 = __shfl_sync(0xffffffffu, p, 0);
-    const int32_t p1 = __shfl_sync(0xffffffffu, p, 1);
-    const int32_t p2 = __shfl_sync(0xffffffffu, p, 2);
-    if (lane == 0) {
-        o[0] = rd_id(D.a.z) | (flags << 24);
-        o[1] = pass ? row * g.NB + col : 0xFFFFFFFFu;
-        o[2] = pass ? (uint32_t)(best >> 32) : 0u;
-        o[3] = (uint32_t)p0;
-        o[4] = (uint32_t)p1;
-        o[5] = (uint32_t)p2;
-        if (pass && counts) atomicAdd((unsigned long long *)(counts + 3), 1ull);
-    }
+    const int32_t pk = __shfl_sync(0xffffffffu, p, (lane + 29) & 31);   // lane 3 + k gets p_k
+    const uint32_t w = lane == 0   ? (rd_id(D.a.z) | (flags << 24))
+                       : lane == 1 ? (pass ? row * g.NB + col : 0xFFFFFFFFu)
+                       : lane == 2 ? (pass ? (uint32_t)(best >> 32) : 0u)
+                                   : (uint32_t)pk;
+    if (lane < 6) o[lane] = w;
+    return pass;
 }
 
 // K4: persistent fit / cut / select / format
@@ -380,6 +377,7 @@ __global__ void __launch_bounds__(512, 2)
     const uint32_t n_big = (uint32_t)*n_big_p;
     const uint32_t sh = 32u - cfg.oshift, qsh = cfg.qshift + sh;
     const uint32_t init_chi = cfg.chi2_cut == 0xFFFFFFFFu ? 0xFFFFFFFFu : cfg.chi2_cut + 1u;
+    uint32_t n_pass = 0;   // passing roads formatted by this warp, added to counts[3] once
 
     // phase 1: items of split roads
     for (;;) {
@@ -408,7 +406,7 @@ __global__ void __launch_bounds__(512, 2)
         if (last) {
             __threadfence();
             const unsigned long long fb = __ldcg(bl.best + j);
-            format_road(sm, D, g, cfg, fb, out + (size_t)r * 6, counts, lane);
+            n_pass += format_road(sm, D, g, cfg, fb, out + (size_t)r * 6, lane) ? 1u : 0u;
         }
         __syncwarp();
     }
@@ -442,10 +440,12 @@ __global__ void __launch_bounds__(512, 2)
                 road_setup(sm, words, D, g, F, q, sh, lane);
                 best = eval_rows<GUARDED>(sm, g, 0, g.NA, qsh, init_chi, lane);
             }
-            format_road(sm, D, g, cfg, best, out + (size_t)(c0 + jj) * 6, counts, lane);
+            n_pass += format_road(sm, D, g, cfg, best, out + (size_t)(c0 + jj) * 6, lane) ? 1u : 0u;
             __syncwarp();
         }
     }
+    if (lane == 0 && n_pass && counts)
+        atomicAdd((unsigned long long *)(counts + 3), (unsigned long long)n_pass);
 }
 
 }  // namespace
