@@ -269,7 +269,7 @@ class PlainPath:
         return status, rec, R
 
 
-FUSED_LAUNCHES_PER_RUN = 9   # set_dims, unpack_count, scan, unpack_roads, unpack_events, 2 scans, big list, fit
+FUSED_LAUNCHES_PER_RUN = 5   # prologue, unpack_count, scan, unpack_roads, fit
 PLAIN_LAUNCHES_PER_RUN = 13  # unpack (5), combine (5), fit, select, format
 
 

@@ -76,6 +76,7 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 struct UnpackWs {
     Dims *dims;
     uint32_t *tile_roads;
+    uint32_t *first_ev;
     size_t bytes;
 };
 UnpackWs carve_unpack(void *base, uint64_t max_words) {
@@ -83,6 +84,7 @@ UnpackWs carve_unpack(void *base, uint64_t max_words) {
     UnpackWs w;
     w.dims = c.take<Dims>(1);
     w.tile_roads = c.take<uint32_t>(n_tiles(max_words) + 1);
+    w.first_ev = c.take<uint32_t>(n_tiles(max_words) + 1);
     w.bytes = c.size();
     return w;
 }
@@ -91,9 +93,8 @@ UnpackWs carve_unpack(void *base, uint64_t max_words) {
 struct RunWs {
     Dims *dims;
     uint64_t *counts;
-    uint64_t *n_big;
-    uint32_t *counters;
-    uint32_t *tile_roads, *tile_big, *tile_bigitems;
+    uint64_t *work;   // [0] split-road reservation, [1] the fit kernel's two queue counters
+    uint32_t *tile_roads, *first_ev;
     RoadDesc *desc;
     uint32_t *big_road, *big_item_off, *big_pending;
     unsigned long long *big_best;
@@ -106,14 +107,12 @@ RunWs carve_run(void *base, uint64_t max_words, uint64_t max_events, uint64_t ro
     const uint64_t T = n_tiles(max_words);
     w.dims = c.take<Dims>(1);
     w.counts = c.take<uint64_t>(4);
-    w.n_big = c.take<uint64_t>(1);
-    w.counters = c.take<uint32_t>(2);
+    w.work = c.take<uint64_t>(2);
     w.tile_roads = c.take<uint32_t>(T + 1);
-    w.tile_big = c.take<uint32_t>(T + 1);
-    w.tile_bigitems = c.take<uint32_t>(T + 1);
+    w.first_ev = c.take<uint32_t>(T + 1);
     w.desc = c.take<RoadDesc>(road_cap);
     w.big_road = c.take<uint32_t>(road_cap);
-    w.big_item_off = c.take<uint32_t>(road_cap + 1);
+    w.big_item_off = c.take<uint32_t>(road_cap);
     w.big_pending = c.take<uint32_t>(road_cap);
     w.big_best = c.take<unsigned long long>(road_cap);
     w.event_road = c.take<uint32_t>(max_events + 1);
@@ -214,13 +213,15 @@ int svt_unpack(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_even
     unsigned long long *status = (unsigned long long *)d_status;
     const int grid = tile_grid();
     svt_config cfg{15, 15, 0, 1, 0, n_sectors};
-    launch_set_dims(w.dims, n_words, n_events, status, d_n_roads, 1, st);
-    launch_unpack_count(d_words, d_event_off, w.dims, n_words, n_sectors, w.tile_roads, status,
-                        grid, st);
+    launch_prologue(w.dims, n_words, n_events, nullptr, d_event_off, w.first_ev, status, d_n_roads,
+                    1, nullptr, 0, grid, st);
+    launch_unpack_count(d_words, d_event_off, w.dims, w.first_ev, n_words, n_sectors, w.tile_roads,
+                        status, grid, st);
     launch_scan_tiles(w.tile_roads, w.dims, nullptr, d_n_roads, d_event_road, status, st);
-    const FusedRoads none{nullptr, nullptr, nullptr, 1, 0};
-    launch_unpack_roads(d_words, d_event_off, w.dims, n_words, w.tile_roads, road_cap, d_road_word,
-                        d_road_nhit, d_event_road, cfg, none, nullptr, status, grid, st);
+    const FusedRoads none{nullptr, BigList{}, 1, 0};
+    launch_unpack_roads(d_words, d_event_off, w.dims, w.first_ev, n_words, w.tile_roads, road_cap,
+                        d_road_word, d_road_nhit, d_event_road, cfg, none, nullptr, status, grid,
+                        st);
     launch_unpack_events(d_words, d_event_off, w.dims, n_events, d_event_road, status, grid, st);
     return launch_status();
 }
@@ -331,23 +332,20 @@ int run_impl(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_
     const int occ = fit_persistent_blocks_per_sm((int)sc.warps_per_block);
     if (occ <= 0) return SVT_ERR_CUDA;
     const int bps = (sc.blocks_per_sm == 0 || (int)sc.blocks_per_sm > occ) ? occ : (int)sc.blocks_per_sm;
-    const FusedRoads fr{w.desc, w.tile_big, w.tile_bigitems, sc.rows_per_item, sc.small_max};
-    const BigList bl{w.big_road, w.big_item_off, w.big_best, w.big_pending, w.counters};
+    const BigList bl{w.big_road, w.big_item_off, w.big_best, w.big_pending,
+                     (unsigned long long *)w.work, (uint32_t *)(w.work + 1)};
+    const FusedRoads fr{w.desc, bl, sc.rows_per_item, sc.small_max};
 
-    launch_set_dims(w.dims, n_words, n_events, status, counts, 4, st, d_sizes);
-    launch_unpack_count(d_words, d_event_off, w.dims, n_words, cfg->n_sectors, w.tile_roads, status,
-                        grid, st);
+    launch_prologue(w.dims, n_words, n_events, d_sizes, d_event_off, w.first_ev, status, counts, 4,
+                    w.work, 2, grid, st);
+    launch_unpack_count(d_words, d_event_off, w.dims, w.first_ev, n_words, cfg->n_sectors,
+                        w.tile_roads, status, grid, st);
     launch_scan_tiles(w.tile_roads, w.dims, nullptr, counts + 0, event_road, status, st);
-    launch_unpack_roads(d_words, d_event_off, w.dims, n_words, w.tile_roads, road_cap, nullptr,
-                        nullptr, event_road, *cfg, fr, counts, status, grid, st);
-    launch_unpack_events(d_words, d_event_off, w.dims, n_events, event_road, status, grid, st);
-    launch_scan_tiles(w.tile_bigitems, w.dims, nullptr, counts + 1, nullptr, status, st);
-    launch_scan_tiles(w.tile_big, w.dims, nullptr, w.n_big, nullptr, status, st);
-    launch_big_list(w.desc, road_cap, w.dims, n_words, w.tile_roads, w.tile_big, w.tile_bigitems,
-                    fr, bl, status, grid, st);
+    launch_unpack_roads(d_words, d_event_off, w.dims, w.first_ev, n_words, w.tile_roads, road_cap,
+                        nullptr, nullptr, event_road, *cfg, fr, counts, status, grid, st);
     if (timer && cudaEventRecord(timer->start, st) != cudaSuccess) return SVT_ERR_CUDA;
-    if (launch_fit_persistent(d_words, w.desc, counts, road_cap, w.n_big, d_F, d_q, *cfg, fr,
-                              sc.roads_per_chunk, bl, d_out, counts, status,
+    if (launch_fit_persistent(d_words, d_event_off, w.dims, event_road, w.desc, counts, road_cap,
+                              d_F, d_q, *cfg, fr, sc.roads_per_chunk, d_out, status,
                               (int)sc.warps_per_block, sms * bps, st) != cudaSuccess)
         return SVT_ERR_CUDA;
     if (timer) {
@@ -507,7 +505,7 @@ int svt_calib_index(const int32_t *d_sector, uint64_t n_tracks, uint32_t n_secto
     if (index_bytes < x.bytes) return SVT_ERR_BAD_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned long long *status = (unsigned long long *)d_status;
-    launch_set_dims(nullptr, 0, 0, status, nullptr, 0, st);
+    launch_prologue(nullptr, 0, 0, nullptr, nullptr, nullptr, status, nullptr, 0, nullptr, 0, 1, st);
     if (cudaMemsetAsync(x.sector_off, 0, sizeof(int32_t) * (n_sectors + 1), st) != cudaSuccess ||
         cudaMemsetAsync(x.sector_item, 0, sizeof(int32_t) * (n_sectors + 1), st) != cudaSuccess ||
         cudaMemsetAsync(x.n_items, 0, sizeof(int32_t), st) != cudaSuccess)

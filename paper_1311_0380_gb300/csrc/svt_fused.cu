@@ -45,47 +45,6 @@ struct WarpSmem {
     uint32_t m[N_LAYERS];                 // division magic of n'_l
 };
 
-// K3: the list of split roads
-__global__ void __launch_bounds__(TILE_THREADS)
-    k_big_list(const RoadDesc *__restrict__ desc, uint64_t road_cap, const Dims *__restrict__ dims,
-               const uint32_t *__restrict__ tile_roads, const uint32_t *__restrict__ tile_big,
-               const uint32_t *__restrict__ tile_bigitems, const FusedRoads fr, BigList bl,
-               unsigned long long *status) {
-    __shared__ uint32_t red[TILE_THREADS / 32 + 1];
-    if (!status_ok(status)) return;
-    const uint64_t T = n_tiles(dims->n_words);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        bl.counters[0] = 0;
-        bl.counters[1] = 0;
-        bl.item_off[tile_big[T]] = tile_bigitems[T];
-    }
-    for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
-        const uint64_t r0 = tile_roads[t], r1 = min((uint64_t)tile_roads[t + 1], road_cap);
-        const uint64_t rb = r0 + (uint64_t)threadIdx.x * TILE_PER_THREAD;
-        uint32_t it[TILE_PER_THREAD], n_it = 0, n_big = 0;
-#pragma unroll
-        for (int j = 0; j < TILE_PER_THREAD; ++j) {
-            it[j] = 0;
-            if (rb + j < r1) it[j] = road_big_items(desc[rb + j], fr);
-            n_it += it[j];
-            n_big += it[j] ? 1u : 0u;
-        }
-        uint32_t tot;
-        uint32_t item_run = tile_bigitems[t] + block_exclusive_scan<uint32_t>(n_it, red, &tot);
-        uint32_t big_run = tile_big[t] + block_exclusive_scan<uint32_t>(n_big, red, &tot);
-#pragma unroll
-        for (int j = 0; j < TILE_PER_THREAD; ++j) {
-            if (!it[j]) continue;
-            bl.road[big_run] = (uint32_t)(rb + j);
-            bl.item_off[big_run] = item_run;
-            bl.best[big_run] = ~0ull;
-            bl.pending[big_run] = it[j];
-            big_run += 1;
-            item_run += it[j];
-        }
-    }
-}
-
 // largest j in [0, n) with off[j] <= it (off non-decreasing, off[0] = 0)
 __device__ __forceinline__ uint32_t find_slot(const uint32_t *__restrict__ off, uint32_t n,
                                               uint32_t it, int lane) {
@@ -358,23 +317,28 @@ __device__ __forceinline__ bool format_road(WarpSmem &sm, const RoadDesc &D, con
 // K4: persistent fit / cut / select / format
 template <bool GUARDED>
 __global__ void __launch_bounds__(512, 2)
-    k_fit_persistent(const uint32_t *__restrict__ words, const RoadDesc *__restrict__ desc,
-                     const uint64_t *__restrict__ counts_in, uint64_t road_cap,
-                     const uint64_t *__restrict__ n_big_p, const int16_t *__restrict__ F,
-                     const int16_t *__restrict__ q, const svt_config cfg, const FusedRoads fr,
-                     uint32_t roads_per_chunk, BigList bl, uint32_t *out, uint64_t *counts,
-                     unsigned long long *status) {
+    k_fit_persistent(const uint32_t *__restrict__ words, const uint64_t *__restrict__ event_off,
+                     const Dims *__restrict__ dims, const uint32_t *__restrict__ event_road,
+                     const RoadDesc *__restrict__ desc, uint64_t *counts, uint64_t road_cap,
+                     const int16_t *__restrict__ F, const int16_t *__restrict__ q,
+                     const svt_config cfg, const FusedRoads fr, uint32_t roads_per_chunk,
+                     uint32_t *out, unsigned long long *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
+    // per-event rules first, whatever the status, so that the key stays the
+    // smallest over all rules
+    check_events(words, event_off, dims->n_words, dims->n_events, event_road, status,
+                 (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                 (uint64_t)gridDim.x * blockDim.x);
+    const BigList &bl = fr.bl;
+    const unsigned long long rv = *(volatile unsigned long long *)bl.reserve;
+    const uint32_t n_big = (uint32_t)rv, n_items = (uint32_t)(rv >> 32);
+    if (blockIdx.x == 0 && threadIdx.x == 0) counts[1] = n_items;
     if (!status_ok(status)) return;
-    const uint64_t R64 = counts_in[0];
+    const uint64_t R64 = counts[0];
     if (R64 > road_cap || R64 == 0) return;
     const uint32_t R = (uint32_t)R64;
-    const uint64_t n_items64 = counts_in[1];
-    if (n_items64 > 0xFFFFFFFFull) return;
-    const uint32_t n_items = (uint32_t)n_items64;
-    const uint32_t n_big = (uint32_t)*n_big_p;
     const uint32_t sh = 32u - cfg.oshift, qsh = cfg.qshift + sh;
     const uint32_t init_chi = cfg.chi2_cut == 0xFFFFFFFFu ? 0xFFFFFFFFu : cfg.chi2_cut + 1u;
     uint32_t n_pass = 0;   // passing roads formatted by this warp, added to counts[3] once
@@ -444,22 +408,11 @@ __global__ void __launch_bounds__(512, 2)
             __syncwarp();
         }
     }
-    if (lane == 0 && n_pass && counts)
+    if (lane == 0 && n_pass)
         atomicAdd((unsigned long long *)(counts + 3), (unsigned long long)n_pass);
 }
 
 }  // namespace
-
-void launch_big_list(const RoadDesc *desc, uint64_t road_cap, const Dims *dims, uint64_t max_words,
-                     const uint32_t *tile_roads, const uint32_t *tile_big,
-                     const uint32_t *tile_bigitems, const FusedRoads fr, BigList bl,
-                     unsigned long long *status, int grid, cudaStream_t st) {
-    uint64_t T = n_tiles(max_words);
-    int g = (int)(T < (uint64_t)grid ? T : (uint64_t)grid);
-    if (g < 1) g = 1;
-    k_big_list<<<g, TILE_THREADS, 0, st>>>(desc, road_cap, dims, tile_roads, tile_big,
-                                          tile_bigitems, fr, bl, status);
-}
 
 size_t fit_smem_bytes(int warps_per_block) { return sizeof(WarpSmem) * (size_t)warps_per_block; }
 
@@ -476,21 +429,22 @@ int fit_persistent_blocks_per_sm(int warps_per_block) {
     return n < n2 ? n : n2;
 }
 
-cudaError_t launch_fit_persistent(const uint32_t *words, const RoadDesc *desc, const uint64_t *counts,
-                                  uint64_t road_cap, const uint64_t *n_big, const int16_t *F,
-                                  const int16_t *q, const svt_config cfg, const FusedRoads fr,
-                                  uint32_t roads_per_chunk, BigList bl, uint32_t *out,
-                                  uint64_t *counts_out, unsigned long long *status,
+cudaError_t launch_fit_persistent(const uint32_t *words, const uint64_t *event_off,
+                                  const Dims *dims, const uint32_t *event_road,
+                                  const RoadDesc *desc, uint64_t *counts, uint64_t road_cap,
+                                  const int16_t *F, const int16_t *q, const svt_config cfg,
+                                  const FusedRoads fr, uint32_t roads_per_chunk,
+                                  uint32_t *out, unsigned long long *status,
                                   int warps_per_block, int grid, cudaStream_t st) {
     size_t smem = fit_smem_bytes(warps_per_block);
     if (cfg.chi2_cut < 32767u * 32767u)
         k_fit_persistent<true><<<grid, warps_per_block * 32, smem, st>>>(
-            words, desc, counts, road_cap, n_big, F, q, cfg, fr, roads_per_chunk, bl, out,
-            counts_out, status);
+            words, event_off, dims, event_road, desc, counts, road_cap, F, q, cfg, fr,
+            roads_per_chunk, out, status);
     else
         k_fit_persistent<false><<<grid, warps_per_block * 32, smem, st>>>(
-            words, desc, counts, road_cap, n_big, F, q, cfg, fr, roads_per_chunk, bl, out,
-            counts_out, status);
+            words, event_off, dims, event_road, desc, counts, road_cap, F, q, cfg, fr,
+            roads_per_chunk, out, status);
     return cudaGetLastError();
 }
 

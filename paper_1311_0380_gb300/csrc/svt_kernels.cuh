@@ -48,11 +48,24 @@ __device__ __forceinline__ RoadDesc make_road_desc(uint32_t rw, uint32_t packed,
     return d;
 }
 
+// Split roads of the fused path.  The road extraction appends each tile's
+// split roads with one 64-bit atomic on `reserve` ((items << 32) | roads), so
+// road slots and item ranges are reserved together and item_off increases
+// with the slot; the fit kernel's work queues are counters[0] (items) and
+// counters[1] (roads).
+struct BigList {
+    uint32_t *road;                // split road of each slot
+    uint32_t *item_off;            // its first work item
+    unsigned long long *best;      // best key so far (UINT64_MAX)
+    uint32_t *pending;             // its items not yet finished
+    unsigned long long *reserve;   // (items << 32) | roads appended so far
+    uint32_t *counters;            // [0] items taken, [1] roads taken
+};
+
 // Fused-path outputs of the road extraction (desc == nullptr: plain path).
 struct FusedRoads {
     RoadDesc *desc;            // per road
-    uint32_t *tile_big;        // per word tile: roads split into items
-    uint32_t *tile_bigitems;   // per word tile: items of those roads
+    BigList bl;                // split roads
     uint32_t rows;             // rows per item
     uint32_t small_max;        // roads above this many combinations are split
 };
@@ -66,10 +79,20 @@ __device__ __forceinline__ uint32_t road_big_items(const RoadDesc &d, const Fuse
 }
 
 // ---- unpack (svt_unpack.cu) --------------------------------------------------
-// K1: per-word validation (rules V2..V7, V9) and road headers per tile.
+// Prologue: batch sizes (from `sizes` on the device when given, bounded by
+// n_words / n_events), status reset, counts[0..n_counts) and zero[0..n_zero)
+// cleared and, when first_ev is given, first_ev[t] = the first event whose
+// offset is at or after word tile t's start, for t = 0..T.  Only block 0
+// writes the sizes and the status; no block reports anything.
+void launch_prologue(Dims *dims, uint64_t n_words, uint64_t n_events, const uint64_t *sizes,
+                     const uint64_t *event_off, uint32_t *first_ev, unsigned long long *status,
+                     uint64_t *counts, int n_counts, uint64_t *zero, int n_zero, int grid,
+                     cudaStream_t st);
+// K1: per-word validation (rules V1..V7, V9) and road headers per tile.
 void launch_unpack_count(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
-                         uint64_t max_words, uint32_t n_sectors, uint32_t *tile_roads,
-                         unsigned long long *status, int grid, cudaStream_t st);
+                         const uint32_t *first_ev, uint64_t max_words, uint32_t n_sectors,
+                         uint32_t *tile_roads, unsigned long long *status, int grid,
+                         cudaStream_t st);
 // Exclusive scan, in place, of a[0..n) where n = *n_dev, or the number of
 // word tiles when n_dev is NULL; writes the total to a[n] and, when given, to
 // *total64 and to event_road[n_events].  A total of 2^32 or more lowers the
@@ -78,41 +101,54 @@ void launch_scan_tiles(uint32_t *a, const Dims *dims, const uint64_t *n_dev, uin
                        uint32_t *event_road, unsigned long long *status, cudaStream_t st);
 // K2: road extraction: road_word, road_nhit (either may be null), rule V8,
 // event_road of events starting in each tile; with fr.desc also the road
-// descriptors, the split roads and items per tile and the evaluated
-// combinations (counts[2]).
+// descriptors, the split-road list and the evaluated combinations (counts[2]).
 void launch_unpack_roads(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
-                         uint64_t max_words, const uint32_t *tile_roads, uint64_t road_cap,
-                         uint32_t *road_word, uint32_t *road_nhit, uint32_t *event_road,
-                         const svt_config cfg, const FusedRoads fr, uint64_t *counts,
-                         unsigned long long *status, int grid, cudaStream_t st);
-// Per-event rules: offsets, V1, V10.
+                         const uint32_t *first_ev, uint64_t max_words, const uint32_t *tile_roads,
+                         uint64_t road_cap, uint32_t *road_word, uint32_t *road_nhit,
+                         uint32_t *event_road, const svt_config cfg, const FusedRoads fr,
+                         uint64_t *counts, unsigned long long *status, int grid, cudaStream_t st);
+// Per-event rules of the plain path: offsets and V10.
 void launch_unpack_events(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
                           uint64_t max_events, const uint32_t *event_road,
                           unsigned long long *status, int grid, cudaStream_t st);
 
+// Per-event rules shared by the plain path's event kernel and the fused fit
+// kernel: the offsets (BAD_ARG) and V10.  `tid`/`stride` enumerate the calling
+// threads.
+__device__ __forceinline__ void check_events(const uint32_t *__restrict__ words,
+                                             const uint64_t *__restrict__ event_off,
+                                             uint64_t n_words, uint64_t n_events,
+                                             const uint32_t *__restrict__ event_road,
+                                             unsigned long long *status, uint64_t tid,
+                                             uint64_t stride) {
+    if (tid == 0) {
+        if (__ldg(event_off) != 0 || __ldg(event_off + n_events) != n_words)
+            report(status, 0, SVT_ERR_BAD_ARG);
+    }
+    for (uint64_t e = tid; e < n_events; e += stride) {
+        const uint64_t s = __ldg(event_off + e), s1 = __ldg(event_off + e + 1);
+        if (s1 <= s || s >= n_words) {
+            report(status, 0, SVT_ERR_BAD_ARG);
+            continue;
+        }
+        const uint32_t h = __ldg(words + s);
+        // V1 is K1's; an event that starts with a non-header word has no count
+        if (w_type(h) == TYPE_EVENT && ev_nroads(h) != event_road[e + 1] - event_road[e])
+            report(status, s, SVT_ERR_NROADS_MISMATCH);                            // V10
+    }
+}
+
 // ---- fused path (svt_fused.cu) -------------------------------------------------
-// K3: list of split roads (big_road, big_item_off with the total at
-// [n_big], big_best = UINT64_MAX, big_pending = items) and reset of the two
-// work counters.
-struct BigList {
-    uint32_t *road;
-    uint32_t *item_off;
-    unsigned long long *best;
-    uint32_t *pending;
-    uint32_t *counters;        // [0] big items taken, [1] roads taken
-};
-void launch_big_list(const RoadDesc *desc, uint64_t road_cap, const Dims *dims, uint64_t max_words,
-                     const uint32_t *tile_roads, const uint32_t *tile_big,
-                     const uint32_t *tile_bigitems, const FusedRoads fr, BigList bl,
-                     unsigned long long *status, int grid, cudaStream_t st);
 // K4: the persistent fit over split-road items, then over chunks of roads.
-cudaError_t launch_fit_persistent(const uint32_t *words, const RoadDesc *desc, const uint64_t *counts,
-                                  uint64_t road_cap, const uint64_t *n_big,
+// It first checks the per-event rules (check_events), then fits; counts[0]
+// holds R on entry, counts[1] receives the number of work items.
+cudaError_t launch_fit_persistent(const uint32_t *words, const uint64_t *event_off,
+                                  const Dims *dims, const uint32_t *event_road,
+                                  const RoadDesc *desc, uint64_t *counts, uint64_t road_cap,
                                   const int16_t *F, const int16_t *q, const svt_config cfg,
-                                  const FusedRoads fr, uint32_t roads_per_chunk, BigList bl,
-                                  uint32_t *out, uint64_t *counts_out,
-                                  unsigned long long *status, int warps_per_block, int grid,
-                                  cudaStream_t st);
+                                  const FusedRoads fr, uint32_t roads_per_chunk,
+                                  uint32_t *out, unsigned long long *status,
+                                  int warps_per_block, int grid, cudaStream_t st);
 int fit_persistent_blocks_per_sm(int warps_per_block);
 size_t fit_smem_bytes(int warps_per_block);
 
@@ -165,12 +201,5 @@ void launch_calib_grad(int mode, const float *x, const float *theta, const float
                        const float *q, const float *w, const float *scale_dev, float scale,
                        float *item_grad, float *dF, float *dq, float *dx, int grid,
                        cudaStream_t st);
-
-// shared by both paths
-// Sets the batch sizes (from `sizes` on the device when given, bounded by
-// n_words / n_events), resets the status and zeroes counts[0..n_counts).
-void launch_set_dims(Dims *dims, uint64_t n_words, uint64_t n_events,
-                     unsigned long long *status, uint64_t *counts, int n_counts, cudaStream_t st,
-                     const uint64_t *sizes = nullptr);
 
 }  // namespace svt

@@ -1,14 +1,16 @@
 // svt_unpack.cu -- stage 1 of the paper's Sec. 2.1 ("unpacking of input data
 // and filling of all the necessary data structures") for GB300.
 //
-// The batch is cut into tiles of 2048 words.  K1 validates every word against
-// its left neighbour (rules V2..V7, V9 of include/svt.h's format) and counts
-// road headers per tile; a single-block scan turns the counts into each
-// tile's first road index; K2 then gives every road header its global index
-// (block scan), records where it sits, walks its hits (rule V8, hits per
-// layer) and, for the fused path, sizes its work; a per-event kernel checks
-// the offsets and rules V1 and V10.  Loads are vectorised (2 x 16 B per
-// thread, coalesced across the warp).
+// The batch is cut into tiles of 2048 words.  A prologue maps every tile to
+// the first event that starts in it (one pass over the event offsets).  K1
+// validates every word against its left neighbour (rules V2..V7, V9 of
+// include/svt.h's format), checks V1 for the events starting in the tile and
+// counts road headers per tile; a single-block scan turns the counts into
+// each tile's first road index; K2 then gives every road header its global
+// index (block scan), records where it sits, counts its hits (rule V8, hits
+// per layer) and, for the fused path, sizes its work and appends split roads
+// to the work list.  The offsets and V10 are checked per event afterwards.
+// Loads are vectorised (2 x 16 B per thread, coalesced across the warp).
 #include "svt_kernels.cuh"
 
 namespace svt {
@@ -54,40 +56,68 @@ __device__ __forceinline__ uint64_t warp_lower_bound64(const uint64_t *__restric
 // Batch sizes for the launch sequence: the given values, or -- when `sizes`
 // is set -- the device-resident pair {n_words, n_events}, which must not
 // exceed the capacities the sequence was sized for (else BAD_ARG, empty batch).
-__global__ void k_set_dims(Dims *dims, uint64_t n_words, uint64_t n_events,
-                           const uint64_t *sizes, unsigned long long *status, uint64_t *counts,
-                           int n_counts) {
-    if (threadIdx.x == 0) {
-        bool bad = false;
-        if (sizes) {
-            const uint64_t w = sizes[0], e = sizes[1];
-            bad = w > n_words || e > n_events;
-            n_words = bad ? 0 : w;
-            n_events = bad ? 0 : e;
-        }
+// Every block derives the sizes itself; block 0 publishes them.
+//
+// first_ev[t] = lower_bound(event_off, t * TILE_WORDS) for t = 0..T: event e
+// writes the tiles t with event_off[e-1] < t * TILE_WORDS <= event_off[e].
+// With increasing offsets every entry is written once; otherwise the offsets
+// are reported as BAD_ARG (the smallest key) by the per-event check, and the
+// consumers clamp what they read to [0, n_events].
+__global__ void k_prologue(Dims *dims, uint64_t n_words, uint64_t n_events,
+                           const uint64_t *sizes, const uint64_t *__restrict__ event_off,
+                           uint32_t *first_ev, unsigned long long *status, uint64_t *counts,
+                           int n_counts, uint64_t *zero, int n_zero) {
+    bool bad = false;
+    if (sizes) {
+        const uint64_t w = sizes[0], e = sizes[1];
+        bad = w > n_words || e > n_events;
+        n_words = bad ? 0 : w;
+        n_events = bad ? 0 : e;
+    }
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    if (tid == 0) {
         if (dims) {
             dims->n_words = n_words;
             dims->n_events = n_events;
         }
         if (status) *status = bad ? (unsigned long long)SVT_ERR_BAD_ARG : ~0ull;
     }
-    if (counts && (int)threadIdx.x < n_counts) counts[threadIdx.x] = 0;
+    if (counts && tid < (uint64_t)n_counts) counts[tid] = 0;
+    if (zero && tid < (uint64_t)n_zero) zero[tid] = 0;
+    if (!first_ev) return;
+    const uint64_t T = n_tiles(n_words);
+    for (uint64_t e = tid; e <= n_events; e += stride) {
+        const uint64_t t0 = e > 0 ? min(__ldg(event_off + e - 1), n_words) / TILE_WORDS + 1 : 0;
+        const uint64_t t1 = e < n_events ? min(__ldg(event_off + e), n_words) / TILE_WORDS : T;
+        for (uint64_t t = t0; t <= min(t1, T); ++t) first_ev[t] = (uint32_t)e;
+    }
+}
+
+// Events [e_lo, e_hi) that start in tile t, clamped to the batch.
+__device__ __forceinline__ void tile_events(const uint32_t *__restrict__ first_ev, uint64_t t,
+                                            uint64_t n_events, uint64_t &e_lo, uint64_t &e_hi) {
+    e_lo = min((uint64_t)__ldg(first_ev + t), n_events);
+    e_hi = max(e_lo, min((uint64_t)__ldg(first_ev + t + 1), n_events));
 }
 
 __global__ void __launch_bounds__(TILE_THREADS)
     k_unpack_count(const uint32_t *__restrict__ words, const uint64_t *__restrict__ event_off,
-                   const Dims *__restrict__ dims, uint32_t n_sectors, uint32_t *tile_roads,
-                   unsigned long long *status) {
+                   const Dims *__restrict__ dims, const uint32_t *__restrict__ first_ev,
+                   uint32_t n_sectors, uint32_t *tile_roads, unsigned long long *status) {
     __shared__ uint32_t red[TILE_THREADS / 32 + 1];
     const uint64_t n_words = dims->n_words, n_events = dims->n_events;
     const uint64_t T = n_tiles(n_words);
     for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
-        const uint64_t base = t * TILE_WORDS + (uint64_t)threadIdx.x * TILE_PER_THREAD;
+        const uint64_t tile_start = t * TILE_WORDS, tile_end = min(tile_start + TILE_WORDS, n_words);
+        const uint64_t base = tile_start + (uint64_t)threadIdx.x * TILE_PER_THREAD;
+        uint64_t e_lo, e_hi;
+        tile_events(first_ev, t, n_events, e_lo, e_hi);
         uint32_t w[TILE_PER_THREAD];
         load8(words, base, n_words, w);
         uint32_t prev = __shfl_up_sync(0xffffffffu, w[TILE_PER_THREAD - 1], 1);
         if ((threadIdx.x & 31) == 0) prev = (base > 0 && base - 1 < n_words) ? __ldg(words + base - 1) : 0u;
-        uint32_t cnt = 0;
+        uint32_t cnt = 0;   // road headers (low 16 bits) and event headers (high 16 bits)
 #pragma unroll
         for (int j = 0; j < TILE_PER_THREAD; ++j) {
             const uint64_t i = base + j;
@@ -101,7 +131,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
             } else if (ty == TYPE_BAD) {
                 report(status, i, SVT_ERR_BAD_TYPE);                                    // V3
             } else if (ty == TYPE_EVENT) {
-                // V2 (an event header must start an event) is checked below by the warp
+                cnt += 1u << 16;   // V2 (an event header must start an event): below
             } else {
                 // V4 and V7 also fire on an event's first word, where V1 already
                 // reports the same word with the smallest code, so the key is unchanged.
@@ -112,23 +142,38 @@ __global__ void __launch_bounds__(TILE_THREADS)
                     report(status, i, SVT_ERR_UNSORTED);                                     // V7
             }
         }
-        // V2: every event-header word must sit at an event offset
-        const int lane = threadIdx.x & 31;
-#pragma unroll
-        for (int j = 0; j < TILE_PER_THREAD; ++j) {
-            uint32_t bal = __ballot_sync(0xffffffffu, base + j < n_words && w_type(w[j]) == TYPE_EVENT);
-            while (bal) {
-                const int src = __ffs(bal) - 1;
-                const uint64_t i = __shfl_sync(0xffffffffu, base + j, src);
-                const uint64_t e = warp_lower_bound64(event_off, n_events, i, lane);
-                const bool start = e < n_events && __ldg(event_off + e) == i;
-                if (lane == src && !start) report(status, i, SVT_ERR_BAD_TYPE);
-                bal &= bal - 1;
+        // V1: the events starting in this tile start with an event header
+        int v1_bad = 0;
+        for (uint64_t e = e_lo + threadIdx.x; e < e_hi; e += TILE_THREADS) {
+            const uint64_t s0 = __ldg(event_off + e);
+            if (s0 >= tile_start && s0 < tile_end && w_type(__ldg(words + s0)) != TYPE_EVENT) {
+                report(status, s0, SVT_ERR_BAD_TYPE);                                   // V1
+                v1_bad = 1;
             }
         }
         uint32_t total;
         block_exclusive_scan<uint32_t>(cnt, red, &total);
-        if (threadIdx.x == 0) tile_roads[t] = total;
+        v1_bad = __syncthreads_or(v1_bad);
+        // V2: every event-header word must sit at an event offset.  When the
+        // tile holds as many headers as events start in it and all of those
+        // start with a header (V1), the headers are exactly those starts;
+        // otherwise every header of the tile is looked up.
+        if ((total >> 16) != e_hi - e_lo || v1_bad) {   // (rare: the batch is invalid)
+            const int lane = threadIdx.x & 31;
+            for (int j = 0; j < TILE_PER_THREAD; ++j) {
+                const bool ev = base + j < n_words && w_type(__ldg(words + base + j)) == TYPE_EVENT;
+                uint32_t bal = __ballot_sync(0xffffffffu, ev);
+                while (bal) {
+                    const int src = __ffs(bal) - 1;
+                    const uint64_t i = __shfl_sync(0xffffffffu, base + j, src);
+                    const uint64_t e = warp_lower_bound64(event_off, n_events, i, lane);
+                    const bool start = e < n_events && __ldg(event_off + e) == i;
+                    if (lane == src && !start) report(status, i, SVT_ERR_BAD_TYPE);
+                    bal &= bal - 1;
+                }
+            }
+        }
+        if (threadIdx.x == 0) tile_roads[t] = total & 0xFFFFu;
     }
 }
 
@@ -177,13 +222,16 @@ __global__ void __launch_bounds__(1024)
 //    contiguous block.  For the smallest status key this matches counting
 //    over the run: the first out-of-order hit of a run is an UNSORTED word
 //    that precedes any later, non-contiguous 17th hit;
-//  * one thread per road then writes the road's outputs.
+//  * one thread per road then writes the road's outputs; for the fused path
+//    the tile's split roads are appended to the work list at a range that
+//    one atomic reserves for the whole tile.
 __global__ void __launch_bounds__(TILE_THREADS)
     k_unpack_roads(const uint32_t *__restrict__ words, const uint64_t *__restrict__ event_off,
-                   const Dims *__restrict__ dims, const uint32_t *__restrict__ tile_roads,
-                   uint64_t road_cap, uint32_t *road_word, uint32_t *road_nhit,
-                   uint32_t *event_road, const svt_config cfg, const FusedRoads fr,
-                   uint64_t *counts, unsigned long long *status) {
+                   const Dims *__restrict__ dims, const uint32_t *__restrict__ first_ev,
+                   const uint32_t *__restrict__ tile_roads, uint64_t road_cap,
+                   uint32_t *road_word, uint32_t *road_nhit, uint32_t *event_road,
+                   const svt_config cfg, const FusedRoads fr, uint64_t *counts,
+                   unsigned long long *status) {
     constexpr int FRONT = 16, BACK = 100;
     constexpr uint32_t SENTINEL = 0xC0000000u;   // an event-header word: ends every run
     __shared__ uint32_t red[TILE_THREADS / 32 + 1];
@@ -191,8 +239,8 @@ __global__ void __launch_bounds__(TILE_THREADS)
     __shared__ uint32_t sw[FRONT + TILE_WORDS + BACK];
     __shared__ uint32_t cnt[TILE_WORDS];              // per road of the tile: 5 bits per layer
     __shared__ uint16_t hdr_pos[TILE_WORDS];          // tile position of each road header
-    __shared__ uint64_t ev_range[2];
     __shared__ int last_nonhit;
+    __shared__ unsigned long long big_base;
     const uint64_t n_words = dims->n_words, n_events = dims->n_events;
     const uint64_t T = n_tiles(n_words);
     for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
@@ -200,15 +248,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
         const uint64_t tile_end = min(tile_start + TILE_WORDS, n_words);
         const int tile_len = (int)(tile_end - tile_start);
         const uint64_t base = tile_start + (uint64_t)threadIdx.x * TILE_PER_THREAD;
-        if (threadIdx.x < 32) {
-            const uint64_t lo = warp_lower_bound64(event_off, n_events, tile_start, threadIdx.x);
-            const uint64_t hi = warp_lower_bound64(event_off, n_events, tile_end, threadIdx.x);
-            if (threadIdx.x == 0) {
-                ev_range[0] = lo;
-                ev_range[1] = hi;
-                last_nonhit = -1;
-            }
-        }
+        if (threadIdx.x == 0) last_nonhit = -1;
         uint32_t w[TILE_PER_THREAD];
         load8(words, base, n_words, w);
         uint32_t nh = 0;
@@ -302,7 +342,8 @@ __global__ void __launch_bounds__(TILE_THREADS)
             }
         }
         __syncthreads();
-        // one thread per road of the tile
+        // one thread per road of the tile; for the fused path cnt[rl] then
+        // holds the road's work items (0 unless it is split)
         uint32_t items_sum = 0, big_sum = 0;
         unsigned long long comb_sum = 0;
         for (uint32_t rl = threadIdx.x; rl < n_roads_tile; rl += TILE_THREADS) {
@@ -310,6 +351,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
             const int p = hdr_pos[rl];
             if (r >= road_cap) {
                 report(status, tile_start + p, SVT_ERR_OOM);
+                cnt[rl] = 0;
                 continue;
             }
             const uint32_t packed = cnt[rl];
@@ -319,6 +361,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 const RoadDesc d = make_road_desc((uint32_t)(tile_start + p), packed, sw[FRONT + p], cfg);
                 const uint32_t it = road_big_items(d, fr);
                 fr.desc[r] = d;
+                cnt[rl] = it;
                 items_sum += it;
                 big_sum += it ? 1u : 0u;
                 comb_sum += d.a.w;
@@ -326,7 +369,8 @@ __global__ void __launch_bounds__(TILE_THREADS)
         }
         // first road of every event that starts inside this tile: the number
         // of road headers before the event's first word
-        const uint64_t e_lo = ev_range[0], e_hi = ev_range[1];
+        uint64_t e_lo, e_hi;
+        tile_events(first_ev, t, n_events, e_lo, e_hi);
         for (uint64_t e = e_lo + threadIdx.x; e < e_hi; e += TILE_THREADS) {
             const uint64_t s0 = __ldg(event_off + e);
             if (s0 >= tile_start && s0 < tile_end) {
@@ -341,15 +385,38 @@ __global__ void __launch_bounds__(TILE_THREADS)
             }
         }
         if (fr.desc) {
+            // this thread's split roads go to slots [base + big_ex, ...) with
+            // items from [base_items + it_ex, ...), in the order it visited them
             uint32_t it_total, big_total;
-            block_exclusive_scan<uint32_t>(items_sum, red, &it_total);
-            block_exclusive_scan<uint32_t>(big_sum, red, &big_total);
+            uint32_t it_ex = block_exclusive_scan<uint32_t>(items_sum, red, &it_total);
+            uint32_t big_ex = block_exclusive_scan<uint32_t>(big_sum, red, &big_total);
             unsigned long long c_total;
             block_exclusive_scan<unsigned long long>(comb_sum, red64, &c_total);
             if (threadIdx.x == 0) {
-                fr.tile_bigitems[t] = it_total;
-                fr.tile_big[t] = big_total;
+                unsigned long long b = 0;
+                if (big_total) {
+                    b = atomicAdd(fr.bl.reserve,
+                                  ((unsigned long long)it_total << 32) | big_total);
+                    if ((b >> 32) + it_total > 0xFFFFFFFFull)
+                        report(status, tile_start, SVT_ERR_OOM);   // item count needs 32 bits
+                }
+                big_base = b;
                 if (counts && c_total) atomicAdd((unsigned long long *)(counts + 2), c_total);
+            }
+            __syncthreads();
+            if (big_sum) {
+                const uint32_t slot0 = (uint32_t)big_base, item0 = (uint32_t)(big_base >> 32);
+                for (uint32_t rl = threadIdx.x; rl < n_roads_tile; rl += TILE_THREADS) {
+                    const uint32_t it = cnt[rl];
+                    if (!it) continue;
+                    const uint32_t j = slot0 + big_ex;   // < R <= road_cap
+                    fr.bl.road[j] = (uint32_t)(tile_base + rl);
+                    fr.bl.item_off[j] = item0 + it_ex;
+                    fr.bl.best[j] = ~0ull;
+                    fr.bl.pending[j] = it;
+                    big_ex += 1;
+                    it_ex += it;
+                }
             }
         }
         __syncthreads();
@@ -361,40 +428,33 @@ __global__ void k_unpack_events(const uint32_t *__restrict__ words,
                                 const Dims *__restrict__ dims,
                                 const uint32_t *__restrict__ event_road,
                                 unsigned long long *status) {
-    const uint64_t n_words = dims->n_words, n_events = dims->n_events;
-    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid == 0) {
-        if (__ldg(event_off) != 0 || __ldg(event_off + n_events) != n_words)
-            report(status, 0, SVT_ERR_BAD_ARG);
-    }
-    for (uint64_t e = tid; e < n_events; e += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t s = __ldg(event_off + e), s1 = __ldg(event_off + e + 1);
-        if (s1 <= s || s >= n_words) {
-            report(status, 0, SVT_ERR_BAD_ARG);
-            continue;
-        }
-        const uint32_t h = __ldg(words + s);
-        if (w_type(h) != TYPE_EVENT) {
-            report(status, s, SVT_ERR_BAD_TYPE);                                   // V1
-        } else if (ev_nroads(h) != event_road[e + 1] - event_road[e]) {
-            report(status, s, SVT_ERR_NROADS_MISMATCH);                            // V10
-        }
-    }
+    check_events(words, event_off, dims->n_words, dims->n_events, event_road, status,
+                 (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                 (uint64_t)gridDim.x * blockDim.x);
 }
 
 }  // namespace
 
-void launch_set_dims(Dims *dims, uint64_t n_words, uint64_t n_events, unsigned long long *status,
-                     uint64_t *counts, int n_counts, cudaStream_t st, const uint64_t *sizes) {
-    k_set_dims<<<1, 32, 0, st>>>(dims, n_words, n_events, sizes, status, counts, n_counts);
+void launch_prologue(Dims *dims, uint64_t n_words, uint64_t n_events, const uint64_t *sizes,
+                     const uint64_t *event_off, uint32_t *first_ev, unsigned long long *status,
+                     uint64_t *counts, int n_counts, uint64_t *zero, int n_zero, int grid,
+                     cudaStream_t st) {
+    uint64_t g = first_ev ? (n_events + 1 + 255) / 256 : 1;
+    if (g > (uint64_t)grid) g = (uint64_t)grid;
+    if (g < 1) g = 1;
+    k_prologue<<<(int)g, 256, 0, st>>>(dims, n_words, n_events, sizes, event_off, first_ev, status,
+                                       counts, n_counts, zero, n_zero);
 }
 
 void launch_unpack_count(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
-                         uint64_t max_words, uint32_t n_sectors, uint32_t *tile_roads,
-                         unsigned long long *status, int grid, cudaStream_t st) {
+                         const uint32_t *first_ev, uint64_t max_words, uint32_t n_sectors,
+                         uint32_t *tile_roads, unsigned long long *status, int grid,
+                         cudaStream_t st) {
     uint64_t T = n_tiles(max_words);
     int g = (int)(T < (uint64_t)grid ? T : (uint64_t)grid);
-    if (g > 0) k_unpack_count<<<g, TILE_THREADS, 0, st>>>(words, event_off, dims, n_sectors, tile_roads, status);
+    if (g > 0)
+        k_unpack_count<<<g, TILE_THREADS, 0, st>>>(words, event_off, dims, first_ev, n_sectors,
+                                                   tile_roads, status);
 }
 
 void launch_scan_tiles(uint32_t *a, const Dims *dims, const uint64_t *n_dev, uint64_t *total64,
@@ -403,16 +463,16 @@ void launch_scan_tiles(uint32_t *a, const Dims *dims, const uint64_t *n_dev, uin
 }
 
 void launch_unpack_roads(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
-                         uint64_t max_words, const uint32_t *tile_roads, uint64_t road_cap,
-                         uint32_t *road_word, uint32_t *road_nhit, uint32_t *event_road,
-                         const svt_config cfg, const FusedRoads fr, uint64_t *counts,
-                         unsigned long long *status, int grid, cudaStream_t st) {
+                         const uint32_t *first_ev, uint64_t max_words, const uint32_t *tile_roads,
+                         uint64_t road_cap, uint32_t *road_word, uint32_t *road_nhit,
+                         uint32_t *event_road, const svt_config cfg, const FusedRoads fr,
+                         uint64_t *counts, unsigned long long *status, int grid, cudaStream_t st) {
     uint64_t T = n_tiles(max_words);
     int g = (int)(T < (uint64_t)grid ? T : (uint64_t)grid);
     if (g > 0)
-        k_unpack_roads<<<g, TILE_THREADS, 0, st>>>(words, event_off, dims, tile_roads, road_cap,
-                                                   road_word, road_nhit, event_road, cfg, fr,
-                                                   counts, status);
+        k_unpack_roads<<<g, TILE_THREADS, 0, st>>>(words, event_off, dims, first_ev, tile_roads,
+                                                   road_cap, road_word, road_nhit, event_road,
+                                                   cfg, fr, counts, status);
 }
 
 void launch_unpack_events(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
