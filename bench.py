@@ -57,6 +57,11 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--no-tune", action="store_true", help="use the default schedule")
+    ap.add_argument("--sweep", action="store_true",
+                    help="latency against the number of fits for the paper-shape workload "
+                         "(Sec. 4.1): CPU oracle serial and per-event threads, fused and "
+                         "plain paths, plain-path stage breakdown; prints one JSON line")
+    ap.add_argument("--sweep-reps", type=int, default=100)
     ap.add_argument("--rows", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--bps", type=int, default=0)
@@ -302,8 +307,154 @@ def run_reference(args, world, rank):
     print(json.dumps(line))
 
 
+SWEEP_EVENTS = (1, 2, 5, 10, 20, 50, 100, 200, 500, 1000, 2000, 3000)
+
+
+def run_sweep(args):
+    """The shape of the paper's Sec. 4.1 on GB300: events of 2048
+    combinations (32 roads x 2^6), 1 to 3000 events per batch, every batch
+    processed `--sweep-reps` times.  Per batch size: the CPU oracle serial and
+    with one event per thread (the paper's embarrassingly parallel strategy),
+    the fused path with inputs resident and end to end from pinned host
+    memory, and the plain per-stage path with the fraction of its time in
+    unpack, combine, fit and select + format (the paper's breakdown)."""
+    import torch
+    import oracle
+    from paper_1311_0380_gb300 import api, synth
+    dev = torch.device("cuda", 0)
+    spec = synth.SPECS["paper"]
+    consts = synth.make_constants(spec.n_sectors)
+    full = synth.make_batch(spec, max(SWEEP_EVENTS), consts)
+    cfg = api.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, spec.n_sectors)
+    ocfg = oracle.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, spec.n_sectors)
+    dconst = api.DeviceConstants.from_numpy(consts.F, consts.q, cfg, dev)
+    stream = torch.cuda.current_stream()
+    reps = max(3, args.sweep_reps)
+
+    def ev_pair():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    rows = []
+    for n_ev in SWEEP_EVENTS:
+        n_words = int(full.event_off[n_ev])
+        words, off = full.words[:n_words], full.event_off[: n_ev + 1].copy()
+        R = int(np.sum(full.n_roads[:n_ev]))
+        fits = int(np.sum(full.combinations(spec.max_comb)[:R]))
+        d_words, d_off = api.to_device_u32(words, dev), api.to_device_u64(off, dev)
+        # fused, resident
+        fp = api.FusedPath(n_words, n_ev, R, dconst, None, dev)
+        for _ in range(3):
+            fp.run(d_words, n_words, d_off, n_ev)
+        evs = [ev_pair() for _ in range(reps)]
+        for a, b in evs:
+            a.record(stream)
+            fp.run(d_words, n_words, d_off, n_ev)
+            b.record(stream)
+        torch.cuda.synchronize()
+        st, rec, _ = fp.result()
+        assert st == api.N.STATUS_OK
+        fused = [a.elapsed_time(b) * 1e3 for a, b in evs]
+        # fused, end to end
+        runner = api.HostRunner(fp, stream)
+        h_w, h_o = api.HostRunner.pin_batch(words, off)
+        for _ in range(3):
+            runner.submit(h_w, h_o, R)
+            runner.wait()
+        e2e = []
+        for _ in range(reps):
+            a, b = ev_pair()
+            a.record(stream)
+            runner.submit(h_w, h_o, R)
+            b.record(stream)
+            runner.wait()
+            e2e.append(a.elapsed_time(b) * 1e3)
+        # zero-copy: words and offsets stay in mapped host memory and the
+        # kernels read them in place (the records go to device memory and are
+        # copied back, or are written straight into host memory)
+        w_bytes = (4 * n_words + 255) // 256 * 256
+        mh = api.MappedHost(w_bytes + 8 * (n_ev + 1) + 24 * max(R, 1))
+        mh.view(np.uint32, 0, n_words)[:] = words
+        mh.view(np.uint64, w_bytes, n_ev + 1)[:] = off
+        out_off = w_bytes + 8 * (n_ev + 1)
+        h_out = torch.empty(6 * max(R, 1), dtype=torch.int32, pin_memory=True)
+        h_status = torch.empty(1, dtype=torch.int64, pin_memory=True)
+        zc = {}
+        for out_host in (False, True):
+            def zc_step():
+                out = mh.device(out_off) if out_host else fp.out
+                api.svt_run(mh.device(0), n_words, mh.device(w_bytes), n_ev, dconst.F, dconst.q,
+                            cfg, R, out, fp.event_road, fp.counts, fp.status, fp.workspace)
+                if not out_host:
+                    h_out[: 6 * R].copy_(fp.out[: 6 * R], non_blocking=True)
+                h_status.copy_(fp.status, non_blocking=True)
+            for _ in range(3):
+                zc_step()
+            torch.cuda.synchronize()
+            lat = []
+            for _ in range(reps):
+                a, b = ev_pair()
+                a.record(stream)
+                zc_step()
+                b.record(stream)
+                b.synchronize()
+                lat.append(a.elapsed_time(b) * 1e3)
+            got = (mh.view(np.uint32, out_off, 6 * R) if out_host else h_out[: 6 * R].numpy().view(np.uint32))
+            zst = int(h_status.numpy().view(np.uint64)[0])
+            assert zst == api.N.STATUS_OK and np.array_equal(got.reshape(-1, 6), rec)
+            zc["zero_copy_in_out_us" if out_host else "zero_copy_in_us"] = statistics.mean(lat)
+        mh.close()
+        # plain per-stage path with its breakdown
+        pp = api.PlainPath(n_words, n_ev, R, fits, dconst, dev)
+        for _ in range(3):
+            pp.run(d_words, n_words, d_off, n_ev)
+        marks = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(reps)]
+        for m in marks:
+            pp.run(d_words, n_words, d_off, n_ev, stage_marks=m)
+        torch.cuda.synchronize()
+        pst, prec, _ = pp.result()
+        assert pst == api.N.STATUS_OK and np.array_equal(prec, rec)
+        stages = np.array([[m[i].elapsed_time(m[i + 1]) * 1e3 for i in range(5)] for m in marks])
+        plain = stages.sum(1)
+        frac = stages.sum(0) / stages.sum()
+        # CPU oracle: serial, and one event per thread
+        cpu_reps = max(1, min(reps, int(4e6 // fits)))
+        t = []
+        for _ in range(cpu_reps):
+            t0 = time.perf_counter()
+            key, orec = oracle.run(words, off, consts.F, consts.q, ocfg, omp=False)
+            t.append((time.perf_counter() - t0) * 1e6)
+        assert key == oracle.KEY_OK and np.array_equal(orec, rec)
+        t_omp = []
+        for _ in range(cpu_reps):
+            t0 = time.perf_counter()
+            oracle.run(words, off, consts.F, consts.q, ocfg, omp=True)
+            t_omp.append((time.perf_counter() - t0) * 1e6)
+        row = {"events": n_ev, "fits": fits,
+               "cpu_serial_us": statistics.mean(t), "cpu_threads_us": statistics.mean(t_omp),
+               "fused_us": statistics.mean(fused), "fused_p50_us": percentile(fused, 50),
+               "fused_e2e_us": statistics.mean(e2e), **zc, "plain_us": float(plain.mean()),
+               "plain_breakdown": {"unpack": float(frac[0]), "combine": float(frac[1]),
+                                   "fit": float(frac[2]), "select_format": float(frac[3] + frac[4])},
+               "cpu_reps": cpu_reps, "gpu_reps": reps}
+        row["speedup_fused_e2e_vs_serial"] = row["cpu_serial_us"] / row["fused_e2e_us"]
+        row["speedup_fused_vs_serial"] = row["cpu_serial_us"] / row["fused_us"]
+        rows.append(row)
+        print(f"{n_ev:5d} ev {fits:8d} fits  serial {row['cpu_serial_us']:10.1f} us  "
+              f"threads {row['cpu_threads_us']:9.1f}  fused {row['fused_us']:7.1f}  "
+              f"e2e {row['fused_e2e_us']:7.1f}  zc {zc['zero_copy_in_us']:7.1f} "
+              f"{zc['zero_copy_in_out_us']:7.1f}  plain {row['plain_us']:8.1f}  "
+              f"[unpack {frac[0]:.2f} combine {frac[1]:.2f} fit {frac[2]:.2f}]",
+              file=sys.stderr, flush=True)
+        del fp, pp, runner
+    print(json.dumps({"sweep": "paper-shape (2048 fits per event)", "cpu_threads": oracle.num_threads(),
+                      "rows": rows}))
+
+
 def main():
     args = parse_args()
+    if args.sweep:
+        run_sweep(args)
+        return
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -347,6 +347,23 @@ int svt_run_noalloc(const uint32_t *d_words, uint64_t n_words, const uint64_t *d
                     const svt_schedule *sched, void *stream);
 
 /* ======================================================================
+ * Host memory the GPU reads and writes in place (zero-copy).  The paper's
+ * Sec. 4.2 compares staging a packet through host buffers with delivering it
+ * straight into GPU memory; on a GB300 node the Grace host memory is itself
+ * reachable from the GPU over NVLink-C2C, so a batch can stay in host memory
+ * and be read by the kernels directly.  svt_host_alloc returns `bytes` of
+ * pinned host memory mapped into the device address space: *host for the
+ * CPU, *device for kernels (both 256-byte aligned); any svt_* argument that
+ * takes device memory may point into it (for example d_words, d_event_off or
+ * d_out of svt_run).  Errors: BAD_ARG (null pointers, zero size), OOM (the
+ * allocation failed), CUDA (no device mapping, or a mapping that is not
+ * 256-byte aligned).  svt_host_free releases the
+ * memory; no work that uses it may still be in flight.
+ * ====================================================================== */
+int svt_host_alloc(size_t bytes, void **host, void **device);
+int svt_host_free(void *host);
+
+/* ======================================================================
  * Serving loop (the single-GPU form of the paper's trigger-node loop,
  * Sec. 3 and Sec. 4.2: data in -> GPU -> data out), with continuous
  * batching.  Events are submitted by reference -- a pointer to the event's

@@ -182,6 +182,49 @@ class DeviceConstants:
         return cls(to_device_i16(F, device), to_device_i16(q, device), cfg)
 
 
+class DevicePointer:
+    """A raw device address with the `data_ptr()` the wrappers take."""
+
+    def __init__(self, ptr: int):
+        self.ptr = int(ptr)
+
+    def data_ptr(self) -> int:
+        return self.ptr
+
+
+class MappedHost:
+    """Pinned host memory mapped into the GPU's address space (svt_host_alloc):
+    `host` is a numpy byte view for the CPU, `device(offset)` an address the
+    kernels read and write in place."""
+
+    def __init__(self, nbytes: int):
+        h, d = ctypes.c_void_p(), ctypes.c_void_p()
+        N.check(N.load().svt_host_alloc(int(nbytes), ctypes.byref(h), ctypes.byref(d)),
+                "svt_host_alloc")
+        self.nbytes = int(nbytes)
+        self._h, self._d = h.value, d.value
+        self.host = np.ctypeslib.as_array((ctypes.c_uint8 * self.nbytes).from_address(self._h))
+
+    def view(self, dtype, offset: int = 0, count: int | None = None) -> np.ndarray:
+        n = (self.nbytes - offset) // np.dtype(dtype).itemsize if count is None else count
+        return self.host[offset: offset + n * np.dtype(dtype).itemsize].view(dtype)
+
+    def device(self, offset: int = 0) -> DevicePointer:
+        return DevicePointer(self._d + int(offset))
+
+    def close(self):
+        if self._h:
+            self.host = None
+            N.check(N.load().svt_host_free(ctypes.c_void_p(self._h)), "svt_host_free")
+            self._h = self._d = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class FusedPath:
     """Buffers of the fused path for batches up to the given capacities."""
 
@@ -240,27 +283,42 @@ class PlainPath:
         self.best = torch.empty(rc * 6, dtype=torch.int32, device=d)
         self.out = torch.empty(rc * 6, dtype=torch.int32, device=d)
 
-    def run(self, words, n_words, event_off, n_events, stream=None, fit_events=None):
-        """All five stages; fit_events = (start, end) torch events recorded
-        around the fit stage on the same stream."""
+    def run(self, words, n_words, event_off, n_events, stream=None, fit_events=None,
+            stage_marks=None):
+        """All five stages.  fit_events = (start, end) torch events recorded
+        around the fit stage; stage_marks = six torch events recorded before
+        unpack and after unpack, combine, fit, select and format -- all on the
+        same stream."""
         c = self.consts
+        st = stream if stream is not None else torch.cuda.current_stream()
+
+        def mark(i):
+            if stage_marks is not None:
+                stage_marks[i].record(st)
+
+        mark(0)
         svt_unpack(words, n_words, event_off, n_events, c.cfg.n_sectors, self.road_cap,
                    self.road_word, self.road_nhit, self.event_road, self.n_roads, self.status,
                    self.ws_unpack, stream)
+        mark(1)
         svt_combine(self.road_nhit, self.n_roads, self.road_cap, c.cfg, self.comb_cap,
                     self.road_flags, self.comb_off, self.comb_road, self.comb_hits, self.n_combs,
                     self.status, self.ws_combine, stream)
+        mark(2)
         if fit_events is not None:
-            fit_events[0].record(stream if stream is not None else torch.cuda.current_stream())
+            fit_events[0].record(st)
         svt_fit(words, self.road_word, self.road_nhit, self.comb_road, self.comb_hits,
                 self.n_combs, self.comb_cap, c.F, c.q, c.cfg, self.fit_chi2, self.fit_par,
                 self.status, stream)
         if fit_events is not None:
-            fit_events[1].record(stream if stream is not None else torch.cuda.current_stream())
+            fit_events[1].record(st)
+        mark(3)
         svt_select(self.fit_chi2, self.fit_par, self.comb_cap, self.comb_off, self.road_flags,
                    self.n_roads, self.road_cap, c.cfg, self.best, self.status, stream)
+        mark(4)
         svt_format(self.best, words, self.road_word, self.n_roads, self.road_cap, self.out,
                    self.status, stream)
+        mark(5)
 
     def result(self):
         status = int(u64(self.status)[0])

@@ -480,6 +480,29 @@ done:
     return SVT_OK;
 }
 
+int svt_host_alloc(size_t bytes, void **host, void **device) {
+    if (!host || !device || bytes == 0) return SVT_ERR_BAD_ARG;
+    *host = nullptr;
+    *device = nullptr;
+    void *h = nullptr;
+    if (cudaHostAlloc(&h, bytes, cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess)
+        return SVT_ERR_OOM;
+    void *d = nullptr;
+    if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess || !d ||
+        (((uintptr_t)h | (uintptr_t)d) & 255u)) {
+        cudaFreeHost(h);
+        return SVT_ERR_CUDA;
+    }
+    *host = h;
+    *device = d;
+    return SVT_OK;
+}
+
+int svt_host_free(void *host) {
+    if (!host) return SVT_ERR_BAD_ARG;
+    return cudaFreeHost(host) == cudaSuccess ? SVT_OK : SVT_ERR_CUDA;
+}
+
 int svt_graph_launch(svt_graph g, void *stream) {
     if (!g) return SVT_ERR_BAD_ARG;
     return cudaGraphLaunch(g->exec, (cudaStream_t)stream) == cudaSuccess ? SVT_OK : SVT_ERR_CUDA;
