@@ -213,15 +213,17 @@ __global__ void __launch_bounds__(1024)
 //  * the tile is staged in shared memory with 16 words before it and 100
 //    after it (a valid road has at most 96 hits, so a road that starts in the
 //    tile ends in the staged range);
-//  * a block scan gives every road header its index; each hit word adds one to
-//    its road's counter of its layer (shared-memory atomics on the packed
-//    5-bits-per-layer word; a field can only overflow with more than 31 hits of
-//    one layer, which rule V8 already rejects);
-//  * rule V8 is checked per word on the staged window: a hit whose 16
-//    predecessors are hits of the same layer is the 17th (or later) of a
-//    contiguous block.  For the smallest status key this matches counting
-//    over the run: the first out-of-order hit of a run is an UNSORTED word
-//    that precedes any later, non-contiguous 17th hit;
+//  * a block scan gives every road header its index; each thread adds its hits
+//    to its road's counters of their layers (one shared-memory atomic per run
+//    of its words in one road, on the packed 5-bits-per-layer word; a field can
+//    only overflow with more than 31 hits of one layer, which rule V8 already
+//    rejects);
+//  * rule V8: a hit whose 16 predecessors are hits of the same layer is the
+//    17th (or later) of a contiguous block.  For the smallest status key this
+//    matches counting over the run: the first out-of-order hit of a run is an
+//    UNSORTED word that precedes any later, non-contiguous 17th hit.  Every
+//    word gets one bit, "a hit of the same layer as the word before", in a
+//    bitmap of the tile and its front halo; V8 fires where 16 set bits end;
 //  * one thread per road then writes the road's outputs; for the fused path
 //    the tile's split roads are appended to the work list at a range that
 //    one atomic reserves for the whole tile.
@@ -241,6 +243,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
     __shared__ uint16_t hdr_pos[TILE_WORDS];          // tile position of each road header
     __shared__ int last_nonhit;
     __shared__ unsigned long long big_base;
+    __shared__ uint32_t same_bits[1 + TILE_WORDS / 32];   // V8 bitmap, see below
     const uint64_t n_words = dims->n_words, n_events = dims->n_events;
     const uint64_t T = n_tiles(n_words);
     for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
@@ -284,39 +287,73 @@ __global__ void __launch_bounds__(TILE_THREADS)
             }
         }
         __syncthreads();
-        // hits: count into their road, check V8, note the tile's last non-hit word
+        // hits: count into their road (one shared atomic per run of the
+        // thread's words that belongs to one road), note the tile's last
+        // non-hit word, and mark "same layer as the word before" for V8
         {
             int r = (int)ex - 1;   // local road of the latest header before this thread's words
             int my_last_nonhit = -1;
+            uint32_t acc = 0;      // hits of road r among this thread's words, 5 bits per layer
+            uint32_t same = 0;     // bit j: word j and the word before are hits of one layer
+            uint32_t prev = sw[FRONT + threadIdx.x * TILE_PER_THREAD - 1];
 #pragma unroll
             for (int j = 0; j < TILE_PER_THREAD; ++j) {
                 const int p = threadIdx.x * TILE_PER_THREAD + j;
-                if (p >= tile_len) break;
                 const uint32_t x = w[j];
+                const bool in = p < tile_len;
                 const uint32_t ty = w_type(x);
-                if (ty == TYPE_ROAD) r += 1;
+                if (in && ty == TYPE_HIT && w_type(prev) == TYPE_HIT && hit_layer(prev) == hit_layer(x))
+                    same |= 1u << j;
+                prev = x;
+                if (!in) continue;
+                if (ty == TYPE_ROAD) {
+                    if (acc && r >= 0) atomicAdd(&cnt[r], acc);
+                    acc = 0;
+                    r += 1;
+                }
                 if (ty != TYPE_HIT) {
                     my_last_nonhit = p;
                     continue;
                 }
-                const uint32_t l = hit_layer(x);
-                if (r >= 0) atomicAdd(&cnt[r], 1u << (5 * l));
-                // the 16 words before p are hits of layer l (checked in full only
-                // when the 16th one back is)
-                const uint32_t y16 = sw[FRONT + p - 16];
-                if (w_type(y16) == TYPE_HIT && hit_layer(y16) == l) {
-                    bool run16 = true;
-#pragma unroll
-                    for (int d = 1; d < 16; ++d) {
-                        const uint32_t y = sw[FRONT + p - d];
-                        run16 = run16 && w_type(y) == TYPE_HIT && hit_layer(y) == l;
-                    }
-                    if (run16) report(status, tile_start + p, SVT_ERR_TOO_MANY_HITS);
-                }
+                acc += 1u << (5 * hit_layer(x));
             }
+            if (acc && r >= 0) atomicAdd(&cnt[r], acc);
             if (my_last_nonhit >= 0) atomicMax(&last_nonhit, my_last_nonhit);
+            // same-layer bits of tile position q at bit q + 32 of the bitmap
+            // (word 1 + q / 32); word 0 covers the front halo
+            uint32_t v = same << (8 * (threadIdx.x & 3));
+            v |= __shfl_xor_sync(0xffffffffu, v, 1);
+            v |= __shfl_xor_sync(0xffffffffu, v, 2);
+            if ((threadIdx.x & 3) == 0) same_bits[1 + threadIdx.x / 4] = v;
+            if (threadIdx.x < 32) {
+                const int q = (int)threadIdx.x - 32;   // halo position, -32..-1 (-15..-1 used)
+                const uint32_t a = q >= -15 ? sw[FRONT + q] : 0u, b = q >= -15 ? sw[FRONT + q - 1] : 0u;
+                const bool s_ = q >= -15 && w_type(a) == TYPE_HIT && w_type(b) == TYPE_HIT &&
+                                hit_layer(a) == hit_layer(b);
+                const uint32_t h = __ballot_sync(0xffffffffu, s_);
+                if (threadIdx.x == 0) same_bits[0] = h;
+            }
         }
         __syncthreads();
+        // V8: a hit whose 16 predecessors are hits of its layer is the 17th (or
+        // later) of a run, i.e. 16 consecutive "same" bits end at it.  Thread k
+        // looks at bitmap words k - 1 and k: bit i of X is position 32 (k - 2) + i,
+        // and after the four steps bit s of y says bits s .. s + 15 of X are set.
+        if (threadIdx.x >= 1 && threadIdx.x <= TILE_WORDS / 32) {
+            const int k = threadIdx.x;
+            const unsigned long long X =
+                (unsigned long long)same_bits[k - 1] | ((unsigned long long)same_bits[k] << 32);
+            unsigned long long y = X & (X >> 1);
+            y &= y >> 2;
+            y &= y >> 4;
+            y &= y >> 8;
+            const unsigned long long m = y & (0xFFFFFFFFull << 17);   // runs ending in word k
+            if (m) {
+                const int s_ = __ffsll((long long)m) - 1;
+                report(status, tile_start + (uint64_t)(32 * (k - 2) + s_ + 15),
+                       SVT_ERR_TOO_MANY_HITS);
+            }
+        }
         // hits after the tile that continue the tile's last road
         if (n_roads_tile > 0 && last_nonhit == (int)hdr_pos[n_roads_tile - 1]) {
             const int r = (int)n_roads_tile - 1;
