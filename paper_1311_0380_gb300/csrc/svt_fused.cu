@@ -43,6 +43,7 @@ struct WarpSmem {
     int32_t q[6];
     uint32_t n[N_LAYERS];                 // n'_l = max(n_l, 1)
     uint32_t m[N_LAYERS];                 // division magic of n'_l
+    uint32_t off[N_LAYERS];               // index of the first hit of layer l in the road
 };
 
 // largest j in [0, n) with off[j] <= it (off non-decreasing, off[0] = 0)
@@ -61,13 +62,13 @@ __device__ __forceinline__ uint32_t find_slot(const uint32_t *__restrict__ off, 
     return lo;
 }
 
+// Smallest 64-bit key over the warp: the smallest high word, then the
+// smallest low word among the lanes that hold it.
 __device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) {
-        unsigned long long o = __shfl_xor_sync(0xffffffffu, v, d);
-        v = o < v ? o : v;
-    }
-    return v;
+    const uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
+    const uint32_t m_hi = __reduce_min_sync(0xffffffffu, hi);
+    const uint32_t m_lo = __reduce_min_sync(0xffffffffu, hi == m_hi ? lo : 0xFFFFFFFFu);
+    return ((unsigned long long)m_hi << 32) | m_lo;
 }
 
 __device__ __forceinline__ int32_t clamp_chi(int32_t y) { return max(min(y, 32767), -32767); }
@@ -111,11 +112,18 @@ __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restr
     sm.F[lane] = f0;
     if (lane < 4) sm.F[32 + lane] = f1;
     else if (lane < 10) sm.q[lane - 4] = f1;
+    const uint32_t nl = lane < N_LAYERS ? nhit_of(packed, lane) : 0u;
+    uint32_t incl = nl;   // inclusive prefix of the layer counts
+#pragma unroll
+    for (int d = 1; d < 8; d <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
     if (lane < N_LAYERS) {
-        const uint32_t nl = nhit_of(packed, lane);
         const uint32_t np = nl ? nl : 1u;
         sm.n[lane] = np;
         sm.m[lane] = kDivMagic[np];
+        sm.off[lane] = incl - nl;
         if (nl == 0) {   // a layer without hits contributes x = 0
             sm.x[lane * MAX_HITS] = 0;
             sm.T[(lane * MAX_HITS) * 3 + 0] = 0;
@@ -129,10 +137,7 @@ __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restr
         const uint32_t h = (uint32_t)lane + 32u * j;
         if (h < g.total_hits) {
             const uint32_t l = hit_layer(hv[j]);
-            uint32_t i = h;
-#pragma unroll
-            for (int ll = 0; ll < N_LAYERS; ++ll)
-                if ((uint32_t)ll < l) i -= nhit_of(packed, ll);
+            const uint32_t i = h - sm.off[l];   // hits are sorted by layer (validated)
             const uint32_t xc = hit_coord(hv[j]);
             sm.x[l * MAX_HITS + i] = xc;
             long long *t = sm.T + (l * MAX_HITS + i) * 3;
@@ -290,22 +295,32 @@ __device__ __forceinline__ bool format_road(WarpSmem &sm, const RoadDesc &D, con
     if (pass) flags |= SVT_FLAG_PASS;
     const uint32_t low = (uint32_t)best;
     const uint32_t row = low >> 9, col = low & 511u;
+    // parameters of the best combination: lane 8k + l (k < 3, l < 6) forms
+    // F[k][l] x_l, the groups of eight lanes sum them, lane 8k adds q_k
     int32_t p = 0;
-    if (pass && lane < 3) {
-        long long acc = (long long)sm.q[lane] * (1ll << cfg.qshift);
-        uint32_t rem = col;
+    if (pass) {
+        const uint32_t k = (uint32_t)lane >> 3, lk = (uint32_t)lane & 7u;
+        uint32_t rem = col, i_own = 0;
 #pragma unroll
         for (int l = N_LAYERS - 1; l >= 0; --l) {
             if ((uint32_t)l + 1u == g.split) rem = row;   // the prefix layers take the row
             const uint32_t nl = sm.n[l];
             const uint32_t qd = div_by(rem, nl, sm.m[l]);
-            const uint32_t i = rem - qd * nl;
+            if ((uint32_t)l == lk) i_own = rem - qd * nl;
             rem = qd;
-            acc += (long long)sm.F[lane * 6 + l] * (long long)sm.x[l * MAX_HITS + i];
         }
-        p = (int32_t)(acc >> cfg.oshift);   // arithmetic shift: floor
+        long long t = 0;
+        if (k < 3 && lk < (uint32_t)N_LAYERS)
+            t = (long long)sm.F[k * 6 + lk] * (long long)sm.x[lk * MAX_HITS + i_own];
+        t += __shfl_xor_sync(0xffffffffu, t, 4);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        if (k < 3 && lk == 0) {
+            const long long acc = (long long)sm.q[k] * (1ll << cfg.qshift) + t;
+            p = (int32_t)(acc >> cfg.oshift);   // arithmetic shift: floor
+        }
     }
-    const int32_t pk = __shfl_sync(0xffffffffu, p, (lane + 29) & 31);   // lane 3 + k gets p_k
+    const int32_t pk = __shfl_sync(0xffffffffu, p, ((lane + 29) & 31) << 3);   // lane 3 + k gets p_k
     const uint32_t w = lane == 0   ? (rd_id(D.a.z) | (flags << 24))
                        : lane == 1 ? (pass ? row * g.NB + col : 0xFFFFFFFFu)
                        : lane == 2 ? (pass ? (uint32_t)(best >> 32) : 0u)
