@@ -36,8 +36,10 @@ constexpr int ROWS_MAX = 64;
 // of a 64-bit sum of such terms is then exactly floor(sum / 2^oshift).
 struct WarpSmem {
     long long T[N_LAYERS * MAX_HITS * 3]; // chi-row terms F[3+k][l] * x * 2^(32-oshift), [l][i][k]
-    longlong2 S[32][2];                   // suffix sums below the top suffix layer, [b'](3 rows)
-    longlong2 A[ROWS_MAX][2];             // prefix sums incl. q, per row: (A3, A4), (A5, -)
+    longlong2 S01[32];                    // suffix sums below the top suffix layer, rows 3, 4 [b']
+    long long S5[32];                     // ... row 5
+    longlong2 A01[ROWS_MAX];              // prefix sums incl. q, rows 3, 4, per row of the chunk
+    long long A5[ROWS_MAX];               // ... row 5
     uint32_t x[N_LAYERS * MAX_HITS];      // hit coordinates [l][i] (x = 0 for an empty layer)
     int32_t F[36];                        // F[s][m][k][l] at k*6+l
     int32_t q[6];
@@ -164,8 +166,8 @@ __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restr
                 S5 += t[2];
             }
         }
-        sm.S[lane][0] = make_longlong2(S3, S4);
-        sm.S[lane][1] = make_longlong2(S5, 0);
+        sm.S01[lane] = make_longlong2(S3, S4);
+        sm.S5[lane] = S5;
     }
     __syncwarp();
 }
@@ -189,8 +191,8 @@ __device__ __forceinline__ void build_row(WarpSmem &sm, uint32_t split, uint32_t
             A5 += t[2];
         }
     }
-    sm.A[slot][0] = make_longlong2(A3, A4);
-    sm.A[slot][1] = make_longlong2(A5, 0);
+    sm.A01[slot] = make_longlong2(A3, A4);
+    sm.A5[slot] = A5;
 }
 
 __device__ __forceinline__ int32_t hi_word(long long v) {
@@ -217,31 +219,32 @@ __device__ __forceinline__ unsigned long long eval_rows(WarpSmem &sm, const Geo 
     const uint32_t is0 = div_by((uint32_t)lane, NBp, mp), bp0 = (uint32_t)lane - is0 * NBp;
     for (uint32_t ac = a_lo; ac < a_hi; ac += ROWS_MAX) {
         const uint32_t ae = min(ac + (uint32_t)ROWS_MAX, a_hi);
-        if (ac + lane < ae) build_row(sm, top, ac + lane, lane, qsh);
-        if (ac + lane + 32 < ae) build_row(sm, top, ac + lane + 32, lane + 32, qsh);
+#pragma unroll
+        for (uint32_t r0 = 0; r0 < (uint32_t)ROWS_MAX; r0 += 32)
+            if (ac + r0 + lane < ae) build_row(sm, top, ac + r0 + lane, r0 + lane, qsh);
         __syncwarp();
         uint32_t is = is0, bp = bp0;   // column b = is * NBp + bp
         for (uint32_t b0 = 0; b0 < NB; b0 += 32) {
             const uint32_t b = b0 + (uint32_t)lane;
             if (b < NB) {
                 const long long *t = sm.T + (top * MAX_HITS + is) * 3;
-                const longlong2 s01 = sm.S[bp][0], s2 = sm.S[bp][1];
+                const longlong2 s01 = sm.S01[bp];
+                const long long s5 = sm.S5[bp];
                 // GUARDED: the column terms carry +32768 in the high word, so the
                 // inner loop sees g_k = y_k + 32768 (mod 2^32) directly
                 const long long bias = GUARDED ? (32768LL << 32) : 0LL;
                 const long long B3 = t[0] + s01.x + bias, B4 = t[1] + s01.y + bias,
-                                B5 = t[2] + s2.x + bias;
+                                B5 = t[2] + s5 + bias;
                 uint32_t a_end = ae;
                 if (ae == NA && (NA - 1) * NB + b >= C_eval) a_end = ae - 1;
                 uint32_t bchi = init_chi, ba = 0;
-                const longlong2 *Ap = &sm.A[0][0];
 #pragma unroll 4
-                for (uint32_t a = ac; a < a_end; ++a, Ap += 2) {
-                    const longlong2 v01 = Ap[0];
-                    const longlong2 v2 = Ap[1];
+                for (uint32_t a = ac; a < a_end; ++a) {
+                    const longlong2 v01 = sm.A01[a - ac];
+                    const long long v5 = sm.A5[a - ac];
                     const int32_t y3 = hi_word(v01.x + B3);
                     const int32_t y4 = hi_word(v01.y + B4);
-                    const int32_t y5 = hi_word(v2.x + B5);
+                    const int32_t y5 = hi_word(v5 + B5);
                     if (GUARDED) {
                         const uint32_t g3 = (uint32_t)y3, g4 = (uint32_t)y4, g5 = (uint32_t)y5;
                         // g_k < 2^16 for all three <=> -32768 <= y_k <= 32767; then
