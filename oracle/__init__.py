@@ -26,12 +26,14 @@ KEY_OK = (1 << 64) - 1
 E_BAD_ARG, E_BAD_TYPE, E_BAD_RESERVED, E_BAD_LAYER = 1, 2, 3, 4
 E_UNSORTED, E_TOO_MANY_HITS, E_BAD_SECTOR, E_NROADS_MISMATCH = 5, 6, 7, 8
 E_BAD_CONFIG = 10
+E_XFT_UNPAIRED = 12
 F_PASS, F_OVERFLOW, F_BAD_PATTERN, F_NO_HITS = 1, 2, 4, 8
 
 
 class OrcConfig(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
-                ("oshift", "qshift", "chi2_cut", "max_comb", "min_layers", "n_sectors")]
+                ("oshift", "qshift", "chi2_cut", "max_comb", "min_layers", "n_sectors",
+                 "xft_pairs")]
 
 
 def build(force: bool = False) -> str:
@@ -62,7 +64,7 @@ def lib():
             cfgp = ctypes.POINTER(OrcConfig)
             u64 = ctypes.c_uint64
             L.orc_validate.restype = u64
-            L.orc_validate.argtypes = [u32p, u64, u64p, u64, ctypes.c_uint32]
+            L.orc_validate.argtypes = [u32p, u64, u64p, u64, ctypes.c_uint32, ctypes.c_uint32]
             L.orc_fit_one.restype = None
             L.orc_fit_one.argtypes = [i16p, i16p, u32p, ctypes.c_uint32, ctypes.c_uint32, i64p, u32p]
             L.orc_road.restype = u64
@@ -86,15 +88,17 @@ def _p(a, ct):
     return a.ctypes.data_as(ctypes.POINTER(ct))
 
 
-def config(oshift=15, qshift=15, chi2_cut=0xFFFFFFFF, max_comb=262144, min_layers=5, n_sectors=512):
-    return OrcConfig(oshift, qshift, chi2_cut, max_comb, min_layers, n_sectors)
+def config(oshift=15, qshift=15, chi2_cut=0xFFFFFFFF, max_comb=262144, min_layers=5, n_sectors=512,
+           xft_pairs=0):
+    return OrcConfig(oshift, qshift, chi2_cut, max_comb, min_layers, n_sectors, xft_pairs)
 
 
-def validate(words, event_off, n_sectors):
+def validate(words, event_off, n_sectors, xft_pairs=0):
     words = np.ascontiguousarray(words, np.uint32)
     event_off = np.ascontiguousarray(event_off, np.uint64)
     return int(lib().orc_validate(_p(words, ctypes.c_uint32), len(words),
-                                  _p(event_off, ctypes.c_uint64), len(event_off) - 1, n_sectors))
+                                  _p(event_off, ctypes.c_uint64), len(event_off) - 1, n_sectors,
+                                  xft_pairs))
 
 
 def decode_key(key):
@@ -129,8 +133,8 @@ def road(n, coords, sector, road_id, F, q, cfg, detail=False):
     q = np.ascontiguousarray(q, np.int16)
     rec = np.zeros(6, np.uint32)
     C = 1
-    for v in n:
-        C *= max(int(v), 1)
+    for l, v in enumerate(n):
+        C *= 1 if (l == 5 and cfg.xft_pairs) else max(int(v), 1)
     n_eval = min(C, cfg.max_comb) if detail else 0
     all_chi2 = np.zeros(max(n_eval, 1), np.uint32)
     all_y = np.zeros((max(n_eval, 1), 6), np.int64)

@@ -24,8 +24,13 @@
  *   - combination index c is mixed radix over layers, layer 0 most
  *     significant and layer 5 fastest; hits keep their order of appearance;
  *   - a road with more than max_comb combinations evaluates only the first
- *     max_comb of them and is flagged OVERFLOW.
- * The input validation follows the word-format rules V1..V10 listed at
+ *     max_comb of them and is flagged OVERFLOW;
+ *   - with xft_pairs set, layers 4 and 5 are the two coordinates (phi and
+ *     curvature) of one track-trigger track: hit i of layer 4 goes with hit i
+ *     of layer 5, a road must carry as many hits in layer 5 as in layer 4
+ *     (rule V11), and the combinations run over layers 0..4 only, layer 5
+ *     taking layer 4's hit index.
+ * The input validation follows the word-format rules V1..V11 listed at
  * orc_validate() below.
  */
 #include <stdint.h>
@@ -44,6 +49,7 @@
 #define ORC_E_BAD_SECTOR 7u
 #define ORC_E_NROADS_MISMATCH 8u
 #define ORC_E_BAD_CONFIG 10u
+#define ORC_E_XFT_UNPAIRED 12u
 
 /* output flags, stored in bits [31:24] of record word 0 */
 #define ORC_F_PASS 1u
@@ -52,7 +58,7 @@
 #define ORC_F_NO_HITS 8u
 
 typedef struct {
-    uint32_t oshift, qshift, chi2_cut, max_comb, min_layers, n_sectors;
+    uint32_t oshift, qshift, chi2_cut, max_comb, min_layers, n_sectors, xft_pairs;
 } orc_config;
 
 /* ---- word fields ---- */
@@ -75,6 +81,7 @@ int orc_config_ok(const orc_config *cfg) {
     if (cfg->qshift > 24) return 0;
     if (cfg->max_comb < 1) return 0;
     if (cfg->min_layers > 6) return 0;
+    if (cfg->xft_pairs > 1) return 0;
     if (cfg->n_sectors < 1 || cfg->n_sectors > 512) return 0;
     return 1;
 }
@@ -97,9 +104,11 @@ int orc_config_ok(const orc_config *cfg) {
  *   V9  t == 2 and sector >= n_sectors                          BAD_SECTOR
  *   V10 i == start, t == 3 and n_roads(w) != number of type-2 words in the
  *       event                                                   NROADS_MISMATCH
+ *   V11 (xft_pairs only) t == 2 and the hit run that follows the header has a
+ *       different number of layer-4 and layer-5 hits           XFT_UNPAIRED
  */
 uint64_t orc_validate(const uint32_t *words, uint64_t n_words, const uint64_t *event_off,
-                      uint64_t n_events, uint32_t n_sectors) {
+                      uint64_t n_events, uint32_t n_sectors, uint32_t xft_pairs) {
     uint64_t key = ORC_KEY_OK;
     if (event_off[0] != 0 || event_off[n_events] != n_words) return make_key(0, ORC_E_BAD_ARG);
     for (uint64_t e = 0; e < n_events; ++e)
@@ -109,9 +118,15 @@ uint64_t orc_validate(const uint32_t *words, uint64_t n_words, const uint64_t *e
         uint64_t start = event_off[e], end = event_off[e + 1];
         uint64_t n_road_headers = 0;
         int in_road_run = 0;       /* inside the hit run that follows a road header */
+        uint64_t header = 0;       /* word index of that header */
         uint32_t run_count[8];
         memset(run_count, 0, sizeof run_count);
-        for (uint64_t i = start; i < end; ++i) {
+        for (uint64_t i = start; i <= end; ++i) {
+            if (i == end) {        /* the end of the event closes the last run */
+                if (in_road_run && xft_pairs && run_count[4] != run_count[5])
+                    note(&key, header, ORC_E_XFT_UNPAIRED);                         /* V11 */
+                break;
+            }
             uint32_t w = words[i], t = w_type(w);
             if (i == start && t != 3) note(&key, i, ORC_E_BAD_TYPE);            /* V1 */
             if (i != start && t == 3) note(&key, i, ORC_E_BAD_TYPE);            /* V2 */
@@ -128,12 +143,15 @@ uint64_t orc_validate(const uint32_t *words, uint64_t n_words, const uint64_t *e
                     if (run_count[hit_layer(w)] > 16) note(&key, i, ORC_E_TOO_MANY_HITS); /* V8 */
                 }
             } else {
+                if (in_road_run && xft_pairs && run_count[4] != run_count[5])
+                    note(&key, header, ORC_E_XFT_UNPAIRED);                         /* V11 */
                 in_road_run = 0;
             }
             if (t == 2) {
                 n_road_headers += 1;
                 if (rd_sector(w) >= n_sectors) note(&key, i, ORC_E_BAD_SECTOR);    /* V9 */
                 in_road_run = 1;
+                header = i;
                 memset(run_count, 0, sizeof run_count);
             }
         }
@@ -197,8 +215,12 @@ uint64_t orc_road(const uint32_t *n, const uint32_t *coords, uint32_t sector, ui
     if (n_layers_hit < cfg->min_layers) {
         flags |= ORC_F_BAD_PATTERN;
     } else {
+        /* with xft_pairs layer 5 is not a digit of its own (radix 1) */
+        uint32_t radix[6];
+        for (int l = 0; l < 6; ++l) radix[l] = (n[l] >= 1) ? n[l] : 1;
+        if (cfg->xft_pairs) radix[5] = 1;
         uint64_t C = 1;
-        for (int l = 0; l < 6; ++l) C *= (n[l] >= 1) ? n[l] : 1;
+        for (int l = 0; l < 6; ++l) C *= radix[l];
         n_eval = C;
         if (C > cfg->max_comb) { flags |= ORC_F_OVERFLOW; n_eval = cfg->max_comb; }
         const int16_t *Fsm = F + ((uint64_t)sector * 64 + mask) * 36;
@@ -207,10 +229,10 @@ uint64_t orc_road(const uint32_t *n, const uint32_t *coords, uint32_t sector, ui
             uint32_t idx[6], x[6];
             uint64_t rem = c;
             for (int l = 5; l >= 0; --l) {
-                uint32_t nl = (n[l] >= 1) ? n[l] : 1;
-                idx[l] = (uint32_t)(rem % nl);
-                rem /= nl;
+                idx[l] = (uint32_t)(rem % radix[l]);
+                rem /= radix[l];
             }
+            if (cfg->xft_pairs) idx[5] = idx[4];   /* the layer-4 hit's own partner */
             for (int l = 0; l < 6; ++l) x[l] = (n[l] >= 1) ? coords[l * 16 + idx[l]] : 0;
             int64_t y[6];
             uint32_t chi2;
@@ -273,7 +295,7 @@ uint64_t orc_run(const uint32_t *words, uint64_t n_words, const uint64_t *event_
                  uint64_t n_events, const int16_t *F, const int16_t *q, const orc_config *cfg,
                  uint32_t *out, uint64_t out_cap_roads, uint64_t *n_roads_out) {
     if (!orc_config_ok(cfg)) return make_key(0, ORC_E_BAD_CONFIG);
-    uint64_t key = orc_validate(words, n_words, event_off, n_events, cfg->n_sectors);
+    uint64_t key = orc_validate(words, n_words, event_off, n_events, cfg->n_sectors, cfg->xft_pairs);
     if (key != ORC_KEY_OK) return key;
     uint64_t R = 0;
     for (uint64_t e = 0; e < n_events; ++e) R += ev_nroads(words[event_off[e]]);
@@ -289,7 +311,7 @@ uint64_t orc_run_omp(const uint32_t *words, uint64_t n_words, const uint64_t *ev
                      uint64_t n_events, const int16_t *F, const int16_t *q, const orc_config *cfg,
                      uint32_t *out, uint64_t out_cap_roads, uint64_t *n_roads_out) {
     if (!orc_config_ok(cfg)) return make_key(0, ORC_E_BAD_CONFIG);
-    uint64_t key = orc_validate(words, n_words, event_off, n_events, cfg->n_sectors);
+    uint64_t key = orc_validate(words, n_words, event_off, n_events, cfg->n_sectors, cfg->xft_pairs);
     if (key != ORC_KEY_OK) return key;
     uint64_t *base = (uint64_t *)malloc((n_events + 1) * sizeof(uint64_t));
     if (!base) return make_key(0, ORC_E_BAD_ARG);

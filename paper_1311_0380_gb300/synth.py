@@ -231,6 +231,7 @@ class BatchSpec:
     seed: int
     noise: float = 0.2
     mode: str = "helix"
+    xft: bool = False          # layers 4, 5 come in pairs from one track-trigger track
 
     def sample_roads(self, rng, n):
         kind = self.roads[0]
@@ -265,6 +266,9 @@ SPECS = {
     "uneven": BatchSpec("uneven", 512, ("loguniform", 2048), ("uniform", 1, 16), 4096, BASE_SEED + 2),
     # the paper's fixed shape: 2048 combinations per event = 32 roads x 2^6
     "paper": BatchSpec("paper", 512, ("const", 32), ("const", 2), 262144, BASE_SEED + 5),
+    # the scaled shape with layers 4 and 5 paired (one track-trigger track per pair)
+    "xft": BatchSpec("xft", 512, ("poisson", 64), ("geom_cap", 1.0 / 3.0, 8), 262144,
+                     BASE_SEED + 6, xft=True),
 }
 
 
@@ -278,6 +282,7 @@ class Batch:
     d0: np.ndarray             # [R] truth per road
     phi0: np.ndarray
     c: np.ndarray
+    xft: bool = False          # layers 4, 5 paired
 
     @property
     def n_events(self):
@@ -288,8 +293,10 @@ class Batch:
         return int(self.n_roads.sum())
 
     def combinations(self, max_comb=None):
-        """Combinations per road, prod(max(n_l,1)), optionally capped."""
-        cnt = np.prod(np.maximum(self.n_hits, 1), axis=1)
+        """Combinations per road, prod(max(n_l,1)) (layer 5 left out when it is
+        paired with layer 4), optionally capped."""
+        n = np.maximum(self.n_hits, 1)
+        cnt = np.prod(n[:, :5] if self.xft else n, axis=1)
         return cnt if max_comb is None else np.minimum(cnt, max_comb)
 
 
@@ -299,6 +306,8 @@ def _gen_chunk(spec, consts, rng, n_events, first_event, first_road):
     n_roads = spec.sample_roads(rng, n_events)
     R = int(n_roads.sum())
     n_hits = spec.sample_hits(rng, R)
+    if spec.xft:
+        n_hits[:, 5] = n_hits[:, 4]
     d0 = rng.uniform(-D0_MAX_CM, D0_MAX_CM, R)
     phi0 = rng.uniform(0.0, 2.0 * np.pi, R)
     pt = rng.uniform(PT_MIN, PT_MAX, R)
@@ -314,6 +323,11 @@ def _gen_chunk(spec, consts, rng, n_events, first_event, first_road):
     road_of_hit = grp // N_LAYERS
     layer_of_hit = grp % N_LAYERS
     noise = rng.random(H) < spec.noise
+    if spec.xft:
+        # hit i of layer 5 is the second coordinate of the track of hit i of
+        # layer 4: both are the road's track or both are a fake track
+        l5 = np.nonzero(layer_of_hit == 5)[0]
+        noise[l5] = noise[l5 - n_hits[road_of_hit[l5], 4]]
     smear = rng.normal(0.0, 1.0, H) * SIGMA_LSB[layer_of_hit]
     coord = np.rint(xt[road_of_hit, layer_of_hit] + smear)
     coord = np.where(noise, rng.integers(0, COORD_MAX + 1, H), coord)
@@ -377,7 +391,7 @@ def make_batch(spec, n_events: int, consts: Constants | None = None, seed: int |
         base += len(p[0])
     event_off = np.concatenate(offs).astype(np.uint64)
     cat = lambda i: np.concatenate([p[i] for p in parts])
-    return Batch(words, event_off, cat(2), cat(3), cat(4), cat(5), cat(6), cat(7))
+    return Batch(words, event_off, cat(2), cat(3), cat(4), cat(5), cat(6), cat(7), spec.xft)
 
 
 def make_tracks_batch(consts: Constants, n_roads: int, seed: int, mode="linear",

@@ -301,3 +301,79 @@ def test_omp_and_road_sample_match_serial_run():
     rec3 = oracle.run_roads(b.words, pos[sel], consts.F, consts.q, cfg)
     assert np.array_equal(rec3, rec[sel])
     assert rec.shape == (b.total_roads, 6)
+
+
+# --------------------------------------------------------------------------- track-trigger pairs
+def test_xft_pairs_enumeration_against_big_integers():
+    """With xft_pairs the combinations run over layers 0..4 (layer 0 most
+    significant, layer 4 fastest) and layer 5 takes layer 4's hit: every y of
+    every combination against Python integers, the count against the closed
+    form prod_{l<5} max(n_l, 1), and the best record against exhaustion."""
+    rng = np.random.default_rng(61)
+    S = 2
+    F = rng.integers(-32768, 32768, (S, 64, 6, 6)).astype(np.int16)
+    q = rng.integers(-32768, 32768, (S, 64, 6)).astype(np.int16)
+    for trial in range(200):
+        n, hits = random_road(rng, max_hits=3)
+        n[5] = n[4]
+        hits[5] = rng.integers(0, 32768, int(n[5])).tolist()
+        sector = int(rng.integers(0, S))
+        cfg = oracle.config(15, 15, 0xFFFFFFFF, 1 << 24, 0, S, xft_pairs=1)
+        rec, chi2s, ys = oracle.road(n, hits, sector, 3, F, q, cfg, detail=True)
+        mask = sum(1 << l for l in range(6) if n[l] > 0)
+        combos = list(itertools.product(*[range(max(int(k), 1)) for k in n[:5]]))
+        assert len(chi2s) == len(combos) == int(np.prod(np.maximum(n[:5], 1)))
+        best = None
+        for c, idx in enumerate(combos):
+            i = list(idx) + [idx[4]]
+            x = [hits[l][i[l]] if n[l] > 0 else 0 for l in range(6)]
+            y_ref, chi_ref = bigint_fit(F[sector, mask].ravel(), q[sector, mask], x, 15, 15)
+            assert list(ys[c]) == y_ref and chi2s[c] == chi_ref
+            if best is None or chi_ref < best[1]:
+                best = (c, chi_ref)
+        assert rec[1] == best[0] and rec[2] == best[1]
+        # without pairing the same road has n_5 times as many combinations
+        cfg0 = oracle.config(15, 15, 0xFFFFFFFF, 1 << 24, 0, S)
+        assert len(oracle.road(n, hits, sector, 3, F, q, cfg0, detail=True)[1]) == \
+            len(combos) * max(int(n[5]), 1)
+
+
+def test_xft_unpaired_rule():
+    """V11: with xft_pairs a road whose layer-4 and layer-5 hit counts differ is
+    reported at its header word (code 12); the same words are valid without
+    pairing, and the smaller key still wins against other rules."""
+    ev = ["E:1:3",
+          "R:0:1", "H:0:5", "H:1:5", "H:2:5", "H:3:5", "H:4:1", "H:4:2", "H:5:9", "H:5:8",   # paired
+          "R:0:2", "H:0:5", "H:4:1", "H:4:2", "H:5:9",                                       # 2 vs 1
+          "R:0:3", "H:0:5", "H:1:5"]                                                         # 0 vs 0
+    w = tokens_to_words(ev)
+    off = np.array([0, len(w)], np.uint64)
+    assert oracle.validate(w, off, 1) == oracle.KEY_OK
+    assert oracle.decode_key(oracle.validate(w, off, 1, xft_pairs=1)) == (10, oracle.E_XFT_UNPAIRED)
+    # the last road of an event is closed by the end of the event
+    w2 = tokens_to_words(["E:1:1", "R:0:1", "H:0:5", "H:5:9"])
+    assert oracle.decode_key(oracle.validate(w2, np.array([0, 4], np.uint64), 1, xft_pairs=1)) == \
+        (1, oracle.E_XFT_UNPAIRED)
+    # an earlier violation gives the smaller key; a later one does not
+    bad_early = list(ev)
+    bad_early[2] = "HX:6:0:5"          # layer 6 at word 2, before the unpaired header at 10
+    k = oracle.validate(tokens_to_words(bad_early), off, 1, xft_pairs=1)
+    assert oracle.decode_key(k) == (2, oracle.E_BAD_LAYER)
+    bad_late = list(ev)
+    bad_late[16] = "HX:6:0:5"          # word 16, after it
+    k = oracle.validate(tokens_to_words(bad_late), off, 1, xft_pairs=1)
+    assert oracle.decode_key(k) == (10, oracle.E_XFT_UNPAIRED)
+    # a batch through orc_run reports the key and no records
+    F = np.zeros((1, 64, 6, 6), np.int16)
+    q = np.zeros((1, 64, 6), np.int16)
+    key, rec = oracle.run(w, off, F, q, oracle.config(n_sectors=1, min_layers=0, xft_pairs=1))
+    assert key == (10 << 8 | oracle.E_XFT_UNPAIRED) and rec is None
+
+
+def test_xft_generated_batches_pair_their_track_trigger_hits():
+    spec = synth.SPECS["xft"]
+    consts = synth.make_constants(spec.n_sectors)
+    b = synth.make_batch(spec, 30, consts)
+    assert np.array_equal(b.n_hits[:, 4], b.n_hits[:, 5])
+    assert oracle.validate(b.words, b.event_off, spec.n_sectors, xft_pairs=1) == oracle.KEY_OK
+    assert oracle.config(xft_pairs=2) and not oracle.lib().orc_config_ok(oracle.config(xft_pairs=2))
