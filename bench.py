@@ -50,7 +50,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="svt", choices=["svt", "reference"])
-    ap.add_argument("--workload", default="scaled", choices=["scaled", "paper", "uneven", "small"])
+    ap.add_argument("--workload", default="scaled",
+                    choices=["scaled", "paper", "uneven", "small", "xft"])
     ap.add_argument("--events", type=int, default=3000)
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
@@ -202,7 +203,8 @@ def percentile(xs, p):
 def cpu_baseline(spec, consts, batch, budget_s=12.0):
     """The oracle as it stands (serial C), on a bounded sample of the batch."""
     import oracle
-    cfg = oracle.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, spec.n_sectors)
+    cfg = oracle.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, spec.n_sectors,
+                        int(spec.xft))
     fits_ev = batch.combinations(spec.max_comb)
     # event prefix sized for about budget_s of serial work (~12 Mfits/s per core)
     road_end = np.cumsum(batch.n_roads)
@@ -270,7 +272,8 @@ def run_reference(args, world, rank):
         return
     import oracle
     spec, consts, batch = workload(args, 0)
-    cfg = oracle.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, spec.n_sectors)
+    cfg = oracle.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, spec.n_sectors,
+                        int(spec.xft))
     # each step: a 30-event slice of the workload (about 1.1M fits for 'scaled')
     step_events = max(1, min(30, batch.n_events))
     ev_of_road = np.repeat(np.arange(batch.n_events), batch.n_roads)
@@ -466,7 +469,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     spec, consts, batch = workload(args, rank)
-    cfg = api.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, spec.n_sectors)
+    cfg = api.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, spec.n_sectors,
+                     int(spec.xft))
     dconst = api.DeviceConstants.from_numpy(consts.F, consts.q, cfg, dev)
     n_words, n_events, R = len(batch.words), batch.n_events, batch.total_roads
     sched = api.schedule(args.warps, args.bps, args.rows)

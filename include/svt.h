@@ -27,6 +27,12 @@
  * C = prod n'_l.  A road with C > max_comb evaluates c < max_comb only and is
  * flagged OVERFLOW.  A road with fewer than min_layers layers hit is flagged
  * BAD_PATTERN and not fitted.
+ * Track-trigger pairing (svt_config.xft_pairs = 1): layers 4 and 5 are the
+ * two coordinates (phi, curvature) of one track-trigger track, so hit i of
+ * layer 4 and hit i of layer 5 form one pair.  A road must then hold as many
+ * layer-5 hits as layer-4 hits (else SVT_ERR_XFT_UNPAIRED at the road's last
+ * hit word); the combination index runs over layers 0..4 only (layer 4 fastest,
+ * C = prod_{l<5} n'_l) and layer 5 takes layer 4's hit index.
  *
  * Input words (uint32, type in bits [31:30]):
  *   event header (3): [29:12] event id, [11:0] number of roads (<= 4095)
@@ -85,6 +91,7 @@ extern "C" {
 #define SVT_ERR_OOM 9             /* a caller-sized buffer is too small                 */
 #define SVT_ERR_BAD_CONFIG 10     /* svt_config out of range                            */
 #define SVT_ERR_TIMEOUT 11        /* a bounded device wait gave up                      */
+#define SVT_ERR_XFT_UNPAIRED 12   /* paired layers 4 and 5 with different hit counts    */
 #define SVT_ERR_CUDA 20           /* a CUDA call failed (host return value only)        */
 
 #define SVT_STATUS_OK UINT64_MAX
@@ -96,8 +103,9 @@ extern "C" {
 #define SVT_FLAG_NO_HITS 8u
 
 /* Fit configuration.  Limits (else SVT_ERR_BAD_CONFIG): 9 <= oshift <= 31,
- * qshift <= 24, max_comb >= 1, min_layers <= 6, 1 <= n_sectors <= 512.
- * These limits keep |y_k| < 2^31 for every int16/uint15 input. */
+ * qshift <= 24, max_comb >= 1, min_layers <= 6, 1 <= n_sectors <= 512,
+ * xft_pairs <= 1.  These limits keep |y_k| < 2^31 for every int16/uint15
+ * input. */
 typedef struct {
     uint32_t oshift;
     uint32_t qshift;
@@ -105,6 +113,7 @@ typedef struct {
     uint32_t max_comb;
     uint32_t min_layers;
     uint32_t n_sectors;
+    uint32_t xft_pairs;   /* 1: layers 4 and 5 come in track-trigger pairs (above) */
 } svt_config;
 
 /* Best combination of one road, as produced by svt_select (24 bytes). */
@@ -153,6 +162,7 @@ size_t svt_unpack_workspace_size(uint64_t n_words);
  * arrays and validate them.
  *   d_words[n_words], d_event_off[n_events+1]  input (see the word format)
  *   n_sectors      sectors of the constant table (road headers must be below)
+ *   xft_pairs      1: check the layer-4/layer-5 pairing (SVT_ERR_XFT_UNPAIRED)
  *   road_cap       capacity of the road arrays
  *   d_road_word[road_cap]   out: word index of each road header, input order
  *   d_road_nhit[road_cap]   out: hits per layer, 5 bits each: n_l = (v >> 5l) & 31
@@ -164,8 +174,9 @@ size_t svt_unpack_workspace_size(uint64_t n_words);
  *   d_workspace    svt_unpack_workspace_size(n_words) bytes
  */
 int svt_unpack(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_off,
-               uint64_t n_events, uint32_t n_sectors, uint64_t road_cap, uint32_t *d_road_word,
-               uint32_t *d_road_nhit, uint32_t *d_event_road, uint64_t *d_n_roads,
+               uint64_t n_events, uint32_t n_sectors, uint32_t xft_pairs, uint64_t road_cap,
+               uint32_t *d_road_word, uint32_t *d_road_nhit, uint32_t *d_event_road,
+               uint64_t *d_n_roads,
                uint64_t *d_status, void *d_workspace, size_t workspace_bytes, void *stream);
 
 /* Workspace bytes svt_combine needs for up to road_cap roads. */

@@ -104,8 +104,11 @@ int orc_config_ok(const orc_config *cfg) {
  *   V9  t == 2 and sector >= n_sectors                          BAD_SECTOR
  *   V10 i == start, t == 3 and n_roads(w) != number of type-2 words in the
  *       event                                                   NROADS_MISMATCH
- *   V11 (xft_pairs only) t == 2 and the hit run that follows the header has a
- *       different number of layer-4 and layer-5 hits           XFT_UNPAIRED
+ *   V11 (xft_pairs only) the hit run that follows a road header has a
+ *       different number of layer-4 and layer-5 hits; reported at the run's
+ *       last word (its last hit)                               XFT_UNPAIRED
+ *       (A run of more than 96 hits always breaks V6, V7 or V8 at one of its
+ *       words, so the smallest key never comes from V11 on such a run.)
  */
 uint64_t orc_validate(const uint32_t *words, uint64_t n_words, const uint64_t *event_off,
                       uint64_t n_events, uint32_t n_sectors, uint32_t xft_pairs) {
@@ -118,13 +121,12 @@ uint64_t orc_validate(const uint32_t *words, uint64_t n_words, const uint64_t *e
         uint64_t start = event_off[e], end = event_off[e + 1];
         uint64_t n_road_headers = 0;
         int in_road_run = 0;       /* inside the hit run that follows a road header */
-        uint64_t header = 0;       /* word index of that header */
         uint32_t run_count[8];
         memset(run_count, 0, sizeof run_count);
         for (uint64_t i = start; i <= end; ++i) {
             if (i == end) {        /* the end of the event closes the last run */
                 if (in_road_run && xft_pairs && run_count[4] != run_count[5])
-                    note(&key, header, ORC_E_XFT_UNPAIRED);                         /* V11 */
+                    note(&key, i - 1, ORC_E_XFT_UNPAIRED);                          /* V11 */
                 break;
             }
             uint32_t w = words[i], t = w_type(w);
@@ -144,14 +146,13 @@ uint64_t orc_validate(const uint32_t *words, uint64_t n_words, const uint64_t *e
                 }
             } else {
                 if (in_road_run && xft_pairs && run_count[4] != run_count[5])
-                    note(&key, header, ORC_E_XFT_UNPAIRED);                         /* V11 */
+                    note(&key, i - 1, ORC_E_XFT_UNPAIRED);                          /* V11 */
                 in_road_run = 0;
             }
             if (t == 2) {
                 n_road_headers += 1;
                 if (rd_sector(w) >= n_sectors) note(&key, i, ORC_E_BAD_SECTOR);    /* V9 */
                 in_road_run = 1;
-                header = i;
                 memset(run_count, 0, sizeof run_count);
             }
         }

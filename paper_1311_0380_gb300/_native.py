@@ -17,7 +17,7 @@ SVT_OK = 0
 ERRORS = {
     1: "BAD_ARG", 2: "BAD_TYPE", 3: "BAD_RESERVED", 4: "BAD_LAYER", 5: "UNSORTED",
     6: "TOO_MANY_HITS", 7: "BAD_SECTOR", 8: "NROADS_MISMATCH", 9: "OOM", 10: "BAD_CONFIG",
-    11: "TIMEOUT", 20: "CUDA",
+    11: "TIMEOUT", 12: "XFT_UNPAIRED", 20: "CUDA",
 }
 STATUS_OK = (1 << 64) - 1
 FLAG_PASS, FLAG_OVERFLOW, FLAG_BAD_PATTERN, FLAG_NO_HITS = 1, 2, 4, 8
@@ -29,7 +29,8 @@ class SvtError(RuntimeError):
 
 class SvtConfig(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
-                ("oshift", "qshift", "chi2_cut", "max_comb", "min_layers", "n_sectors")]
+                ("oshift", "qshift", "chi2_cut", "max_comb", "min_layers", "n_sectors",
+                 "xft_pairs")]
 
 
 class SvtSchedule(ctypes.Structure):
@@ -74,8 +75,8 @@ SIGNATURES = {
     "svt_version": (ctypes.c_int, []),
     "svt_device_sm_count": (ctypes.c_int, [ctypes.c_int]),
     "svt_unpack_workspace_size": (_sz, [_u64]),
-    "svt_unpack": (ctypes.c_int, [_vp, _u64, _vp, _u64, _u32, _u64, _vp, _vp, _vp, _vp, _vp, _vp,
-                                  _sz, _vp]),
+    "svt_unpack": (ctypes.c_int, [_vp, _u64, _vp, _u64, _u32, _u32, _u64, _vp, _vp, _vp, _vp,
+                                  _vp, _vp, _sz, _vp]),
     "svt_combine_workspace_size": (_sz, [_u64]),
     "svt_combine": (ctypes.c_int, [_vp, _vp, _u64, _cfgp, _u64, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                                    _sz, _vp]),

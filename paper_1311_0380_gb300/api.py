@@ -28,8 +28,8 @@ def _stream(stream):
 
 
 def config(oshift=15, qshift=15, chi2_cut=0xFFFFFFFF, max_comb=262144, min_layers=5,
-           n_sectors=512) -> SvtConfig:
-    return SvtConfig(oshift, qshift, chi2_cut, max_comb, min_layers, n_sectors)
+           n_sectors=512, xft_pairs=0) -> SvtConfig:
+    return SvtConfig(oshift, qshift, chi2_cut, max_comb, min_layers, n_sectors, xft_pairs)
 
 
 def schedule(warps_per_block=0, blocks_per_sm=0, rows_per_item=0, roads_per_chunk=0,
@@ -51,10 +51,11 @@ def svt_unpack_workspace_size(n_words: int) -> int:
 
 
 def svt_unpack(words, n_words, event_off, n_events, n_sectors, road_cap, road_word, road_nhit,
-               event_road, n_roads, status, workspace, stream=None):
-    N.check(N.load().svt_unpack(_p(words), n_words, _p(event_off), n_events, n_sectors, road_cap,
-                                _p(road_word), _p(road_nhit), _p(event_road), _p(n_roads),
-                                _p(status), _p(workspace), workspace.numel(), _stream(stream)),
+               event_road, n_roads, status, workspace, stream=None, xft_pairs=0):
+    N.check(N.load().svt_unpack(_p(words), n_words, _p(event_off), n_events, n_sectors, xft_pairs,
+                                road_cap, _p(road_word), _p(road_nhit), _p(event_road),
+                                _p(n_roads), _p(status), _p(workspace), workspace.numel(),
+                                _stream(stream)),
             "svt_unpack")
 
 
@@ -299,7 +300,7 @@ class PlainPath:
         mark(0)
         svt_unpack(words, n_words, event_off, n_events, c.cfg.n_sectors, self.road_cap,
                    self.road_word, self.road_nhit, self.event_road, self.n_roads, self.status,
-                   self.ws_unpack, stream)
+                   self.ws_unpack, stream, c.cfg.xft_pairs)
         mark(1)
         svt_combine(self.road_nhit, self.n_roads, self.road_cap, c.cfg, self.comb_cap,
                     self.road_flags, self.comb_off, self.comb_road, self.comb_hits, self.n_combs,

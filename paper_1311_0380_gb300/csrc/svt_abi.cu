@@ -39,6 +39,7 @@ bool config_ok(const svt_config *c) {
     if (c->max_comb < 1) return false;
     if (c->min_layers > 6) return false;
     if (c->n_sectors < 1 || c->n_sectors > 512) return false;
+    if (c->xft_pairs > 1) return false;
     return true;
 }
 
@@ -197,22 +198,23 @@ int svt_device_sm_count(int device) { return sm_count_of(device); }
 size_t svt_unpack_workspace_size(uint64_t n_words) { return carve_unpack(nullptr, n_words).bytes; }
 
 int svt_unpack(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_off,
-               uint64_t n_events, uint32_t n_sectors, uint64_t road_cap, uint32_t *d_road_word,
-               uint32_t *d_road_nhit, uint32_t *d_event_road, uint64_t *d_n_roads,
-               uint64_t *d_status, void *d_workspace, size_t workspace_bytes, void *stream) {
+               uint64_t n_events, uint32_t n_sectors, uint32_t xft_pairs, uint64_t road_cap,
+               uint32_t *d_road_word, uint32_t *d_road_nhit, uint32_t *d_event_road,
+               uint64_t *d_n_roads, uint64_t *d_status, void *d_workspace,
+               size_t workspace_bytes, void *stream) {
     if (!d_event_off || !d_event_road || !d_n_roads || !d_status || !d_workspace)
         return SVT_ERR_BAD_ARG;
     if (n_words > 0 && (!d_words || !aligned16(d_words))) return SVT_ERR_BAD_ARG;
     if (road_cap > 0 && (!d_road_word || !d_road_nhit)) return SVT_ERR_BAD_ARG;
     if (n_words >= (1ull << 32) || n_events >= (1ull << 31) || road_cap >= (1ull << 32))
         return SVT_ERR_BAD_ARG;
-    if (n_sectors < 1 || n_sectors > 512) return SVT_ERR_BAD_ARG;
+    if (n_sectors < 1 || n_sectors > 512 || xft_pairs > 1) return SVT_ERR_BAD_ARG;
     UnpackWs w = carve_unpack(d_workspace, n_words);
     if (workspace_bytes < w.bytes) return SVT_ERR_BAD_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned long long *status = (unsigned long long *)d_status;
     const int grid = tile_grid();
-    svt_config cfg{15, 15, 0, 1, 0, n_sectors};
+    svt_config cfg{15, 15, 0, 1, 0, n_sectors, xft_pairs};
     launch_prologue(w.dims, n_words, n_events, nullptr, d_event_off, w.first_ev, status, d_n_roads,
                     1, nullptr, 0, grid, st);
     launch_unpack_count(d_words, d_event_off, w.dims, w.first_ev, n_words, n_sectors, w.tile_roads,
@@ -248,8 +250,8 @@ int svt_combine(const uint32_t *d_road_nhit, const uint64_t *d_n_roads, uint64_t
                          grid, st);
     launch_scan_u64(d_comb_off, d_n_roads, road_cap, (uint64_t *)d_workspace, d_n_combs, status,
                     grid, st);
-    launch_combine_write(d_road_nhit, d_n_roads, road_cap, d_comb_off, comb_cap, d_comb_road,
-                         d_comb_hits, status, grid, st);
+    launch_combine_write(d_road_nhit, d_n_roads, road_cap, d_comb_off, comb_cap, cfg->xft_pairs,
+                         d_comb_road, d_comb_hits, status, grid, st);
     return launch_status();
 }
 

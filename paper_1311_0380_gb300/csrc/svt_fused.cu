@@ -98,7 +98,8 @@ __device__ __forceinline__ Geo geo_of(const RoadDesc &D) {
 __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restrict__ words,
                                            const RoadDesc &D, const Geo &g,
                                            const int16_t *__restrict__ F,
-                                           const int16_t *__restrict__ q, uint32_t sh, int lane) {
+                                           const int16_t *__restrict__ q, uint32_t sh,
+                                           uint32_t xft, int lane) {
     const uint32_t rw = D.a.x, packed = D.a.y;
     const size_t cs = (size_t)rd_sector(D.a.z) * 64 + g.mask;
     const int32_t f0 = __ldg(F + cs * 36 + lane);
@@ -122,7 +123,8 @@ __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restr
         if (lane >= d) incl += v;
     }
     if (lane < N_LAYERS) {
-        const uint32_t np = nl ? nl : 1u;
+        // with track-trigger pairs layer 5 is no digit of its own (radix 1)
+        const uint32_t np = (nl && !(xft && lane == N_LAYERS - 1)) ? nl : 1u;
         sm.n[lane] = np;
         sm.m[lane] = kDivMagic[np];
         sm.off[lane] = incl - nl;
@@ -147,6 +149,21 @@ __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restr
             t[1] = (long long)(sm.F[24 + l] * (int32_t)xc) << sh;
             t[2] = (long long)(sm.F[30 + l] * (int32_t)xc) << sh;
         }
+    }
+    __syncwarp();
+    if (xft) {
+        // pair i: layer 4's entry i carries both coordinates of track-trigger
+        // track i (equal counts are validated); layer 5 then adds nothing
+        const uint32_t n4 = nhit_of(packed, 4);
+        if ((uint32_t)lane < n4) {
+            long long *t4 = sm.T + (4 * MAX_HITS + lane) * 3;
+            const long long *t5 = sm.T + (5 * MAX_HITS + lane) * 3;
+            t4[0] += t5[0];
+            t4[1] += t5[1];
+            t4[2] += t5[2];
+        }
+        __syncwarp();
+        if (lane < 3) sm.T[(5 * MAX_HITS) * 3 + lane] = 0;
     }
     __syncwarp();
     // S[b'] = sum over the suffix layers below the top one, b' < NBp (< 32)
@@ -309,7 +326,7 @@ __device__ __forceinline__ bool format_road(WarpSmem &sm, const RoadDesc &D, con
             if ((uint32_t)l + 1u == g.split) rem = row;   // the prefix layers take the row
             const uint32_t nl = sm.n[l];
             const uint32_t qd = div_by(rem, nl, sm.m[l]);
-            if ((uint32_t)l == lk) i_own = rem - qd * nl;
+            if ((uint32_t)l == (cfg.xft_pairs && lk == 5u ? 4u : lk)) i_own = rem - qd * nl;
             rem = qd;
         }
         long long t = 0;
@@ -374,7 +391,7 @@ __global__ void __launch_bounds__(512, 2)
         D.a = __ldg(&desc[r].a);
         D.b = __ldg(&desc[r].b);
         const Geo g = geo_of(D);
-        road_setup(sm, words, D, g, F, q, sh, lane);
+        road_setup(sm, words, D, g, F, q, sh, cfg.xft_pairs, lane);
         const uint32_t a_lo = k * fr.rows;
         const uint32_t a_hi = min(a_lo + fr.rows, g.NA);
         const unsigned long long best = eval_rows<GUARDED>(sm, g, a_lo, a_hi, qsh, init_chi, lane);
@@ -419,7 +436,7 @@ __global__ void __launch_bounds__(512, 2)
             const Geo g = geo_of(D);
             unsigned long long best = ~0ull;
             if (g.C_eval > 0) {
-                road_setup(sm, words, D, g, F, q, sh, lane);
+                road_setup(sm, words, D, g, F, q, sh, cfg.xft_pairs, lane);
                 best = eval_rows<GUARDED>(sm, g, 0, g.NA, qsh, init_chi, lane);
             }
             n_pass += format_road(sm, D, g, cfg, best, out + (size_t)(c0 + jj) * 6, lane) ? 1u : 0u;

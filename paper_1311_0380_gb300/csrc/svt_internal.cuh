@@ -116,7 +116,9 @@ struct RoadShape {
     uint32_t n_layers_hit;
     uint64_t C;             // prod n'_l
 };
-__device__ __forceinline__ RoadShape road_shape(uint32_t packed) {
+// With xft_pairs layer 5 is no digit of its own: its radix is 1 (it takes
+// layer 4's hit index), while the mask and the hit count keep its hits.
+__device__ __forceinline__ RoadShape road_shape(uint32_t packed, uint32_t xft_pairs = 0) {
     RoadShape s;
     s.mask = 0;
     s.total_hits = 0;
@@ -130,7 +132,7 @@ __device__ __forceinline__ RoadShape road_shape(uint32_t packed) {
             s.mask |= 1u << l;
             s.n_layers_hit += 1;
         }
-        s.n[l] = nl ? nl : 1u;
+        s.n[l] = (nl && !(xft_pairs && l == N_LAYERS - 1)) ? nl : 1u;
         s.C *= s.n[l];
     }
     return s;

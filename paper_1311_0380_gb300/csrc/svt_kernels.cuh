@@ -27,7 +27,7 @@ struct RoadDesc {
 };
 __device__ __forceinline__ RoadDesc make_road_desc(uint32_t rw, uint32_t packed, uint32_t hw,
                                                    const svt_config &cfg) {
-    const RoadShape s = road_shape(packed);
+    const RoadShape s = road_shape(packed, cfg.xft_pairs);
     const bool bad = s.n_layers_hit < cfg.min_layers;
     const uint32_t C = (uint32_t)s.C;
     const uint32_t C_eval = bad ? 0u : (C > cfg.max_comb ? cfg.max_comb : C);
@@ -160,9 +160,9 @@ void launch_combine_count(const uint32_t *road_nhit, const uint64_t *n_roads, ui
 void launch_scan_u64(uint64_t *a, const uint64_t *n_dev, uint64_t cap, uint64_t *tile_sums,
                      uint64_t *total, const unsigned long long *status, int grid, cudaStream_t st);
 void launch_combine_write(const uint32_t *road_nhit, const uint64_t *n_roads, uint64_t road_cap,
-                          const uint64_t *comb_off, uint64_t comb_cap, uint32_t *comb_road,
-                          uint32_t *comb_hits, unsigned long long *status, int grid,
-                          cudaStream_t st);
+                          const uint64_t *comb_off, uint64_t comb_cap, uint32_t xft_pairs,
+                          uint32_t *comb_road, uint32_t *comb_hits, unsigned long long *status,
+                          int grid, cudaStream_t st);
 void launch_fit_plain(const uint32_t *words, const uint32_t *road_word, const uint32_t *road_nhit,
                       const uint32_t *comb_road, const uint32_t *comb_hits,
                       const uint64_t *n_combs, uint64_t comb_cap, const int16_t *F,

@@ -23,7 +23,7 @@ __global__ void k_combine_count(const uint32_t *__restrict__ road_nhit,
     const uint64_t R = road_count(n_roads, road_cap);
     for (uint64_t r = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R;
          r += (uint64_t)gridDim.x * blockDim.x) {
-        const RoadShape s = road_shape(road_nhit[r]);
+        const RoadShape s = road_shape(road_nhit[r], cfg.xft_pairs);
         uint32_t flags = s.total_hits == 0 ? SVT_FLAG_NO_HITS : 0u;
         uint64_t n = 0;
         if (s.n_layers_hit < cfg.min_layers) {
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(SCAN_THREADS)
 __global__ void k_combine_write(const uint32_t *__restrict__ road_nhit,
                                 const uint64_t *__restrict__ n_roads, uint64_t road_cap,
                                 const uint64_t *__restrict__ comb_off, uint64_t comb_cap,
-                                uint32_t *comb_road, uint32_t *comb_hits,
+                                uint32_t xft_pairs, uint32_t *comb_road, uint32_t *comb_hits,
                                 unsigned long long *status) {
     if (!status_ok(status)) return;
     const uint64_t R = road_count(n_roads, road_cap);
@@ -124,7 +124,7 @@ __global__ void k_combine_write(const uint32_t *__restrict__ road_nhit,
     for (uint64_t r = warp0; r < R; r += n_warps) {
         const uint64_t off = comb_off[r], n = comb_off[r + 1] - off;
         if (off + n > comb_cap) continue;
-        const RoadShape s = road_shape(road_nhit[r]);
+        const RoadShape s = road_shape(road_nhit[r], xft_pairs);
         for (uint64_t c = lane; c < n; c += 32) {
             uint32_t rem = (uint32_t)c, packed = 0;
 #pragma unroll
@@ -133,6 +133,7 @@ __global__ void k_combine_write(const uint32_t *__restrict__ road_nhit,
                 rem /= s.n[l];
                 packed |= i << (4 * l);
             }
+            if (xft_pairs) packed |= ((packed >> 16) & 15u) << 20;   // layer 5 takes layer 4's hit
             comb_road[off + c] = (uint32_t)r;
             comb_hits[off + c] = packed;
         }
@@ -289,11 +290,11 @@ void launch_scan_u64(uint64_t *a, const uint64_t *n_dev, uint64_t cap, uint64_t 
 size_t scan_u64_tile_count(uint64_t cap) { return (cap + SCAN_TILE - 1) / SCAN_TILE + 1; }
 
 void launch_combine_write(const uint32_t *road_nhit, const uint64_t *n_roads, uint64_t road_cap,
-                          const uint64_t *comb_off, uint64_t comb_cap, uint32_t *comb_road,
-                          uint32_t *comb_hits, unsigned long long *status, int grid,
-                          cudaStream_t st) {
+                          const uint64_t *comb_off, uint64_t comb_cap, uint32_t xft_pairs,
+                          uint32_t *comb_road, uint32_t *comb_hits, unsigned long long *status,
+                          int grid, cudaStream_t st) {
     k_combine_write<<<grid_for(road_cap * 32, 256, grid), 256, 0, st>>>(
-        road_nhit, n_roads, road_cap, comb_off, comb_cap, comb_road, comb_hits, status);
+        road_nhit, n_roads, road_cap, comb_off, comb_cap, xft_pairs, comb_road, comb_hits, status);
 }
 
 void launch_fit_plain(const uint32_t *words, const uint32_t *road_word, const uint32_t *road_nhit,

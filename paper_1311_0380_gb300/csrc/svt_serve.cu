@@ -196,9 +196,9 @@ bool svt_server_s::launch(Slot &s) {
     } else {
         // the plain per-stage path, sized by the host-known batch
         const svt_config *fc = &cfg;
-        if (svt_unpack(s.d_words, off, s.d_off, E, fc->n_sectors, c.max_roads, s.d_road_word,
-                       s.d_road_nhit, s.d_event_road, s.d_n_roads, s.d_status, s.d_ws_unpack,
-                       s.ws_unpack, st) != SVT_OK ||
+        if (svt_unpack(s.d_words, off, s.d_off, E, fc->n_sectors, fc->xft_pairs, c.max_roads,
+                       s.d_road_word, s.d_road_nhit, s.d_event_road, s.d_n_roads, s.d_status,
+                       s.d_ws_unpack, s.ws_unpack, st) != SVT_OK ||
             svt_combine(s.d_road_nhit, s.d_n_roads, c.max_roads, fc, c.max_combs, s.d_road_flags,
                         s.d_comb_off, s.d_comb_road, s.d_comb_hits, s.d_n_combs, s.d_status,
                         s.d_ws_combine, s.ws_combine, st) != SVT_OK ||

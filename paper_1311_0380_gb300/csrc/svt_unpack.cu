@@ -209,6 +209,35 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
+// Largest v over the lower threads of the block (-1 when there are none);
+// `smem` holds TILE_THREADS / 32 entries.
+__device__ __forceinline__ int block_exclusive_max(int v, int *smem) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x = max(x, y);
+    }
+    if (lane == 31) smem[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int t = lane < n_warps ? smem[lane] : -1;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, t, d);
+            if (lane >= d) t = max(t, y);
+        }
+        if (lane < n_warps) smem[lane] = t;   // inclusive over warps
+    }
+    __syncthreads();
+    int e = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0) e = -1;
+    const int res = max(e, warp > 0 ? smem[warp - 1] : -1);
+    __syncthreads();
+    return res;
+}
+
 // K2, data-parallel per tile:
 //  * the tile is staged in shared memory with 16 words before it and 100
 //    after it (a valid road has at most 96 hits, so a road that starts in the
@@ -237,9 +266,14 @@ __global__ void __launch_bounds__(TILE_THREADS)
     constexpr int FRONT = 16, BACK = 100;
     constexpr uint32_t SENTINEL = 0xC0000000u;   // an event-header word: ends every run
     __shared__ uint32_t red[TILE_THREADS / 32 + 1];
+    __shared__ int redi[TILE_THREADS / 32];
     __shared__ unsigned long long red64[TILE_THREADS / 32 + 1];
     __shared__ uint32_t sw[FRONT + TILE_WORDS + BACK];
     __shared__ uint32_t cnt[TILE_WORDS];              // per road of the tile: 5 bits per layer
+    // V11 counts of each road's hit run: layer 4 [9:0], layer 5 [19:10], all
+    // hits [31:20].  A field can only overflow in a run of more than 1023 hits,
+    // which then also shows more than 96 hits and is not checked.
+    __shared__ uint32_t cnt45[TILE_WORDS];
     __shared__ uint16_t hdr_pos[TILE_WORDS];          // tile position of each road header
     __shared__ int last_nonhit;
     __shared__ unsigned long long big_base;
@@ -282,6 +316,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 if (p < tile_len && w_type(w[j]) == TYPE_ROAD) {
                     hdr_pos[r] = (uint16_t)p;
                     cnt[r] = 0u;
+                    cnt45[r] = 0u;
                     r += 1;
                 }
             }
@@ -294,8 +329,26 @@ __global__ void __launch_bounds__(TILE_THREADS)
             int r = (int)ex - 1;   // local road of the latest header before this thread's words
             int my_last_nonhit = -1;
             uint32_t acc = 0;      // hits of road r among this thread's words, 5 bits per layer
+            uint32_t acc45 = 0;    // ... in cnt45's fields, within the road's run (pairing only)
             uint32_t same = 0;     // bit j: word j and the word before are hits of one layer
             uint32_t prev = sw[FRONT + threadIdx.x * TILE_PER_THREAD - 1];
+            // pairing counts only hits inside a road's run (a road header and
+            // the hits right after it): is this thread's first word inside
+            // one, i.e. is the latest earlier non-hit word of the tile a road
+            // header?  (Hits before the tile's first header are not counted:
+            // the tile before takes them through its back halo.)
+            bool in_run = true;
+            if (cfg.xft_pairs) {
+                int mine = -1;   // (position << 1) | is-road of this thread's last non-hit word
+#pragma unroll
+                for (int j = 0; j < TILE_PER_THREAD; ++j) {
+                    const int p = threadIdx.x * TILE_PER_THREAD + j;
+                    if (p < tile_len && w_type(w[j]) != TYPE_HIT)
+                        mine = (p << 1) | (w_type(w[j]) == TYPE_ROAD ? 1 : 0);
+                }
+                const int before = block_exclusive_max(mine, redi);
+                in_run = before >= 0 && (before & 1);
+            }
 #pragma unroll
             for (int j = 0; j < TILE_PER_THREAD; ++j) {
                 const int p = threadIdx.x * TILE_PER_THREAD + j;
@@ -308,16 +361,22 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 if (!in) continue;
                 if (ty == TYPE_ROAD) {
                     if (acc && r >= 0) atomicAdd(&cnt[r], acc);
+                    if (acc45 && r >= 0) atomicAdd(&cnt45[r], acc45);
                     acc = 0;
+                    acc45 = 0;
                     r += 1;
                 }
                 if (ty != TYPE_HIT) {
                     my_last_nonhit = p;
+                    in_run = ty == TYPE_ROAD;
                     continue;
                 }
                 acc += 1u << (5 * hit_layer(x));
+                if (cfg.xft_pairs && in_run)
+                    acc45 += (1u << 20) + (hit_layer(x) == 4 ? 1u : 0u) + (hit_layer(x) == 5 ? 1u << 10 : 0u);
             }
             if (acc && r >= 0) atomicAdd(&cnt[r], acc);
+            if (acc45 && r >= 0) atomicAdd(&cnt45[r], acc45);
             if (my_last_nonhit >= 0) atomicMax(&last_nonhit, my_last_nonhit);
             // same-layer bits of tile position q at bit q + 32 of the bitmap
             // (word 1 + q / 32); word 0 covers the front halo
@@ -375,6 +434,8 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 for (int h = threadIdx.x; h < run; h += 32) {
                     const uint32_t l = hit_layer(sw[FRONT + tile_len + h]);
                     atomicAdd(&cnt[r], 1u << (5 * l));
+                    if (cfg.xft_pairs)
+                        atomicAdd(&cnt45[r], (1u << 20) + (l == 4 ? 1u : 0u) + (l == 5 ? 1u << 10 : 0u));
                 }
             }
         }
@@ -386,6 +447,14 @@ __global__ void __launch_bounds__(TILE_THREADS)
         for (uint32_t rl = threadIdx.x; rl < n_roads_tile; rl += TILE_THREADS) {
             const uint64_t r = tile_base + rl;
             const int p = hdr_pos[rl];
+            if (cfg.xft_pairs) {
+                // V11, at the last word of the road's run.  A run of more than 96
+                // hits (or one that goes past the back halo) breaks V6, V7 or V8
+                // at one of its own words, which is then the smaller key.
+                const uint32_t v = cnt45[rl], run = v >> 20;
+                if (run <= 96u && (v & 1023u) != ((v >> 10) & 1023u))
+                    report(status, tile_start + p + run, SVT_ERR_XFT_UNPAIRED);
+            }
             if (r >= road_cap) {
                 report(status, tile_start + p, SVT_ERR_OOM);
                 cnt[rl] = 0;

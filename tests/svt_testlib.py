@@ -7,10 +7,10 @@ from paper_1311_0380_gb300 import synth
 
 
 def cfg_pair(oshift=15, qshift=15, chi2_cut=0xFFFFFFFF, max_comb=262144, min_layers=5,
-             n_sectors=512):
+             n_sectors=512, xft_pairs=0):
     from paper_1311_0380_gb300 import api
-    return (api.config(oshift, qshift, chi2_cut, max_comb, min_layers, n_sectors),
-            oracle.config(oshift, qshift, chi2_cut, max_comb, min_layers, n_sectors))
+    return (api.config(oshift, qshift, chi2_cut, max_comb, min_layers, n_sectors, xft_pairs),
+            oracle.config(oshift, qshift, chi2_cut, max_comb, min_layers, n_sectors, xft_pairs))
 
 
 def oracle_run(words, event_off, F, q, ocfg):

@@ -340,8 +340,9 @@ def test_xft_pairs_enumeration_against_big_integers():
 
 def test_xft_unpaired_rule():
     """V11: with xft_pairs a road whose layer-4 and layer-5 hit counts differ is
-    reported at its header word (code 12); the same words are valid without
-    pairing, and the smaller key still wins against other rules."""
+    reported at the last word of its hit run (code 12); the same words are
+    valid without pairing, and the smaller key still wins against other
+    rules."""
     ev = ["E:1:3",
           "R:0:1", "H:0:5", "H:1:5", "H:2:5", "H:3:5", "H:4:1", "H:4:2", "H:5:9", "H:5:8",   # paired
           "R:0:2", "H:0:5", "H:4:1", "H:4:2", "H:5:9",                                       # 2 vs 1
@@ -349,25 +350,31 @@ def test_xft_unpaired_rule():
     w = tokens_to_words(ev)
     off = np.array([0, len(w)], np.uint64)
     assert oracle.validate(w, off, 1) == oracle.KEY_OK
-    assert oracle.decode_key(oracle.validate(w, off, 1, xft_pairs=1)) == (10, oracle.E_XFT_UNPAIRED)
+    assert oracle.decode_key(oracle.validate(w, off, 1, xft_pairs=1)) == (14, oracle.E_XFT_UNPAIRED)
     # the last road of an event is closed by the end of the event
     w2 = tokens_to_words(["E:1:1", "R:0:1", "H:0:5", "H:5:9"])
     assert oracle.decode_key(oracle.validate(w2, np.array([0, 4], np.uint64), 1, xft_pairs=1)) == \
-        (1, oracle.E_XFT_UNPAIRED)
+        (3, oracle.E_XFT_UNPAIRED)
     # an earlier violation gives the smaller key; a later one does not
     bad_early = list(ev)
-    bad_early[2] = "HX:6:0:5"          # layer 6 at word 2, before the unpaired header at 10
+    bad_early[2] = "HX:6:0:5"          # layer 6 at word 2, before the unpaired run ending at 14
     k = oracle.validate(tokens_to_words(bad_early), off, 1, xft_pairs=1)
     assert oracle.decode_key(k) == (2, oracle.E_BAD_LAYER)
     bad_late = list(ev)
     bad_late[16] = "HX:6:0:5"          # word 16, after it
     k = oracle.validate(tokens_to_words(bad_late), off, 1, xft_pairs=1)
-    assert oracle.decode_key(k) == (10, oracle.E_XFT_UNPAIRED)
+    assert oracle.decode_key(k) == (14, oracle.E_XFT_UNPAIRED)
     # a batch through orc_run reports the key and no records
     F = np.zeros((1, 64, 6, 6), np.int16)
     q = np.zeros((1, 64, 6), np.int16)
     key, rec = oracle.run(w, off, F, q, oracle.config(n_sectors=1, min_layers=0, xft_pairs=1))
-    assert key == (10 << 8 | oracle.E_XFT_UNPAIRED) and rec is None
+    assert key == (14 << 8 | oracle.E_XFT_UNPAIRED) and rec is None
+    # a long run: V11 would sit at its last word, after the run's 17th hit
+    # of one layer (V8), so the smaller key is V8's
+    long = ["E:1:1", "R:0:1"] + ["H:4:1"] * 17 + ["H:5:2"] * 2
+    wl = tokens_to_words(long)
+    k = oracle.validate(wl, np.array([0, len(wl)], np.uint64), 1, xft_pairs=1)
+    assert oracle.decode_key(k) == (18, oracle.E_TOO_MANY_HITS)
 
 
 def test_xft_generated_batches_pair_their_track_trigger_hits():

@@ -289,3 +289,4 @@ def test_road_capacity_overflow_is_reported():
     cfg, _ = cfg_pair(n_sectors=64)
     st, _, _ = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "fused", road_cap=7)
     assert st & 0xFF == 9
+
