@@ -453,6 +453,68 @@ def run_sweep(args):
                       "rows": rows}))
 
 
+E2E_POOL_SLICES = 10
+
+
+def end_to_end(args, spec, consts, dconst, sched, rank, world, dev, barrier):
+    """Steps through the public API from pinned host memory: every step copies
+    its own batch in (words and offsets) and reads its records and status
+    back; the streaming runner overlaps step i's compute with step i+1's
+    copy-in and step i-1's copy-out.  The steps cycle through E2E_POOL_SLICES
+    distinct batches of the workload (a pool larger than the 129 MB L2), so
+    no step finds its inputs cached from an earlier one."""
+    import torch
+    from paper_1311_0380_gb300 import api, synth
+    n_ev = args.events
+    pool = synth.make_batch(spec, n_ev * E2E_POOL_SLICES, consts,
+                            seed=spec.seed + 104729 + 7919 * rank)
+    h_pool = torch.from_numpy(pool.words.view(np.int32)).pin_memory()
+    road_end = np.concatenate([[0], np.cumsum(pool.n_roads)])
+    fits_road = np.concatenate([[0], np.cumsum(pool.combinations(spec.max_comb))])
+    slices = []
+    for k in range(E2E_POOL_SLICES):
+        e0, e1 = k * n_ev, (k + 1) * n_ev
+        w0, w1 = int(pool.event_off[e0]), int(pool.event_off[e1])
+        off = torch.from_numpy((pool.event_off[e0:e1 + 1] - pool.event_off[e0]).astype(np.int64))
+        r0, r1 = int(road_end[e0]), int(road_end[e1])
+        slices.append((h_pool[w0:w1], off.pin_memory(), r1 - r0, int(fits_road[r1] - fits_road[r0])))
+    max_words = max(sl[0].numel() for sl in slices)
+    road_cap = max(sl[2] for sl in slices)
+    runner = api.StreamingRunner(max_words, n_ev, road_cap, dconst, sched, dev)
+    for i in range(args.warmup):
+        sl = slices[i % E2E_POOL_SLICES]
+        runner.submit(sl[0], sl[1], sl[2])
+    runner.wait()
+    marks = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(args.steps)]
+    fits = h2d = d2h = 0
+    used = []
+    barrier()
+    for i in range(args.steps):
+        k = (args.warmup + i) % E2E_POOL_SLICES
+        sl = slices[k]
+        bi, bo = runner.submit(sl[0], sl[1], sl[2], marks=marks[i])
+        fits += sl[3]
+        h2d += bi
+        d2h += bo
+        used.append(k)
+    st, _ = runner.wait()
+    barrier()
+    assert st == api.N.STATUS_OK
+    last = runner.paths[(runner.i - 1) % runner.depth]
+    assert int(api.u64(last.counts)[2]) == slices[used[-1]][3]   # evaluated combinations
+    total_ms = marks[0][0].elapsed_time(marks[-1][1])
+    lat = [a.elapsed_time(b) * 1e3 for a, b in marks]
+    job_ms, (job_fits,) = reduce_over_ranks(world, total_ms, [fits], dev)
+    return {"value": job_fits / (job_ms / 1e3), "unit": UNIT,
+            "h2d_bytes_per_step": int(h2d // args.steps), "d2h_bytes_per_step": int(d2h // args.steps),
+            "p50_us": percentile(lat, 50), "p99_us": percentile(lat, 99),
+            "inputs": f"{E2E_POOL_SLICES} distinct {n_ev}-event batches "
+                      f"({4 * h_pool.numel() / 1e6:.0f} MB) cycled, copied from pinned host memory "
+                      "every step; copy-in, compute and copy-out of consecutive steps overlap",
+            "ms_per_step": job_ms / args.steps}
+
+
 def main():
     args = parse_args()
     if args.sweep:
@@ -530,34 +592,10 @@ def main():
                 "fit_kernel_ms": statistics.mean(fit_ms),
                 "peak_source": "derived: 152 SM x 128 int32 lanes x 2.07 GHz"}
 
-    # ---- end to end through host buffers (fused)
+    # ---- end to end from pinned host memory (fused, copies overlapped with compute)
     e2e = None
-    lat_fused = []
     if not args.no_e2e:
-        runner = api.HostRunner(fused, stream)
-        h_words, h_off = api.HostRunner.pin_batch(batch.words, batch.event_off)
-        for _ in range(args.warmup):
-            runner.submit(h_words, h_off, R)
-            runner.wait()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        h2d = d2h = 0
-        barrier()
-        for i in range(args.steps):
-            flush.fill_(i)
-            evs[i][0].record(stream)
-            h2d, d2h = runner.submit(h_words, h_off, R)
-            evs[i][1].record(stream)
-            st, out = runner.wait()
-        assert st == api.N.STATUS_OK
-        assert np.array_equal(out, rec)
-        lat_fused = [a.elapsed_time(b) * 1e3 for a, b in evs]   # us
-        barrier()
-        e2e_ms, (e2e_fits,) = reduce_over_ranks(world, sum(lat_fused) / 1e3,
-                                                [fits_per_step * args.steps], dev)
-        e2e = {"value": e2e_fits / (e2e_ms / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "p50_us": percentile(lat_fused, 50), "p99_us": percentile(lat_fused, 99)}
+        e2e = end_to_end(args, spec, consts, dconst, fused.sched, rank, world, dev, barrier)
 
     # ---- plain per-stage path beside it
     plain = None
@@ -591,6 +629,7 @@ def main():
                                   "fit_kernel_ms": fms * 1e3,
                                   "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}}
         if not args.no_e2e:
+            h_words, h_off = api.HostRunner.pin_batch(batch.words, batch.event_off)
             prun = api.HostRunner(pp, stream)
             for _ in range(args.warmup):
                 prun.submit(h_words, h_off, R)

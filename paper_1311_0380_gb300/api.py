@@ -328,6 +328,72 @@ class PlainPath:
         return status, rec, R
 
 
+class StreamingRunner:
+    """A stream of batches from pinned host memory through the fused path with
+    the copies overlapped: while step i computes, step i+1's words and
+    offsets are copied in and step i-1's records are copied out.  Each step
+    still carries its own H2D copy and D2H read.  `depth` device sets (words,
+    offsets, workspace, records) alternate; copy-in, compute and copy-out run
+    on three streams ordered by events."""
+
+    def __init__(self, max_words, max_events, road_cap, consts: DeviceConstants, sched=None,
+                 device="cuda", depth: int = 2):
+        self.depth = int(depth)
+        self.paths = [FusedPath(max_words, max_events, road_cap, consts, sched, device)
+                      for _ in range(self.depth)]
+        self.d_words = [torch.empty(max(int(max_words), 4), dtype=torch.int32, device=device)
+                        for _ in range(self.depth)]
+        self.d_off = [torch.empty(int(max_events) + 1, dtype=torch.int64, device=device)
+                      for _ in range(self.depth)]
+        self.h_out = [torch.empty(max(int(road_cap), 1) * 6, dtype=torch.int32, pin_memory=True)
+                      for _ in range(self.depth)]
+        self.h_status = [torch.empty(1, dtype=torch.int64, pin_memory=True) for _ in range(self.depth)]
+        self.s_in, self.s_run, self.s_out = (torch.cuda.Stream(device=device) for _ in range(3))
+        self.ev_in = [torch.cuda.Event() for _ in range(self.depth)]
+        self.ev_run = [torch.cuda.Event() for _ in range(self.depth)]
+        self.used = [False] * self.depth
+        self.n_out = [0] * self.depth
+        self.i = 0
+
+    def submit(self, h_words, h_event_off, n_roads, marks=None):
+        """Enqueue one step; `marks` = (start, end) torch events recorded before
+        its copy-in and after its copy-out.  Returns the bytes (h2d, d2h)."""
+        k = self.i % self.depth
+        n_words, n_events = h_words.numel(), h_event_off.numel() - 1
+        path = self.paths[k]
+        n_out = min(int(n_roads), path.road_cap) * 6
+        with torch.cuda.stream(self.s_in):
+            if self.used[k]:   # step i - depth has finished reading this set
+                self.s_in.wait_event(self.ev_run[k])
+            if marks is not None:
+                marks[0].record(self.s_in)
+            self.d_words[k][:n_words].copy_(h_words, non_blocking=True)
+            self.d_off[k][: n_events + 1].copy_(h_event_off, non_blocking=True)
+            self.ev_in[k].record(self.s_in)
+        with torch.cuda.stream(self.s_run):
+            self.s_run.wait_event(self.ev_in[k])
+            path.run(self.d_words[k], n_words, self.d_off[k], n_events, stream=self.s_run)
+            self.ev_run[k].record(self.s_run)
+        with torch.cuda.stream(self.s_out):
+            self.s_out.wait_event(self.ev_run[k])
+            self.h_out[k][:n_out].copy_(path.out[:n_out], non_blocking=True)
+            self.h_status[k].copy_(path.status, non_blocking=True)
+            if marks is not None:
+                marks[1].record(self.s_out)
+        self.used[k] = True
+        self.n_out[k] = n_out
+        self.i += 1
+        return 4 * n_words + 8 * (n_events + 1), 4 * n_out + 8
+
+    def wait(self):
+        """(status key, records [R, 6] uint32) of the last submitted step."""
+        self.s_out.synchronize()
+        k = (self.i - 1) % self.depth
+        status = int(self.h_status[k].numpy().view(np.uint64)[0])
+        rec = self.h_out[k][: self.n_out[k]].numpy().view(np.uint32).reshape(-1, 6)
+        return status, rec
+
+
 FUSED_LAUNCHES_PER_RUN = 5   # prologue, unpack_count, scan, unpack_roads, fit
 PLAIN_LAUNCHES_PER_RUN = 13  # unpack (5), combine (5), fit, select, format
 

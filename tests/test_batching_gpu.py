@@ -91,3 +91,31 @@ def test_autotuner_picks_a_schedule_that_stays_bit_exact(tmp_path):
     sch2, ms2 = autotune.tuned_schedule(fp, dw, len(b.words), de, b.n_events, cache=cache)
     assert (sch2.warps_per_block, sch2.rows_per_item, sch2.roads_per_chunk, sch2.small_max) == \
         (sch.warps_per_block, sch.rows_per_item, sch.roads_per_chunk, sch.small_max)
+
+
+def test_streaming_runner_overlapped_steps_are_exact():
+    """Copies and compute of consecutive steps overlap on three streams; the
+    records of each step still equal the oracle's for that step's batch."""
+    import torch
+    from paper_1311_0380_gb300 import api
+    consts = synth.make_constants(512)
+    spec = synth.SPECS["scaled"]
+    batches = [synth.make_batch(spec, 40, consts, seed=500 + k) for k in range(3)]
+    cfg = api.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, 512)
+    ocfg = oracle.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, 512)
+    want = [oracle.run(b.words, b.event_off, consts.F, consts.q, ocfg, omp=True)[1] for b in batches]
+    dc = api.DeviceConstants.from_numpy(consts.F, consts.q, cfg)
+    runner = api.StreamingRunner(max(len(b.words) for b in batches), 40,
+                                 max(b.total_roads for b in batches), dc, depth=2)
+    pinned = [api.HostRunner.pin_batch(b.words, b.event_off) for b in batches]
+    order = [0, 1, 2, 1, 0]
+    for k in order:
+        runner.submit(pinned[k][0], pinned[k][1], batches[k].total_roads)
+    st, rec = runner.wait()
+    assert st == oracle.KEY_OK and np.array_equal(rec, want[order[-1]])
+    # the other set holds the step before
+    k_prev = (runner.i - 2) % runner.depth
+    n = batches[order[-2]].total_roads
+    prev = runner.h_out[k_prev][: 6 * n].numpy().view(np.uint32).reshape(-1, 6)
+    assert np.array_equal(prev, want[order[-2]])
+    assert int(runner.h_status[k_prev].numpy().view(np.uint64)[0]) == oracle.KEY_OK
