@@ -180,12 +180,20 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
+TILE_DRAW = 4096   # batches larger than this many events repeat one draw of it
+
+
 def workload(args, rank):
     from paper_1311_0380_gb300 import synth
     spec = synth.SPECS[args.workload]
     consts = synth.make_constants(spec.n_sectors)
     # every rank fits its own batch (independent events): weak scaling
-    batch = synth.make_batch(spec, args.events, consts, seed=spec.seed + 7919 * rank)
+    seed = spec.seed + 7919 * rank
+    if args.events > TILE_DRAW and args.events % TILE_DRAW == 0:
+        batch = synth.tile_batch(synth.make_batch(spec, TILE_DRAW, consts, seed=seed),
+                                 args.events // TILE_DRAW)
+    else:
+        batch = synth.make_batch(spec, args.events, consts, seed=seed)
     return spec, consts, batch
 
 

@@ -394,6 +394,20 @@ def make_batch(spec, n_events: int, consts: Constants | None = None, seed: int |
     return Batch(words, event_off, cat(2), cat(3), cat(4), cat(5), cat(6), cat(7), spec.xft)
 
 
+def tile_batch(b: Batch, times: int) -> Batch:
+    """`times` copies of batch `b` back to back (event and road ids repeat; the
+    word format does not require them to be unique).  Full-size batches of
+    the uneven workload are built this way from a smaller draw."""
+    n_w = len(b.words)
+    words = np.tile(b.words, times)
+    step = np.arange(times, dtype=np.uint64)[:, None] * np.uint64(n_w)
+    off = (b.event_off[None, :-1] + step).ravel()
+    event_off = np.concatenate([off, [np.uint64(n_w * times)]]).astype(np.uint64)
+    rep = lambda a: np.concatenate([a] * times)
+    return Batch(words, event_off, rep(b.n_roads), rep(b.n_hits), rep(b.sector), rep(b.d0),
+                 rep(b.phi0), rep(b.c), b.xft)
+
+
 def make_tracks_batch(consts: Constants, n_roads: int, seed: int, mode="linear",
                       sigma_scale=0.0, roads_per_event=16):
     """Roads holding exactly one hit per layer from one track (no noise).

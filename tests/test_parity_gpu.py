@@ -290,3 +290,35 @@ def test_road_capacity_overflow_is_reported():
     st, _, _ = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "fused", road_cap=7)
     assert st & 0xFF == 9
 
+
+
+def test_uneven_full_size_65536_events_sampled():
+    """The uneven workload at its full size, 65536 events per launch (16 copies
+    of a 4096-event draw: 17 million roads, 69 billion evaluated
+    combinations), through the fused path in the schedule the bench uses:
+    every copy's records equal the first copy's, and a random sample of 3000
+    roads equals the oracle's records for those roads, fitted one by one."""
+    import torch
+    from paper_1311_0380_gb300 import api
+    spec = synth.SPECS["uneven"]
+    consts = consts_for(512)
+    base = synth.make_batch(spec, 4096, consts)
+    b = synth.tile_batch(base, 16)
+    R0 = base.total_roads
+    cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb)
+    dc = api.DeviceConstants.from_numpy(consts.F, consts.q, cfg)
+    fp = api.FusedPath(len(b.words), b.n_events, b.total_roads, dc)
+    fp.run(api.to_device_u32(b.words), len(b.words), api.to_device_u64(b.event_off), b.n_events)
+    torch.cuda.synchronize()
+    st, rec, counts = fp.result()
+    assert st == oracle.KEY_OK
+    assert counts[0] == b.total_roads == 16 * R0
+    assert counts[2] == int(b.combinations(spec.max_comb).sum())
+    blocks = rec.reshape(16, R0, 6)
+    assert all(np.array_equal(blocks[k], blocks[0]) for k in range(1, 16))
+    rng = np.random.default_rng(65536)
+    sample = np.sort(rng.choice(b.total_roads, 3000, replace=False))
+    road_pos = np.flatnonzero((b.words >> 30) == 2)[sample]
+    want = oracle.run_roads(b.words, road_pos.astype(np.uint64), consts.F, consts.q, ocfg)
+    assert np.array_equal(rec[sample], want)
+    assert np.mean((want[:, 0] >> 24) & oracle.F_OVERFLOW > 0) > 0.5   # mostly capped roads
