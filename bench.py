@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--no-calib", action="store_true", help="skip the FP32 calibration measurement")
     ap.add_argument("--no-tune", action="store_true", help="use the default schedule")
     ap.add_argument("--sweep", action="store_true",
                     help="latency against the number of fits for the paper-shape workload "
@@ -231,6 +232,84 @@ def cpu_baseline(spec, consts, batch, budget_s=12.0):
     return {"value": fits / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {n_ev} of {batch.n_events} events ({fits} fits), serial C oracle, one pass",
             "seconds": round(dt, 3)}
+
+
+CALIB_TRACKS = 1 << 20
+
+
+def calibration(dev, reps=20):
+    """The calibration section of the bench line: the workload's 1M tracks,
+    and a 16M-track batch beside it (large-batch bandwidth)."""
+    out = calibration_one(dev, CALIB_TRACKS, reps)
+    out["large_batch"] = calibration_one(dev, 16 * CALIB_TRACKS, reps)
+    return out
+
+
+def calibration_one(dev, n_tracks, reps):
+    """The FP32 relaxation on n_tracks generated tracks over 512 sectors: the
+    forward y = F[s] x + q[s], the loss, and the hand-written backward of the
+    loss (dL/dF, dL/dq), each timed with CUDA events over `reps` calls with
+    the L2 flushed (by a 256 MB read) before each, every call replayed from a
+    one-call CUDA graph.  Algorithmic bytes per track: the forward reads
+    x (24 B) and writes y (24 B); the loss and its backward read x and the
+    true parameters (36 B)."""
+    import torch
+    from paper_1311_0380_gb300 import calib, synth
+    consts = synth.make_constants(512)
+    cs = synth.make_calib(n_tracks, consts)
+    data = calib.CalibData(cs.x, cs.sector, cs.theta, 512, cs.weight, device=dev)
+    F = torch.tensor(cs.F0, dtype=torch.float32, device=dev, requires_grad=True)
+    q = torch.tensor(cs.q0, dtype=torch.float32, device=dev, requires_grad=True)
+    # L2 flush by reading 256 MB (the lines it leaves are clean, so the timed
+    # kernel pays no write-back of the flush's own data)
+    flush_src = torch.ones(64 << 20, dtype=torch.int32, device=dev)
+    flush_dst = torch.empty((), dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream()
+    peak = measured_hbm_peak()
+
+    def timed(fn):
+        # one call captured in a CUDA graph and replayed right after the L2
+        # flush, so host-side call overhead cannot stretch the device time
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        with torch.cuda.stream(side):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=side):
+                fn()
+        stream.wait_stream(side)
+        ms = []
+        for i in range(reps):
+            torch.sum(flush_src, 0, out=flush_dst)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            g.replay()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    class _Ctx:   # what the autograd Functions keep between forward and backward
+        def save_for_backward(self, *t):
+            self.saved_tensors = t
+
+    ctx_f, ctx_l = _Ctx(), _Ctx()
+    g1 = torch.ones((), device=dev)
+    with torch.no_grad():
+        t_fwd = timed(lambda: calib.FitFP32.forward(ctx_f, F, q, data))
+        t_loss = timed(lambda: calib.CalibLoss.forward(ctx_l, F, q, data))
+        t_bwd = timed(lambda: calib.CalibLoss.backward(ctx_l, g1))
+    loss = calib.calib_loss(F, q, data)
+    n = n_tracks
+    out = {"tracks": n, "sectors": 512, "loss_value": float(loss.item()), "peak_gbs": peak,
+           "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+    for name, ms, bpt in (("forward", t_fwd, 48), ("loss", t_loss, 36), ("loss_backward", t_bwd, 36)):
+        gbs = n * bpt / (ms / 1e3) / 1e9
+        out[name] = {"us": ms * 1e3, "bytes_per_track": bpt, "achieved_gbs": gbs,
+                     "frac": gbs / peak, "tracks_per_s": n / (ms / 1e3)}
+    return out
 
 
 def serving(dev):
@@ -659,6 +738,10 @@ def main():
     if rank == 0 and not args.no_serve:
         serve_out = serving(dev)
 
+    calib_out = None
+    if rank == 0 and not args.no_calib:
+        calib_out = calibration(dev)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(spec, consts, batch)
@@ -681,6 +764,7 @@ def main():
                            "p99": percentile([m * 1e3 for m in step_ms], 99)},
             "e2e": e2e, "plain": plain, "roofline": roofline, "cpu_baseline": cpu,
             "serving": serve_out,
+            "calibration": calib_out,
             "clocks": clock_summary,
             "gpu_launches": api.FUSED_LAUNCHES_PER_RUN * args.steps,
         }

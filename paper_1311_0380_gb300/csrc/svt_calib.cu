@@ -192,7 +192,8 @@ __device__ __forceinline__ void eval_track(const float *c, const float *__restri
     }
 }
 
-__global__ void k_forward(const float *__restrict__ x, const int32_t *__restrict__ item_sector,
+__global__ void __launch_bounds__(256, 6)
+    k_forward(const float *__restrict__ x, const int32_t *__restrict__ item_sector,
                           const int32_t *__restrict__ item_start,
                           const int32_t *__restrict__ sector_off, const int32_t *__restrict__ n_items,
                           const float *__restrict__ F, const float *__restrict__ q, float *y) {
@@ -202,7 +203,12 @@ __global__ void k_forward(const float *__restrict__ x, const int32_t *__restrict
     for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + wib; i < NI; i += gridDim.x * (blockDim.x >> 5)) {
         const Item it = item_of(item_sector, item_start, sector_off, i);
         load_consts(cs[wib], F, q, it.s, lane);
-        for (uint32_t t = it.start + lane; t < it.end; t += 32) {
+        // the item's tracks in CALIB_CHUNK / 32 unrolled steps, so their loads
+        // are in flight together (same order as a plain loop)
+#pragma unroll
+        for (int k = 0; k < CALIB_CHUNK / 32; ++k) {
+            const uint32_t t = it.start + (uint32_t)lane + 32u * k;
+            if (t >= it.end) continue;
             float xv[6], yv[6];
             eval_track(cs[wib], x, t, xv, yv);
             float2 *yp = reinterpret_cast<float2 *>(y + (size_t)t * 6);
@@ -214,7 +220,8 @@ __global__ void k_forward(const float *__restrict__ x, const int32_t *__restrict
     }
 }
 
-__global__ void k_loss_items(const float *__restrict__ x, const float *__restrict__ theta,
+__global__ void __launch_bounds__(256, 8)
+    k_loss_items(const float *__restrict__ x, const float *__restrict__ theta,
                              const int32_t *__restrict__ item_sector,
                              const int32_t *__restrict__ item_start,
                              const int32_t *__restrict__ sector_off,
@@ -229,7 +236,10 @@ __global__ void k_loss_items(const float *__restrict__ x, const float *__restric
         const Item it = item_of(item_sector, item_start, sector_off, i);
         load_consts(cs[wib], F, q, it.s, lane);
         float acc = 0.f;
-        for (uint32_t t = it.start + lane; t < it.end; t += 32) {
+#pragma unroll
+        for (int k = 0; k < CALIB_CHUNK / 32; ++k) {
+            const uint32_t t = it.start + (uint32_t)lane + 32u * k;
+            if (t >= it.end) continue;
             float xv[6], yv[6];
             eval_track(cs[wib], x, t, xv, yv);
             const float r0 = yv[0] - theta[(size_t)t * 3 + 0];
@@ -384,7 +394,9 @@ void launch_calib_gather(const float *src, uint32_t width, const int32_t *perm, 
 void launch_calib_forward(const float *x, const int32_t *item_sector, const int32_t *item_start,
                           const int32_t *sector_off, const int32_t *n_items, uint32_t max_items,
                           const float *F, const float *q, float *y, int grid, cudaStream_t st) {
-    const int g = (int)min((uint32_t)grid, (max_items + 7) / 8 + 1);
+    // one warp per item (8 per block); the block scheduler keeps the SMs full
+    const int g = (int)((max_items + 7) / 8 + 1);
+    (void)grid;
     k_forward<<<g, 256, 0, st>>>(x, item_sector, item_start, sector_off, n_items, F, q, y);
 }
 
@@ -393,7 +405,9 @@ void launch_calib_loss(const float *x, const float *theta, const int32_t *item_s
                        const int32_t *n_items, uint32_t max_items, uint64_t n, const float *F,
                        const float *q, const float *w, float *item_loss, float *loss, int grid,
                        cudaStream_t st) {
-    const int g = (int)min((uint32_t)grid, (max_items + 7) / 8 + 1);
+    // one warp per item (8 per block); the block scheduler keeps the SMs full
+    const int g = (int)((max_items + 7) / 8 + 1);
+    (void)grid;
     k_loss_items<<<g, 256, 0, st>>>(x, theta, item_sector, item_start, sector_off, n_items, F, q, w,
                                    item_loss);
     k_loss_final<<<1, 1024, 0, st>>>(item_loss, n_items, n, loss);
