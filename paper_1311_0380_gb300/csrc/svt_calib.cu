@@ -194,9 +194,9 @@ __device__ __forceinline__ void eval_track(const float *c, const float *__restri
 
 __global__ void __launch_bounds__(256, 6)
     k_forward(const float *__restrict__ x, const int32_t *__restrict__ item_sector,
-                          const int32_t *__restrict__ item_start,
-                          const int32_t *__restrict__ sector_off, const int32_t *__restrict__ n_items,
-                          const float *__restrict__ F, const float *__restrict__ q, float *y) {
+              const int32_t *__restrict__ item_start,
+              const int32_t *__restrict__ sector_off, const int32_t *__restrict__ n_items,
+              const float *__restrict__ F, const float *__restrict__ q, float *y) {
     __shared__ float cs[8][48];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint32_t NI = (uint32_t)*n_items;
@@ -222,12 +222,12 @@ __global__ void __launch_bounds__(256, 6)
 
 __global__ void __launch_bounds__(256, 8)
     k_loss_items(const float *__restrict__ x, const float *__restrict__ theta,
-                             const int32_t *__restrict__ item_sector,
-                             const int32_t *__restrict__ item_start,
-                             const int32_t *__restrict__ sector_off,
-                             const int32_t *__restrict__ n_items, const float *__restrict__ F,
-                             const float *__restrict__ q, const float *__restrict__ w,
-                             float *item_loss) {
+                 const int32_t *__restrict__ item_sector,
+                 const int32_t *__restrict__ item_start,
+                 const int32_t *__restrict__ sector_off,
+                 const int32_t *__restrict__ n_items, const float *__restrict__ F,
+                 const float *__restrict__ q, const float *__restrict__ w,
+                 float *item_loss) {
     __shared__ float cs[8][48];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint32_t NI = (uint32_t)*n_items;
