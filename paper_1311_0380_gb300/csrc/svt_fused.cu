@@ -35,7 +35,9 @@ constexpr int ROWS_MAX = 64;
 // All accumulator terms are kept multiplied by 2^(32 - oshift): the high word
 // of a 64-bit sum of such terms is then exactly floor(sum / 2^oshift).
 struct WarpSmem {
-    long long T[N_LAYERS * MAX_HITS * 3]; // chi-row terms F[3+k][l] * x * 2^(32-oshift), [l][i][k]
+    longlong2 T[N_LAYERS * MAX_HITS][2];  // chi-row terms F[3+k][l] * x * 2^(32-oshift) of hit i of
+                                          // layer l at [l*16+i]: (k=3, k=4), (k=5, -); 32-byte entries
+                                          // so a lookup is one 16-byte and one 8-byte load
     longlong2 S01[32];                    // suffix sums below the top suffix layer, rows 3, 4 [b']
     long long S5[32];                     // ... row 5
     longlong2 A01[ROWS_MAX];              // prefix sums incl. q, rows 3, 4, per row of the chunk
@@ -130,9 +132,8 @@ __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restr
         sm.off[lane] = incl - nl;
         if (nl == 0) {   // a layer without hits contributes x = 0
             sm.x[lane * MAX_HITS] = 0;
-            sm.T[(lane * MAX_HITS) * 3 + 0] = 0;
-            sm.T[(lane * MAX_HITS) * 3 + 1] = 0;
-            sm.T[(lane * MAX_HITS) * 3 + 2] = 0;
+            sm.T[lane * MAX_HITS][0] = make_longlong2(0, 0);
+            sm.T[lane * MAX_HITS][1].x = 0;
         }
     }
     __syncwarp();
@@ -144,10 +145,10 @@ __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restr
             const uint32_t i = h - sm.off[l];   // hits are sorted by layer (validated)
             const uint32_t xc = hit_coord(hv[j]);
             sm.x[l * MAX_HITS + i] = xc;
-            long long *t = sm.T + (l * MAX_HITS + i) * 3;
-            t[0] = (long long)(sm.F[18 + l] * (int32_t)xc) << sh;
-            t[1] = (long long)(sm.F[24 + l] * (int32_t)xc) << sh;
-            t[2] = (long long)(sm.F[30 + l] * (int32_t)xc) << sh;
+            longlong2 *t = sm.T[l * MAX_HITS + i];
+            t[0] = make_longlong2((long long)(sm.F[18 + l] * (int32_t)xc) << sh,
+                                  (long long)(sm.F[24 + l] * (int32_t)xc) << sh);
+            t[1].x = (long long)(sm.F[30 + l] * (int32_t)xc) << sh;
         }
     }
     __syncwarp();
@@ -156,14 +157,17 @@ __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restr
         // track i (equal counts are validated); layer 5 then adds nothing
         const uint32_t n4 = nhit_of(packed, 4);
         if ((uint32_t)lane < n4) {
-            long long *t4 = sm.T + (4 * MAX_HITS + lane) * 3;
-            const long long *t5 = sm.T + (5 * MAX_HITS + lane) * 3;
-            t4[0] += t5[0];
-            t4[1] += t5[1];
-            t4[2] += t5[2];
+            longlong2 *t4 = sm.T[4 * MAX_HITS + lane];
+            const longlong2 *t5 = sm.T[5 * MAX_HITS + lane];
+            t4[0].x += t5[0].x;
+            t4[0].y += t5[0].y;
+            t4[1].x += t5[1].x;
         }
         __syncwarp();
-        if (lane < 3) sm.T[(5 * MAX_HITS) * 3 + lane] = 0;
+        if (lane == 0) {
+            sm.T[5 * MAX_HITS][0] = make_longlong2(0, 0);
+            sm.T[5 * MAX_HITS][1].x = 0;
+        }
     }
     __syncwarp();
     // S[b'] = sum over the suffix layers below the top one, b' < NBp (< 32)
@@ -177,10 +181,10 @@ __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restr
                 const uint32_t qd = div_by(rem, nl, sm.m[l]);
                 const uint32_t i = rem - qd * nl;
                 rem = qd;
-                const long long *t = sm.T + (l * MAX_HITS + i) * 3;
-                S3 += t[0];
-                S4 += t[1];
-                S5 += t[2];
+                const longlong2 t01 = sm.T[l * MAX_HITS + i][0];
+                S3 += t01.x;
+                S4 += t01.y;
+                S5 += sm.T[l * MAX_HITS + i][1].x;
             }
         }
         sm.S01[lane] = make_longlong2(S3, S4);
@@ -202,10 +206,10 @@ __device__ __forceinline__ void build_row(WarpSmem &sm, uint32_t split, uint32_t
             const uint32_t qd = div_by(rem, nl, sm.m[l]);
             const uint32_t i = rem - qd * nl;
             rem = qd;
-            const long long *t = sm.T + (l * MAX_HITS + i) * 3;
-            A3 += t[0];
-            A4 += t[1];
-            A5 += t[2];
+            const longlong2 t01 = sm.T[l * MAX_HITS + i][0];
+            A3 += t01.x;
+            A4 += t01.y;
+            A5 += sm.T[l * MAX_HITS + i][1].x;
         }
     }
     sm.A01[slot] = make_longlong2(A3, A4);
@@ -244,14 +248,15 @@ __device__ __forceinline__ unsigned long long eval_rows(WarpSmem &sm, const Geo 
         for (uint32_t b0 = 0; b0 < NB; b0 += 32) {
             const uint32_t b = b0 + (uint32_t)lane;
             if (b < NB) {
-                const long long *t = sm.T + (top * MAX_HITS + is) * 3;
+                const longlong2 t01 = sm.T[top * MAX_HITS + is][0];
+                const long long t5 = sm.T[top * MAX_HITS + is][1].x;
                 const longlong2 s01 = sm.S01[bp];
                 const long long s5 = sm.S5[bp];
                 // GUARDED: the column terms carry +32768 in the high word, so the
                 // inner loop sees g_k = y_k + 32768 (mod 2^32) directly
                 const long long bias = GUARDED ? (32768LL << 32) : 0LL;
-                const long long B3 = t[0] + s01.x + bias, B4 = t[1] + s01.y + bias,
-                                B5 = t[2] + s5 + bias;
+                const long long B3 = t01.x + s01.x + bias, B4 = t01.y + s01.y + bias,
+                                B5 = t5 + s5 + bias;
                 uint32_t a_end = ae;
                 if (ae == NA && (NA - 1) * NB + b >= C_eval) a_end = ae - 1;
                 uint32_t bchi = init_chi, ba = 0;
