@@ -40,6 +40,8 @@ N_SM, LANES_PER_SM, SM_MAX_GHZ = 152, 128, 2.07
 # plain-path fit kernel: 8 B of combination record read, 16 B of results written
 PLAIN_BYTES_PER_FIT = 24
 ALU_PEAK_TOPS = N_SM * LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12
+# instruction issue: 4 schedulers per SM, one warp instruction each per cycle
+ISSUE_PEAK_GINST = N_SM * 4 * SM_MAX_GHZ
 FIT_KERNEL_SRC = os.path.join(ROOT, "paper_1311_0380_gb300", "csrc", "svt_fused.cu")
 TRAFFIC_NOTE = os.path.join(ROOT, "profiles", "fit_persistent_scaled3000.md")
 
@@ -112,17 +114,23 @@ def file_sha(path):
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def recorded_traffic():
-    """Per-launch DRAM bytes of the fit kernel from the committed ncu summary,
-    or None when the summary is absent or the kernel source changed since."""
+def recorded_profile(key):
+    """A figure of the fit kernel from the committed ncu summary (`key: value
+    kernel_sha: sha`), or None when the summary is absent or the kernel source
+    changed since."""
     try:
         text = open(TRAFFIC_NOTE).read()
     except OSError:
         return None
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)\s+kernel_sha:\s*([0-9a-f]+)", text)
+    m = re.search(key + r":\s*([0-9.eE+]+)\s+kernel_sha:\s*([0-9a-f]+)", text)
     if not m or m.group(2) != file_sha(FIT_KERNEL_SRC):
         return None
     return float(m.group(1))
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the fit kernel (ncu, full-size launch)."""
+    return recorded_profile("traffic_bytes_per_launch")
 
 
 class ClockSampler:
@@ -678,6 +686,15 @@ def main():
                 "kernel": "k_fit_persistent", "ops_per_fit": OPS_PER_FIT,
                 "fit_kernel_ms": statistics.mean(fit_ms),
                 "peak_source": "derived: 152 SM x 128 int32 lanes x 2.07 GHz"}
+    # the kernel's own bound: warp instructions it issues (per combination,
+    # from the committed ncu summary) against the schedulers' issue rate
+    ipf = recorded_profile("warp_instructions_per_fit")
+    roofline["issue"] = None if ipf is None else {
+        "warp_instructions_per_fit": ipf,
+        "achieved_ginst_s": ipf * fits_per_step / fit_mean_s / 1e9,
+        "peak_ginst_s": ISSUE_PEAK_GINST,
+        "frac": ipf * fits_per_step / fit_mean_s / 1e9 / ISSUE_PEAK_GINST,
+        "peak_source": "derived: 152 SM x 4 schedulers x 2.07 GHz"}
 
     # ---- end to end from pinned host memory (fused, copies overlapped with compute)
     e2e = None
