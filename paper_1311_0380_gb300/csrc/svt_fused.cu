@@ -19,9 +19,10 @@
 //     short list of split roads).  Then warps take chunks of consecutive
 //     roads (one coalesced load of their 16-byte descriptors) and fit every
 //     remaining road whole, one warp per road.
-//   * Each lane visits its combinations in increasing c within a column, so a
-//     strict '<' keeps the smallest index among equal chi2; across columns,
-//     lanes and items the (chi2, c) pairs are merged as 64-bit keys (warp
+//   * Each lane visits its combinations in increasing c within a column (or
+//     within its block of rows of a column), so a strict '<' keeps the
+//     smallest index among equal chi2; across columns, row blocks, lanes and
+//     items the (chi2, c) pairs are merged as 64-bit keys (warp
 //     shuffles; atomicMin on the road's slot for split roads, whose record is
 //     written by the warp that retires the road's last item).
 #include "svt_kernels.cuh"
@@ -101,7 +102,7 @@ __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restr
                                            const RoadDesc &D, const Geo &g,
                                            const int16_t *__restrict__ F,
                                            const int16_t *__restrict__ q, uint32_t sh,
-                                           uint32_t xft, int lane) {
+                                           uint32_t xft, long long bias, int lane) {
     const uint32_t rw = D.a.x, packed = D.a.y;
     const size_t cs = (size_t)rd_sector(D.a.z) * 64 + g.mask;
     const int32_t f0 = __ldg(F + cs * 36 + lane);
@@ -170,10 +171,10 @@ __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restr
         }
     }
     __syncwarp();
-    // S[b'] = sum over the suffix layers below the top one, b' < NBp (< 32)
+    // S[b'] = bias + sum over the suffix layers below the top one, b' < NBp (< 32)
     if ((uint32_t)lane < g.NBp) {
         uint32_t rem = lane;
-        long long S3 = 0, S4 = 0, S5 = 0;
+        long long S3 = bias, S4 = bias, S5 = bias;
 #pragma unroll
         for (int l = N_LAYERS - 1; l >= 1; --l) {
             if ((uint32_t)l > g.split) {
@@ -220,9 +221,17 @@ __device__ __forceinline__ int32_t hi_word(long long v) {
     return (int32_t)((unsigned long long)v >> 32);
 }
 
+// Bias carried by the column terms (in the suffix table): with GUARDED the
+// high word of a sum is g_k = y_k + 32768 (mod 2^32) instead of y_k.
+template <bool GUARDED>
+constexpr long long kColBias = GUARDED ? (32768LL << 32) : 0LL;
+
 // Best key over rows [a_lo, a_hi) of the road, reduced over the warp.  The key
 // is (chi2 << 32) | (row << 9) | column; since columns < NB < 512 its low word
 // orders exactly like the combination index c = row * NB + column.
+// Each lane takes one column and runs down the rows of the chunk; in the last
+// pass over the columns, when only w < 32 of them are left, the lanes form
+// floor(32 / w) groups of w and each group takes one block of the rows.
 // GUARDED (valid when chi2_cut < 32767^2): a combination with a chi component
 // of magnitude 32767 or more cannot pass, clamped or not.  One range test keeps
 // only combinations with -32768 <= y_k <= 32767 for all three components; for
@@ -236,68 +245,63 @@ __device__ __forceinline__ unsigned long long eval_rows(WarpSmem &sm, const Geo 
     unsigned long long best = ~0ull;
     const uint32_t NB = g.NB, NA = g.NA, C_eval = g.C_eval, NBp = g.NBp, top = g.split;
     const uint32_t mp = kDivMagic[NBp];
-    const uint32_t d_hi = div_by(32u, NBp, mp), d_lo = 32u - d_hi * NBp;
-    const uint32_t is0 = div_by((uint32_t)lane, NBp, mp), bp0 = (uint32_t)lane - is0 * NBp;
     for (uint32_t ac = a_lo; ac < a_hi; ac += ROWS_MAX) {
-        const uint32_t ae = min(ac + (uint32_t)ROWS_MAX, a_hi);
+        const uint32_t ae = min(ac + (uint32_t)ROWS_MAX, a_hi), rows = ae - ac;
 #pragma unroll
         for (uint32_t r0 = 0; r0 < (uint32_t)ROWS_MAX; r0 += 32)
-            if (ac + r0 + lane < ae) build_row(sm, top, ac + r0 + lane, r0 + lane, qsh);
+            if (r0 + lane < rows) build_row(sm, top, ac + r0 + lane, r0 + lane, qsh);
         __syncwarp();
-        uint32_t is = is0, bp = bp0;   // column b = is * NBp + bp
         for (uint32_t b0 = 0; b0 < NB; b0 += 32) {
-            const uint32_t b = b0 + (uint32_t)lane;
-            if (b < NB) {
-                const longlong2 t01 = sm.T[top * MAX_HITS + is][0];
-                const long long t5 = sm.T[top * MAX_HITS + is][1].x;
-                const longlong2 s01 = sm.S01[bp];
-                const long long s5 = sm.S5[bp];
-                // GUARDED: the column terms carry +32768 in the high word, so the
-                // inner loop sees g_k = y_k + 32768 (mod 2^32) directly
-                const long long bias = GUARDED ? (32768LL << 32) : 0LL;
-                const long long B3 = t01.x + s01.x + bias, B4 = t01.y + s01.y + bias,
-                                B5 = t5 + s5 + bias;
-                uint32_t a_end = ae;
-                if (ae == NA && (NA - 1) * NB + b >= C_eval) a_end = ae - 1;
-                uint32_t bchi = init_chi, ba = 0;
+            uint32_t b = b0 + (uint32_t)lane, lo = ac, hi = ae;
+            if (NB - b0 < 32u) {   // warp-uniform: the last, partial pass
+                const uint32_t w = NB - b0, mw = kDivMagic[w];
+                const uint32_t grp = div_by((uint32_t)lane, w, mw), n_grp = div_by(32u, w, mw);
+                const uint32_t len = div_by(rows + n_grp - 1u, n_grp, kDivMagic[n_grp]);
+                b -= grp * w;
+                lo = min(ac + grp * len, ae);   // groups past the last row get none
+                hi = min(lo + len, ae);
+            }
+            // column b = is * NBp + bp: hit `is` of the top suffix layer and
+            // entry bp of the suffix table
+            const uint32_t is = div_by(b, NBp, mp), bp = b - is * NBp;
+            const longlong2 t01 = sm.T[top * MAX_HITS + is][0];
+            const long long t5 = sm.T[top * MAX_HITS + is][1].x;
+            const longlong2 s01 = sm.S01[bp];
+            const long long s5 = sm.S5[bp];
+            const long long B3 = t01.x + s01.x, B4 = t01.y + s01.y, B5 = t5 + s5;
+            if (hi == NA && lo < hi && (NA - 1) * NB + b >= C_eval) hi -= 1;
+            uint32_t bchi = init_chi, ba = 0;
 #pragma unroll 4
-                for (uint32_t a = ac; a < a_end; ++a) {
-                    const longlong2 v01 = sm.A01[a - ac];
-                    const long long v5 = sm.A5[a - ac];
-                    const int32_t y3 = hi_word(v01.x + B3);
-                    const int32_t y4 = hi_word(v01.y + B4);
-                    const int32_t y5 = hi_word(v5 + B5);
-                    if (GUARDED) {
-                        const uint32_t g3 = (uint32_t)y3, g4 = (uint32_t)y4, g5 = (uint32_t)y5;
-                        // g_k < 2^16 for all three <=> -32768 <= y_k <= 32767; then
-                        // sum (g_k - 32768)^2 = sum g_k^2 - 2^16 sum g_k + 3 * 2^30
-                        // holds exactly in 32-bit arithmetic
-                        const uint32_t range = g3 | g4 | g5;
-                        const uint32_t chi2 = g3 * g3 + g4 * g4 + g5 * g5 + (3u << 30) -
-                                              ((g3 + g4 + g5) << 16);
-                        if (range < 65536u && chi2 < bchi) {
-                            bchi = chi2;
-                            ba = a;
-                        }
-                    } else {
-                        const int32_t c3 = clamp_chi(y3), c4 = clamp_chi(y4), c5 = clamp_chi(y5);
-                        const uint32_t chi2 = (uint32_t)(c3 * c3) + (uint32_t)(c4 * c4) + (uint32_t)(c5 * c5);
-                        if (chi2 < bchi) {
-                            bchi = chi2;
-                            ba = a;
-                        }
+            for (uint32_t a = lo; a < hi; ++a) {
+                const longlong2 v01 = sm.A01[a - ac];
+                const long long v5 = sm.A5[a - ac];
+                const int32_t y3 = hi_word(v01.x + B3);
+                const int32_t y4 = hi_word(v01.y + B4);
+                const int32_t y5 = hi_word(v5 + B5);
+                if (GUARDED) {
+                    const uint32_t g3 = (uint32_t)y3, g4 = (uint32_t)y4, g5 = (uint32_t)y5;
+                    // g_k < 2^16 for all three <=> -32768 <= y_k <= 32767; then
+                    // sum (g_k - 32768)^2 = sum g_k^2 - 2^16 sum g_k + 3 * 2^30
+                    // holds exactly in 32-bit arithmetic
+                    const uint32_t range = g3 | g4 | g5;
+                    const uint32_t chi2 = g3 * g3 + g4 * g4 + g5 * g5 + (3u << 30) -
+                                          ((g3 + g4 + g5) << 16);
+                    if (range < 65536u && chi2 < bchi) {
+                        bchi = chi2;
+                        ba = a;
+                    }
+                } else {
+                    const int32_t c3 = clamp_chi(y3), c4 = clamp_chi(y4), c5 = clamp_chi(y5);
+                    const uint32_t chi2 = (uint32_t)(c3 * c3) + (uint32_t)(c4 * c4) + (uint32_t)(c5 * c5);
+                    if (chi2 < bchi) {
+                        bchi = chi2;
+                        ba = a;
                     }
                 }
-                if (bchi != init_chi) {
-                    const unsigned long long key = ((unsigned long long)bchi << 32) | (ba << 9) | b;
-                    best = key < best ? key : best;
-                }
             }
-            bp += d_lo;
-            is += d_hi;
-            if (bp >= NBp) {
-                bp -= NBp;
-                is += 1;
+            if (bchi != init_chi) {
+                const unsigned long long key = ((unsigned long long)bchi << 32) | (ba << 9) | b;
+                best = key < best ? key : best;
             }
         }
         __syncwarp();
@@ -396,7 +400,7 @@ __global__ void __launch_bounds__(512, 2)
         D.a = __ldg(&desc[r].a);
         D.b = __ldg(&desc[r].b);
         const Geo g = geo_of(D);
-        road_setup(sm, words, D, g, F, q, sh, cfg.xft_pairs, lane);
+        road_setup(sm, words, D, g, F, q, sh, cfg.xft_pairs, kColBias<GUARDED>, lane);
         const uint32_t a_lo = k * fr.rows;
         const uint32_t a_hi = min(a_lo + fr.rows, g.NA);
         const unsigned long long best = eval_rows<GUARDED>(sm, g, a_lo, a_hi, qsh, init_chi, lane);
@@ -441,7 +445,7 @@ __global__ void __launch_bounds__(512, 2)
             const Geo g = geo_of(D);
             unsigned long long best = ~0ull;
             if (g.C_eval > 0) {
-                road_setup(sm, words, D, g, F, q, sh, cfg.xft_pairs, lane);
+                road_setup(sm, words, D, g, F, q, sh, cfg.xft_pairs, kColBias<GUARDED>, lane);
                 best = eval_rows<GUARDED>(sm, g, 0, g.NA, qsh, init_chi, lane);
             }
             n_pass += format_road(sm, D, g, cfg, best, out + (size_t)(c0 + jj) * 6, lane) ? 1u : 0u;
