@@ -370,6 +370,7 @@ __global__ void __launch_bounds__(512, 2)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
+    wait_prior_grid();   // road extraction has completed (see launch_after)
     // per-event rules first, whatever the status, so that the key stays the
     // smallest over all rules
     check_events(words, event_off, dims->n_words, dims->n_events, event_road, status,
@@ -482,13 +483,13 @@ cudaError_t launch_fit_persistent(const uint32_t *words, const uint64_t *event_o
                                   int warps_per_block, int grid, cudaStream_t st) {
     size_t smem = fit_smem_bytes(warps_per_block);
     if (cfg.chi2_cut < 32767u * 32767u)
-        k_fit_persistent<true><<<grid, warps_per_block * 32, smem, st>>>(
-            words, event_off, dims, event_road, desc, counts, road_cap, F, q, cfg, fr,
-            roads_per_chunk, out, status);
+        launch_after(k_fit_persistent<true>, grid, warps_per_block * 32, smem, st, words,
+                     event_off, dims, event_road, desc, counts, road_cap, F, q, cfg, fr,
+                     roads_per_chunk, out, status);
     else
-        k_fit_persistent<false><<<grid, warps_per_block * 32, smem, st>>>(
-            words, event_off, dims, event_road, desc, counts, road_cap, F, q, cfg, fr,
-            roads_per_chunk, out, status);
+        launch_after(k_fit_persistent<false>, grid, warps_per_block * 32, smem, st, words,
+                     event_off, dims, event_road, desc, counts, road_cap, F, q, cfg, fr,
+                     roads_per_chunk, out, status);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,39 @@ struct Dims {
     uint64_t n_events;
 };
 
+// ---- programmatic dependent launch --------------------------------------------
+// The kernels of a sequence after its first are launched with programmatic
+// stream serialization (launch_after): once every block of the kernel before
+// has started and called allow_next_grid, the next kernel's blocks may be
+// scheduled as SMs free up, and each waits in wait_prior_grid
+// (griddepcontrol.wait: the kernel before has completed and its writes are
+// visible) before it touches anything.  Every kernel of a sequence calls
+// wait_prior_grid first, in every block, so the completion of one kernel
+// implies that of all kernels before it.  For a kernel launched without the
+// attribute both calls return at once.
+__device__ __forceinline__ void wait_prior_grid() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void allow_next_grid() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_after(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                         cudaStream_t st, Args... args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t c = {};
+    c.gridDim = grid;
+    c.blockDim = block;
+    c.dynamicSmemBytes = smem;
+    c.stream = st;
+    c.attrs = attr;
+    c.numAttrs = 1;
+    cudaLaunchKernelEx(&c, kernel, args...);   // errors surface through cudaGetLastError
+}
+
 // Per-road descriptor of the fused path (32 bytes), built once by the road
 // extraction:
 //   a = {header word index, hits per layer (5 bits each), header word,

@@ -67,6 +67,9 @@ __global__ void k_prologue(Dims *dims, uint64_t n_words, uint64_t n_events,
                            const uint64_t *sizes, const uint64_t *__restrict__ event_off,
                            uint32_t *first_ev, unsigned long long *status, uint64_t *counts,
                            int n_counts, uint64_t *zero, int n_zero) {
+    // first of its sequence: launched in stream order after whatever came
+    // before, so only the next kernel is let in early
+    allow_next_grid();
     bool bad = false;
     if (sizes) {
         const uint64_t w = sizes[0], e = sizes[1];
@@ -106,6 +109,8 @@ __global__ void __launch_bounds__(TILE_THREADS)
                    const Dims *__restrict__ dims, const uint32_t *__restrict__ first_ev,
                    uint32_t n_sectors, uint32_t *tile_roads, unsigned long long *status) {
     __shared__ uint32_t red[TILE_THREADS / 32 + 1];
+    wait_prior_grid();
+    allow_next_grid();
     const uint64_t n_words = dims->n_words, n_events = dims->n_events;
     const uint64_t T = n_tiles(n_words);
     for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
@@ -181,6 +186,8 @@ __global__ void __launch_bounds__(1024)
     k_scan_tiles(uint32_t *a, const Dims *__restrict__ dims, const uint64_t *n_dev,
                  uint64_t *total64, uint32_t *event_road, unsigned long long *status) {
     __shared__ uint32_t sm[33];
+    wait_prior_grid();
+    allow_next_grid();
     const uint64_t n = n_dev ? *n_dev : n_tiles(dims->n_words);
     uint64_t carry = 0;
     for (uint64_t c0 = 0; c0 < n; c0 += 4096) {
@@ -278,6 +285,8 @@ __global__ void __launch_bounds__(TILE_THREADS)
     __shared__ int last_nonhit;
     __shared__ unsigned long long big_base;
     __shared__ uint32_t same_bits[1 + TILE_WORDS / 32];   // V8 bitmap, see below
+    wait_prior_grid();
+    allow_next_grid();
     const uint64_t n_words = dims->n_words, n_events = dims->n_events;
     const uint64_t T = n_tiles(n_words);
     for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
@@ -534,6 +543,8 @@ __global__ void k_unpack_events(const uint32_t *__restrict__ words,
                                 const Dims *__restrict__ dims,
                                 const uint32_t *__restrict__ event_road,
                                 unsigned long long *status) {
+    wait_prior_grid();
+    allow_next_grid();
     check_events(words, event_off, dims->n_words, dims->n_events, event_road, status,
                  (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
                  (uint64_t)gridDim.x * blockDim.x);
@@ -559,13 +570,13 @@ void launch_unpack_count(const uint32_t *words, const uint64_t *event_off, const
     uint64_t T = n_tiles(max_words);
     int g = (int)(T < (uint64_t)grid ? T : (uint64_t)grid);
     if (g > 0)
-        k_unpack_count<<<g, TILE_THREADS, 0, st>>>(words, event_off, dims, first_ev, n_sectors,
-                                                   tile_roads, status);
+        launch_after(k_unpack_count, g, TILE_THREADS, 0, st, words, event_off, dims, first_ev,
+                     n_sectors, tile_roads, status);
 }
 
 void launch_scan_tiles(uint32_t *a, const Dims *dims, const uint64_t *n_dev, uint64_t *total64,
                        uint32_t *event_road, unsigned long long *status, cudaStream_t st) {
-    k_scan_tiles<<<1, 1024, 0, st>>>(a, dims, n_dev, total64, event_road, status);
+    launch_after(k_scan_tiles, 1, 1024, 0, st, a, dims, n_dev, total64, event_road, status);
 }
 
 void launch_unpack_roads(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
@@ -576,9 +587,9 @@ void launch_unpack_roads(const uint32_t *words, const uint64_t *event_off, const
     uint64_t T = n_tiles(max_words);
     int g = (int)(T < (uint64_t)grid ? T : (uint64_t)grid);
     if (g > 0)
-        k_unpack_roads<<<g, TILE_THREADS, 0, st>>>(words, event_off, dims, first_ev, tile_roads,
-                                                   road_cap, road_word, road_nhit, event_road,
-                                                   cfg, fr, counts, status);
+        launch_after(k_unpack_roads, g, TILE_THREADS, 0, st, words, event_off, dims, first_ev,
+                     tile_roads, road_cap, road_word, road_nhit, event_road, cfg, fr, counts,
+                     status);
 }
 
 void launch_unpack_events(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
@@ -587,7 +598,7 @@ void launch_unpack_events(const uint32_t *words, const uint64_t *event_off, cons
     uint64_t blocks = (max_events + 255) / 256;
     if (blocks < 1) blocks = 1;
     int g = (int)(blocks < (uint64_t)grid ? blocks : (uint64_t)grid);
-    k_unpack_events<<<g, 256, 0, st>>>(words, event_off, dims, event_road, status);
+    launch_after(k_unpack_events, g, 256, 0, st, words, event_off, dims, event_road, status);
 }
 
 }  // namespace svt
