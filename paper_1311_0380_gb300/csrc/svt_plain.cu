@@ -125,13 +125,16 @@ __global__ void k_combine_write(const uint32_t *__restrict__ road_nhit,
         const uint64_t off = comb_off[r], n = comb_off[r + 1] - off;
         if (off + n > comb_cap) continue;
         const RoadShape s = road_shape(road_nhit[r], xft_pairs);
+        uint32_t m[N_LAYERS];
+#pragma unroll
+        for (int l = 0; l < N_LAYERS; ++l) m[l] = kDivMagic[s.n[l]];
         for (uint64_t c = lane; c < n; c += 32) {
-            uint32_t rem = (uint32_t)c, packed = 0;
+            uint32_t rem = (uint32_t)c, packed = 0;   // c < max_comb < 2^32
 #pragma unroll
             for (int l = N_LAYERS - 1; l >= 0; --l) {
-                const uint32_t i = rem % s.n[l];
-                rem /= s.n[l];
-                packed |= i << (4 * l);
+                const uint32_t qd = div_by(rem, s.n[l], m[l]);
+                packed |= (rem - qd * s.n[l]) << (4 * l);
+                rem = qd;
             }
             if (xft_pairs) packed |= ((packed >> 16) & 15u) << 20;   // layer 5 takes layer 4's hit
             comb_road[off + c] = (uint32_t)r;
@@ -170,24 +173,33 @@ __global__ void k_fit_plain(const uint32_t *__restrict__ words,
         const size_t cs = (size_t)rd_sector(hw) * 64 + mask;
         const int16_t *Fs = F + cs * 36;
         const int16_t *qs = q + cs * 6;
-        long long y[N_LAYERS];
+        // acc_k exactly, with 32-bit products: |F_kl x_l| <= 32768 * 32767 < 2^30,
+        // so every sum of two products is exact in int32; the three pair sums
+        // and q_k 2^qshift (|.| < 2^39) are added in int64.  With oshift >= 9,
+        // |y_k| < 2^31 and y_k is exact in int32.
+        int32_t y[N_LAYERS];
 #pragma unroll
         for (int k = 0; k < N_LAYERS; ++k) {
-            long long acc = (long long)__ldg(qs + k) * (1ll << cfg.qshift);
+            int32_t s2[3];
 #pragma unroll
-            for (int l = 0; l < N_LAYERS; ++l) acc += (long long)__ldg(Fs + k * 6 + l) * (long long)x[l];
-            y[k] = acc >> cfg.oshift;   // arithmetic shift: floor
+            for (int m = 0; m < 3; ++m)
+                s2[m] = (int32_t)__ldg(Fs + k * 6 + 2 * m) * (int32_t)x[2 * m] +
+                        (int32_t)__ldg(Fs + k * 6 + 2 * m + 1) * (int32_t)x[2 * m + 1];
+            const long long acc =
+                (long long)((unsigned long long)(long long)__ldg(qs + k) << cfg.qshift) +
+                (long long)s2[0] + (long long)s2[1] + (long long)s2[2];
+            y[k] = (int32_t)(acc >> cfg.oshift);   // arithmetic shift: floor
         }
         uint32_t chi2 = 0;
 #pragma unroll
         for (int k = 3; k < N_LAYERS; ++k) {
-            const long long c = y[k] > 32767 ? 32767 : (y[k] < -32767 ? -32767 : y[k]);
+            const int32_t c = max(min(y[k], 32767), -32767);
             chi2 += (uint32_t)(c * c);
         }
         fit_chi2[j] = chi2;
-        fit_par[j] = (int32_t)y[0];
-        fit_par[comb_cap + j] = (int32_t)y[1];
-        fit_par[2 * comb_cap + j] = (int32_t)y[2];
+        fit_par[j] = y[0];
+        fit_par[comb_cap + j] = y[1];
+        fit_par[2 * comb_cap + j] = y[2];
     }
 }
 
