@@ -133,13 +133,22 @@ typedef struct {
  *   roads_per_chunk  consecutive roads a warp takes at once (1..32, default 4)
  *   small_max        roads with more evaluated combinations than this are
  *                    split into work items; the others are fitted whole by
- *                    one warp (default 4096) */
+ *                    one warp (default 4096)
+ *   pair_small       1: two consecutive roads of a chunk that are both small
+ *                    (at most 8 hits per layer, at most 16 rows and 16
+ *                    suffix-table entries) and of the same split geometry are
+ *                    fitted side by side by the two halves of one warp;
+ *                    0 (default): one road per warp.  Pairing pays when most
+ *                    roads are small and alike (the paper's fixed shape); on
+ *                    mixed roads the warps keep switching between the two
+ *                    code paths and it costs. */
 typedef struct {
     uint32_t warps_per_block;
     uint32_t blocks_per_sm;
     uint32_t rows_per_item;
     uint32_t roads_per_chunk;
     uint32_t small_max;
+    uint32_t pair_small;
 } svt_schedule;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -303,8 +312,10 @@ int svt_run_sized(const uint32_t *d_words, uint64_t max_words, const uint64_t *d
 /* Schedule autotuner: runs svt_run on one device-resident batch for every
  * schedule of {4, 8, 16} warps per block x {8, 16, 32, 64} rows per item x
  * {1, 2, 4, 8} roads per chunk x {1024, 4096, 16384} small_max (blocks per SM
- * as many as fit), one warm-up and `reps` timed runs each (CUDA events on
- * `stream`), and returns the fastest schedule and its mean time per run.
+ * as many as fit, no pairing), then the fastest of those with pair_small = 1
+ * and {2, 4, 8} roads per chunk, one warm-up and `reps` timed runs each (CUDA
+ * events on `stream`), and returns the fastest schedule and its mean time per
+ * run.
  * Synchronises the stream.  Buffers as for svt_run; on return d_out and
  * d_status hold a valid result of the batch (every schedule gives the same
  * bits). */

@@ -36,7 +36,7 @@ class SvtConfig(ctypes.Structure):
 class SvtSchedule(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
                 ("warps_per_block", "blocks_per_sm", "rows_per_item", "roads_per_chunk",
-                 "small_max")]
+                 "small_max", "pair_small")]
 
 
 class SvtServerConfig(ctypes.Structure):

@@ -33,8 +33,9 @@ def config(oshift=15, qshift=15, chi2_cut=0xFFFFFFFF, max_comb=262144, min_layer
 
 
 def schedule(warps_per_block=0, blocks_per_sm=0, rows_per_item=0, roads_per_chunk=0,
-             small_max=0) -> SvtSchedule:
-    return SvtSchedule(warps_per_block, blocks_per_sm, rows_per_item, roads_per_chunk, small_max)
+             small_max=0, pair_small=0) -> SvtSchedule:
+    return SvtSchedule(warps_per_block, blocks_per_sm, rows_per_item, roads_per_chunk, small_max,
+                       pair_small)
 
 
 # ------------------------------------------------------------------ raw entry points

@@ -51,7 +51,7 @@ def tuned_schedule(path, words, n_words, event_off, n_events, cache: str | None 
     if key in table:
         v = table[key]
         return SvtSchedule(v["warps_per_block"], v["blocks_per_sm"], v["rows_per_item"],
-                           v["roads_per_chunk"], v["small_max"]), v.get("ms")
+                           v["roads_per_chunk"], v["small_max"], v.get("pair_small", 0)), v.get("ms")
     sch, ms = tune(path, words, n_words, event_off, n_events, reps)
     table[key] = {f: getattr(sch, f) for f, _ in SvtSchedule._fields_}
     table[key]["ms"] = ms

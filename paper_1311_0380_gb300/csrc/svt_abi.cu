@@ -44,13 +44,14 @@ bool config_ok(const svt_config *c) {
 }
 
 svt_schedule resolve(const svt_schedule *s) {
-    svt_schedule r{8, 0, 16, 4, 4096};
+    svt_schedule r{8, 0, 16, 4, 4096, 0};
     if (s) {
         if (s->warps_per_block) r.warps_per_block = s->warps_per_block;
         if (s->blocks_per_sm) r.blocks_per_sm = s->blocks_per_sm;
         if (s->rows_per_item) r.rows_per_item = s->rows_per_item;
         if (s->roads_per_chunk) r.roads_per_chunk = s->roads_per_chunk;
         if (s->small_max) r.small_max = s->small_max;
+        r.pair_small = s->pair_small;
     }
     return r;
 }
@@ -58,7 +59,7 @@ svt_schedule resolve(const svt_schedule *s) {
 bool schedule_ok(const svt_schedule &s) {
     return s.warps_per_block >= 1 && s.warps_per_block <= 16 && s.blocks_per_sm <= 32 &&
            s.rows_per_item >= 1 && s.rows_per_item <= 64 && s.roads_per_chunk >= 1 &&
-           s.roads_per_chunk <= 32 && s.small_max >= 1;
+           s.roads_per_chunk <= 32 && s.small_max >= 1 && s.pair_small <= 1;
 }
 
 int tile_grid() {
@@ -347,8 +348,8 @@ int run_impl(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_
                         nullptr, nullptr, event_road, *cfg, fr, counts, status, grid, st);
     if (timer && cudaEventRecord(timer->start, st) != cudaSuccess) return SVT_ERR_CUDA;
     if (launch_fit_persistent(d_words, d_event_off, w.dims, event_road, w.desc, counts, road_cap,
-                              d_F, d_q, *cfg, fr, sc.roads_per_chunk, d_out, status,
-                              (int)sc.warps_per_block, sms * bps, st) != cudaSuccess)
+                              d_F, d_q, *cfg, fr, sc.roads_per_chunk, sc.pair_small != 0, d_out,
+                              status, (int)sc.warps_per_block, sms * bps, st) != cudaSuccess)
         return SVT_ERR_CUDA;
     if (timer) {
         if (cudaEventRecord(timer->end, st) != cudaSuccess) return SVT_ERR_CUDA;
@@ -442,37 +443,44 @@ int svt_autotune(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_ev
         return SVT_ERR_CUDA;
     }
     float best_t = 3.4e38f;
-    svt_schedule best_s{0, 0, 0, 0, 0};
+    svt_schedule best_s{0, 0, 0, 0, 0, 0};
     int rc = SVT_OK;
+    // mean time per run of schedule sc (one warm-up, then reps runs); keeps the fastest
+    auto trial = [&](const svt_schedule &sc) -> int {
+        int r = svt_run(d_words, n_words, d_event_off, n_events, d_F, d_q, cfg, road_cap, d_out,
+                        nullptr, nullptr, d_status, d_workspace, workspace_bytes, &sc, nullptr,
+                        stream);   // warm-up
+        if (r != SVT_OK) return r;
+        if (cudaEventRecord(e0, st) != cudaSuccess) return SVT_ERR_CUDA;
+        for (uint32_t k = 0; k < reps; ++k) {
+            r = svt_run(d_words, n_words, d_event_off, n_events, d_F, d_q, cfg, road_cap, d_out,
+                        nullptr, nullptr, d_status, d_workspace, workspace_bytes, &sc, nullptr,
+                        stream);
+            if (r != SVT_OK) return r;
+        }
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+            return SVT_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)reps;
+        if (ms < best_t) {
+            best_t = ms;
+            best_s = sc;
+        }
+        return SVT_OK;
+    };
     for (uint32_t w : kWarps)
         for (uint32_t r : kRows)
             for (uint32_t c : kChunk)
-                for (uint32_t m : kSmall) {
-                    const svt_schedule sc{w, 0, r, c, m};
-                    rc = svt_run(d_words, n_words, d_event_off, n_events, d_F, d_q, cfg, road_cap,
-                                 d_out, nullptr, nullptr, d_status, d_workspace, workspace_bytes,
-                                 &sc, nullptr, stream);   // warm-up
-                    if (rc != SVT_OK) goto done;
-                    if (cudaEventRecord(e0, st) != cudaSuccess) { rc = SVT_ERR_CUDA; goto done; }
-                    for (uint32_t k = 0; k < reps; ++k) {
-                        rc = svt_run(d_words, n_words, d_event_off, n_events, d_F, d_q, cfg,
-                                     road_cap, d_out, nullptr, nullptr, d_status, d_workspace,
-                                     workspace_bytes, &sc, nullptr, stream);
-                        if (rc != SVT_OK) goto done;
-                    }
-                    if (cudaEventRecord(e1, st) != cudaSuccess ||
-                        cudaEventSynchronize(e1) != cudaSuccess) {
-                        rc = SVT_ERR_CUDA;
-                        goto done;
-                    }
-                    float ms = 0.f;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    ms /= (float)reps;
-                    if (ms < best_t) {
-                        best_t = ms;
-                        best_s = sc;
-                    }
-                }
+                for (uint32_t m : kSmall)
+                    if ((rc = trial(svt_schedule{w, 0, r, c, m, 0})) != SVT_OK) goto done;
+    {
+        const svt_schedule base = best_s;
+        for (uint32_t c : {2u, 4u, 8u})
+            if ((rc = trial(svt_schedule{base.warps_per_block, 0, base.rows_per_item, c,
+                                         base.small_max, 1})) != SVT_OK)
+                goto done;
+    }
 done:
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

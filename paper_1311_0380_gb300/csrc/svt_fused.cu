@@ -33,23 +33,50 @@ namespace {
 
 constexpr int ROWS_MAX = 64;
 
-// All accumulator terms are kept multiplied by 2^(32 - oshift): the high word
-// of a 64-bit sum of such terms is then exactly floor(sum / 2^oshift).
-struct WarpSmem {
-    longlong2 T[N_LAYERS * MAX_HITS][2];  // chi-row terms F[3+k][l] * x * 2^(32-oshift) of hit i of
-                                          // layer l at [l*16+i]: (k=3, k=4), (k=5, -); 32-byte entries
-                                          // so a lookup is one 16-byte and one 8-byte load
-    longlong2 S01[32];                    // suffix sums below the top suffix layer, rows 3, 4 [b']
-    long long S5[32];                     // ... row 5
-    longlong2 A01[ROWS_MAX];              // prefix sums incl. q, rows 3, 4, per row of the chunk
-    long long A5[ROWS_MAX];               // ... row 5
-    uint32_t x[N_LAYERS * MAX_HITS];      // hit coordinates [l][i] (x = 0 for an empty layer)
-    int32_t F[36];                        // F[s][m][k][l] at k*6+l
+// A road's working set in shared memory, for roads with at most MH hits on
+// every layer, NS suffix-table entries and NR rows per chunk.  All
+// accumulator terms are kept multiplied by 2^(32 - oshift): the high word of a
+// 64-bit sum of such terms is then exactly floor(sum / 2^oshift).
+template <int MH, int NS, int NR>
+struct RoadSmem {
+    longlong2 T[N_LAYERS * MH][2];  // chi-row terms F[3+k][l] * x * 2^(32-oshift) of hit i of
+                                    // layer l at [l*MH+i]: (k=3, k=4), (k=5, -); 32-byte entries
+                                    // so a lookup is one 16-byte and one 8-byte load
+    longlong2 S01[NS];              // suffix sums below the top suffix layer, rows 3, 4 [b']
+    long long S5[NS];               // ... row 5
+    longlong2 A01[NR];              // prefix sums incl. q, rows 3, 4, per row of the chunk
+    long long A5[NR];               // ... row 5
+    uint32_t x[N_LAYERS * MH];      // hit coordinates [l][i] (x = 0 for an empty layer)
+    int32_t F[36];                  // F[s][m][k][l] at k*6+l
     int32_t q[6];
-    uint32_t n[N_LAYERS];                 // n'_l = max(n_l, 1)
-    uint32_t m[N_LAYERS];                 // division magic of n'_l
-    uint32_t off[N_LAYERS];               // index of the first hit of layer l in the road
+    uint32_t n[N_LAYERS];           // n'_l = max(n_l, 1)
+    uint32_t m[N_LAYERS];           // division magic of n'_l
+    uint32_t off[N_LAYERS];         // index of the first hit of layer l in the road
+    static constexpr uint32_t kMH = MH, kNR = NR;
 };
+// one road per warp; or two roads marked SMALL, one per half warp, each in
+// half of the same space
+using WarpSmem = RoadSmem<MAX_HITS, 32, ROWS_MAX>;
+using HalfSmem = RoadSmem<8, 16, 16>;
+static_assert(2 * sizeof(HalfSmem) <= sizeof(WarpSmem), "two half slots fit in a warp slot");
+static_assert(sizeof(HalfSmem) % 16 == 0, "half slots keep 16-byte alignment");
+constexpr uint32_t GEO_SMALL = 1u << 28;
+
+// The W lanes (the warp, or one half of it) that fit one road.  Every
+// warp-synchronous step of the per-road code names only these lanes, so the
+// two halves of a warp may run their roads' loops with different trip counts.
+template <int W>
+struct Lanes {
+    uint32_t gl;     // lane within the group
+    uint32_t mask;   // the group's lanes
+};
+template <int W>
+__device__ __forceinline__ Lanes<W> lanes_of(int lane) {
+    Lanes<W> L;
+    L.gl = (uint32_t)lane & (uint32_t)(W - 1);
+    L.mask = W == 32 ? 0xffffffffu : (0xFFFFu << ((uint32_t)lane & 16u));
+    return L;
+}
 
 // largest j in [0, n) with off[j] <= it (off non-decreasing, off[0] = 0)
 __device__ __forceinline__ uint32_t find_slot(const uint32_t *__restrict__ off, uint32_t n,
@@ -67,19 +94,31 @@ __device__ __forceinline__ uint32_t find_slot(const uint32_t *__restrict__ off, 
     return lo;
 }
 
-// Smallest 64-bit key over the warp: the smallest high word, then the
+// Smallest 64-bit key over the group: the smallest high word, then the
 // smallest low word among the lanes that hold it.
-__device__ __forceinline__ unsigned long long warp_min64(unsigned long long v) {
+template <int W>
+__device__ __forceinline__ unsigned long long group_min64(unsigned long long v,
+                                                          const Lanes<W> &L) {
     const uint32_t hi = (uint32_t)(v >> 32), lo = (uint32_t)v;
-    const uint32_t m_hi = __reduce_min_sync(0xffffffffu, hi);
-    const uint32_t m_lo = __reduce_min_sync(0xffffffffu, hi == m_hi ? lo : 0xFFFFFFFFu);
+    uint32_t m_hi, m_lo;
+    if constexpr (W == 32) {
+        m_hi = __reduce_min_sync(0xffffffffu, hi);
+        m_lo = __reduce_min_sync(0xffffffffu, hi == m_hi ? lo : 0xFFFFFFFFu);
+    } else {
+        m_hi = hi;
+#pragma unroll
+        for (int d = W / 2; d >= 1; d >>= 1) m_hi = min(m_hi, __shfl_xor_sync(L.mask, m_hi, d, W));
+        m_lo = hi == m_hi ? lo : 0xFFFFFFFFu;
+#pragma unroll
+        for (int d = W / 2; d >= 1; d >>= 1) m_lo = min(m_lo, __shfl_xor_sync(L.mask, m_lo, d, W));
+    }
     return ((unsigned long long)m_hi << 32) | m_lo;
 }
 
 __device__ __forceinline__ int32_t clamp_chi(int32_t y) { return max(min(y, 32767), -32767); }
 
 
-// Road geometry unpacked from its descriptor (warp-uniform values).
+// Road geometry unpacked from its descriptor (uniform over the road's lanes).
 struct Geo {
     uint32_t split, NBp, NB, NA, C_eval, mask, total_hits;
 };
@@ -97,83 +136,95 @@ __device__ __forceinline__ Geo geo_of(const RoadDesc &D) {
 }
 
 // Constants, hit coordinates, per-hit chi terms and the suffix table of road D
-// in the warp's slot.  Global loads are issued before any shared-memory work.
-__device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restrict__ words,
+// in the group's slot.  Global loads are issued before any shared-memory work.
+// A road has at most 96 hits (at most 48 in a half slot: 8 per layer), so
+// three passes of W = 32 lanes, or of W = 16 lanes over a SMALL road, hold
+// them all.
+template <int W, typename SM>
+__device__ __forceinline__ void road_setup(SM &sm, const uint32_t *__restrict__ words,
                                            const RoadDesc &D, const Geo &g,
                                            const int16_t *__restrict__ F,
                                            const int16_t *__restrict__ q, uint32_t sh,
-                                           uint32_t xft, long long bias, int lane) {
-    const uint32_t rw = D.a.x, packed = D.a.y;
+                                           uint32_t xft, long long bias, const Lanes<W> &L) {
+    constexpr uint32_t MH = SM::kMH;
+    constexpr int NFQ = (42 + W - 1) / W;   // passes over the 36 + 6 constants
+    const uint32_t rw = D.a.x, packed = D.a.y, gl = L.gl;
     const size_t cs = (size_t)rd_sector(D.a.z) * 64 + g.mask;
-    const int32_t f0 = __ldg(F + cs * 36 + lane);
-    int32_t f1 = 0;
-    if (lane < 4) f1 = __ldg(F + cs * 36 + 32 + lane);
-    else if (lane < 10) f1 = __ldg(q + cs * 6 + (lane - 4));
+    int32_t fv[NFQ];
+#pragma unroll
+    for (int j = 0; j < NFQ; ++j) {
+        const uint32_t e = gl + (uint32_t)W * j;
+        fv[j] = e < 36 ? __ldg(F + cs * 36 + e) : (e < 42 ? __ldg(q + cs * 6 + (e - 36)) : 0);
+    }
     uint32_t hv[3];
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const uint32_t h = (uint32_t)lane + 32u * j;
+        const uint32_t h = gl + (uint32_t)W * j;
         hv[j] = h < g.total_hits ? __ldg(words + rw + 1 + h) : 0u;
     }
-    sm.F[lane] = f0;
-    if (lane < 4) sm.F[32 + lane] = f1;
-    else if (lane < 10) sm.q[lane - 4] = f1;
-    const uint32_t nl = lane < N_LAYERS ? nhit_of(packed, lane) : 0u;
+#pragma unroll
+    for (int j = 0; j < NFQ; ++j) {
+        const uint32_t e = gl + (uint32_t)W * j;
+        if (e < 36) sm.F[e] = fv[j];
+        else if (e < 42) sm.q[e - 36] = fv[j];
+    }
+    const uint32_t nl = gl < N_LAYERS ? nhit_of(packed, gl) : 0u;
     uint32_t incl = nl;   // inclusive prefix of the layer counts
 #pragma unroll
     for (int d = 1; d < 8; d <<= 1) {
-        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += v;
+        const uint32_t v = __shfl_up_sync(L.mask, incl, d, W);
+        if (gl >= (uint32_t)d) incl += v;
     }
-    if (lane < N_LAYERS) {
+    if (gl < N_LAYERS) {
         // with track-trigger pairs layer 5 is no digit of its own (radix 1)
-        const uint32_t np = (nl && !(xft && lane == N_LAYERS - 1)) ? nl : 1u;
-        sm.n[lane] = np;
-        sm.m[lane] = kDivMagic[np];
-        sm.off[lane] = incl - nl;
+        const uint32_t np = (nl && !(xft && gl == N_LAYERS - 1)) ? nl : 1u;
+        sm.n[gl] = np;
+        sm.m[gl] = kDivMagic[np];
+        sm.off[gl] = incl - nl;
         if (nl == 0) {   // a layer without hits contributes x = 0
-            sm.x[lane * MAX_HITS] = 0;
-            sm.T[lane * MAX_HITS][0] = make_longlong2(0, 0);
-            sm.T[lane * MAX_HITS][1].x = 0;
+            sm.x[gl * MH] = 0;
+            sm.T[gl * MH][0] = make_longlong2(0, 0);
+            sm.T[gl * MH][1].x = 0;
         }
     }
-    __syncwarp();
+    __syncwarp(L.mask);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        const uint32_t h = (uint32_t)lane + 32u * j;
+        const uint32_t h = gl + (uint32_t)W * j;
         if (h < g.total_hits) {
             const uint32_t l = hit_layer(hv[j]);
             const uint32_t i = h - sm.off[l];   // hits are sorted by layer (validated)
             const uint32_t xc = hit_coord(hv[j]);
-            sm.x[l * MAX_HITS + i] = xc;
-            longlong2 *t = sm.T[l * MAX_HITS + i];
+            sm.x[l * MH + i] = xc;
+            longlong2 *t = sm.T[l * MH + i];
             t[0] = make_longlong2((long long)(sm.F[18 + l] * (int32_t)xc) << sh,
                                   (long long)(sm.F[24 + l] * (int32_t)xc) << sh);
             t[1].x = (long long)(sm.F[30 + l] * (int32_t)xc) << sh;
         }
     }
-    __syncwarp();
+    __syncwarp(L.mask);
     if (xft) {
         // pair i: layer 4's entry i carries both coordinates of track-trigger
         // track i (equal counts are validated); layer 5 then adds nothing
         const uint32_t n4 = nhit_of(packed, 4);
-        if ((uint32_t)lane < n4) {
-            longlong2 *t4 = sm.T[4 * MAX_HITS + lane];
-            const longlong2 *t5 = sm.T[5 * MAX_HITS + lane];
+        if (gl < n4) {
+            longlong2 *t4 = sm.T[4 * MH + gl];
+            const longlong2 *t5 = sm.T[5 * MH + gl];
             t4[0].x += t5[0].x;
             t4[0].y += t5[0].y;
             t4[1].x += t5[1].x;
         }
-        __syncwarp();
-        if (lane == 0) {
-            sm.T[5 * MAX_HITS][0] = make_longlong2(0, 0);
-            sm.T[5 * MAX_HITS][1].x = 0;
+        __syncwarp(L.mask);
+        if (gl == 0) {
+            sm.T[5 * MH][0] = make_longlong2(0, 0);
+            sm.T[5 * MH][1].x = 0;
         }
     }
-    __syncwarp();
-    // S[b'] = bias + sum over the suffix layers below the top one, b' < NBp (< 32)
-    if ((uint32_t)lane < g.NBp) {
-        uint32_t rem = lane;
+    __syncwarp(L.mask);
+    // S[b'] = bias + sum over the suffix layers below the top one, b' < NBp
+    // (< 32; <= 16 for a SMALL road)
+    if (gl < g.NBp) {
+        uint32_t rem = gl;
         long long S3 = bias, S4 = bias, S5 = bias;
 #pragma unroll
         for (int l = N_LAYERS - 1; l >= 1; --l) {
@@ -182,20 +233,22 @@ __device__ __forceinline__ void road_setup(WarpSmem &sm, const uint32_t *__restr
                 const uint32_t qd = div_by(rem, nl, sm.m[l]);
                 const uint32_t i = rem - qd * nl;
                 rem = qd;
-                const longlong2 t01 = sm.T[l * MAX_HITS + i][0];
+                const longlong2 t01 = sm.T[l * MH + i][0];
                 S3 += t01.x;
                 S4 += t01.y;
-                S5 += sm.T[l * MAX_HITS + i][1].x;
+                S5 += sm.T[l * MH + i][1].x;
             }
         }
-        sm.S01[lane] = make_longlong2(S3, S4);
-        sm.S5[lane] = S5;
+        sm.S01[gl] = make_longlong2(S3, S4);
+        sm.S5[gl] = S5;
     }
-    __syncwarp();
+    __syncwarp(L.mask);
 }
 
-__device__ __forceinline__ void build_row(WarpSmem &sm, uint32_t split, uint32_t a,
-                                          uint32_t slot, uint32_t qsh) {
+template <typename SM>
+__device__ __forceinline__ void build_row(SM &sm, uint32_t split, uint32_t a, uint32_t slot,
+                                          uint32_t qsh) {
+    constexpr uint32_t MH = SM::kMH;
     uint32_t rem = a;
     long long A3 = (long long)sm.q[3] << qsh;
     long long A4 = (long long)sm.q[4] << qsh;
@@ -207,10 +260,10 @@ __device__ __forceinline__ void build_row(WarpSmem &sm, uint32_t split, uint32_t
             const uint32_t qd = div_by(rem, nl, sm.m[l]);
             const uint32_t i = rem - qd * nl;
             rem = qd;
-            const longlong2 t01 = sm.T[l * MAX_HITS + i][0];
+            const longlong2 t01 = sm.T[l * MH + i][0];
             A3 += t01.x;
             A4 += t01.y;
-            A5 += sm.T[l * MAX_HITS + i][1].x;
+            A5 += sm.T[l * MH + i][1].x;
         }
     }
     sm.A01[slot] = make_longlong2(A3, A4);
@@ -226,36 +279,37 @@ __device__ __forceinline__ int32_t hi_word(long long v) {
 template <bool GUARDED>
 constexpr long long kColBias = GUARDED ? (32768LL << 32) : 0LL;
 
-// Best key over rows [a_lo, a_hi) of the road, reduced over the warp.  The key
-// is (chi2 << 32) | (row << 9) | column; since columns < NB < 512 its low word
-// orders exactly like the combination index c = row * NB + column.
+// Best key over rows [a_lo, a_hi) of the road, reduced over the group.  The
+// key is (chi2 << 32) | (row << 9) | column; since columns < NB < 512 its low
+// word orders exactly like the combination index c = row * NB + column.
 // Each lane takes one column and runs down the rows of the chunk; in the last
-// pass over the columns, when only w < 32 of them are left, the lanes form
-// floor(32 / w) groups of w and each group takes one block of the rows.
+// pass over the columns, when only w < W of them are left, the lanes form
+// floor(W / w) groups of w and each group takes one block of the rows.
 // GUARDED (valid when chi2_cut < 32767^2): a combination with a chi component
 // of magnitude 32767 or more cannot pass, clamped or not.  One range test keeps
 // only combinations with -32768 <= y_k <= 32767 for all three components; for
 // those the sum of the squares is below 3 * 2^30 < 2^32 and is formed exactly
 // in 32 bits, and the clamp changes no square that could still pass.
 // Pass/fail, chi2 of passing combinations and the argmin are unchanged.
-template <bool GUARDED>
-__device__ __forceinline__ unsigned long long eval_rows(WarpSmem &sm, const Geo &g, uint32_t a_lo,
+template <bool GUARDED, int W, typename SM>
+__device__ __forceinline__ unsigned long long eval_rows(SM &sm, const Geo &g, uint32_t a_lo,
                                                         uint32_t a_hi, uint32_t qsh,
-                                                        uint32_t init_chi, int lane) {
+                                                        uint32_t init_chi, const Lanes<W> &L) {
+    constexpr uint32_t MH = SM::kMH, NR = SM::kNR;
     unsigned long long best = ~0ull;
     const uint32_t NB = g.NB, NA = g.NA, C_eval = g.C_eval, NBp = g.NBp, top = g.split;
-    const uint32_t mp = kDivMagic[NBp];
-    for (uint32_t ac = a_lo; ac < a_hi; ac += ROWS_MAX) {
-        const uint32_t ae = min(ac + (uint32_t)ROWS_MAX, a_hi), rows = ae - ac;
+    const uint32_t mp = kDivMagic[NBp], gl = L.gl;
+    for (uint32_t ac = a_lo; ac < a_hi; ac += NR) {
+        const uint32_t ae = min(ac + NR, a_hi), rows = ae - ac;
 #pragma unroll
-        for (uint32_t r0 = 0; r0 < (uint32_t)ROWS_MAX; r0 += 32)
-            if (r0 + lane < rows) build_row(sm, top, ac + r0 + lane, r0 + lane, qsh);
-        __syncwarp();
-        for (uint32_t b0 = 0; b0 < NB; b0 += 32) {
-            uint32_t b = b0 + (uint32_t)lane, lo = ac, hi = ae;
-            if (NB - b0 < 32u) {   // warp-uniform: the last, partial pass
+        for (uint32_t r0 = 0; r0 < NR; r0 += (uint32_t)W)
+            if (r0 + gl < rows) build_row(sm, top, ac + r0 + gl, r0 + gl, qsh);
+        __syncwarp(L.mask);
+        for (uint32_t b0 = 0; b0 < NB; b0 += (uint32_t)W) {
+            uint32_t b = b0 + gl, lo = ac, hi = ae;
+            if (NB - b0 < (uint32_t)W) {   // uniform over the group: the last, partial pass
                 const uint32_t w = NB - b0, mw = kDivMagic[w];
-                const uint32_t grp = div_by((uint32_t)lane, w, mw), n_grp = div_by(32u, w, mw);
+                const uint32_t grp = div_by(gl, w, mw), n_grp = div_by((uint32_t)W, w, mw);
                 const uint32_t len = div_by(rows + n_grp - 1u, n_grp, kDivMagic[n_grp]);
                 b -= grp * w;
                 lo = min(ac + grp * len, ae);   // groups past the last row get none
@@ -264,8 +318,8 @@ __device__ __forceinline__ unsigned long long eval_rows(WarpSmem &sm, const Geo 
             // column b = is * NBp + bp: hit `is` of the top suffix layer and
             // entry bp of the suffix table
             const uint32_t is = div_by(b, NBp, mp), bp = b - is * NBp;
-            const longlong2 t01 = sm.T[top * MAX_HITS + is][0];
-            const long long t5 = sm.T[top * MAX_HITS + is][1].x;
+            const longlong2 t01 = sm.T[top * MH + is][0];
+            const long long t5 = sm.T[top * MH + is][1].x;
             const longlong2 s01 = sm.S01[bp];
             const long long s5 = sm.S5[bp];
             const long long B3 = t01.x + s01.x, B4 = t01.y + s01.y, B5 = t5 + s5;
@@ -304,18 +358,21 @@ __device__ __forceinline__ unsigned long long eval_rows(WarpSmem &sm, const Geo 
                 best = key < best ? key : best;
             }
         }
-        __syncwarp();
+        __syncwarp(L.mask);
     }
-    return warp_min64(best);
+    return group_min64<W>(best, L);
 }
 
-// Record of a road from its best key (all lanes call; lanes 0..2 recompute the
-// parameters from the warp's slot, which still holds this road; lanes 0..5
-// store one word each).  Returns whether the road passed.
-__device__ __forceinline__ bool format_road(WarpSmem &sm, const RoadDesc &D, const Geo &g,
+// Record of a road from its best key (all lanes of the group call; lanes of
+// the group form the parameters from its slot, which still holds this road;
+// lanes 0..5 of the group store one word each).  Returns whether the road
+// passed.
+template <int W, typename SM>
+__device__ __forceinline__ bool format_road(SM &sm, const RoadDesc &D, const Geo &g,
                                             const svt_config &cfg, unsigned long long best,
-                                            uint32_t *o, int lane) {
-    const uint32_t geo = D.b.x;
+                                            uint32_t *o, const Lanes<W> &L) {
+    constexpr uint32_t MH = SM::kMH;
+    const uint32_t geo = D.b.x, gl = L.gl;
     const bool pass = best != ~0ull;
     uint32_t flags = 0;
     if (g.total_hits == 0) flags |= SVT_FLAG_NO_HITS;
@@ -324,42 +381,99 @@ __device__ __forceinline__ bool format_road(WarpSmem &sm, const RoadDesc &D, con
     if (pass) flags |= SVT_FLAG_PASS;
     const uint32_t low = (uint32_t)best;
     const uint32_t row = low >> 9, col = low & 511u;
-    // parameters of the best combination: lane 8k + l (k < 3, l < 6) forms
-    // F[k][l] x_l, the groups of eight lanes sum them, lane 8k adds q_k
-    int32_t p = 0;
+    int32_t pk = 0;   // parameter k = gl - 3 of the best combination, on lanes 3..5
     if (pass) {
-        const uint32_t k = (uint32_t)lane >> 3, lk = (uint32_t)lane & 7u;
-        uint32_t rem = col, i_own = 0;
+        if constexpr (W == 32) {
+            // lane 8k + l (k < 3, l < 6) forms F[k][l] x_l, the groups of
+            // eight lanes sum them, lane 8k adds q_k
+            const uint32_t k = gl >> 3, lk = gl & 7u;
+            uint32_t rem = col, i_own = 0;
 #pragma unroll
-        for (int l = N_LAYERS - 1; l >= 0; --l) {
-            if ((uint32_t)l + 1u == g.split) rem = row;   // the prefix layers take the row
-            const uint32_t nl = sm.n[l];
-            const uint32_t qd = div_by(rem, nl, sm.m[l]);
-            if ((uint32_t)l == (cfg.xft_pairs && lk == 5u ? 4u : lk)) i_own = rem - qd * nl;
-            rem = qd;
-        }
-        long long t = 0;
-        if (k < 3 && lk < (uint32_t)N_LAYERS)
-            t = (long long)sm.F[k * 6 + lk] * (long long)sm.x[lk * MAX_HITS + i_own];
-        t += __shfl_xor_sync(0xffffffffu, t, 4);
-        t += __shfl_xor_sync(0xffffffffu, t, 2);
-        t += __shfl_xor_sync(0xffffffffu, t, 1);
-        if (k < 3 && lk == 0) {
-            const long long acc = (long long)sm.q[k] * (1ll << cfg.qshift) + t;
-            p = (int32_t)(acc >> cfg.oshift);   // arithmetic shift: floor
+            for (int l = N_LAYERS - 1; l >= 0; --l) {
+                if ((uint32_t)l + 1u == g.split) rem = row;   // the prefix layers take the row
+                const uint32_t nl = sm.n[l];
+                const uint32_t qd = div_by(rem, nl, sm.m[l]);
+                if ((uint32_t)l == (cfg.xft_pairs && lk == 5u ? 4u : lk)) i_own = rem - qd * nl;
+                rem = qd;
+            }
+            long long t = 0;
+            if (k < 3 && lk < (uint32_t)N_LAYERS)
+                t = (long long)sm.F[k * 6 + lk] * (long long)sm.x[lk * MH + i_own];
+            t += __shfl_xor_sync(0xffffffffu, t, 4);
+            t += __shfl_xor_sync(0xffffffffu, t, 2);
+            t += __shfl_xor_sync(0xffffffffu, t, 1);
+            int32_t p = 0;
+            if (k < 3 && lk == 0) {
+                const long long acc = (long long)sm.q[k] * (1ll << cfg.qshift) + t;
+                p = (int32_t)(acc >> cfg.oshift);   // arithmetic shift: floor
+            }
+            pk = __shfl_sync(0xffffffffu, p, ((gl + 29) & 31) << 3);   // lane 3 + k gets p_k
+        } else {
+            // lane 3 + k (k < 3) sums the six terms of parameter k itself
+            uint32_t rem = col, i_l[N_LAYERS];
+#pragma unroll
+            for (int l = N_LAYERS - 1; l >= 0; --l) {
+                if ((uint32_t)l + 1u == g.split) rem = row;   // the prefix layers take the row
+                const uint32_t nl = sm.n[l];
+                const uint32_t qd = div_by(rem, nl, sm.m[l]);
+                i_l[l] = rem - qd * nl;
+                rem = qd;
+            }
+            if (cfg.xft_pairs) i_l[5] = i_l[4];   // layer 5 takes layer 4's hit
+            if (gl >= 3 && gl < 6) {
+                const uint32_t k = gl - 3;
+                long long acc = (long long)sm.q[k] * (1ll << cfg.qshift);
+#pragma unroll
+                for (int l = 0; l < N_LAYERS; ++l)
+                    acc += (long long)sm.F[k * 6 + l] * (long long)sm.x[l * MH + i_l[l]];
+                pk = (int32_t)(acc >> cfg.oshift);   // arithmetic shift: floor
+            }
         }
     }
-    const int32_t pk = __shfl_sync(0xffffffffu, p, ((lane + 29) & 31) << 3);   // lane 3 + k gets p_k
-    const uint32_t w = lane == 0   ? (rd_id(D.a.z) | (flags << 24))
-                       : lane == 1 ? (pass ? row * g.NB + col : 0xFFFFFFFFu)
-                       : lane == 2 ? (pass ? (uint32_t)(best >> 32) : 0u)
-                                   : (uint32_t)pk;
-    if (lane < 6) o[lane] = w;
+    const uint32_t w = gl == 0   ? (rd_id(D.a.z) | (flags << 24))
+                       : gl == 1 ? (pass ? row * g.NB + col : 0xFFFFFFFFu)
+                       : gl == 2 ? (pass ? (uint32_t)(best >> 32) : 0u)
+                                 : (uint32_t)pk;
+    if (gl < 6) o[gl] = w;
     return pass;
 }
 
-// K4: persistent fit / cut / select / format
-template <bool GUARDED>
+// One road fitted whole by a group of W lanes: set-up, all its rows, record.
+// Returns 1 on the group's first lane when the road passed, else 0.
+template <bool GUARDED, int W, typename SM>
+__device__ __forceinline__ uint32_t fit_road(SM &sm, const uint32_t *__restrict__ words,
+                                             const RoadDesc &D, const int16_t *__restrict__ F,
+                                             const int16_t *__restrict__ q,
+                                             const svt_config &cfg, uint32_t sh, uint32_t qsh,
+                                             uint32_t init_chi, uint32_t *o, const Lanes<W> &L) {
+    const Geo g = geo_of(D);
+    unsigned long long best = ~0ull;
+    if (g.C_eval > 0) {
+        road_setup<W>(sm, words, D, g, F, q, sh, cfg.xft_pairs, kColBias<GUARDED>, L);
+        best = eval_rows<GUARDED, W>(sm, g, 0, g.NA, qsh, init_chi, L);
+    }
+    const bool pass = format_road<W>(sm, D, g, cfg, best, o, L);
+    return (pass && L.gl == 0) ? 1u : 0u;
+}
+
+__device__ __forceinline__ RoadDesc shfl_desc(const uint4 &da, const uint4 &db, uint32_t src) {
+    RoadDesc D;
+    D.a.x = __shfl_sync(0xffffffffu, da.x, src);
+    D.a.y = __shfl_sync(0xffffffffu, da.y, src);
+    D.a.z = __shfl_sync(0xffffffffu, da.z, src);
+    D.a.w = __shfl_sync(0xffffffffu, da.w, src);
+    D.b.x = __shfl_sync(0xffffffffu, db.x, src);
+    D.b.y = __shfl_sync(0xffffffffu, db.y, src);
+    D.b.z = __shfl_sync(0xffffffffu, db.z, src);
+    D.b.w = 0;
+    return D;
+}
+
+// K4: persistent fit / cut / select / format.  PAIR: two consecutive SMALL
+// roads of one chunk with the same geometry go to the two halves of the warp
+// (a separate instance, so that warps never switch between the two code
+// paths unless pairing was asked for).
+template <bool GUARDED, bool PAIR>
 __global__ void __launch_bounds__(512, 2)
     k_fit_persistent(const uint32_t *__restrict__ words, const uint64_t *__restrict__ event_off,
                      const Dims *__restrict__ dims, const uint32_t *__restrict__ event_road,
@@ -370,6 +484,7 @@ __global__ void __launch_bounds__(512, 2)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
+    const Lanes<32> LW = lanes_of<32>(lane);
     wait_prior_grid();   // road extraction has completed (see launch_after)
     // per-event rules first, whatever the status, so that the key stays the
     // smallest over all rules
@@ -386,7 +501,7 @@ __global__ void __launch_bounds__(512, 2)
     const uint32_t R = (uint32_t)R64;
     const uint32_t sh = 32u - cfg.oshift, qsh = cfg.qshift + sh;
     const uint32_t init_chi = cfg.chi2_cut == 0xFFFFFFFFu ? 0xFFFFFFFFu : cfg.chi2_cut + 1u;
-    uint32_t n_pass = 0;   // passing roads formatted by this warp, added to counts[3] once
+    uint32_t n_pass = 0;   // passing roads formatted by this lane's group, summed at exit
 
     // phase 1: items of split roads
     for (;;) {
@@ -401,10 +516,10 @@ __global__ void __launch_bounds__(512, 2)
         D.a = __ldg(&desc[r].a);
         D.b = __ldg(&desc[r].b);
         const Geo g = geo_of(D);
-        road_setup(sm, words, D, g, F, q, sh, cfg.xft_pairs, kColBias<GUARDED>, lane);
+        road_setup<32>(sm, words, D, g, F, q, sh, cfg.xft_pairs, kColBias<GUARDED>, LW);
         const uint32_t a_lo = k * fr.rows;
         const uint32_t a_hi = min(a_lo + fr.rows, g.NA);
-        const unsigned long long best = eval_rows<GUARDED>(sm, g, a_lo, a_hi, qsh, init_chi, lane);
+        const unsigned long long best = eval_rows<GUARDED, 32>(sm, g, a_lo, a_hi, qsh, init_chi, LW);
         uint32_t last = 0;
         if (lane == 0) {
             if (best != ~0ull) atomicMin(bl.best + j, best);
@@ -415,12 +530,14 @@ __global__ void __launch_bounds__(512, 2)
         if (last) {
             __threadfence();
             const unsigned long long fb = __ldcg(bl.best + j);
-            n_pass += format_road(sm, D, g, cfg, fb, out + (size_t)r * 6, lane) ? 1u : 0u;
+            const bool pass = format_road<32>(sm, D, g, cfg, fb, out + (size_t)r * 6, LW);
+            n_pass += (pass && lane == 0) ? 1u : 0u;
         }
         __syncwarp();
     }
 
-    // phase 2: chunks of consecutive roads, each fitted whole by this warp
+    // phase 2: chunks of consecutive roads, each fitted whole by this warp,
+    // or two SMALL roads side by side by its two halves
     for (;;) {
         uint32_t c0 = 0;
         if (lane == 0) c0 = atomicAdd(bl.counters + 1, roads_per_chunk);
@@ -432,27 +549,37 @@ __global__ void __launch_bounds__(512, 2)
             da = __ldg(&desc[c0 + lane].a);
             db = __ldg(&desc[c0 + lane].b);
         }
-        for (uint32_t jj = 0; jj < n; ++jj) {
-            RoadDesc D;
-            D.a.x = __shfl_sync(0xffffffffu, da.x, jj);
-            D.a.y = __shfl_sync(0xffffffffu, da.y, jj);
-            D.a.z = __shfl_sync(0xffffffffu, da.z, jj);
-            D.a.w = __shfl_sync(0xffffffffu, da.w, jj);
-            D.b.x = __shfl_sync(0xffffffffu, db.x, jj);
-            D.b.y = __shfl_sync(0xffffffffu, db.y, jj);
-            D.b.z = __shfl_sync(0xffffffffu, db.z, jj);
-            D.b.w = 0;
-            if (D.a.w > fr.small_max) continue;   // split road: done in phase 1
-            const Geo g = geo_of(D);
-            unsigned long long best = ~0ull;
-            if (g.C_eval > 0) {
-                road_setup(sm, words, D, g, F, q, sh, cfg.xft_pairs, kColBias<GUARDED>, lane);
-                best = eval_rows<GUARDED>(sm, g, 0, g.NA, qsh, init_chi, lane);
+        for (uint32_t jj = 0; jj < n;) {
+            const RoadDesc D = shfl_desc(da, db, jj);
+            if (D.a.w > fr.small_max) {   // split road: done in phase 1
+                ++jj;
+                continue;
             }
-            n_pass += format_road(sm, D, g, cfg, best, out + (size_t)(c0 + jj) * 6, lane) ? 1u : 0u;
+            if constexpr (PAIR) {
+                // two SMALL roads of the same geometry (split, NBp, ntop and NA),
+                // so that the two halves run their loops in step
+                if ((D.b.x & GEO_SMALL) && jj + 1 < n) {
+                    const RoadDesc D2 = shfl_desc(da, db, jj + 1);
+                    if ((D2.b.x & GEO_SMALL) && ((D.b.x ^ D2.b.x) & 0x1FFFu) == 0 &&
+                        D.b.z == D2.b.z && D2.a.w <= fr.small_max) {
+                        const uint32_t h = (uint32_t)lane >> 4;   // this lane's half and road
+                        HalfSmem &hs = reinterpret_cast<HalfSmem *>(&sm)[h];
+                        n_pass += fit_road<GUARDED, 16>(hs, words, h ? D2 : D, F, q, cfg, sh, qsh,
+                                                        init_chi, out + (size_t)(c0 + jj + h) * 6,
+                                                        lanes_of<16>(lane));
+                        jj += 2;
+                        __syncwarp();
+                        continue;
+                    }
+                }
+            }
+            n_pass += fit_road<GUARDED, 32>(sm, words, D, F, q, cfg, sh, qsh, init_chi,
+                                            out + (size_t)(c0 + jj) * 6, LW);
+            jj += 1;
             __syncwarp();
         }
     }
+    n_pass = __reduce_add_sync(0xffffffffu, n_pass);
     if (lane == 0 && n_pass)
         atomicAdd((unsigned long long *)(counts + 3), (unsigned long long)n_pass);
 }
@@ -462,34 +589,41 @@ __global__ void __launch_bounds__(512, 2)
 size_t fit_smem_bytes(int warps_per_block) { return sizeof(WarpSmem) * (size_t)warps_per_block; }
 
 int fit_persistent_blocks_per_sm(int warps_per_block) {
-    int n = 0, n2 = 0;
-    size_t smem = fit_smem_bytes(warps_per_block);
-    cudaFuncSetAttribute(k_fit_persistent<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(k_fit_persistent<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fit_persistent<true>, warps_per_block * 32,
-                                                      smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n2, k_fit_persistent<false>,
-                                                      warps_per_block * 32, smem) != cudaSuccess)
-        return 0;
-    return n < n2 ? n : n2;
+    const size_t smem = fit_smem_bytes(warps_per_block);
+    int occ = 1 << 30;
+    auto one = [&](auto kernel) {
+        int n = 0;
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, warps_per_block * 32, smem) !=
+            cudaSuccess)
+            n = 0;
+        occ = n < occ ? n : occ;
+    };
+    one(k_fit_persistent<true, false>);
+    one(k_fit_persistent<false, false>);
+    one(k_fit_persistent<true, true>);
+    one(k_fit_persistent<false, true>);
+    return occ;
 }
 
 cudaError_t launch_fit_persistent(const uint32_t *words, const uint64_t *event_off,
                                   const Dims *dims, const uint32_t *event_road,
                                   const RoadDesc *desc, uint64_t *counts, uint64_t road_cap,
                                   const int16_t *F, const int16_t *q, const svt_config cfg,
-                                  const FusedRoads fr, uint32_t roads_per_chunk,
+                                  const FusedRoads fr, uint32_t roads_per_chunk, bool pair_small,
                                   uint32_t *out, unsigned long long *status,
                                   int warps_per_block, int grid, cudaStream_t st) {
-    size_t smem = fit_smem_bytes(warps_per_block);
-    if (cfg.chi2_cut < 32767u * 32767u)
-        launch_after(k_fit_persistent<true>, grid, warps_per_block * 32, smem, st, words,
-                     event_off, dims, event_road, desc, counts, road_cap, F, q, cfg, fr,
-                     roads_per_chunk, out, status);
+    const size_t smem = fit_smem_bytes(warps_per_block);
+    const bool guarded = cfg.chi2_cut < 32767u * 32767u;
+    auto launch = [&](auto kernel) {
+        launch_after(kernel, grid, warps_per_block * 32, smem, st, words, event_off, dims,
+                     event_road, desc, counts, road_cap, F, q, cfg, fr, roads_per_chunk, out,
+                     status);
+    };
+    if (guarded)
+        pair_small ? launch(k_fit_persistent<true, true>) : launch(k_fit_persistent<true, false>);
     else
-        launch_after(k_fit_persistent<false>, grid, warps_per_block * 32, smem, st, words,
-                     event_off, dims, event_road, desc, counts, road_cap, F, q, cfg, fr,
-                     roads_per_chunk, out, status);
+        pair_small ? launch(k_fit_persistent<false, true>) : launch(k_fit_persistent<false, false>);
     return cudaGetLastError();
 }
 

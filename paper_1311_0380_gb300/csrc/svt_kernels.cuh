@@ -54,7 +54,9 @@ inline void launch_after(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t
 //   b = {geo, NB, NA, 0} with the split c = a_row * NB + b_col (see road_split),
 //       NA = ceil(C_eval / NB) rows, and geo bits [2:0] split, [7:3] NBp (columns
 //       below the top suffix layer, NB = ntop * NBp), [12:8] ntop, [18:13] layer
-//       mask, [25:19] total hits, [26] OVERFLOW, [27] BAD_PATTERN.
+//       mask, [25:19] total hits, [26] OVERFLOW, [27] BAD_PATTERN, [28] SMALL:
+//       at most 8 hits on every layer, NBp <= 16 and NA <= 16, so that half a
+//       warp can fit the road (the fit kernel pairs such roads).
 struct RoadDesc {
     uint4 a, b;
 };
@@ -73,8 +75,12 @@ __device__ __forceinline__ RoadDesc make_road_desc(uint32_t rw, uint32_t packed,
         if ((uint32_t)l == split) ntop = s.n[l];
     }
     const uint32_t NA = C_eval ? (C_eval + NB - 1) / NB : 0u;
+    bool small = NBp <= 16u && NA <= 16u;
+#pragma unroll
+    for (int l = 0; l < N_LAYERS; ++l) small = small && nhit_of(packed, l) <= 8u;
     const uint32_t geo = split | (NBp << 3) | (ntop << 8) | (s.mask << 13) | (s.total_hits << 19) |
-                         ((!bad && C > cfg.max_comb) ? (1u << 26) : 0u) | (bad ? (1u << 27) : 0u);
+                         ((!bad && C > cfg.max_comb) ? (1u << 26) : 0u) | (bad ? (1u << 27) : 0u) |
+                         (small ? (1u << 28) : 0u);
     RoadDesc d;
     d.a = make_uint4(rw, packed, hw, C_eval);
     d.b = make_uint4(geo, NB, NA, 0u);
@@ -179,7 +185,7 @@ cudaError_t launch_fit_persistent(const uint32_t *words, const uint64_t *event_o
                                   const Dims *dims, const uint32_t *event_road,
                                   const RoadDesc *desc, uint64_t *counts, uint64_t road_cap,
                                   const int16_t *F, const int16_t *q, const svt_config cfg,
-                                  const FusedRoads fr, uint32_t roads_per_chunk,
+                                  const FusedRoads fr, uint32_t roads_per_chunk, bool pair_small,
                                   uint32_t *out, unsigned long long *status,
                                   int warps_per_block, int grid, cudaStream_t st);
 int fit_persistent_blocks_per_sm(int warps_per_block);

@@ -35,7 +35,7 @@ def consts_for(S):
     return CONSTS[S]
 
 
-@pytest.mark.parametrize("path", ["fused", "plain"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair"])
 def test_small_batch(path):
     spec, consts, b = batch_for("small", 100, consts_for(64))
     cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb, n_sectors=64)
@@ -73,7 +73,7 @@ def test_paper_shape_3000_events():
     assert int(b.combinations().sum()) == 2048 * 3000
     cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb)
     key, rec = oracle_run(b.words, b.event_off, consts.F, consts.q, ocfg)
-    for path in ("fused", "plain"):
+    for path in ("fused", "plain", "fused_pair"):
         st, got, _ = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, path,
                              comb_cap=2048 * 3000)
         assert_same(st, got, key, rec, "paper/" + path)
@@ -89,7 +89,9 @@ def test_uneven_batch_capped():
 
 
 @pytest.mark.parametrize("sched", [(1, 1, 1, 1, 1), (4, 3, 7, 3, 100), (16, 1, 64, 32, 64),
-                                   (8, 4, 32, 8, 1 << 30), (2, 8, 2, 2, 33), (8, 0, 16, 4, 4096)])
+                                   (8, 4, 32, 8, 1 << 30), (2, 8, 2, 2, 33), (8, 0, 16, 4, 4096),
+                                   (8, 0, 16, 4, 4096, 1), (4, 3, 7, 3, 100, 1),
+                                   (16, 1, 64, 32, 64, 1), (2, 8, 2, 2, 33, 1), (1, 1, 1, 2, 1, 1)])
 def test_schedules_give_identical_results(sched):
     from paper_1311_0380_gb300 import api
     spec, consts, b = batch_for("scaled", 60, consts_for(512))
@@ -98,6 +100,16 @@ def test_schedules_give_identical_results(sched):
     st, got, _ = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "fused",
                          sched=api.schedule(*sched))
     assert_same(st, got, key, rec, f"sched{sched}")
+
+
+def test_schedule_limits_are_checked():
+    from paper_1311_0380_gb300 import api
+    spec, consts, b = batch_for("scaled", 4, consts_for(512))
+    cfg, _ = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb)
+    for bad in (api.schedule(pair_small=2), api.schedule(warps_per_block=17),
+                api.schedule(roads_per_chunk=33), api.schedule(rows_per_item=65)):
+        with pytest.raises(RuntimeError, match="BAD_ARG"):
+            gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "fused", sched=bad)
 
 
 # ----------------------------------------------------------------------------- edge cases
@@ -120,7 +132,7 @@ def random_consts(S, seed, scale=32768):
     return F, q
 
 
-@pytest.mark.parametrize("path", ["fused", "plain"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair"])
 def test_empty_batch_and_events_without_roads(path):
     F, q = random_consts(4, 1)
     cfg, ocfg = cfg_pair(n_sectors=4)
@@ -134,7 +146,7 @@ def test_empty_batch_and_events_without_roads(path):
     assert_same(st, got, key, rec, "no roads")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair"])
 def test_missing_layers_patterns_and_no_hits(path):
     rng = np.random.default_rng(3)
     F, q = random_consts(8, 2, scale=3000)
@@ -154,7 +166,7 @@ def test_missing_layers_patterns_and_no_hits(path):
         assert_same(st, got, key, rec, f"min_layers{min_layers}")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair"])
 def test_ties_and_extreme_constants(path):
     rng = np.random.default_rng(4)
     S = 2
@@ -176,7 +188,7 @@ def test_ties_and_extreme_constants(path):
             assert_same(st, got, key, rec, f"cut{cut} os{oshift} qs{qshift}")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair"])
 def test_chi_components_at_the_clamp_boundary(path):
     """chi components straddling +-32767 / +-32768 (the clamp of Eq. 2's
     chi-square), with cuts just below, at and above 32767^2: the range test of
@@ -210,7 +222,7 @@ def test_chi_components_at_the_clamp_boundary(path):
     assert 0 < n_pass[0] < n_pass[1] < n_pass[2] < n_pass[3]   # each cut decides roads
 
 
-@pytest.mark.parametrize("path", ["fused", "plain"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair"])
 def test_maximum_hits_per_layer(path):
     # 16 hits in every layer: 16^6 combinations, capped
     rng = np.random.default_rng(6)
@@ -251,7 +263,7 @@ def test_uncapped_giant_road_fused():
     assert_same(st, got, key, rec, "giant")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair"])
 def test_validation_cases_match_oracle(path):
     from test_oracle_pins import tokens_to_words
     data = json.load(open(os.path.join(GOLDEN, "validation_cases.json")))
