@@ -428,6 +428,9 @@ def run_sweep(args):
     dconst = api.DeviceConstants.from_numpy(consts.F, consts.q, cfg, dev)
     stream = torch.cuda.current_stream()
     reps = max(3, args.sweep_reps)
+    # every road of this shape is small and alike: the fused runs pair them on
+    # half warps, the schedule the autotuner picks for it
+    sched = api.schedule(roads_per_chunk=4, pair_small=1)
 
     def ev_pair():
         return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -440,7 +443,7 @@ def run_sweep(args):
         fits = int(np.sum(full.combinations(spec.max_comb)[:R]))
         d_words, d_off = api.to_device_u32(words, dev), api.to_device_u64(off, dev)
         # fused, resident
-        fp = api.FusedPath(n_words, n_ev, R, dconst, None, dev)
+        fp = api.FusedPath(n_words, n_ev, R, dconst, sched, dev)
         for _ in range(3):
             fp.run(d_words, n_words, d_off, n_ev)
         evs = [ev_pair() for _ in range(reps)]
@@ -545,6 +548,7 @@ def run_sweep(args):
               file=sys.stderr, flush=True)
         del fp, pp, runner
     print(json.dumps({"sweep": "paper-shape (2048 fits per event)", "cpu_threads": oracle.num_threads(),
+                      "fused_schedule": {f: getattr(sched, f) for f, _ in api.SvtSchedule._fields_},
                       "rows": rows}))
 
 
