@@ -69,6 +69,8 @@ def parse_args():
     ap.add_argument("--rows", type=int, default=0)
     ap.add_argument("--warps", type=int, default=0)
     ap.add_argument("--bps", type=int, default=0)
+    ap.add_argument("--pair", action="store_true",
+                    help="pair small roads on half warps (schedule field pair_small)")
     return ap.parse_args()
 
 
@@ -634,7 +636,7 @@ def main():
                      int(spec.xft))
     dconst = api.DeviceConstants.from_numpy(consts.F, consts.q, cfg, dev)
     n_words, n_events, R = len(batch.words), batch.n_events, batch.total_roads
-    sched = api.schedule(args.warps, args.bps, args.rows)
+    sched = api.schedule(args.warps, args.bps, args.rows, pair_small=int(args.pair))
     fused = api.FusedPath(n_words, n_events, R, dconst, sched, dev)
     d_words = api.to_device_u32(batch.words, dev)
     d_off = api.to_device_u64(batch.event_off, dev)
@@ -642,7 +644,7 @@ def main():
     flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)   # 256 MB > 129 MB L2
     stream = torch.cuda.current_stream()
     tuned = None
-    if not args.no_tune and not (args.warps or args.rows or args.bps):
+    if not args.no_tune and not (args.warps or args.rows or args.bps or args.pair):
         from paper_1311_0380_gb300 import autotune
         sch, tms = autotune.tuned_schedule(fused, d_words, n_words, d_off, n_events, cache=None)
         fused.sched = sch

@@ -502,9 +502,12 @@ __global__ void __launch_bounds__(TILE_THREADS)
         if (fr.desc) {
             // this thread's split roads go to slots [base + big_ex, ...) with
             // items from [base_items + it_ex, ...), in the order it visited them
-            uint32_t it_total, big_total;
-            uint32_t it_ex = block_exclusive_scan<uint32_t>(items_sum, red, &it_total);
-            uint32_t big_ex = block_exclusive_scan<uint32_t>(big_sum, red, &big_total);
+            // (most tiles hold no split road and skip both scans)
+            uint32_t it_total = 0, big_total = 0, it_ex = 0, big_ex = 0;
+            if (__syncthreads_or(big_sum != 0)) {
+                it_ex = block_exclusive_scan<uint32_t>(items_sum, red, &it_total);
+                big_ex = block_exclusive_scan<uint32_t>(big_sum, red, &big_total);
+            }
             unsigned long long c_total;
             block_exclusive_scan<unsigned long long>(comb_sum, red64, &c_total);
             if (threadIdx.x == 0) {
