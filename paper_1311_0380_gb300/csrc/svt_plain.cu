@@ -143,63 +143,197 @@ __global__ void k_combine_write(const uint32_t *__restrict__ road_nhit,
     }
 }
 
-__global__ void k_fit_plain(const uint32_t *__restrict__ words,
-                            const uint32_t *__restrict__ road_word,
-                            const uint32_t *__restrict__ road_nhit,
-                            const uint32_t *__restrict__ comb_road,
-                            const uint32_t *__restrict__ comb_hits,
-                            const uint64_t *__restrict__ n_combs, uint64_t comb_cap,
-                            const int16_t *__restrict__ F, const int16_t *__restrict__ q,
-                            const svt_config cfg, uint32_t *fit_chi2, int32_t *fit_par,
-                            const unsigned long long *status) {
+// acc_k = q_k 2^qshift + sum_l F_kl x_l exactly, with 32-bit products:
+// |F_kl x_l| <= 32768 * 32767 < 2^30, so every sum of two products is exact
+// in int32; the three pair sums and q_k 2^qshift (|.| < 2^39) are added in
+// int64.  With oshift >= 9, |y_k| < 2^31 and y_k = floor(acc_k / 2^oshift) is
+// exact in int32.  Results: chi2 over the three clamped chi rows, p_0..p_2.
+__device__ __forceinline__ uint32_t fit_rows(const int32_t (&Fk)[36], const long long (&qk)[6],
+                                             const int32_t (&x)[N_LAYERS], uint32_t oshift,
+                                             int32_t (&p)[3]) {
+    int32_t y[N_LAYERS];
+#pragma unroll
+    for (int k = 0; k < N_LAYERS; ++k) {
+        int32_t s2[3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+            s2[m] = Fk[k * 6 + 2 * m] * x[2 * m] + Fk[k * 6 + 2 * m + 1] * x[2 * m + 1];
+        const long long acc = qk[k] + (long long)s2[0] + (long long)s2[1] + (long long)s2[2];
+        y[k] = (int32_t)(acc >> oshift);   // arithmetic shift: floor
+    }
+    uint32_t chi2 = 0;
+#pragma unroll
+    for (int k = 3; k < N_LAYERS; ++k) {
+        const int32_t c = max(min(y[k], 32767), -32767);
+        chi2 += (uint32_t)(c * c);
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) p[k] = y[k];
+    return chi2;
+}
+
+// One combination with every input read from global memory (road data, hit
+// words, the sector/pattern row of the constants).
+__device__ __forceinline__ uint32_t fit_direct(const uint32_t *__restrict__ words,
+                                               const uint32_t *__restrict__ road_word,
+                                               const uint32_t *__restrict__ road_nhit,
+                                               const int16_t *__restrict__ F,
+                                               const int16_t *__restrict__ q,
+                                               const svt_config &cfg, uint32_t r, uint32_t hits,
+                                               int32_t (&p)[3]) {
+    const uint32_t rw = __ldg(road_word + r);
+    const uint32_t packed = __ldg(road_nhit + r);
+    const uint32_t hw = __ldg(words + rw);
+    uint32_t mask = 0, hoff = rw + 1;
+    int32_t x[N_LAYERS];
+#pragma unroll
+    for (int l = 0; l < N_LAYERS; ++l) {
+        const uint32_t nl = nhit_of(packed, l);
+        x[l] = nl ? (int32_t)hit_coord(__ldg(words + hoff + ((hits >> (4 * l)) & 15u))) : 0;
+        mask |= nl ? (1u << l) : 0u;
+        hoff += nl;
+    }
+    const size_t cs = (size_t)rd_sector(hw) * 64 + mask;
+    int32_t Fk[36];
+    long long qk[6];
+#pragma unroll
+    for (int i = 0; i < 36; ++i) Fk[i] = __ldg(F + cs * 36 + i);
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+        qk[k] = (long long)((unsigned long long)(long long)__ldg(q + cs * 6 + k) << cfg.qshift);
+    return fit_rows(Fk, qk, x, cfg.oshift, p);
+}
+
+// A road's row staged in shared memory by the plain fit: its constants as
+// int32, q_k 2^qshift as int64 and, per layer, the index of its first hit in
+// the road's coordinate list (0xFF for a layer without hits); the road's hit
+// coordinates sit beside it (at most 96: 6 layers x 16).
+constexpr int FIT_THREADS = 256;
+constexpr int FIT_PER_THREAD = 8;
+constexpr int FIT_TILE = FIT_THREADS * FIT_PER_THREAD;   // combinations per block tile
+constexpr int FIT_STAGE_ROADS = 64;   // tiles over more roads read their inputs directly
+struct alignas(16) StagedRow {
+    int32_t F[36];
+    long long q[6];
+    uint8_t first[8];
+    uint32_t pad[2];
+};
+
+__device__ __forceinline__ uint32_t fit_staged(const StagedRow &row,
+                                               const uint16_t *__restrict__ coord,
+                                               uint32_t oshift, uint32_t hits, int32_t (&p)[3]) {
+    const uint2 fw = *reinterpret_cast<const uint2 *>(row.first);
+    int32_t x[N_LAYERS];
+#pragma unroll
+    for (int l = 0; l < N_LAYERS; ++l) {
+        const uint32_t f0 = ((l < 4 ? fw.x : fw.y) >> (8 * (l & 3))) & 0xFFu;
+        x[l] = f0 != 0xFFu ? (int32_t)coord[f0 + ((hits >> (4 * l)) & 15u)] : 0;
+    }
+    int32_t Fk[36];
+    long long qk[6];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int4 v = reinterpret_cast<const int4 *>(row.F)[i];
+        Fk[4 * i] = v.x;
+        Fk[4 * i + 1] = v.y;
+        Fk[4 * i + 2] = v.z;
+        Fk[4 * i + 3] = v.w;
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const longlong2 v = reinterpret_cast<const longlong2 *>(row.q)[i];
+        qk[2 * i] = v.x;
+        qk[2 * i + 1] = v.y;
+    }
+    return fit_rows(Fk, qk, x, oshift, p);
+}
+
+// One thread per combination, over block tiles of FIT_TILE consecutive
+// combinations (thread t takes combinations t, t + 256, t + 512, ... of the
+// tile and loads their entries first; 48 registers leave five blocks per SM).  Combinations are road-major, so a
+// tile covers the roads comb_road[first] .. comb_road[last]; when there are
+// at most FIT_STAGE_ROADS of them, their rows and hit coordinates are staged
+// in shared memory once (coalesced loads) and the combinations of the tile
+// need no other global load; otherwise each reads its inputs directly.
+__global__ void __launch_bounds__(FIT_THREADS, 5)
+    k_fit_plain(const uint32_t *__restrict__ words, const uint32_t *__restrict__ road_word,
+                const uint32_t *__restrict__ road_nhit, const uint32_t *__restrict__ comb_road,
+                const uint32_t *__restrict__ comb_hits, const uint64_t *__restrict__ n_combs,
+                uint64_t comb_cap, const int16_t *__restrict__ F, const int16_t *__restrict__ q,
+                const svt_config cfg, uint32_t *fit_chi2, int32_t *fit_par,
+                const unsigned long long *status) {
+    __shared__ StagedRow rows[FIT_STAGE_ROADS];
+    __shared__ uint16_t coords[FIT_STAGE_ROADS][N_LAYERS * MAX_HITS];
+    __shared__ uint32_t tile_r0, tile_nr;
     if (!status_ok(status)) return;
     const uint64_t n = *n_combs < comb_cap ? *n_combs : comb_cap;
-    for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n;
-         j += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t r = __ldg(comb_road + j);
-        const uint32_t hits = __ldg(comb_hits + j);
-        const uint32_t rw = __ldg(road_word + r);
-        const uint32_t packed = __ldg(road_nhit + r);
-        const uint32_t hw = __ldg(words + rw);
-        uint32_t mask = 0, hoff = rw + 1;
-        uint32_t x[N_LAYERS];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (uint64_t j0 = (uint64_t)blockIdx.x * FIT_TILE; j0 < n; j0 += (uint64_t)gridDim.x * FIT_TILE) {
+        const uint64_t j1 = min(j0 + (uint64_t)FIT_TILE, n);
+        uint32_t rr[FIT_PER_THREAD], hh[FIT_PER_THREAD];
 #pragma unroll
-        for (int l = 0; l < N_LAYERS; ++l) {
-            const uint32_t nl = nhit_of(packed, l);
-            x[l] = nl ? hit_coord(__ldg(words + hoff + ((hits >> (4 * l)) & 15u))) : 0u;
-            mask |= nl ? (1u << l) : 0u;
-            hoff += nl;
+        for (int i = 0; i < FIT_PER_THREAD; ++i) {
+            const uint64_t j = j0 + (uint64_t)(i * FIT_THREADS) + threadIdx.x;
+            rr[i] = j < j1 ? __ldg(comb_road + j) : 0u;
+            hh[i] = j < j1 ? __ldg(comb_hits + j) : 0u;
         }
-        const size_t cs = (size_t)rd_sector(hw) * 64 + mask;
-        const int16_t *Fs = F + cs * 36;
-        const int16_t *qs = q + cs * 6;
-        // acc_k exactly, with 32-bit products: |F_kl x_l| <= 32768 * 32767 < 2^30,
-        // so every sum of two products is exact in int32; the three pair sums
-        // and q_k 2^qshift (|.| < 2^39) are added in int64.  With oshift >= 9,
-        // |y_k| < 2^31 and y_k is exact in int32.
-        int32_t y[N_LAYERS];
-#pragma unroll
-        for (int k = 0; k < N_LAYERS; ++k) {
-            int32_t s2[3];
-#pragma unroll
-            for (int m = 0; m < 3; ++m)
-                s2[m] = (int32_t)__ldg(Fs + k * 6 + 2 * m) * (int32_t)x[2 * m] +
-                        (int32_t)__ldg(Fs + k * 6 + 2 * m + 1) * (int32_t)x[2 * m + 1];
-            const long long acc =
-                (long long)((unsigned long long)(long long)__ldg(qs + k) << cfg.qshift) +
-                (long long)s2[0] + (long long)s2[1] + (long long)s2[2];
-            y[k] = (int32_t)(acc >> cfg.oshift);   // arithmetic shift: floor
+        if (threadIdx.x == 0) {
+            const uint32_t r0 = __ldg(comb_road + j0), r1 = __ldg(comb_road + j1 - 1);
+            tile_r0 = r0;
+            tile_nr = r1 - r0 + 1;   // roads are non-decreasing in j
         }
-        uint32_t chi2 = 0;
+        __syncthreads();
+        const uint32_t r0 = tile_r0, nr = tile_nr;
+        const bool staged = nr <= (uint32_t)FIT_STAGE_ROADS;
+        if (staged) {
+            // warp w stages roads w, w + 8, ...: lane i of the F row (lanes
+            // 0..3 twice), lanes 4..9 the q row, lanes 10..15 the layers, and
+            // every lane some of the hit coordinates
+            for (uint32_t rho = warp; rho < nr; rho += FIT_THREADS / 32) {
+                const uint32_t r = r0 + rho;
+                const uint32_t rw = __ldg(road_word + r), packed = __ldg(road_nhit + r);
+                uint32_t mask = 0, total = 0;
 #pragma unroll
-        for (int k = 3; k < N_LAYERS; ++k) {
-            const int32_t c = max(min(y[k], 32767), -32767);
-            chi2 += (uint32_t)(c * c);
+                for (int l = 0; l < N_LAYERS; ++l) {
+                    mask |= nhit_of(packed, l) ? (1u << l) : 0u;
+                    total += nhit_of(packed, l);
+                }
+                total = min(total, (uint32_t)(N_LAYERS * MAX_HITS));
+                const size_t cs = (size_t)rd_sector(__ldg(words + rw)) * 64 + mask;
+                StagedRow &row = rows[rho];
+                row.F[lane] = __ldg(F + cs * 36 + lane);
+                if (lane < 4) {
+                    row.F[32 + lane] = __ldg(F + cs * 36 + 32 + lane);
+                } else if (lane < 10) {
+                    const int k = lane - 4;
+                    row.q[k] = (long long)((unsigned long long)(long long)__ldg(q + cs * 6 + k)
+                                           << cfg.qshift);
+                } else if (lane < 16) {
+                    const int l = lane - 10;
+                    uint32_t before = 0;   // hits on the layers below l
+#pragma unroll
+                    for (int m = 0; m < N_LAYERS - 1; ++m) before += m < l ? nhit_of(packed, m) : 0u;
+                    row.first[l] = nhit_of(packed, l) ? (uint8_t)before : (uint8_t)0xFF;
+                }
+                for (uint32_t h = lane; h < total; h += 32)
+                    coords[rho][h] = (uint16_t)hit_coord(__ldg(words + rw + 1 + h));
+            }
+            __syncthreads();
         }
-        fit_chi2[j] = chi2;
-        fit_par[j] = y[0];
-        fit_par[comb_cap + j] = y[1];
-        fit_par[2 * comb_cap + j] = y[2];
+#pragma unroll
+        for (int i = 0; i < FIT_PER_THREAD; ++i) {
+            const uint64_t j = j0 + (uint64_t)(i * FIT_THREADS) + threadIdx.x;
+            if (j < j1) {
+                int32_t p[3];
+                const uint32_t chi2 =
+                    staged ? fit_staged(rows[rr[i] - r0], coords[rr[i] - r0], cfg.oshift, hh[i], p)
+                           : fit_direct(words, road_word, road_nhit, F, q, cfg, rr[i], hh[i], p);
+                fit_chi2[j] = chi2;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) fit_par[k * comb_cap + j] = p[k];
+            }
+        }
+        __syncthreads();   // rows are reused by the next tile
     }
 }
 
@@ -315,7 +449,8 @@ void launch_fit_plain(const uint32_t *words, const uint32_t *road_word, const ui
                       const int16_t *q, const svt_config cfg, uint32_t *fit_chi2,
                       int32_t *fit_par, const unsigned long long *status, int grid,
                       cudaStream_t st) {
-    k_fit_plain<<<grid_for(comb_cap, 256, grid), 256, 0, st>>>(
+    k_fit_plain<<<grid_for((comb_cap + FIT_TILE - 1) / FIT_TILE * FIT_THREADS, FIT_THREADS, grid),
+                  FIT_THREADS, 0, st>>>(
         words, road_word, road_nhit, comb_road, comb_hits, n_combs, comb_cap, F, q, cfg, fit_chi2,
         fit_par, status);
 }
