@@ -132,6 +132,36 @@ def random_consts(S, seed, scale=32768):
     return F, q
 
 
+def test_plain_fit_tiles_over_many_and_few_roads():
+    """The plain fit stages the rows of a tile of 2048 combinations when the
+    tile spans at most 64 roads and reads them directly otherwise: runs of
+    one-combination roads (direct), of 2048-combination roads (one road per
+    tile), of 48-combination roads (about 43 per tile) and a mix, with
+    missing layers and random constants, against the oracle."""
+    rng = np.random.default_rng(11)
+    S = 8
+    F, q = random_consts(S, 12)
+    roads, rid = [], 0
+
+    def road(n_per_layer):
+        nonlocal rid
+        hits = [(l, int(rng.integers(0, 32768))) for l in range(6) for _ in range(n_per_layer[l])]
+        rid += 1
+        return (int(rng.integers(0, S)), rid % 4096, hits)
+
+    roads += [road([1, 1, 1, 1, 1, 1]) for _ in range(3000)]            # C = 1
+    roads += [road([2, 4, 4, 4, 4, 2]) for _ in range(4)]                # C = 2048
+    roads += [road([2, 3, 2, 2, 2, 1]) for _ in range(300)]              # C = 48
+    roads += [road([int(v) for v in rng.integers(0, 5, 6)]) for _ in range(700)]
+    events = [(e, roads[e * 50:(e + 1) * 50]) for e in range((len(roads) + 49) // 50)]
+    w, off = words_of(events)
+    cfg, ocfg = cfg_pair(15, 15, 3 * 12000 ** 2, 4096, 3, S)
+    key, rec = oracle_run(w, off, F, q, ocfg)
+    assert key == oracle.KEY_OK
+    st, got, _ = gpu_run(w, off, F, q, cfg, "plain", comb_cap=len(roads) * 4096)
+    assert_same(st, got, key, rec, "plain tiles")
+
+
 @pytest.mark.parametrize("path", ["fused", "plain", "fused_pair"])
 def test_empty_batch_and_events_without_roads(path):
     F, q = random_consts(4, 1)
