@@ -110,35 +110,168 @@ __global__ void __launch_bounds__(SCAN_THREADS)
     }
 }
 
-__global__ void k_combine_write(const uint32_t *__restrict__ road_nhit,
-                                const uint64_t *__restrict__ n_roads, uint64_t road_cap,
-                                const uint64_t *__restrict__ comb_off, uint64_t comb_cap,
-                                uint32_t xft_pairs, uint32_t *comb_road, uint32_t *comb_hits,
-                                unsigned long long *status) {
+// Roads with more combinations than this are written (combine) and scanned
+// (select) by a whole block in a second launch, so that one long road does
+// not hold up a warp while the others have finished.
+constexpr uint64_t PLAIN_BIG = 4096;
+
+// Per-road metadata for the plain combine and select, read for a group of
+// roads at once (one coalesced load per field) instead of road by road.
+struct RoadMeta {
+    uint64_t off, n;
+    uint32_t word;   // road_nhit (combine) or road_flags (select)
+};
+
+// Metadata of road r (zeros past the last road).
+__device__ __forceinline__ RoadMeta road_meta(const uint64_t *__restrict__ comb_off,
+                                              const uint32_t *__restrict__ word, uint64_t R,
+                                              uint64_t r) {
+    RoadMeta m{0, 0, 0};
+    if (r < R) {
+        m.off = __ldg(comb_off + r);
+        m.n = __ldg(comb_off + r + 1) - m.off;
+        m.word = __ldg(word + r);
+    }
+    return m;
+}
+
+// Big roads of a block's group of blockDim.x roads, compacted into `list`
+// (their metadata and index); returns how many (a block-wide call).
+__device__ __forceinline__ uint32_t big_roads_of_group(const RoadMeta &mine, uint64_t r,
+                                                       bool big, RoadMeta *list,
+                                                       uint32_t *list_r, uint32_t *count) {
+    if (threadIdx.x == 0) *count = 0;
+    __syncthreads();
+    if (big) {
+        const uint32_t k = atomicAdd(count, 1u);
+        list[k] = mine;
+        list_r[k] = (uint32_t)r;
+    }
+    __syncthreads();
+    return *count;
+}
+
+// Rows [a_begin, a_end) of one road's combinations in index order
+// c = a * NB + b, with the layers split as in the fused path (road_split: a
+// suffix of at least 32 combinations gives the column b, the prefix the row
+// a).  A lane derives the suffix digits of its column once per pass over the
+// columns; the prefix digits (the same for all lanes) are derived for the
+// first row and then counted up row by row (layer split-1 fastest, a carry
+// only when a digit wraps), so a combination costs a few instructions and
+// two coalesced stores.
+__device__ __forceinline__ void write_rows(uint32_t r, const RoadMeta &m, const RoadShape &s,
+                                           uint32_t split, uint32_t NB, uint32_t a_begin,
+                                           uint32_t a_end, uint32_t xft_pairs, int lane,
+                                           uint32_t *comb_road, uint32_t *comb_hits) {
+    uint32_t mg[N_LAYERS], top = 0;   // top: n'_l - 1 of every layer, 4 bits each
+#pragma unroll
+    for (int l = 0; l < N_LAYERS; ++l) {
+        mg[l] = kDivMagic[s.n[l]];
+        top |= (s.n[l] - 1u) << (4 * l);
+    }
+    uint32_t ra = a_begin, pa0 = 0;   // prefix digits of the first row
+#pragma unroll
+    for (int l = N_LAYERS - 1; l >= 0; --l) {
+        if ((uint32_t)l < split) {
+            const uint32_t qd = div_by(ra, s.n[l], mg[l]);
+            pa0 |= (ra - qd * s.n[l]) << (4 * l);
+            ra = qd;
+        }
+    }
+    for (uint32_t b0 = 0; b0 < NB; b0 += 32) {
+        const uint32_t b = b0 + (uint32_t)lane;
+        uint32_t rem = b, pb = 0;   // digits of the suffix layers split..5
+#pragma unroll
+        for (int l = N_LAYERS - 1; l >= 0; --l) {
+            if ((uint32_t)l >= split) {
+                const uint32_t qd = div_by(rem, s.n[l], mg[l]);
+                pb |= (rem - qd * s.n[l]) << (4 * l);
+                rem = qd;
+            }
+        }
+        uint32_t pa = pa0;
+        uint64_t c = (uint64_t)a_begin * NB + b;
+        for (uint32_t a = a_begin; a < a_end; ++a, c += NB) {
+            if (b < NB && c < m.n) {
+                uint32_t packed = pa | pb;
+                if (xft_pairs) packed |= ((packed >> 16) & 15u) << 20;   // layer 5 takes layer 4's hit
+                comb_road[m.off + c] = r;
+                comb_hits[m.off + c] = packed;
+            }
+            for (int l = (int)split - 1; l >= 0; --l) {   // next row
+                const uint32_t sh = 4u * (uint32_t)l;
+                if (((pa >> sh) & 15u) != ((top >> sh) & 15u)) {
+                    pa += 1u << sh;
+                    break;
+                }
+                pa &= ~(15u << sh);
+            }
+        }
+    }
+}
+
+// A road per warp (roads of at most PLAIN_BIG combinations, each combination's
+// digits by division; the next road's entries are read while this one is
+// written), or a big road per block whose eight warps take one block of rows
+// each (write_rows).
+template <bool BIG>
+__global__ void __launch_bounds__(256)
+    k_combine_write(const uint32_t *__restrict__ road_nhit, const uint64_t *__restrict__ n_roads,
+                    uint64_t road_cap, const uint64_t *__restrict__ comb_off, uint64_t comb_cap,
+                    uint32_t xft_pairs, uint32_t *comb_road, uint32_t *comb_hits,
+                    unsigned long long *status) {
+    __shared__ RoadMeta list[256];
+    __shared__ uint32_t list_r[256], list_n;
     if (!status_ok(status)) return;
     const uint64_t R = road_count(n_roads, road_cap);
     const int lane = threadIdx.x & 31;
     const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    if (warp0 == 0 && lane == 0 && comb_off[R] > comb_cap) report(status, 0, SVT_ERR_OOM);
-    for (uint64_t r = warp0; r < R; r += n_warps) {
-        const uint64_t off = comb_off[r], n = comb_off[r + 1] - off;
-        if (off + n > comb_cap) continue;
-        const RoadShape s = road_shape(road_nhit[r], xft_pairs);
-        uint32_t m[N_LAYERS];
+    if (!BIG && warp0 == 0 && lane == 0 && comb_off[R] > comb_cap) report(status, 0, SVT_ERR_OOM);
+    if (!BIG) {
+        RoadMeta m = road_meta(comb_off, road_nhit, R, warp0);
+        for (uint64_t r = warp0; r < R; r += n_warps) {
+            const RoadMeta next = road_meta(comb_off, road_nhit, R, r + n_warps);
+            if (m.n && m.n <= PLAIN_BIG && m.off + m.n <= comb_cap) {
+                const RoadShape s = road_shape(m.word, xft_pairs);
+                uint32_t mg[N_LAYERS];
 #pragma unroll
-        for (int l = 0; l < N_LAYERS; ++l) m[l] = kDivMagic[s.n[l]];
-        for (uint64_t c = lane; c < n; c += 32) {
-            uint32_t rem = (uint32_t)c, packed = 0;   // c < max_comb < 2^32
+                for (int l = 0; l < N_LAYERS; ++l) mg[l] = kDivMagic[s.n[l]];
+                for (uint64_t c = lane; c < m.n; c += 32) {
+                    uint32_t rem = (uint32_t)c, packed = 0;
 #pragma unroll
-            for (int l = N_LAYERS - 1; l >= 0; --l) {
-                const uint32_t qd = div_by(rem, s.n[l], m[l]);
-                packed |= (rem - qd * s.n[l]) << (4 * l);
-                rem = qd;
+                    for (int l = N_LAYERS - 1; l >= 0; --l) {
+                        const uint32_t qd = div_by(rem, s.n[l], mg[l]);
+                        packed |= (rem - qd * s.n[l]) << (4 * l);
+                        rem = qd;
+                    }
+                    if (xft_pairs) packed |= ((packed >> 16) & 15u) << 20;
+                    comb_road[m.off + c] = (uint32_t)r;
+                    comb_hits[m.off + c] = packed;
+                }
             }
-            if (xft_pairs) packed |= ((packed >> 16) & 15u) << 20;   // layer 5 takes layer 4's hit
-            comb_road[off + c] = (uint32_t)r;
-            comb_hits[off + c] = packed;
+            m = next;
+        }
+    } else {
+        const uint32_t warp = threadIdx.x >> 5, n_w = blockDim.x >> 5;
+        for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x; g < R;
+             g += (uint64_t)gridDim.x * blockDim.x) {
+            const uint64_t r = g + threadIdx.x;
+            const RoadMeta mine = road_meta(comb_off, road_nhit, R, r);
+            const bool big = mine.n > PLAIN_BIG && mine.off + mine.n <= comb_cap;
+            const uint32_t nb = big_roads_of_group(mine, r, big, list, list_r, &list_n);
+            for (uint32_t k = 0; k < nb; ++k) {
+                const RoadMeta m = list[k];
+                const RoadShape s = road_shape(m.word, xft_pairs);
+                uint32_t split, NB;
+                road_split(s, split, NB);
+                const uint32_t NA = (uint32_t)((m.n + NB - 1) / NB);
+                const uint32_t per = (NA + n_w - 1) / n_w;
+                const uint32_t a0 = min(warp * per, NA), a1 = min(a0 + per, NA);
+                write_rows(list_r[k], m, s, split, NB, a0, a1, xft_pairs, lane, comb_road,
+                           comb_hits);
+            }
+            __syncthreads();   // the list is rebuilt for the next group
         }
     }
 }
@@ -337,54 +470,115 @@ __global__ void __launch_bounds__(FIT_THREADS, 5)
     }
 }
 
-__global__ void k_select(const uint32_t *__restrict__ fit_chi2,
-                         const int32_t *__restrict__ fit_par, uint64_t comb_cap,
-                         const uint64_t *__restrict__ comb_off,
-                         const uint32_t *__restrict__ road_flags,
-                         const uint64_t *__restrict__ n_roads, uint64_t road_cap,
-                         const svt_config cfg, svt_best *best,
-                         const unsigned long long *status) {
+// Best passing combination of road r from its chi2 values, over the threads
+// [idx, idx + step, ...) of the warp (step 32) or block (step 256): each
+// visits its combinations in increasing c (a block keeps four loads in
+// flight), so a strict '<' keeps the smallest index among equal chi2; the
+// (chi2, c) keys are then merged (over the block through red, when BIG).
+// Written by thread idx 0.
+template <bool BIG>
+__device__ __forceinline__ void select_road(uint32_t r, const RoadMeta &m,
+                                            const uint32_t *__restrict__ fit_chi2,
+                                            const int32_t *__restrict__ fit_par,
+                                            uint64_t comb_cap, uint32_t init_chi, uint32_t idx,
+                                            uint32_t step, int lane, unsigned long long *red,
+                                            svt_best *best) {
+    uint32_t bchi = init_chi, bc = 0;
+    if (!BIG && m.off + m.n <= comb_cap) {
+        for (uint64_t c = idx; c < m.n; c += step) {
+            const uint32_t v = __ldg(fit_chi2 + m.off + c);
+            if (v < bchi) {
+                bchi = v;
+                bc = (uint32_t)c;
+            }
+        }
+    } else if (m.off + m.n <= comb_cap) {
+        for (uint64_t c0 = idx; c0 < m.n; c0 += 4ull * step) {
+            uint32_t v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint64_t c = c0 + (uint64_t)u * step;
+                v[u] = c < m.n ? __ldg(fit_chi2 + m.off + c) : 0xFFFFFFFFu;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (v[u] < bchi) {
+                    bchi = v[u];
+                    bc = (uint32_t)(c0 + (uint64_t)u * step);
+                }
+        }
+    }
+    unsigned long long key = bchi != init_chi ? (((unsigned long long)bchi << 32) | bc) : ~0ull;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        unsigned long long o = __shfl_xor_sync(0xffffffffu, key, d);
+        key = o < key ? o : key;
+    }
+    if (BIG) {
+        if (lane == 0) red[threadIdx.x >> 5] = key;
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int w = 1; w < (int)(blockDim.x >> 5); ++w) key = red[w] < key ? red[w] : key;
+        __syncthreads();   // red is reused by the next road
+    }
+    if (idx == 0) {
+        svt_best b;
+        b.flags = m.word;
+        if (key != ~0ull) {
+            const uint32_t c = (uint32_t)key;
+            b.flags |= SVT_FLAG_PASS;
+            b.comb = c;
+            b.chi2 = (uint32_t)(key >> 32);
+            b.p[0] = fit_par[m.off + c];
+            b.p[1] = fit_par[comb_cap + m.off + c];
+            b.p[2] = fit_par[2 * comb_cap + m.off + c];
+        } else {
+            b.comb = 0xFFFFFFFFu;
+            b.chi2 = 0;
+            b.p[0] = b.p[1] = b.p[2] = 0;
+        }
+        best[r] = b;
+    }
+}
+
+// Chi-square cut and best combination of each road: a road per warp (roads of
+// at most PLAIN_BIG combinations), or a big road per block.
+template <bool BIG>
+__global__ void __launch_bounds__(256)
+    k_select(const uint32_t *__restrict__ fit_chi2, const int32_t *__restrict__ fit_par,
+             uint64_t comb_cap, const uint64_t *__restrict__ comb_off,
+             const uint32_t *__restrict__ road_flags, const uint64_t *__restrict__ n_roads,
+             uint64_t road_cap, const svt_config cfg, svt_best *best,
+             const unsigned long long *status) {
+    __shared__ unsigned long long red[8];
+    __shared__ RoadMeta list[256];
+    __shared__ uint32_t list_r[256], list_n;
     if (!status_ok(status)) return;
     const uint64_t R = road_count(n_roads, road_cap);
     const int lane = threadIdx.x & 31;
     const uint64_t warp0 = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint32_t init_chi = cfg.chi2_cut == 0xFFFFFFFFu ? 0xFFFFFFFFu : cfg.chi2_cut + 1u;
-    for (uint64_t r = warp0; r < R; r += n_warps) {
-        const uint64_t off = comb_off[r], n = comb_off[r + 1] - off;
-        uint32_t bchi = init_chi, bc = 0;
-        if (off + n <= comb_cap) {
-            for (uint64_t c = lane; c < n; c += 32) {
-                const uint32_t chi2 = __ldg(fit_chi2 + off + c);
-                if (chi2 < bchi) {   // c increases per lane: keeps the smallest index
-                    bchi = chi2;
-                    bc = (uint32_t)c;
-                }
-            }
+    if (!BIG) {
+        RoadMeta m = road_meta(comb_off, road_flags, R, warp0);
+        for (uint64_t r = warp0; r < R; r += n_warps) {
+            const RoadMeta next = road_meta(comb_off, road_flags, R, r + n_warps);
+            if (m.n <= PLAIN_BIG)
+                select_road<false>((uint32_t)r, m, fit_chi2, fit_par, comb_cap, init_chi,
+                                   (uint32_t)lane, 32u, lane, red, best);
+            m = next;
         }
-        unsigned long long key = bchi != init_chi ? (((unsigned long long)bchi << 32) | bc) : ~0ull;
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) {
-            unsigned long long o = __shfl_xor_sync(0xffffffffu, key, d);
-            key = o < key ? o : key;
-        }
-        if (lane == 0) {
-            svt_best b;
-            b.flags = road_flags[r];
-            if (key != ~0ull) {
-                const uint32_t c = (uint32_t)key;
-                b.flags |= SVT_FLAG_PASS;
-                b.comb = c;
-                b.chi2 = (uint32_t)(key >> 32);
-                b.p[0] = fit_par[off + c];
-                b.p[1] = fit_par[comb_cap + off + c];
-                b.p[2] = fit_par[2 * comb_cap + off + c];
-            } else {
-                b.comb = 0xFFFFFFFFu;
-                b.chi2 = 0;
-                b.p[0] = b.p[1] = b.p[2] = 0;
-            }
-            best[r] = b;
+    } else {
+        for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x; g < R;
+             g += (uint64_t)gridDim.x * blockDim.x) {
+            const uint64_t r = g + threadIdx.x;
+            const RoadMeta mine = road_meta(comb_off, road_flags, R, r);
+            const uint32_t nb = big_roads_of_group(mine, r, mine.n > PLAIN_BIG, list, list_r,
+                                                   &list_n);
+            for (uint32_t k = 0; k < nb; ++k)
+                select_road<true>(list_r[k], list[k], fit_chi2, fit_par, comb_cap, init_chi,
+                                  threadIdx.x, blockDim.x, lane, red, best);
+            __syncthreads();   // the list is rebuilt for the next group
         }
     }
 }
@@ -439,7 +633,9 @@ void launch_combine_write(const uint32_t *road_nhit, const uint64_t *n_roads, ui
                           const uint64_t *comb_off, uint64_t comb_cap, uint32_t xft_pairs,
                           uint32_t *comb_road, uint32_t *comb_hits, unsigned long long *status,
                           int grid, cudaStream_t st) {
-    k_combine_write<<<grid_for(road_cap * 32, 256, grid), 256, 0, st>>>(
+    k_combine_write<false><<<grid_for(road_cap * 32, 256, grid), 256, 0, st>>>(
+        road_nhit, n_roads, road_cap, comb_off, comb_cap, xft_pairs, comb_road, comb_hits, status);
+    k_combine_write<true><<<grid_for(road_cap, 1, grid / 4), 256, 0, st>>>(
         road_nhit, n_roads, road_cap, comb_off, comb_cap, xft_pairs, comb_road, comb_hits, status);
 }
 
@@ -459,7 +655,9 @@ void launch_select(const uint32_t *fit_chi2, const int32_t *fit_par, uint64_t co
                    const uint64_t *comb_off, const uint32_t *road_flags, const uint64_t *n_roads,
                    uint64_t road_cap, const svt_config cfg, svt_best *best,
                    const unsigned long long *status, int grid, cudaStream_t st) {
-    k_select<<<grid_for(road_cap * 32, 256, grid), 256, 0, st>>>(
+    k_select<false><<<grid_for(road_cap * 32, 256, grid), 256, 0, st>>>(
+        fit_chi2, fit_par, comb_cap, comb_off, road_flags, n_roads, road_cap, cfg, best, status);
+    k_select<true><<<grid_for(road_cap, 1, grid / 4), 256, 0, st>>>(
         fit_chi2, fit_par, comb_cap, comb_off, road_flags, n_roads, road_cap, cfg, best, status);
 }
 
