@@ -351,7 +351,13 @@ def serving(dev):
                 "p999_us": float(np.percentile(us, 99.9)), "events_per_s": n / wall,
                 "fits_per_s": fits / wall, "wall_s": wall}
 
-    srv = serve.Server(dc, n_slots=4, max_words=1 << 22, max_events=256, max_roads=1 << 17)
+    # one road per chunk of the fit's work queue; batches of up to four events
+    # replay a second graph with one persistent block per SM
+    sched = api.schedule(8, 0, 16, 1, 4096, 0)
+    srv = serve.Server(dc, n_slots=4, max_words=1 << 22, max_events=256, max_roads=1 << 17,
+                       sched=sched, small_batch_events=4, small_blocks_per_sm=1)
+    out["fused_schedule"] = dict({f: getattr(sched, f) for f, _ in api.SvtSchedule._fields_},
+                                 small_batch_events=4, small_blocks_per_sm=1)
     out["fused_graph_4slots"] = [run(srv, 30e3, 30000), run(srv, 300e3, 100000)]
     st = srv.stats()
     out["fused_graph_4slots_stats"] = {k: st[k] for k in ("batches", "h2d_bytes", "d2h_bytes")}

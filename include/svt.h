@@ -411,6 +411,11 @@ typedef struct {
     uint64_t max_combs;          /* per batch, mode 1 only (combination records) */
     uint64_t device_budget;      /* bytes; 0 = no limit (else create fails with OOM) */
     uint64_t max_queued_words;   /* admission queue bound; 0 = unbounded */
+    uint32_t small_batch_events; /* mode 0: batches of at most this many events replay a
+                                    second graph whose fit launch has small_blocks_per_sm
+                                    persistent blocks per SM (fewer resident warps suit
+                                    small batches); 0 = one graph per slot */
+    uint32_t small_blocks_per_sm;   /* 0 = 1 */
 } svt_server_config;
 
 typedef struct {

@@ -43,7 +43,8 @@ class SvtServerConfig(ctypes.Structure):
     _fields_ = [("n_slots", ctypes.c_uint32), ("mode", ctypes.c_uint32),
                 ("max_words", ctypes.c_uint64), ("max_events", ctypes.c_uint64),
                 ("max_roads", ctypes.c_uint64), ("max_combs", ctypes.c_uint64),
-                ("device_budget", ctypes.c_uint64), ("max_queued_words", ctypes.c_uint64)]
+                ("device_budget", ctypes.c_uint64), ("max_queued_words", ctypes.c_uint64),
+                ("small_batch_events", ctypes.c_uint32), ("small_blocks_per_sm", ctypes.c_uint32)]
 
 
 class SvtEventResult(ctypes.Structure):

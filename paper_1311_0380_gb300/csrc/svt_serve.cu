@@ -56,6 +56,7 @@ struct Slot {
     cudaStream_t st = nullptr;
     cudaEvent_t done = nullptr;
     svt_graph graph = nullptr;
+    svt_graph graph_small = nullptr;   // for batches of at most small_batch_events events
     bool busy = false;
     std::vector<Pending> events;
     uint64_t n_words = 0, n_roads = 0;
@@ -192,7 +193,8 @@ bool svt_server_s::launch(Slot &s) {
             cudaSuccess)
         return false;
     if (c.mode == 0) {
-        if (svt_graph_launch(s.graph, st) != SVT_OK) return false;
+        const bool small = s.graph_small && E <= c.small_batch_events;
+        if (svt_graph_launch(small ? s.graph_small : s.graph, st) != SVT_OK) return false;
     } else {
         // the plain per-stage path, sized by the host-known batch
         const svt_config *fc = &cfg;
@@ -388,11 +390,21 @@ int svt_server_create(const svt_server_config *c, const int16_t *d_F, const int1
                                   s.d_status, s.d_ws, s.ws_bytes,
                                   srv->has_sched ? &srv->sched : nullptr, &s.graph);
             if (rc != SVT_OK) break;
+            if (c->small_batch_events) {
+                svt_schedule small = srv->has_sched ? srv->sched : svt_schedule{0, 0, 0, 0, 0, 0};
+                small.blocks_per_sm = c->small_blocks_per_sm ? c->small_blocks_per_sm : 1u;
+                rc = svt_graph_create(s.d_words, c->max_words, s.d_off, c->max_events, s.d_sizes,
+                                      d_F, d_q, cfg, c->max_roads, s.d_out, s.d_event_road,
+                                      s.d_counts, s.d_status, s.d_ws, s.ws_bytes, &small,
+                                      &s.graph_small);
+                if (rc != SVT_OK) break;
+            }
         }
     }
     if (rc != SVT_OK) {
         for (auto &s : srv->slots) {
             if (s.graph) svt_graph_destroy(s.graph);
+            if (s.graph_small) svt_graph_destroy(s.graph_small);
             if (s.done) cudaEventDestroy(s.done);
             if (s.st) cudaStreamDestroy(s.st);
         }
@@ -459,6 +471,7 @@ int svt_server_destroy(svt_server srv) {
     for (auto &s : srv->slots) {
         if (s.busy) cudaEventSynchronize(s.done);
         if (s.graph) svt_graph_destroy(s.graph);
+        if (s.graph_small) svt_graph_destroy(s.graph_small);
         if (s.done) cudaEventDestroy(s.done);
         if (s.st) cudaStreamDestroy(s.st);
     }

@@ -17,15 +17,18 @@ from .api import _p
 
 class Server:
     """Continuous-batching server over the fused path (mode 0) or the plain
-    per-stage path (mode 1)."""
+    per-stage path (mode 1).  small_batch_events / small_blocks_per_sm: batches
+    of at most that many events replay a second graph whose fit launch keeps
+    fewer persistent blocks per SM (mode 0)."""
 
     def __init__(self, consts, n_slots=4, max_words=1 << 22, max_events=256, max_roads=1 << 16,
                  mode=0, max_combs=0, device_budget=0, max_queued_words=0, sched=None,
-                 device="cuda"):
+                 small_batch_events=0, small_blocks_per_sm=0, device="cuda"):
         L = N.load()
         self.consts = consts
         self.cfgs = N.SvtServerConfig(n_slots, mode, max_words, max_events, max_roads, max_combs,
-                                      device_budget, max_queued_words)
+                                      device_budget, max_queued_words, small_batch_events,
+                                      small_blocks_per_sm)
         self.sched = sched
         d, h = ctypes.c_size_t(), ctypes.c_size_t()
         sp = ctypes.byref(sched) if sched is not None else None

@@ -62,14 +62,18 @@ def collect(srv, n, timeout_polls=20000):
     return got
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_alone_and_in_mix_are_bit_exact(mode):
-    from paper_1311_0380_gb300 import serve
+@pytest.mark.parametrize("mode,small", [(0, 0), (1, 0), (0, 4)])
+def test_alone_and_in_mix_are_bit_exact(mode, small):
+    """small: batches of at most that many events replay the slot's second
+    graph (one persistent block per SM, one road per chunk)."""
+    from paper_1311_0380_gb300 import api, serve
     consts, words, off = mixed_events()
     ocfg = oracle.config(15, 15, consts.chi2_cut_99, 4096, 5, 512)
     want, nr = oracle_per_event(words, off, consts, ocfg)
     pool = serve.pinned_pool(words)
-    srv, _ = make_server(consts, mode)
+    kw = {} if not small else dict(sched=api.schedule(8, 0, 16, 1, 4096, 0), small_batch_events=small,
+                                   small_blocks_per_sm=1)
+    srv, _ = make_server(consts, mode, **kw)
     E = len(nr)
     views = [pool[int(off[e]):int(off[e + 1])] for e in range(E)]
     # in the mix: everything submitted back to back
