@@ -313,9 +313,9 @@ int svt_run_sized(const uint32_t *d_words, uint64_t max_words, const uint64_t *d
  * schedule of {4, 8, 16} warps per block x {8, 16, 32, 64} rows per item x
  * {1, 2, 4, 8} roads per chunk x {1024, 4096, 16384} small_max (blocks per SM
  * as many as fit, no pairing), then the fastest of those with pair_small = 1
- * and {2, 4, 8} roads per chunk, one warm-up and `reps` timed runs each (CUDA
- * events on `stream`), and returns the fastest schedule and its mean time per
- * run.
+ * and {2, 4, 8} roads per chunk, then the fastest so far with 1 and 2 blocks
+ * per SM, one warm-up and `reps` timed runs each (CUDA events on `stream`),
+ * and returns the fastest schedule and its mean time per run.
  * Synchronises the stream.  Buffers as for svt_run; on return d_out and
  * d_status hold a valid result of the batch (every schedule gives the same
  * bits). */

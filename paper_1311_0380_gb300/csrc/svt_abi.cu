@@ -481,6 +481,16 @@ int svt_autotune(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_ev
                                          base.small_max, 1})) != SVT_OK)
                 goto done;
     }
+    {
+        // fewer resident blocks: small batches leave most warps idle and
+        // finish sooner with less contention
+        const svt_schedule base = best_s;
+        for (uint32_t b : {1u, 2u}) {
+            svt_schedule sc = base;
+            sc.blocks_per_sm = b;
+            if ((rc = trial(sc)) != SVT_OK) goto done;
+        }
+    }
 done:
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
