@@ -472,8 +472,8 @@ __global__ void __launch_bounds__(FIT_THREADS, 5)
 
 // Best passing combination of road r from its chi2 values, over the threads
 // [idx, idx + step, ...) of the warp (step 32) or block (step 256): each
-// visits its combinations in increasing c (a block keeps four loads in
-// flight), so a strict '<' keeps the smallest index among equal chi2; the
+// visits its combinations in increasing c (a block keeps eight loads per
+// thread in flight), so a strict '<' keeps the smallest index among equal chi2; the
 // (chi2, c) keys are then merged (over the block through red, when BIG).
 // Written by thread idx 0.
 template <bool BIG>
@@ -493,15 +493,15 @@ __device__ __forceinline__ void select_road(uint32_t r, const RoadMeta &m,
             }
         }
     } else if (m.off + m.n <= comb_cap) {
-        for (uint64_t c0 = idx; c0 < m.n; c0 += 4ull * step) {
-            uint32_t v[4];
+        for (uint64_t c0 = idx; c0 < m.n; c0 += 8ull * step) {
+            uint32_t v[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < 8; ++u) {
                 const uint64_t c = c0 + (uint64_t)u * step;
                 v[u] = c < m.n ? __ldg(fit_chi2 + m.off + c) : 0xFFFFFFFFu;
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
                 if (v[u] < bchi) {
                     bchi = v[u];
                     bc = (uint32_t)(c0 + (uint64_t)u * step);
@@ -635,7 +635,7 @@ void launch_combine_write(const uint32_t *road_nhit, const uint64_t *n_roads, ui
                           int grid, cudaStream_t st) {
     k_combine_write<false><<<grid_for(road_cap * 32, 256, grid), 256, 0, st>>>(
         road_nhit, n_roads, road_cap, comb_off, comb_cap, xft_pairs, comb_road, comb_hits, status);
-    k_combine_write<true><<<grid_for(road_cap, 1, grid / 4), 256, 0, st>>>(
+    k_combine_write<true><<<grid_for(road_cap, 256, grid), 256, 0, st>>>(
         road_nhit, n_roads, road_cap, comb_off, comb_cap, xft_pairs, comb_road, comb_hits, status);
 }
 
@@ -657,7 +657,7 @@ void launch_select(const uint32_t *fit_chi2, const int32_t *fit_par, uint64_t co
                    const unsigned long long *status, int grid, cudaStream_t st) {
     k_select<false><<<grid_for(road_cap * 32, 256, grid), 256, 0, st>>>(
         fit_chi2, fit_par, comb_cap, comb_off, road_flags, n_roads, road_cap, cfg, best, status);
-    k_select<true><<<grid_for(road_cap, 1, grid / 4), 256, 0, st>>>(
+    k_select<true><<<grid_for(road_cap, 256, grid), 256, 0, st>>>(
         fit_chi2, fit_par, comb_cap, comb_off, road_flags, n_roads, road_cap, cfg, best, status);
 }
 
