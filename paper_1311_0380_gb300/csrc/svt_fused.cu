@@ -9,16 +9,19 @@
 //     A_k(a) = q_k 2^qshift + sum_{prefix l} F_kl x_l,  B_k(b) = sum_{suffix l} F_kl x_l,
 //     exactly in int64.  A warp builds the per-hit terms F_kl x_l and up to 64
 //     A rows in shared memory; each lane holds the B of one column in
-//     registers.  One combination then costs three 64-bit adds, three funnel
-//     shifts, the clamp, three multiply-adds and one compare.  Only the three
-//     chi rows are evaluated in the loop; the parameters are recomputed once
-//     for the winning combination.
+//     registers.  One combination then costs three 64-bit adds, a 16-bit
+//     range test, three multiply-adds and one compare-select (the high word
+//     of each sum is y_k + 32768; see eval_rows).  Only the three chi rows are
+//     evaluated in the loop; the parameters are formed once for the winning
+//     combination.
 //   * Work: roads with more than small_max evaluated combinations are split
 //     into items of `rows` rows and handled first (items taken from an atomic
 //     counter; the road of an item is found by a 32-way warp search of the
 //     short list of split roads).  Then warps take chunks of consecutive
-//     roads (one coalesced load of their 16-byte descriptors) and fit every
-//     remaining road whole, one warp per road.
+//     roads (one coalesced load of their 32-byte descriptors) and fit every
+//     remaining road whole, one warp per road; with the PAIR instance two
+//     consecutive SMALL roads of the same geometry go to the two halves of a
+//     warp instead.
 //   * Each lane visits its combinations in increasing c within a column (or
 //     within its block of rows of a column), so a strict '<' keeps the
 //     smallest index among equal chi2; across columns, row blocks, lanes and
