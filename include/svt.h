@@ -215,7 +215,8 @@ int svt_combine(const uint32_t *d_road_nhit, const uint64_t *d_n_roads, uint64_t
 
 /*
  * svt_fit -- stage 3 of Sec. 2.1: the linearised fit of every combination
- * (one thread per combination).
+ * (one thread per combination; a block stages the constant rows and hit
+ * coordinates of the roads of its tile of combinations in shared memory).
  *   d_words                       the input words (coordinates are read there)
  *   d_road_word, d_road_nhit      from svt_unpack
  *   d_comb_road, d_comb_hits, d_n_combs, comb_cap   from svt_combine
@@ -230,7 +231,8 @@ int svt_fit(const uint32_t *d_words, const uint32_t *d_road_word, const uint32_t
 
 /*
  * svt_select -- chi-square cut and best combination per road (one warp per
- * road, shuffle argmin).
+ * road, shuffle argmin; roads of more than 4096 combinations one block each,
+ * in a second launch).
  *   d_fit_chi2, d_fit_par, comb_cap   from svt_fit
  *   d_comb_off, d_road_flags          from svt_combine
  *   d_best[road_cap]       out: per-road best (svt_best)
