@@ -43,6 +43,16 @@ def svt_version() -> int:
     return N.load().svt_version()
 
 
+def int_peak(mode: int, iters: int = 1 << 14, stream=None):
+    """Measured integer throughput of the current GPU (svt_int_peak): returns
+    (operations per second, seconds of the timed launch).  mode 0: 3-input
+    adds, 1: multiply-adds, 2: both interleaved."""
+    ops, sec = ctypes.c_double(), ctypes.c_double()
+    N.check(N.load().svt_int_peak(mode, iters, ctypes.byref(ops), ctypes.byref(sec),
+                                  _stream(stream)), "svt_int_peak")
+    return ops.value, sec.value
+
+
 def svt_device_sm_count(device: int = 0) -> int:
     return N.load().svt_device_sm_count(device)
 
