@@ -694,35 +694,34 @@ def main():
     value = job_fits / (total_ms / 1e3)
     clock_summary = clocks.summary()
 
-    # ---- roofline of the persistent fit kernel (ALU / issue bound), against
-    # the integer throughput measured on this GPU (svt_int_peak: chains of
-    # 3-input adds, of multiply-adds, and the two interleaved; the fit keeps
-    # both pipes busy, so the interleaved stream is the denominator)
-    int_peak = {name: api.int_peak(mode)[0] for mode, name in
-                ((0, "add3"), (1, "imad"), (2, "add3_imad"))}
-    alu_peak = int_peak["add3_imad"] / 1e12
-    issue_peak = int_peak["add3_imad"] / 32 / 1e9
+    # ---- roofline of the persistent fit kernel (ALU / issue bound).  The peak
+    # is derived from the unit counts and the clock; beside it, what this GPU
+    # measurably sustains (svt_pipe_peak: int32 3-input adds, multiply-adds,
+    # both, and the fp32 FMA stream that shows the schedulers' issue rate)
+    pipe = {name: api.pipe_peak(mode)[0] for mode, name in
+            ((0, "int32_add3"), (1, "int32_imad"), (2, "int32_add3_imad"), (3, "fp32_fma"))}
+    issue_measured = pipe["fp32_fma"] / 32 / 1e9
     fit_mean_s = statistics.mean(fit_ms) / 1e3
     achieved = fits_per_step * OPS_PER_FIT / fit_mean_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
-                "frac": achieved / alu_peak, "traffic": recorded_traffic(),
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                "frac": achieved / ALU_PEAK_TOPS, "traffic": recorded_traffic(),
                 "kernel": "k_fit_persistent", "ops_per_fit": OPS_PER_FIT,
                 "fit_kernel_ms": statistics.mean(fit_ms),
-                "peak_source": "measured (svt_int_peak, int32 3-input adds and multiply-adds "
-                               "interleaved); derived 152 SM x 128 lanes x 2.07 GHz = %.1f"
-                               % ALU_PEAK_TOPS,
-                "measured_int_tops": {k: v / 1e12 for k, v in int_peak.items()}}
+                "peak_source": "derived: 152 SM x 128 int32 lanes x 2.07 GHz",
+                "measured_tlanes_per_s": {k: v / 1e12 for k, v in pipe.items()}}
     # the kernel's own bound: warp instructions it issues (per combination,
-    # from the committed ncu summary) against the measured issue rate of an
-    # integer stream
+    # from the committed ncu summary) against the schedulers' issue rate
     ipf = recorded_profile("warp_instructions_per_fit")
-    roofline["issue"] = None if ipf is None else {
-        "warp_instructions_per_fit": ipf,
-        "achieved_ginst_s": ipf * fits_per_step / fit_mean_s / 1e9,
-        "peak_ginst_s": issue_peak,
-        "frac": ipf * fits_per_step / fit_mean_s / 1e9 / issue_peak,
-        "peak_source": "measured (svt_int_peak interleaved stream / 32 lanes); derived "
-                       "152 SM x 4 schedulers x 2.07 GHz = %.1f" % ISSUE_PEAK_GINST}
+    if ipf is not None:
+        ach = ipf * fits_per_step / fit_mean_s / 1e9
+        roofline["issue"] = {
+            "warp_instructions_per_fit": ipf, "achieved_ginst_s": ach,
+            "peak_ginst_s": ISSUE_PEAK_GINST, "frac": ach / ISSUE_PEAK_GINST,
+            "peak_source": "derived: 152 SM x 4 schedulers x 2.07 GHz",
+            "measured_peak_ginst_s": issue_measured, "frac_of_measured": ach / issue_measured,
+            "measured_source": "svt_pipe_peak fp32 FMA stream / 32 lanes"}
+    else:
+        roofline["issue"] = None
 
     # ---- end to end from pinned host memory (fused, copies overlapped with compute)
     e2e = None

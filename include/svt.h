@@ -157,17 +157,19 @@ int svt_version(void);
 /* Number of CUDA devices visible and the SM count of `device` (0 on error). */
 int svt_device_sm_count(int device);
 
-/* Integer throughput of the current device, measured: every thread of a full
- * grid runs eight chains of 32-bit operations for 4 x iters steps (mode 0:
- * 3-input adds, the integer ALU pipe; 1: multiply-adds, the FMA pipe; 2: the
- * two interleaved), timed with CUDA events on `stream` after a warm-up
- * launch.  *ops_per_s receives the operations (lanes) per second, *seconds
- * (may be NULL) the timed launch's duration.  This is the measured peak the
- * fused fit kernel's integer-ALU and issue rooflines are quoted against.
- * Synchronises the stream; allocates 1 KB of device memory for the call.
- * Errors: SVT_ERR_BAD_ARG (mode > 2, iters = 0, null output), SVT_ERR_CUDA. */
-int svt_int_peak(uint32_t mode, uint32_t iters, double *ops_per_s, double *seconds,
-                 void *stream);
+/* Arithmetic throughput of the current device, measured: every thread of a
+ * full grid runs rings of eight dependent chains for 4 x iters steps (mode 0:
+ * int32 3-input adds; 1: int32 multiply-adds; 2: both, as two independent
+ * rings; 3: fp32 multiplies and fused multiply-adds, the fastest instruction
+ * stream and so a measure of the schedulers' issue rate), timed with CUDA
+ * events on `stream` after a warm-up launch.  *ops_per_s receives the
+ * operations (lanes) per second, *seconds (may be NULL) the timed launch's
+ * duration.  Context for the fused fit kernel's integer-ALU and issue
+ * rooflines.  Synchronises the stream; allocates 1 KB of device memory for
+ * the call.  Errors: SVT_ERR_BAD_ARG (mode > 3, iters = 0, null output),
+ * SVT_ERR_CUDA. */
+int svt_pipe_peak(uint32_t mode, uint32_t iters, double *ops_per_s, double *seconds,
+                  void *stream);
 
 /* ======================================================================
  * Plain path: one call per stage, one or more launches each, every

@@ -75,8 +75,8 @@ _schp = ctypes.POINTER(SvtSchedule)
 SIGNATURES = {
     "svt_version": (ctypes.c_int, []),
     "svt_device_sm_count": (ctypes.c_int, [ctypes.c_int]),
-    "svt_int_peak": (ctypes.c_int, [_u32, _u32, ctypes.POINTER(ctypes.c_double),
-                                    ctypes.POINTER(ctypes.c_double), _vp]),
+    "svt_pipe_peak": (ctypes.c_int, [_u32, _u32, ctypes.POINTER(ctypes.c_double),
+                                     ctypes.POINTER(ctypes.c_double), _vp]),
     "svt_unpack_workspace_size": (_sz, [_u64]),
     "svt_unpack": (ctypes.c_int, [_vp, _u64, _vp, _u64, _u32, _u32, _u64, _vp, _vp, _vp, _vp,
                                   _vp, _vp, _sz, _vp]),

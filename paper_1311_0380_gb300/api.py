@@ -43,13 +43,14 @@ def svt_version() -> int:
     return N.load().svt_version()
 
 
-def int_peak(mode: int, iters: int = 1 << 14, stream=None):
-    """Measured integer throughput of the current GPU (svt_int_peak): returns
-    (operations per second, seconds of the timed launch).  mode 0: 3-input
-    adds, 1: multiply-adds, 2: both interleaved."""
+def pipe_peak(mode: int, iters: int = 1 << 14, stream=None):
+    """Measured arithmetic throughput of the current GPU (svt_pipe_peak):
+    returns (operations per second, seconds of the timed launch).  mode 0:
+    int32 3-input adds, 1: int32 multiply-adds, 2: both, 3: fp32 multiply and
+    fused multiply-add (the issue rate)."""
     ops, sec = ctypes.c_double(), ctypes.c_double()
-    N.check(N.load().svt_int_peak(mode, iters, ctypes.byref(ops), ctypes.byref(sec),
-                                  _stream(stream)), "svt_int_peak")
+    N.check(N.load().svt_pipe_peak(mode, iters, ctypes.byref(ops), ctypes.byref(sec),
+                                   _stream(stream)), "svt_pipe_peak")
     return ops.value, sec.value
 
 

@@ -1,4 +1,4 @@
-"""svt_int_peak: the measured integer throughput the fit kernel's rooflines use."""
+"""svt_pipe_peak: the measured arithmetic throughput beside the fit kernel's rooflines."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -11,18 +11,20 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def test_int_peak_is_plausible_and_checks_its_arguments():
+def test_pipe_peak_is_plausible_and_checks_its_arguments():
     from paper_1311_0380_gb300 import api, _native as N
     sms = N.load().svt_device_sm_count(0)
     ops = {}
-    for mode in (0, 1, 2):
-        v, sec = api.int_peak(mode, 1 << 12)
+    for mode in (0, 1, 2, 3):
+        v, sec = api.pipe_peak(mode, 1 << 12)
         assert sec > 0
         ops[mode] = v
-        # at most 128 int32 lanes per SM per cycle, at a clock below 3 GHz
+        # at most 128 lanes per SM per cycle, at a clock below 3 GHz
         assert 0 < v < sms * 128 * 3.0e9, (mode, v)
-    # both pipes together carry at least as much as either alone
+    # both integer rings together carry at least as much as either alone, and
+    # the fp32 stream issues at least as fast as the integer ones
     assert ops[2] > 0.9 * max(ops[0], ops[1])
-    for bad in ((3, 16), (0, 0)):
+    assert ops[3] > 0.9 * ops[2]
+    for bad in ((4, 16), (0, 0)):
         with pytest.raises(RuntimeError, match="BAD_ARG"):
-            api.int_peak(*bad)
+            api.pipe_peak(*bad)
