@@ -296,6 +296,10 @@ __global__ void k_grad_items(const float *__restrict__ x, const float *__restric
         float acc[NPAR];
 #pragma unroll
         for (int j = 0; j < NPAR; ++j) acc[j] = 0.f;
+        // two tracks per step keep two tracks' loads in flight (the 42
+        // accumulators leave room for only 16 warps per SM); each lane still
+        // adds its tracks in increasing order
+#pragma unroll 2
         for (uint32_t t = it.start + lane; t < it.end; t += 32) {
             float xv[6], g[6];
             if (MODE == 0) {
