@@ -10,7 +10,7 @@
 // of one sector, one warp per item.  Reductions are two-level and in a fixed
 // order (lanes -> shuffle tree -> items in index order), so results are
 // bitwise reproducible run to run.
-#include "svt_internal.cuh"
+#include "svt_kernels.cuh"
 
 namespace svt {
 
@@ -229,6 +229,7 @@ __global__ void __launch_bounds__(256, 8)
                  const float *__restrict__ q, const float *__restrict__ w,
                  float *item_loss) {
     __shared__ float cs[8][48];
+    allow_next_grid();   // the final reduction may be scheduled; it waits for this grid
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint32_t NI = (uint32_t)*n_items;
     const float w0 = w[0], w1 = w[1], w2 = w[2];
@@ -259,6 +260,7 @@ __global__ void __launch_bounds__(1024)
     k_loss_final(const float *__restrict__ item_loss, const int32_t *__restrict__ n_items,
                  uint64_t n, float *loss) {
     __shared__ float sm[32];
+    wait_prior_grid();   // the item partials are complete (see launch_after)
     const uint32_t NI = (uint32_t)*n_items;
     float total = 0.f;
     for (uint32_t c0 = 0; c0 < NI; c0 += 1024) {
@@ -288,6 +290,7 @@ __global__ void k_grad_items(const float *__restrict__ x, const float *__restric
                              const float *__restrict__ q, const float *__restrict__ w,
                              float *item_grad, float *dx) {
     __shared__ float cs[8][48];
+    allow_next_grid();   // the final reduction may be scheduled; it waits for this grid
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint32_t NI = (uint32_t)*n_items;
     for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + wib; i < NI; i += gridDim.x * (blockDim.x >> 5)) {
@@ -355,6 +358,7 @@ __global__ void k_grad_final(const float *__restrict__ item_grad,
                              const int32_t *__restrict__ sector_item, uint32_t S,
                              const float *__restrict__ scale_dev, float scale, float *dF,
                              float *dq) {
+    wait_prior_grid();   // the item partials are complete (see launch_after)
     const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= S * NPAR) return;
     const uint32_t s = k / NPAR, j = k % NPAR;
@@ -414,7 +418,7 @@ void launch_calib_loss(const float *x, const float *theta, const int32_t *item_s
     (void)grid;
     k_loss_items<<<g, 256, 0, st>>>(x, theta, item_sector, item_start, sector_off, n_items, F, q, w,
                                    item_loss);
-    k_loss_final<<<1, 1024, 0, st>>>(item_loss, n_items, n, loss);
+    launch_after(k_loss_final, 1, 1024, 0, st, item_loss, n_items, n, loss);
 }
 
 void launch_calib_grad(int mode, const float *x, const float *theta, const float *grad_y,
@@ -431,8 +435,8 @@ void launch_calib_grad(int mode, const float *x, const float *theta, const float
     else
         k_grad_items<1><<<g, 256, 0, st>>>(x, theta, grad_y, item_sector, item_start, sector_off,
                                           n_items, F, q, w, item_grad, dx);
-    k_grad_final<<<(S * NPAR + 255) / 256, 256, 0, st>>>(item_grad, sector_item, S, scale_dev,
-                                                        scale, dF, dq);
+    launch_after(k_grad_final, (S * NPAR + 255) / 256, 256, 0, st, item_grad, sector_item, S,
+                 scale_dev, scale, dF, dq);
 }
 
 }  // namespace svt
