@@ -274,7 +274,6 @@ __global__ void __launch_bounds__(TILE_THREADS)
     constexpr uint32_t SENTINEL = 0xC0000000u;   // an event-header word: ends every run
     __shared__ uint32_t red[TILE_THREADS / 32 + 1];
     __shared__ int redi[TILE_THREADS / 32];
-    __shared__ unsigned long long red64[TILE_THREADS / 32 + 1];
     __shared__ uint32_t sw[FRONT + TILE_WORDS + BACK];
     __shared__ uint32_t cnt[TILE_WORDS];              // per road of the tile: 5 bits per layer
     // V11 counts of each road's hit run: layer 4 [9:0], layer 5 [19:10], all
@@ -284,9 +283,11 @@ __global__ void __launch_bounds__(TILE_THREADS)
     __shared__ uint16_t hdr_pos[TILE_WORDS];          // tile position of each road header
     __shared__ int last_nonhit;
     __shared__ unsigned long long big_base;
+    __shared__ unsigned long long tile_comb;   // evaluated combinations of the tile
     __shared__ uint32_t same_bits[1 + TILE_WORDS / 32];   // V8 bitmap, see below
     wait_prior_grid();
     allow_next_grid();
+    if (threadIdx.x == 0) tile_comb = 0;   // visible after the tile loop's first barrier
     const uint64_t n_words = dims->n_words, n_events = dims->n_events;
     const uint64_t T = n_tiles(n_words);
     for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
@@ -502,15 +503,21 @@ __global__ void __launch_bounds__(TILE_THREADS)
         if (fr.desc) {
             // this thread's split roads go to slots [base + big_ex, ...) with
             // items from [base_items + it_ex, ...), in the order it visited them
-            // (most tiles hold no split road and skip both scans)
+            // (most tiles hold no split road and skip both scans); the tile's
+            // evaluated combinations are summed per warp into tile_comb, which
+            // the barrier of __syncthreads_or orders before thread 0 reads it
+            unsigned long long cw = comb_sum;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) cw += __shfl_xor_sync(0xffffffffu, cw, d);
+            if ((threadIdx.x & 31) == 0 && cw) atomicAdd(&tile_comb, cw);
             uint32_t it_total = 0, big_total = 0, it_ex = 0, big_ex = 0;
             if (__syncthreads_or(big_sum != 0)) {
                 it_ex = block_exclusive_scan<uint32_t>(items_sum, red, &it_total);
                 big_ex = block_exclusive_scan<uint32_t>(big_sum, red, &big_total);
             }
-            unsigned long long c_total;
-            block_exclusive_scan<unsigned long long>(comb_sum, red64, &c_total);
             if (threadIdx.x == 0) {
+                const unsigned long long c_total = tile_comb;
+                tile_comb = 0;   // the next tile adds to it only after further barriers
                 unsigned long long b = 0;
                 if (big_total) {
                     b = atomicAdd(fr.bl.reserve,
