@@ -60,6 +60,25 @@ inline void launch_after(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t
 struct RoadDesc {
     uint4 a, b;
 };
+// Estimated warp instructions of the fused fit for a road of C evaluated
+// combinations whose suffix starts at layer l and has nb entries: about 20
+// per row step of a lane (full passes of 32 columns, then the partial pass in
+// lane groups of nb mod 32, each with its own rows), 45 per pass over the
+// columns of a 64-row chunk, 15 per prefix layer and 32 rows of the row
+// build, 15 per suffix-table layer.  Only ever compared with itself, so single
+// precision with approximate quotients is ample.
+__device__ __forceinline__ float split_cost(uint32_t C, uint32_t nb, uint32_t l) {
+    const float na = ceilf(__fdividef((float)C, (float)nb));
+    const uint32_t full = nb >> 5, w = nb & 31u;
+    const float chunks = ceilf(na * (1.f / 64.f));
+    // lane groups of the partial pass; 32 / w is either exact or at least
+    // 1/31 above its floor, so the small bias keeps floorf exact
+    const float groups = w ? floorf(__fdividef(32.f, (float)w) + 1e-3f) : 1.f;
+    const float tail = w ? ceilf(__fdividef(na, groups)) + chunks : 0.f;
+    return 20.f * ((float)full * na + tail) + 45.f * chunks * (float)(full + (w ? 1u : 0u)) +
+           15.f * (float)l * (ceilf(na * (1.f / 32.f)) - 1.f);
+}
+
 __device__ __forceinline__ RoadDesc make_road_desc(uint32_t rw, uint32_t packed, uint32_t hw,
                                                    const svt_config &cfg) {
     const RoadShape s = road_shape(packed, cfg.xft_pairs);
@@ -68,6 +87,20 @@ __device__ __forceinline__ RoadDesc make_road_desc(uint32_t rw, uint32_t packed,
     const uint32_t C_eval = bad ? 0u : (C > cfg.max_comb ? cfg.max_comb : C);
     uint32_t split, NB;
     road_split(s, split, NB);
+    // The fit kernel takes one column per lane (the last, partial pass over
+    // the columns in groups of lanes, each with a block of rows), so one layer
+    // fewer in the suffix, under 32 columns, can cost less than the rule's
+    // split: keep whichever of the two the estimate favours.
+    if (C_eval > 0 && split + 1 < (uint32_t)N_LAYERS) {
+        uint32_t nb1 = 1;
+#pragma unroll
+        for (int l = 0; l < N_LAYERS; ++l)
+            if ((uint32_t)l > split) nb1 *= s.n[l];
+        if (split_cost(C_eval, nb1, split + 1) < split_cost(C_eval, NB, split)) {
+            split += 1;
+            NB = nb1;
+        }
+    }
     uint32_t NBp = 1, ntop = 1;
 #pragma unroll
     for (int l = 0; l < N_LAYERS; ++l) {
