@@ -330,16 +330,25 @@ int svt_run_sized(const uint32_t *d_words, uint64_t max_words, const uint64_t *d
  * {1, 2, 4, 8} roads per chunk x {1024, 4096, 16384} small_max (blocks per SM
  * as many as fit, no pairing), then the fastest of those with pair_small = 1
  * and {2, 4, 8} roads per chunk, then the fastest so far with 1 and 2 blocks
- * per SM, one warm-up and `reps` timed runs each (CUDA events on `stream`),
- * and returns the fastest schedule and its mean time per run.
+ * per SM, one warm-up and `reps` timed runs each (CUDA events on `stream`);
+ * finally the four fastest of all these once more with 3 * reps runs each,
+ * and returns the fastest of that pass and its mean time per run.
+ *   d_flush, flush_bytes  device scratch (may be NULL with flush_bytes 0):
+ *                      when given, every timed run is preceded by a write of
+ *                      flush_bytes to it outside the timed region and timed
+ *                      alone, so that with flush_bytes above the L2 size no
+ *                      run finds the batch in L2 (as for batches that arrive
+ *                      one after another); without it the runs go back to back
+ * Errors: SVT_ERR_BAD_ARG for reps outside [1, 100], a NULL best / best_ms or
+ * flush_bytes > 0 with a NULL d_flush; else as svt_run.
  * Synchronises the stream.  Buffers as for svt_run; on return d_out and
  * d_status hold a valid result of the batch (every schedule gives the same
  * bits). */
 int svt_autotune(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_off,
                  uint64_t n_events, const int16_t *d_F, const int16_t *d_q, const svt_config *cfg,
                  uint64_t road_cap, uint32_t *d_out, uint64_t *d_status, void *d_workspace,
-                 size_t workspace_bytes, uint32_t reps, svt_schedule *best, float *best_ms,
-                 void *stream);
+                 size_t workspace_bytes, uint32_t reps, void *d_flush, size_t flush_bytes,
+                 svt_schedule *best, float *best_ms, void *stream);
 
 /* CUDA graph of svt_run_sized's launch sequence, captured once on a private
  * stream (same arguments).  svt_graph_launch replays it on `stream`; every

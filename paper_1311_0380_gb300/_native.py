@@ -95,7 +95,8 @@ SIGNATURES = {
     "svt_graph_create": (ctypes.c_int, [_vp, _u64, _vp, _u64, _vp, _vp, _vp, _cfgp, _u64, _vp,
                                         _vp, _vp, _vp, _vp, _sz, _schp, ctypes.POINTER(_vp)]),
     "svt_autotune": (ctypes.c_int, [_vp, _u64, _vp, _u64, _vp, _vp, _cfgp, _u64, _vp, _vp, _vp,
-                                    _sz, _u32, _schp, ctypes.POINTER(ctypes.c_float), _vp]),
+                                    _sz, _u32, _vp, _sz, _schp, ctypes.POINTER(ctypes.c_float),
+                                    _vp]),
     "svt_graph_launch": (ctypes.c_int, [_vp, _vp]),
     "svt_graph_destroy": (ctypes.c_int, [_vp]),
     "svt_host_alloc": (ctypes.c_int, [_sz, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),

@@ -428,13 +428,15 @@ int svt_graph_create(const uint32_t *d_words, uint64_t max_words, const uint64_t
 int svt_autotune(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_off,
                  uint64_t n_events, const int16_t *d_F, const int16_t *d_q, const svt_config *cfg,
                  uint64_t road_cap, uint32_t *d_out, uint64_t *d_status, void *d_workspace,
-                 size_t workspace_bytes, uint32_t reps, svt_schedule *best, float *best_ms,
-                 void *stream) {
-    if (!best || !best_ms || reps < 1 || reps > 100) return SVT_ERR_BAD_ARG;
+                 size_t workspace_bytes, uint32_t reps, void *d_flush, size_t flush_bytes,
+                 svt_schedule *best, float *best_ms, void *stream) {
+    if (!best || !best_ms || reps < 1 || reps > 100 || (flush_bytes && !d_flush))
+        return SVT_ERR_BAD_ARG;
     static const uint32_t kWarps[] = {4, 8, 16};
     static const uint32_t kRows[] = {8, 16, 32, 64};
     static const uint32_t kChunk[] = {1, 2, 4, 8};
     static const uint32_t kSmall[] = {1024, 4096, 16384};
+    constexpr int kTop = 4;
     cudaStream_t st = (cudaStream_t)stream;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess) return SVT_ERR_CUDA;
@@ -442,31 +444,63 @@ int svt_autotune(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_ev
         cudaEventDestroy(e0);
         return SVT_ERR_CUDA;
     }
-    float best_t = 3.4e38f;
-    svt_schedule best_s{0, 0, 0, 0, 0, 0};
+    // the fastest schedules so far, fastest first
+    svt_schedule top_s[kTop] = {};
+    float top_t[kTop];
+    for (float &t : top_t) t = 3.4e38f;
     int rc = SVT_OK;
-    // mean time per run of schedule sc (one warm-up, then reps runs); keeps the fastest
-    auto trial = [&](const svt_schedule &sc) -> int {
-        int r = svt_run(d_words, n_words, d_event_off, n_events, d_F, d_q, cfg, road_cap, d_out,
-                        nullptr, nullptr, d_status, d_workspace, workspace_bytes, &sc, nullptr,
-                        stream);   // warm-up
+    auto run = [&](const svt_schedule &sc) {
+        return svt_run(d_words, n_words, d_event_off, n_events, d_F, d_q, cfg, road_cap, d_out,
+                       nullptr, nullptr, d_status, d_workspace, workspace_bytes, &sc, nullptr,
+                       stream);
+    };
+    // mean time per run of schedule sc over n runs after one warm-up.  With a
+    // flush buffer every run is timed alone, after the buffer has been
+    // overwritten (outside the timed region), so that no run finds the batch
+    // or the previous run's results in L2; without one the runs go back to
+    // back.
+    auto time_runs = [&](const svt_schedule &sc, uint32_t n, float &ms) -> int {
+        int r = run(sc);
         if (r != SVT_OK) return r;
-        if (cudaEventRecord(e0, st) != cudaSuccess) return SVT_ERR_CUDA;
-        for (uint32_t k = 0; k < reps; ++k) {
-            r = svt_run(d_words, n_words, d_event_off, n_events, d_F, d_q, cfg, road_cap, d_out,
-                        nullptr, nullptr, d_status, d_workspace, workspace_bytes, &sc, nullptr,
-                        stream);
-            if (r != SVT_OK) return r;
+        ms = 0.f;
+        if (!flush_bytes && cudaEventRecord(e0, st) != cudaSuccess) return SVT_ERR_CUDA;
+        for (uint32_t k = 0; k < n; ++k) {
+            if (flush_bytes) {
+                if (cudaMemsetAsync(d_flush, (int)(k & 0xFFu), flush_bytes, st) != cudaSuccess ||
+                    cudaEventRecord(e0, st) != cudaSuccess)
+                    return SVT_ERR_CUDA;
+            }
+            if ((r = run(sc)) != SVT_OK) return r;
+            if (flush_bytes) {
+                float one = 0.f;
+                if (cudaEventRecord(e1, st) != cudaSuccess ||
+                    cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&one, e0, e1) != cudaSuccess)
+                    return SVT_ERR_CUDA;
+                ms += one;
+            }
         }
-        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess)
+        if (!flush_bytes && (cudaEventRecord(e1, st) != cudaSuccess ||
+                             cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
             return SVT_ERR_CUDA;
+        ms /= (float)n;
+        return SVT_OK;
+    };
+    auto trial = [&](const svt_schedule &sc) -> int {
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= (float)reps;
-        if (ms < best_t) {
-            best_t = ms;
-            best_s = sc;
-        }
+        const int r = time_runs(sc, reps, ms);
+        if (r != SVT_OK) return r;
+        for (int i = 0; i < kTop; ++i)
+            if (ms < top_t[i]) {
+                for (int j = kTop - 1; j > i; --j) {
+                    top_t[j] = top_t[j - 1];
+                    top_s[j] = top_s[j - 1];
+                }
+                top_t[i] = ms;
+                top_s[i] = sc;
+                break;
+            }
         return SVT_OK;
     };
     for (uint32_t w : kWarps)
@@ -475,7 +509,7 @@ int svt_autotune(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_ev
                 for (uint32_t m : kSmall)
                     if ((rc = trial(svt_schedule{w, 0, r, c, m, 0})) != SVT_OK) goto done;
     {
-        const svt_schedule base = best_s;
+        const svt_schedule base = top_s[0];
         for (uint32_t c : {2u, 4u, 8u})
             if ((rc = trial(svt_schedule{base.warps_per_block, 0, base.rows_per_item, c,
                                          base.small_max, 1})) != SVT_OK)
@@ -484,20 +518,33 @@ int svt_autotune(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_ev
     {
         // fewer resident blocks: small batches leave most warps idle and
         // finish sooner with less contention
-        const svt_schedule base = best_s;
+        const svt_schedule base = top_s[0];
         for (uint32_t b : {1u, 2u}) {
             svt_schedule sc = base;
             sc.blocks_per_sm = b;
             if ((rc = trial(sc)) != SVT_OK) goto done;
         }
     }
+    {
+        // the few fastest again, with three times the runs: the first pass
+        // over a hundred and fifty schedules favours a lucky measurement
+        int pick = 0;
+        float pick_t = 3.4e38f;
+        for (int i = 0; i < kTop && top_t[i] < 3.4e38f; ++i) {
+            float ms = 0.f;
+            if ((rc = time_runs(top_s[i], 3 * reps, ms)) != SVT_OK) goto done;
+            if (ms < pick_t) {
+                pick_t = ms;
+                pick = i;
+            }
+        }
+        *best = top_s[pick];
+        *best_ms = pick_t;
+    }
 done:
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc != SVT_OK) return rc;
-    *best = best_s;
-    *best_ms = best_t;
-    return SVT_OK;
+    return rc;
 }
 
 int svt_host_alloc(size_t bytes, void **host, void **device) {

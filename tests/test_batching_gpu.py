@@ -2,6 +2,7 @@
 batches of different sizes (sizes read on the device), and the schedule
 autotuner, both bit-exact with the oracle."""
 import ctypes
+import json
 
 import numpy as np
 import pytest
@@ -91,6 +92,41 @@ def test_autotuner_picks_a_schedule_that_stays_bit_exact(tmp_path):
     sch2, ms2 = autotune.tuned_schedule(fp, dw, len(b.words), de, b.n_events, cache=cache)
     assert (sch2.warps_per_block, sch2.rows_per_item, sch2.roads_per_chunk, sch2.small_max) == \
         (sch.warps_per_block, sch.rows_per_item, sch.roads_per_chunk, sch.small_max)
+
+
+def test_autotune_with_l2_flush(tmp_path):
+    """Timing every run after a flush write still leaves a valid result, keys
+    the cache apart from back-to-back tuning, and a flush size without a
+    buffer is refused."""
+    import torch
+    from paper_1311_0380_gb300 import api, autotune, synth
+    consts = synth.make_constants(512)
+    spec = synth.SPECS["scaled"]
+    b = synth.make_batch(spec, 40, consts)
+    cfg = api.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, 512)
+    key, rec = oracle.run(b.words, b.event_off, consts.F, consts.q,
+                          oracle.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, 512), omp=True)
+    dc = api.DeviceConstants.from_numpy(consts.F, consts.q, cfg)
+    fp = api.FusedPath(len(b.words), b.n_events, b.total_roads, dc)
+    dw, de = api.to_device_u32(b.words), api.to_device_u64(b.event_off)
+    flush = torch.empty(2 << 20, dtype=torch.int32, device="cuda")
+    cache = str(tmp_path / "sched.json")
+    sch, ms = autotune.tuned_schedule(fp, dw, len(b.words), de, b.n_events, cache=cache, reps=1,
+                                      flush=flush)
+    assert ms > 0 and sch.warps_per_block in (4, 8, 16)
+    st = int(api.u64(fp.status)[0])
+    got = api.u32(fp.out[: b.total_roads * 6]).reshape(-1, 6)
+    assert st == key and np.array_equal(got, rec)
+    table = json.load(open(cache))
+    assert len(table) == 1 and next(iter(table)).endswith("|l1")
+    best, bms = api.SvtSchedule(), ctypes.c_float()
+    c = fp.consts
+    rc = api.N.load().svt_autotune(api._p(dw), len(b.words), api._p(de), b.n_events, api._p(c.F),
+                                   api._p(c.q), ctypes.byref(c.cfg), fp.road_cap, api._p(fp.out),
+                                   api._p(fp.status), api._p(fp.workspace),
+                                   fp.workspace.numel(), 1, None, 1 << 20, ctypes.byref(best),
+                                   ctypes.byref(bms), api._stream(None))
+    assert api.N.ERRORS[rc] == "BAD_ARG"
 
 
 def test_streaming_runner_overlapped_steps_are_exact():
