@@ -366,97 +366,21 @@ __device__ __forceinline__ unsigned long long eval_rows(SM &sm, const Geo &g, ui
     return group_min64<W>(best, L);
 }
 
-// Record of a road from its best key (all lanes of the group call; lanes of
-// the group form the parameters from its slot, which still holds this road;
-// lanes 0..5 of the group store one word each).  Returns whether the road
-// passed.
-template <int W, typename SM>
-__device__ __forceinline__ bool format_road(SM &sm, const RoadDesc &D, const Geo &g,
-                                            const svt_config &cfg, unsigned long long best,
-                                            uint32_t *o, const Lanes<W> &L) {
-    constexpr uint32_t MH = SM::kMH;
-    const uint32_t geo = D.b.x, gl = L.gl;
-    const bool pass = best != ~0ull;
-    uint32_t flags = 0;
-    if (g.total_hits == 0) flags |= SVT_FLAG_NO_HITS;
-    if (geo & (1u << 27)) flags |= SVT_FLAG_BAD_PATTERN;
-    if (geo & (1u << 26)) flags |= SVT_FLAG_OVERFLOW;
-    if (pass) flags |= SVT_FLAG_PASS;
-    const uint32_t low = (uint32_t)best;
-    const uint32_t row = low >> 9, col = low & 511u;
-    int32_t pk = 0;   // parameter k = gl - 3 of the best combination, on lanes 3..5
-    if (pass) {
-        if constexpr (W == 32) {
-            // lane 8k + l (k < 3, l < 6) forms F[k][l] x_l, the groups of
-            // eight lanes sum them, lane 8k adds q_k
-            const uint32_t k = gl >> 3, lk = gl & 7u;
-            uint32_t rem = col, i_own = 0;
-#pragma unroll
-            for (int l = N_LAYERS - 1; l >= 0; --l) {
-                if ((uint32_t)l + 1u == g.split) rem = row;   // the prefix layers take the row
-                const uint32_t nl = sm.n[l];
-                const uint32_t qd = div_by(rem, nl, sm.m[l]);
-                if ((uint32_t)l == (cfg.xft_pairs && lk == 5u ? 4u : lk)) i_own = rem - qd * nl;
-                rem = qd;
-            }
-            long long t = 0;
-            if (k < 3 && lk < (uint32_t)N_LAYERS)
-                t = (long long)sm.F[k * 6 + lk] * (long long)sm.x[lk * MH + i_own];
-            t += __shfl_xor_sync(0xffffffffu, t, 4);
-            t += __shfl_xor_sync(0xffffffffu, t, 2);
-            t += __shfl_xor_sync(0xffffffffu, t, 1);
-            int32_t p = 0;
-            if (k < 3 && lk == 0) {
-                const long long acc = (long long)sm.q[k] * (1ll << cfg.qshift) + t;
-                p = (int32_t)(acc >> cfg.oshift);   // arithmetic shift: floor
-            }
-            pk = __shfl_sync(0xffffffffu, p, ((gl + 29) & 31) << 3);   // lane 3 + k gets p_k
-        } else {
-            // lane 3 + k (k < 3) sums the six terms of parameter k itself
-            uint32_t rem = col, i_l[N_LAYERS];
-#pragma unroll
-            for (int l = N_LAYERS - 1; l >= 0; --l) {
-                if ((uint32_t)l + 1u == g.split) rem = row;   // the prefix layers take the row
-                const uint32_t nl = sm.n[l];
-                const uint32_t qd = div_by(rem, nl, sm.m[l]);
-                i_l[l] = rem - qd * nl;
-                rem = qd;
-            }
-            if (cfg.xft_pairs) i_l[5] = i_l[4];   // layer 5 takes layer 4's hit
-            if (gl >= 3 && gl < 6) {
-                const uint32_t k = gl - 3;
-                long long acc = (long long)sm.q[k] * (1ll << cfg.qshift);
-#pragma unroll
-                for (int l = 0; l < N_LAYERS; ++l)
-                    acc += (long long)sm.F[k * 6 + l] * (long long)sm.x[l * MH + i_l[l]];
-                pk = (int32_t)(acc >> cfg.oshift);   // arithmetic shift: floor
-            }
-        }
-    }
-    const uint32_t w = gl == 0   ? (rd_id(D.a.z) | (flags << 24))
-                       : gl == 1 ? (pass ? row * g.NB + col : 0xFFFFFFFFu)
-                       : gl == 2 ? (pass ? (uint32_t)(best >> 32) : 0u)
-                                 : (uint32_t)pk;
-    if (gl < 6) o[gl] = w;
-    return pass;
-}
-
-// One road fitted whole by a group of W lanes: set-up, all its rows, record.
-// Returns 1 on the group's first lane when the road passed, else 0.
+// Best key of one road fitted whole by a group of W lanes (set-up and all its
+// rows), on every lane of the group; UINT64_MAX when no combination passed or
+// the road has none to evaluate.
 template <bool GUARDED, int W, typename SM>
-__device__ __forceinline__ uint32_t fit_road(SM &sm, const uint32_t *__restrict__ words,
-                                             const RoadDesc &D, const int16_t *__restrict__ F,
-                                             const int16_t *__restrict__ q,
-                                             const svt_config &cfg, uint32_t sh, uint32_t qsh,
-                                             uint32_t init_chi, uint32_t *o, const Lanes<W> &L) {
+__device__ __forceinline__ unsigned long long fit_road(SM &sm, const uint32_t *__restrict__ words,
+                                                       const RoadDesc &D,
+                                                       const int16_t *__restrict__ F,
+                                                       const int16_t *__restrict__ q,
+                                                       const svt_config &cfg, uint32_t sh,
+                                                       uint32_t qsh, uint32_t init_chi,
+                                                       const Lanes<W> &L) {
     const Geo g = geo_of(D);
-    unsigned long long best = ~0ull;
-    if (g.C_eval > 0) {
-        road_setup<W>(sm, words, D, g, F, q, sh, cfg.xft_pairs, kColBias<GUARDED>, L);
-        best = eval_rows<GUARDED, W>(sm, g, 0, g.NA, qsh, init_chi, L);
-    }
-    const bool pass = format_road<W>(sm, D, g, cfg, best, o, L);
-    return (pass && L.gl == 0) ? 1u : 0u;
+    if (g.C_eval == 0) return ~0ull;
+    road_setup<W>(sm, words, D, g, F, q, sh, cfg.xft_pairs, kColBias<GUARDED>, L);
+    return eval_rows<GUARDED, W>(sm, g, 0, g.NA, qsh, init_chi, L);
 }
 
 __device__ __forceinline__ RoadDesc shfl_desc(const uint4 &da, const uint4 &db, uint32_t src) {
@@ -483,7 +407,7 @@ __global__ void __launch_bounds__(512, 2)
                      const RoadDesc *__restrict__ desc, uint64_t *counts, uint64_t road_cap,
                      const int16_t *__restrict__ F, const int16_t *__restrict__ q,
                      const svt_config cfg, const FusedRoads fr, uint32_t roads_per_chunk,
-                     uint32_t *out, unsigned long long *status) {
+                     unsigned long long *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
@@ -504,7 +428,6 @@ __global__ void __launch_bounds__(512, 2)
     const uint32_t R = (uint32_t)R64;
     const uint32_t sh = 32u - cfg.oshift, qsh = cfg.qshift + sh;
     const uint32_t init_chi = cfg.chi2_cut == 0xFFFFFFFFu ? 0xFFFFFFFFu : cfg.chi2_cut + 1u;
-    uint32_t n_pass = 0;   // passing roads formatted by this lane's group, summed at exit
 
     // phase 1: items of split roads
     for (;;) {
@@ -523,19 +446,7 @@ __global__ void __launch_bounds__(512, 2)
         const uint32_t a_lo = k * fr.rows;
         const uint32_t a_hi = min(a_lo + fr.rows, g.NA);
         const unsigned long long best = eval_rows<GUARDED, 32>(sm, g, a_lo, a_hi, qsh, init_chi, LW);
-        uint32_t last = 0;
-        if (lane == 0) {
-            if (best != ~0ull) atomicMin(bl.best + j, best);
-            __threadfence();
-            last = (atomicSub(bl.pending + j, 1u) == 1u) ? 1u : 0u;
-        }
-        last = __shfl_sync(0xffffffffu, last, 0);
-        if (last) {
-            __threadfence();
-            const unsigned long long fb = __ldcg(bl.best + j);
-            const bool pass = format_road<32>(sm, D, g, cfg, fb, out + (size_t)r * 6, LW);
-            n_pass += (pass && lane == 0) ? 1u : 0u;
-        }
+        if (lane == 0 && best != ~0ull) atomicMin(fr.key + r, best);
         __syncwarp();
     }
 
@@ -567,23 +478,117 @@ __global__ void __launch_bounds__(512, 2)
                         D.b.z == D2.b.z && D2.a.w <= fr.small_max) {
                         const uint32_t h = (uint32_t)lane >> 4;   // this lane's half and road
                         HalfSmem &hs = reinterpret_cast<HalfSmem *>(&sm)[h];
-                        n_pass += fit_road<GUARDED, 16>(hs, words, h ? D2 : D, F, q, cfg, sh, qsh,
-                                                        init_chi, out + (size_t)(c0 + jj + h) * 6,
-                                                        lanes_of<16>(lane));
+                        const unsigned long long best = fit_road<GUARDED, 16>(
+                            hs, words, h ? D2 : D, F, q, cfg, sh, qsh, init_chi, lanes_of<16>(lane));
+                        if ((lane & 15) == 0) fr.key[c0 + jj + h] = best;
                         jj += 2;
                         __syncwarp();
                         continue;
                     }
                 }
             }
-            n_pass += fit_road<GUARDED, 32>(sm, words, D, F, q, cfg, sh, qsh, init_chi,
-                                            out + (size_t)(c0 + jj) * 6, LW);
+            const unsigned long long best =
+                fit_road<GUARDED, 32>(sm, words, D, F, q, cfg, sh, qsh, init_chi, LW);
+            if (lane == 0) fr.key[c0 + jj] = best;
             jj += 1;
             __syncwarp();
         }
     }
+}
+
+// K5: the record of each road from its best key, one thread per road (the
+// fit kernel keeps only the key, so that a warp never spends its lanes on the
+// per-road tail of the paper's Sec. 2.1 output).  For a road that passed the
+// hits of its best combination are the digits of c = row * NB + column in the
+// radices n'_l (the column's digits for the suffix layers, the row's for the
+// prefix layers), and the parameters p_k = floor((q_k 2^qshift + sum_l
+// F_kl x_l) / 2^oshift), k = 0..2, are formed from them in int64 (Eq. 1 for
+// the three parameter rows).
+constexpr int FORMAT_THREADS = 256;
+
+__global__ void __launch_bounds__(FORMAT_THREADS)
+    k_format_fused(const uint32_t *__restrict__ words, const RoadDesc *__restrict__ desc,
+                   const unsigned long long *key, uint64_t *counts, uint64_t road_cap,
+                   const int16_t *__restrict__ F, const int16_t *__restrict__ q,
+                   const svt_config cfg, uint32_t *out, const unsigned long long *status) {
+    wait_prior_grid();   // the fit kernel has completed: every key is final
+    // the road count is read together with the first road's data (slots below
+    // road_cap are always in bounds; a slot at or past R is discarded)
+    const uint64_t R64 = counts[0];
+    const bool ok = status_ok(status);
+    uint32_t n_pass = 0;
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < road_cap;
+         r += gridDim.x * blockDim.x) {
+        const uint4 da = __ldg(&desc[r].a), db = __ldg(&desc[r].b);
+        const unsigned long long best = key[r];
+        if (!ok || R64 > road_cap || r >= R64) break;
+        const uint32_t geo = db.x, packed = da.y, total_hits = (geo >> 19) & 127u;
+        const bool pass = best != ~0ull;
+        uint32_t flags = 0;
+        if (total_hits == 0) flags |= SVT_FLAG_NO_HITS;
+        if (geo & (1u << 27)) flags |= SVT_FLAG_BAD_PATTERN;
+        if (geo & (1u << 26)) flags |= SVT_FLAG_OVERFLOW;
+        uint32_t c = 0xFFFFFFFFu, chi2 = 0;
+        int32_t p[3] = {0, 0, 0};
+        if (pass) {
+            flags |= SVT_FLAG_PASS;
+            const uint32_t low = (uint32_t)best, row = low >> 9, col = low & 511u;
+            const uint32_t split = geo & 7u;
+            c = row * db.y + col;
+            chi2 = (uint32_t)(best >> 32);
+            uint32_t digit[N_LAYERS];
+            uint32_t rem = col;
+#pragma unroll
+            for (int l = N_LAYERS - 1; l >= 0; --l) {
+                if ((uint32_t)l + 1u == split) rem = row;   // the prefix layers take the row
+                const uint32_t nl = nhit_of(packed, l);
+                const uint32_t np = (nl && !(cfg.xft_pairs && l == N_LAYERS - 1)) ? nl : 1u;
+                const uint32_t qd = div_by(rem, np, kDivMagic[np]);
+                digit[l] = rem - qd * np;
+                rem = qd;
+            }
+            if (cfg.xft_pairs) digit[N_LAYERS - 1] = digit[N_LAYERS - 2];   // the pair's own index
+            // every load first, with no branch between them (a layer without
+            // hits reads the road's header word and discards it), so that a
+            // thread waits for memory once
+            const size_t cs = (size_t)rd_sector(da.z) * 64 + ((geo >> 13) & 63u);
+            uint32_t hw[N_LAYERS];
+            uint32_t off = da.x + 1;   // first hit word of layer l (hits are sorted by layer)
+#pragma unroll
+            for (int l = 0; l < N_LAYERS; ++l) {
+                const uint32_t nl = nhit_of(packed, l);
+                hw[l] = __ldg(words + (nl ? off + digit[l] : da.x));
+                off += nl;
+            }
+            int32_t f[3][N_LAYERS], qk[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                qk[k] = __ldg(q + cs * 6 + k);
+#pragma unroll
+                for (int l = 0; l < N_LAYERS; ++l) f[k][l] = __ldg(F + cs * 36 + k * 6 + l);
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                long long acc = (long long)qk[k] * (1ll << cfg.qshift);
+#pragma unroll
+                for (int l = 0; l < N_LAYERS; ++l) {
+                    const int32_t x = nhit_of(packed, l) ? (int32_t)hit_coord(hw[l]) : 0;
+                    acc += (long long)f[k][l] * (long long)x;
+                }
+                p[k] = (int32_t)(acc >> cfg.oshift);   // floor
+            }
+            n_pass += 1;
+        }
+        uint32_t *o = out + (size_t)r * 6;
+        o[0] = rd_id(da.z) | (flags << 24);
+        o[1] = c;
+        o[2] = chi2;
+        o[3] = (uint32_t)p[0];
+        o[4] = (uint32_t)p[1];
+        o[5] = (uint32_t)p[2];
+    }
     n_pass = __reduce_add_sync(0xffffffffu, n_pass);
-    if (lane == 0 && n_pass)
+    if ((threadIdx.x & 31) == 0 && n_pass)
         atomicAdd((unsigned long long *)(counts + 3), (unsigned long long)n_pass);
 }
 
@@ -614,19 +619,28 @@ cudaError_t launch_fit_persistent(const uint32_t *words, const uint64_t *event_o
                                   const RoadDesc *desc, uint64_t *counts, uint64_t road_cap,
                                   const int16_t *F, const int16_t *q, const svt_config cfg,
                                   const FusedRoads fr, uint32_t roads_per_chunk, bool pair_small,
-                                  uint32_t *out, unsigned long long *status,
-                                  int warps_per_block, int grid, cudaStream_t st) {
+                                  unsigned long long *status, int warps_per_block, int grid,
+                                  cudaStream_t st) {
     const size_t smem = fit_smem_bytes(warps_per_block);
     const bool guarded = cfg.chi2_cut < 32767u * 32767u;
     auto launch = [&](auto kernel) {
         launch_after(kernel, grid, warps_per_block * 32, smem, st, words, event_off, dims,
-                     event_road, desc, counts, road_cap, F, q, cfg, fr, roads_per_chunk, out,
-                     status);
+                     event_road, desc, counts, road_cap, F, q, cfg, fr, roads_per_chunk, status);
     };
     if (guarded)
         pair_small ? launch(k_fit_persistent<true, true>) : launch(k_fit_persistent<true, false>);
     else
         pair_small ? launch(k_fit_persistent<false, true>) : launch(k_fit_persistent<false, false>);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_format_fused(const uint32_t *words, const RoadDesc *desc,
+                                const unsigned long long *key, uint64_t *counts,
+                                uint64_t road_cap, const int16_t *F, const int16_t *q,
+                                const svt_config cfg, uint32_t *out,
+                                const unsigned long long *status, int grid, cudaStream_t st) {
+    launch_after(k_format_fused, grid, FORMAT_THREADS, 0, st, words, desc, key, counts, road_cap,
+                 F, q, cfg, out, status);
     return cudaGetLastError();
 }
 

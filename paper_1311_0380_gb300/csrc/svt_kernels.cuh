@@ -91,12 +91,15 @@ __device__ __forceinline__ RoadDesc make_road_desc(uint32_t rw, uint32_t packed,
     // the columns in groups of lanes, each with a block of rows), so one layer
     // fewer in the suffix, under 32 columns, can cost less than the rule's
     // split: keep whichever of the two the estimate favours.
+    // (The row of a combination must stay below 2^23 in the fit's 64-bit
+    // keys: the shorter suffix is taken only while rows stay below 2^16.)
     if (C_eval > 0 && split + 1 < (uint32_t)N_LAYERS) {
         uint32_t nb1 = 1;
 #pragma unroll
         for (int l = 0; l < N_LAYERS; ++l)
             if ((uint32_t)l > split) nb1 *= s.n[l];
-        if (split_cost(C_eval, nb1, split + 1) < split_cost(C_eval, NB, split)) {
+        if (((uint64_t)nb1 << 16) >= C_eval &&
+            split_cost(C_eval, nb1, split + 1) < split_cost(C_eval, NB, split)) {
             split += 1;
             NB = nb1;
         }
@@ -128,8 +131,6 @@ __device__ __forceinline__ RoadDesc make_road_desc(uint32_t rw, uint32_t packed,
 struct BigList {
     uint32_t *road;                // split road of each slot
     uint32_t *item_off;            // its first work item
-    unsigned long long *best;      // best key so far (UINT64_MAX)
-    uint32_t *pending;             // its items not yet finished
     unsigned long long *reserve;   // (items << 32) | roads appended so far
     uint32_t *counters;            // [0] items taken, [1] roads taken
 };
@@ -137,6 +138,9 @@ struct BigList {
 // Fused-path outputs of the road extraction (desc == nullptr: plain path).
 struct FusedRoads {
     RoadDesc *desc;            // per road
+    unsigned long long *key;   // per road: best key of the fit (UINT64_MAX: none
+                               // passed), set to UINT64_MAX for split roads by
+                               // the road extraction and lowered by their items
     BigList bl;                // split roads
     uint32_t rows;             // rows per item
     uint32_t small_max;        // roads above this many combinations are split
@@ -219,8 +223,15 @@ cudaError_t launch_fit_persistent(const uint32_t *words, const uint64_t *event_o
                                   const RoadDesc *desc, uint64_t *counts, uint64_t road_cap,
                                   const int16_t *F, const int16_t *q, const svt_config cfg,
                                   const FusedRoads fr, uint32_t roads_per_chunk, bool pair_small,
-                                  uint32_t *out, unsigned long long *status,
-                                  int warps_per_block, int grid, cudaStream_t st);
+                                  unsigned long long *status, int warps_per_block, int grid,
+                                  cudaStream_t st);
+// K5: the record of every road from its best key (thread per road); counts[3]
+// receives the number of roads that passed.
+cudaError_t launch_format_fused(const uint32_t *words, const RoadDesc *desc,
+                                const unsigned long long *key, uint64_t *counts,
+                                uint64_t road_cap, const int16_t *F, const int16_t *q,
+                                const svt_config cfg, uint32_t *out,
+                                const unsigned long long *status, int grid, cudaStream_t st);
 int fit_persistent_blocks_per_sm(int warps_per_block);
 size_t fit_smem_bytes(int warps_per_block);
 

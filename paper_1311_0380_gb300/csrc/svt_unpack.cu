@@ -537,8 +537,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
                     const uint32_t j = slot0 + big_ex;   // < R <= road_cap
                     fr.bl.road[j] = (uint32_t)(tile_base + rl);
                     fr.bl.item_off[j] = item0 + it_ex;
-                    fr.bl.best[j] = ~0ull;
-                    fr.bl.pending[j] = it;
+                    fr.key[tile_base + rl] = ~0ull;
                     big_ex += 1;
                     it_ex += it;
                 }
