@@ -269,8 +269,8 @@ int svt_format(const svt_best *d_best, const uint32_t *d_words, const uint32_t *
 /* ======================================================================
  * Kernel timer: a pair of CUDA events that svt_run records, on its stream,
  * right before and right after its persistent fit kernel (the events keep
- * that kernel from overlapping its neighbours, so time whole runs without a
- * timer).  The timer is a
+ * that kernel from overlapping the one before it, so time whole runs without
+ * a timer).  The timer is a
  * host object; create/destroy are the only calls that allocate (two events).
  * ====================================================================== */
 typedef struct svt_timer_s *svt_timer;
@@ -281,10 +281,9 @@ int svt_timer_fit_ms(svt_timer timer, float *ms);
 
 /* ======================================================================
  * Fused path: unpack, combine, fit, cut, select and format of a whole batch
- * of uneven events, with the combine, fit, cut and select in one persistent
- * kernel (dynamic work queue over warp-sized work items) that keeps each
- * road's best combination as a 64-bit key, and the format in a last kernel
- * with one thread per road.
+ * of uneven events, with the combine, fit, cut, select and format in one
+ * persistent kernel (dynamic work queue over warp-sized work items; each
+ * warp writes the records of the roads it finished, one road per lane).
  * ====================================================================== */
 
 /* Workspace bytes svt_run needs for batches of up to max_words words and

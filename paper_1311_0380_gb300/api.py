@@ -406,7 +406,7 @@ class StreamingRunner:
         return status, rec
 
 
-FUSED_LAUNCHES_PER_RUN = 6   # prologue, unpack_count, scan, unpack_roads, fit, records
+FUSED_LAUNCHES_PER_RUN = 5   # prologue, unpack_count, scan, unpack_roads, fit
 PLAIN_LAUNCHES_PER_RUN = 13  # unpack (5), combine (5), fit, select, format
 
 

@@ -67,14 +67,6 @@ int tile_grid() {
     return (sms > 0 ? sms : 1) * 8;
 }
 
-// Record kernel of the fused path: one thread per road, at most 8 blocks of
-// 256 per SM (grid-stride beyond).
-int format_grid(uint64_t road_cap, int sms) {
-    const uint64_t need = (road_cap + 255) / 256;
-    const uint64_t cap = (uint64_t)(sms > 0 ? sms : 1) * 8;
-    return (int)(need < 1 ? 1 : (need < cap ? need : cap));
-}
-
 int launch_status() {
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SVT_OK : SVT_ERR_CUDA;
@@ -106,7 +98,7 @@ struct RunWs {
     uint64_t *work;   // [0] split-road reservation, [1] the fit kernel's two queue counters
     uint32_t *tile_roads, *first_ev;
     RoadDesc *desc;
-    uint32_t *big_road, *big_item_off;
+    uint32_t *big_road, *big_item_off, *big_pending;
     unsigned long long *key;
     uint32_t *event_road;
     size_t bytes;
@@ -123,6 +115,7 @@ RunWs carve_run(void *base, uint64_t max_words, uint64_t max_events, uint64_t ro
     w.desc = c.take<RoadDesc>(road_cap);
     w.big_road = c.take<uint32_t>(road_cap);
     w.big_item_off = c.take<uint32_t>(road_cap);
+    w.big_pending = c.take<uint32_t>(road_cap);
     w.key = c.take<unsigned long long>(road_cap);
     w.event_road = c.take<uint32_t>(max_events + 1);
     w.bytes = c.size();
@@ -342,7 +335,7 @@ int run_impl(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_
     const int occ = fit_persistent_blocks_per_sm((int)sc.warps_per_block);
     if (occ <= 0) return SVT_ERR_CUDA;
     const int bps = (sc.blocks_per_sm == 0 || (int)sc.blocks_per_sm > occ) ? occ : (int)sc.blocks_per_sm;
-    const BigList bl{w.big_road, w.big_item_off, (unsigned long long *)w.work,
+    const BigList bl{w.big_road, w.big_item_off, w.big_pending, (unsigned long long *)w.work,
                      (uint32_t *)(w.work + 1)};
     const FusedRoads fr{w.desc, w.key, bl, sc.rows_per_item, sc.small_max};
 
@@ -355,16 +348,13 @@ int run_impl(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_
                         nullptr, nullptr, event_road, *cfg, fr, counts, status, grid, st);
     if (timer && cudaEventRecord(timer->start, st) != cudaSuccess) return SVT_ERR_CUDA;
     if (launch_fit_persistent(d_words, d_event_off, w.dims, event_road, w.desc, counts, road_cap,
-                              d_F, d_q, *cfg, fr, sc.roads_per_chunk, sc.pair_small != 0, status,
-                              (int)sc.warps_per_block, sms * bps, st) != cudaSuccess)
+                              d_F, d_q, *cfg, fr, sc.roads_per_chunk, sc.pair_small != 0, d_out,
+                              status, (int)sc.warps_per_block, sms * bps, st) != cudaSuccess)
         return SVT_ERR_CUDA;
     if (timer) {
         if (cudaEventRecord(timer->end, st) != cudaSuccess) return SVT_ERR_CUDA;
         timer->recorded = true;
     }
-    if (launch_format_fused(d_words, w.desc, w.key, counts, road_cap, d_F, d_q, *cfg, d_out,
-                            status, format_grid(road_cap, sms), st) != cudaSuccess)
-        return SVT_ERR_CUDA;
     return launch_status();
 }
 

@@ -26,8 +26,12 @@
 //     within its block of rows of a column), so a strict '<' keeps the
 //     smallest index among equal chi2; across columns, row blocks, lanes and
 //     items the (chi2, c) pairs are merged as 64-bit keys (warp
-//     shuffles; atomicMin on the road's slot for split roads, whose record is
-//     written by the warp that retires the road's last item).
+//     shuffles; atomicMin on the road's key for split roads, which the warp
+//     that retires the road's last item takes over).
+//   * A warp lists the roads it has finished with their keys and, 31 or 32
+//     at a time, writes their records one road per lane: recovering the hits
+//     of the best combination and forming its three parameters is scalar
+//     work that would otherwise hold all 32 lanes for every road.
 #include "svt_kernels.cuh"
 
 namespace svt {
@@ -63,6 +67,15 @@ using WarpSmem = RoadSmem<MAX_HITS, 32, ROWS_MAX>;
 using HalfSmem = RoadSmem<8, 16, 16>;
 static_assert(2 * sizeof(HalfSmem) <= sizeof(WarpSmem), "two half slots fit in a warp slot");
 static_assert(sizeof(HalfSmem) % 16 == 0, "half slots keep 16-byte alignment");
+static_assert(sizeof(WarpSmem) % 16 == 0, "warp slots keep 16-byte alignment");
+
+// Roads a warp has finished but whose records it has not yet written: when 31
+// or 32 are listed (and when the warp runs out of work) each lane writes one
+// (write_record), so the per-road tail costs a lane rather than a warp.
+struct RecordList {
+    unsigned long long key[32];   // best key (UINT64_MAX: none passed)
+    uint32_t road[32];
+};
 constexpr uint32_t GEO_SMALL = 1u << 28;
 
 // The W lanes (the warp, or one half of it) that fit one road.  Every
@@ -396,6 +409,86 @@ __device__ __forceinline__ RoadDesc shfl_desc(const uint4 &da, const uint4 &db, 
     return D;
 }
 
+// Record of road r from its best key, formed by one lane (the warps of the
+// fit kernel hand their finished roads out one per lane, see RecordList).
+// For a road that passed, the hits of its best combination are the digits of
+// c = row * NB + column in the radices n'_l (the column's digits for the
+// suffix layers, the row's for the prefix layers), and the parameters
+// p_k = floor((q_k 2^qshift + sum_l F_kl x_l) / 2^oshift), k = 0..2, are
+// formed from them in int64 (Eq. 1 for the three parameter rows).  Every load
+// is issued before any is used, with no branch between them (a layer without
+// hits reads the road's header word and discards it).  Returns whether the
+// road passed.
+__device__ __forceinline__ bool write_record(const uint32_t *__restrict__ words,
+                                             const RoadDesc *__restrict__ desc, uint32_t r,
+                                             unsigned long long best,
+                                             const int16_t *__restrict__ F,
+                                             const int16_t *__restrict__ q,
+                                             const svt_config &cfg, uint32_t *out) {
+    const uint4 da = __ldg(&desc[r].a), db = __ldg(&desc[r].b);
+    const uint32_t geo = db.x, packed = da.y, total_hits = (geo >> 19) & 127u;
+    const bool pass = best != ~0ull;
+    uint32_t flags = 0;
+    if (total_hits == 0) flags |= SVT_FLAG_NO_HITS;
+    if (geo & (1u << 27)) flags |= SVT_FLAG_BAD_PATTERN;
+    if (geo & (1u << 26)) flags |= SVT_FLAG_OVERFLOW;
+    uint32_t c = 0xFFFFFFFFu, chi2 = 0;
+    int32_t p[3] = {0, 0, 0};
+    if (pass) {
+        flags |= SVT_FLAG_PASS;
+        const uint32_t low = (uint32_t)best, row = low >> 9, col = low & 511u;
+        const uint32_t split = geo & 7u;
+        c = row * db.y + col;
+        chi2 = (uint32_t)(best >> 32);
+        uint32_t digit[N_LAYERS];
+        uint32_t rem = col;
+#pragma unroll
+        for (int l = N_LAYERS - 1; l >= 0; --l) {
+            if ((uint32_t)l + 1u == split) rem = row;   // the prefix layers take the row
+            const uint32_t nl = nhit_of(packed, l);
+            const uint32_t np = (nl && !(cfg.xft_pairs && l == N_LAYERS - 1)) ? nl : 1u;
+            const uint32_t qd = div_by(rem, np, kDivMagic[np]);
+            digit[l] = rem - qd * np;
+            rem = qd;
+        }
+        if (cfg.xft_pairs) digit[N_LAYERS - 1] = digit[N_LAYERS - 2];   // the pair's own index
+        const size_t cs = (size_t)rd_sector(da.z) * 64 + ((geo >> 13) & 63u);
+        uint32_t hw[N_LAYERS];
+        uint32_t off = da.x + 1;   // first hit word of layer l (hits are sorted by layer)
+#pragma unroll
+        for (int l = 0; l < N_LAYERS; ++l) {
+            const uint32_t nl = nhit_of(packed, l);
+            hw[l] = __ldg(words + (nl ? off + digit[l] : da.x));
+            off += nl;
+        }
+        int32_t f[3][N_LAYERS], qk[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            qk[k] = __ldg(q + cs * 6 + k);
+#pragma unroll
+            for (int l = 0; l < N_LAYERS; ++l) f[k][l] = __ldg(F + cs * 36 + k * 6 + l);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            long long acc = (long long)qk[k] * (1ll << cfg.qshift);
+#pragma unroll
+            for (int l = 0; l < N_LAYERS; ++l) {
+                const int32_t x = nhit_of(packed, l) ? (int32_t)hit_coord(hw[l]) : 0;
+                acc += (long long)f[k][l] * (long long)x;
+            }
+            p[k] = (int32_t)(acc >> cfg.oshift);   // floor
+        }
+    }
+    uint32_t *o = out + (size_t)r * 6;
+    o[0] = rd_id(da.z) | (flags << 24);
+    o[1] = c;
+    o[2] = chi2;
+    o[3] = (uint32_t)p[0];
+    o[4] = (uint32_t)p[1];
+    o[5] = (uint32_t)p[2];
+    return pass;
+}
+
 // K4: persistent fit / cut / select / format.  PAIR: two consecutive SMALL
 // roads of one chunk with the same geometry go to the two halves of the warp
 // (a separate instance, so that warps never switch between the two code
@@ -407,9 +500,11 @@ __global__ void __launch_bounds__(512, 2)
                      const RoadDesc *__restrict__ desc, uint64_t *counts, uint64_t road_cap,
                      const int16_t *__restrict__ F, const int16_t *__restrict__ q,
                      const svt_config cfg, const FusedRoads fr, uint32_t roads_per_chunk,
-                     unsigned long long *status) {
+                     uint32_t *out, unsigned long long *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[threadIdx.x >> 5];
+    RecordList &rl = reinterpret_cast<RecordList *>(
+        smem_raw + sizeof(WarpSmem) * (blockDim.x >> 5))[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const Lanes<32> LW = lanes_of<32>(lane);
     wait_prior_grid();   // road extraction has completed (see launch_after)
@@ -428,6 +523,16 @@ __global__ void __launch_bounds__(512, 2)
     const uint32_t R = (uint32_t)R64;
     const uint32_t sh = 32u - cfg.oshift, qsh = cfg.qshift + sh;
     const uint32_t init_chi = cfg.chi2_cut == 0xFFFFFFFFu ? 0xFFFFFFFFu : cfg.chi2_cut + 1u;
+    uint32_t n_rec = 0;    // entries of rl (uniform over the warp)
+    uint32_t n_pass = 0;   // passing roads whose records this lane wrote, summed at exit
+    auto flush = [&]() {
+        __syncwarp();
+        if ((uint32_t)lane < n_rec &&
+            write_record(words, desc, rl.road[lane], rl.key[lane], F, q, cfg, out))
+            ++n_pass;
+        n_rec = 0;
+        __syncwarp();
+    };
 
     // phase 1: items of split roads
     for (;;) {
@@ -446,7 +551,22 @@ __global__ void __launch_bounds__(512, 2)
         const uint32_t a_lo = k * fr.rows;
         const uint32_t a_hi = min(a_lo + fr.rows, g.NA);
         const unsigned long long best = eval_rows<GUARDED, 32>(sm, g, a_lo, a_hi, qsh, init_chi, LW);
-        if (lane == 0 && best != ~0ull) atomicMin(fr.key + r, best);
+        uint32_t last = 0;
+        if (lane == 0) {
+            if (best != ~0ull) atomicMin(fr.key + r, best);
+            __threadfence();
+            last = (atomicSub(bl.pending + j, 1u) == 1u) ? 1u : 0u;
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last) {   // every item of road r is done: list it with its final key
+            if (n_rec == 32) flush();
+            if (lane == 0) {
+                __threadfence();
+                rl.key[n_rec] = __ldcg(fr.key + r);
+                rl.road[n_rec] = r;
+            }
+            n_rec += 1;
+        }
         __syncwarp();
     }
 
@@ -469,6 +589,7 @@ __global__ void __launch_bounds__(512, 2)
                 ++jj;
                 continue;
             }
+            if (n_rec > 30) flush();   // room for two more
             if constexpr (PAIR) {
                 // two SMALL roads of the same geometry (split, NBp, ntop and NA),
                 // so that the two halves run their loops in step
@@ -480,7 +601,11 @@ __global__ void __launch_bounds__(512, 2)
                         HalfSmem &hs = reinterpret_cast<HalfSmem *>(&sm)[h];
                         const unsigned long long best = fit_road<GUARDED, 16>(
                             hs, words, h ? D2 : D, F, q, cfg, sh, qsh, init_chi, lanes_of<16>(lane));
-                        if ((lane & 15) == 0) fr.key[c0 + jj + h] = best;
+                        if ((lane & 15) == 0) {
+                            rl.key[n_rec + h] = best;
+                            rl.road[n_rec + h] = c0 + jj + h;
+                        }
+                        n_rec += 2;
                         jj += 2;
                         __syncwarp();
                         continue;
@@ -489,112 +614,26 @@ __global__ void __launch_bounds__(512, 2)
             }
             const unsigned long long best =
                 fit_road<GUARDED, 32>(sm, words, D, F, q, cfg, sh, qsh, init_chi, LW);
-            if (lane == 0) fr.key[c0 + jj] = best;
+            if (lane == 0) {
+                rl.key[n_rec] = best;
+                rl.road[n_rec] = c0 + jj;
+            }
+            n_rec += 1;
             jj += 1;
             __syncwarp();
         }
     }
-}
-
-// K5: the record of each road from its best key, one thread per road (the
-// fit kernel keeps only the key, so that a warp never spends its lanes on the
-// per-road tail of the paper's Sec. 2.1 output).  For a road that passed the
-// hits of its best combination are the digits of c = row * NB + column in the
-// radices n'_l (the column's digits for the suffix layers, the row's for the
-// prefix layers), and the parameters p_k = floor((q_k 2^qshift + sum_l
-// F_kl x_l) / 2^oshift), k = 0..2, are formed from them in int64 (Eq. 1 for
-// the three parameter rows).
-constexpr int FORMAT_THREADS = 256;
-
-__global__ void __launch_bounds__(FORMAT_THREADS)
-    k_format_fused(const uint32_t *__restrict__ words, const RoadDesc *__restrict__ desc,
-                   const unsigned long long *key, uint64_t *counts, uint64_t road_cap,
-                   const int16_t *__restrict__ F, const int16_t *__restrict__ q,
-                   const svt_config cfg, uint32_t *out, const unsigned long long *status) {
-    wait_prior_grid();   // the fit kernel has completed: every key is final
-    // the road count is read together with the first road's data (slots below
-    // road_cap are always in bounds; a slot at or past R is discarded)
-    const uint64_t R64 = counts[0];
-    const bool ok = status_ok(status);
-    uint32_t n_pass = 0;
-    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < road_cap;
-         r += gridDim.x * blockDim.x) {
-        const uint4 da = __ldg(&desc[r].a), db = __ldg(&desc[r].b);
-        const unsigned long long best = key[r];
-        if (!ok || R64 > road_cap || r >= R64) break;
-        const uint32_t geo = db.x, packed = da.y, total_hits = (geo >> 19) & 127u;
-        const bool pass = best != ~0ull;
-        uint32_t flags = 0;
-        if (total_hits == 0) flags |= SVT_FLAG_NO_HITS;
-        if (geo & (1u << 27)) flags |= SVT_FLAG_BAD_PATTERN;
-        if (geo & (1u << 26)) flags |= SVT_FLAG_OVERFLOW;
-        uint32_t c = 0xFFFFFFFFu, chi2 = 0;
-        int32_t p[3] = {0, 0, 0};
-        if (pass) {
-            flags |= SVT_FLAG_PASS;
-            const uint32_t low = (uint32_t)best, row = low >> 9, col = low & 511u;
-            const uint32_t split = geo & 7u;
-            c = row * db.y + col;
-            chi2 = (uint32_t)(best >> 32);
-            uint32_t digit[N_LAYERS];
-            uint32_t rem = col;
-#pragma unroll
-            for (int l = N_LAYERS - 1; l >= 0; --l) {
-                if ((uint32_t)l + 1u == split) rem = row;   // the prefix layers take the row
-                const uint32_t nl = nhit_of(packed, l);
-                const uint32_t np = (nl && !(cfg.xft_pairs && l == N_LAYERS - 1)) ? nl : 1u;
-                const uint32_t qd = div_by(rem, np, kDivMagic[np]);
-                digit[l] = rem - qd * np;
-                rem = qd;
-            }
-            if (cfg.xft_pairs) digit[N_LAYERS - 1] = digit[N_LAYERS - 2];   // the pair's own index
-            // every load first, with no branch between them (a layer without
-            // hits reads the road's header word and discards it), so that a
-            // thread waits for memory once
-            const size_t cs = (size_t)rd_sector(da.z) * 64 + ((geo >> 13) & 63u);
-            uint32_t hw[N_LAYERS];
-            uint32_t off = da.x + 1;   // first hit word of layer l (hits are sorted by layer)
-#pragma unroll
-            for (int l = 0; l < N_LAYERS; ++l) {
-                const uint32_t nl = nhit_of(packed, l);
-                hw[l] = __ldg(words + (nl ? off + digit[l] : da.x));
-                off += nl;
-            }
-            int32_t f[3][N_LAYERS], qk[3];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                qk[k] = __ldg(q + cs * 6 + k);
-#pragma unroll
-                for (int l = 0; l < N_LAYERS; ++l) f[k][l] = __ldg(F + cs * 36 + k * 6 + l);
-            }
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                long long acc = (long long)qk[k] * (1ll << cfg.qshift);
-#pragma unroll
-                for (int l = 0; l < N_LAYERS; ++l) {
-                    const int32_t x = nhit_of(packed, l) ? (int32_t)hit_coord(hw[l]) : 0;
-                    acc += (long long)f[k][l] * (long long)x;
-                }
-                p[k] = (int32_t)(acc >> cfg.oshift);   // floor
-            }
-            n_pass += 1;
-        }
-        uint32_t *o = out + (size_t)r * 6;
-        o[0] = rd_id(da.z) | (flags << 24);
-        o[1] = c;
-        o[2] = chi2;
-        o[3] = (uint32_t)p[0];
-        o[4] = (uint32_t)p[1];
-        o[5] = (uint32_t)p[2];
-    }
+    flush();
     n_pass = __reduce_add_sync(0xffffffffu, n_pass);
-    if ((threadIdx.x & 31) == 0 && n_pass)
+    if (lane == 0 && n_pass)
         atomicAdd((unsigned long long *)(counts + 3), (unsigned long long)n_pass);
 }
 
 }  // namespace
 
-size_t fit_smem_bytes(int warps_per_block) { return sizeof(WarpSmem) * (size_t)warps_per_block; }
+size_t fit_smem_bytes(int warps_per_block) {
+    return (sizeof(WarpSmem) + sizeof(RecordList)) * (size_t)warps_per_block;
+}
 
 int fit_persistent_blocks_per_sm(int warps_per_block) {
     const size_t smem = fit_smem_bytes(warps_per_block);
@@ -619,28 +658,19 @@ cudaError_t launch_fit_persistent(const uint32_t *words, const uint64_t *event_o
                                   const RoadDesc *desc, uint64_t *counts, uint64_t road_cap,
                                   const int16_t *F, const int16_t *q, const svt_config cfg,
                                   const FusedRoads fr, uint32_t roads_per_chunk, bool pair_small,
-                                  unsigned long long *status, int warps_per_block, int grid,
-                                  cudaStream_t st) {
+                                  uint32_t *out, unsigned long long *status,
+                                  int warps_per_block, int grid, cudaStream_t st) {
     const size_t smem = fit_smem_bytes(warps_per_block);
     const bool guarded = cfg.chi2_cut < 32767u * 32767u;
     auto launch = [&](auto kernel) {
         launch_after(kernel, grid, warps_per_block * 32, smem, st, words, event_off, dims,
-                     event_road, desc, counts, road_cap, F, q, cfg, fr, roads_per_chunk, status);
+                     event_road, desc, counts, road_cap, F, q, cfg, fr, roads_per_chunk, out,
+                     status);
     };
     if (guarded)
         pair_small ? launch(k_fit_persistent<true, true>) : launch(k_fit_persistent<true, false>);
     else
         pair_small ? launch(k_fit_persistent<false, true>) : launch(k_fit_persistent<false, false>);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_format_fused(const uint32_t *words, const RoadDesc *desc,
-                                const unsigned long long *key, uint64_t *counts,
-                                uint64_t road_cap, const int16_t *F, const int16_t *q,
-                                const svt_config cfg, uint32_t *out,
-                                const unsigned long long *status, int grid, cudaStream_t st) {
-    launch_after(k_format_fused, grid, FORMAT_THREADS, 0, st, words, desc, key, counts, road_cap,
-                 F, q, cfg, out, status);
     return cudaGetLastError();
 }
 

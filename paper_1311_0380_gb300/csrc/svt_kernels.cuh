@@ -131,6 +131,7 @@ __device__ __forceinline__ RoadDesc make_road_desc(uint32_t rw, uint32_t packed,
 struct BigList {
     uint32_t *road;                // split road of each slot
     uint32_t *item_off;            // its first work item
+    uint32_t *pending;             // its items not yet finished
     unsigned long long *reserve;   // (items << 32) | roads appended so far
     uint32_t *counters;            // [0] items taken, [1] roads taken
 };
@@ -138,9 +139,9 @@ struct BigList {
 // Fused-path outputs of the road extraction (desc == nullptr: plain path).
 struct FusedRoads {
     RoadDesc *desc;            // per road
-    unsigned long long *key;   // per road: best key of the fit (UINT64_MAX: none
-                               // passed), set to UINT64_MAX for split roads by
-                               // the road extraction and lowered by their items
+    unsigned long long *key;   // per split road: best key so far (UINT64_MAX:
+                               // none passed), set by the road extraction and
+                               // lowered by the road's items
     BigList bl;                // split roads
     uint32_t rows;             // rows per item
     uint32_t small_max;        // roads above this many combinations are split
@@ -223,15 +224,8 @@ cudaError_t launch_fit_persistent(const uint32_t *words, const uint64_t *event_o
                                   const RoadDesc *desc, uint64_t *counts, uint64_t road_cap,
                                   const int16_t *F, const int16_t *q, const svt_config cfg,
                                   const FusedRoads fr, uint32_t roads_per_chunk, bool pair_small,
-                                  unsigned long long *status, int warps_per_block, int grid,
-                                  cudaStream_t st);
-// K5: the record of every road from its best key (thread per road); counts[3]
-// receives the number of roads that passed.
-cudaError_t launch_format_fused(const uint32_t *words, const RoadDesc *desc,
-                                const unsigned long long *key, uint64_t *counts,
-                                uint64_t road_cap, const int16_t *F, const int16_t *q,
-                                const svt_config cfg, uint32_t *out,
-                                const unsigned long long *status, int grid, cudaStream_t st);
+                                  uint32_t *out, unsigned long long *status,
+                                  int warps_per_block, int grid, cudaStream_t st);
 int fit_persistent_blocks_per_sm(int warps_per_block);
 size_t fit_smem_bytes(int warps_per_block);
 

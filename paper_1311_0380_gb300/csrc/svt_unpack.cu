@@ -538,6 +538,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
                     fr.bl.road[j] = (uint32_t)(tile_base + rl);
                     fr.bl.item_off[j] = item0 + it_ex;
                     fr.key[tile_base + rl] = ~0ull;
+                    fr.bl.pending[j] = it;
                     big_ex += 1;
                     it_ex += it;
                 }
