@@ -714,16 +714,19 @@ def main():
             ((0, "int32_add3"), (1, "int32_imad"), (2, "int32_add3_imad"), (3, "fp32_fma"))}
     issue_measured = pipe["fp32_fma"] / 32 / 1e9
     fit_mean_s = statistics.mean(fit_ms) / 1e3
+    profiled = args.workload == "scaled" and args.events == 3000
     achieved = fits_per_step * OPS_PER_FIT / fit_mean_s / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
-                "frac": achieved / ALU_PEAK_TOPS, "traffic": recorded_traffic(),
+                "frac": achieved / ALU_PEAK_TOPS,
+                # the ncu figures were taken on the scaled workload at 3000 events
+                "traffic": recorded_traffic() if profiled else None,
                 "kernel": "k_fit_persistent", "ops_per_fit": OPS_PER_FIT,
                 "fit_kernel_ms": statistics.mean(fit_ms),
                 "peak_source": "derived: 152 SM x 128 int32 lanes x 2.07 GHz",
                 "measured_tlanes_per_s": {k: v / 1e12 for k, v in pipe.items()}}
     # the kernel's own bound: warp instructions it issues (per combination,
     # from the committed ncu summary) against the schedulers' issue rate
-    ipf = recorded_profile("warp_instructions_per_fit")
+    ipf = recorded_profile("warp_instructions_per_fit") if profiled else None
     if ipf is not None:
         ach = ipf * fits_per_step / fit_mean_s / 1e9
         roofline["issue"] = {

@@ -68,6 +68,7 @@ using HalfSmem = RoadSmem<8, 16, 16>;
 static_assert(2 * sizeof(HalfSmem) <= sizeof(WarpSmem), "two half slots fit in a warp slot");
 static_assert(sizeof(HalfSmem) % 16 == 0, "half slots keep 16-byte alignment");
 static_assert(sizeof(WarpSmem) % 16 == 0, "warp slots keep 16-byte alignment");
+static_assert(sizeof(WarpSmem) >= 32 * 6 * sizeof(uint32_t), "a road slot holds 32 records");
 
 // Roads a warp has finished but whose records it has not yet written: when 31
 // or 32 are listed (and when the warp runs out of work) each lane writes one
@@ -409,8 +410,9 @@ __device__ __forceinline__ RoadDesc shfl_desc(const uint4 &da, const uint4 &db, 
     return D;
 }
 
-// Record of road r from its best key, formed by one lane (the warps of the
-// fit kernel hand their finished roads out one per lane, see RecordList).
+// Record of road r from its best key (six words into w), formed by one lane
+// (the warps of the fit kernel hand their finished roads out one per lane,
+// see RecordList).
 // For a road that passed, the hits of its best combination are the digits of
 // c = row * NB + column in the radices n'_l (the column's digits for the
 // suffix layers, the row's for the prefix layers), and the parameters
@@ -419,12 +421,12 @@ __device__ __forceinline__ RoadDesc shfl_desc(const uint4 &da, const uint4 &db, 
 // is issued before any is used, with no branch between them (a layer without
 // hits reads the road's header word and discards it).  Returns whether the
 // road passed.
-__device__ __forceinline__ bool write_record(const uint32_t *__restrict__ words,
-                                             const RoadDesc *__restrict__ desc, uint32_t r,
-                                             unsigned long long best,
-                                             const int16_t *__restrict__ F,
-                                             const int16_t *__restrict__ q,
-                                             const svt_config &cfg, uint32_t *out) {
+__device__ __forceinline__ bool form_record(const uint32_t *__restrict__ words,
+                                            const RoadDesc *__restrict__ desc, uint32_t r,
+                                            unsigned long long best,
+                                            const int16_t *__restrict__ F,
+                                            const int16_t *__restrict__ q,
+                                            const svt_config &cfg, uint32_t *w) {
     const uint4 da = __ldg(&desc[r].a), db = __ldg(&desc[r].b);
     const uint32_t geo = db.x, packed = da.y, total_hits = (geo >> 19) & 127u;
     const bool pass = best != ~0ull;
@@ -479,13 +481,12 @@ __device__ __forceinline__ bool write_record(const uint32_t *__restrict__ words,
             p[k] = (int32_t)(acc >> cfg.oshift);   // floor
         }
     }
-    uint32_t *o = out + (size_t)r * 6;
-    o[0] = rd_id(da.z) | (flags << 24);
-    o[1] = c;
-    o[2] = chi2;
-    o[3] = (uint32_t)p[0];
-    o[4] = (uint32_t)p[1];
-    o[5] = (uint32_t)p[2];
+    w[0] = rd_id(da.z) | (flags << 24);
+    w[1] = c;
+    w[2] = chi2;
+    w[3] = (uint32_t)p[0];
+    w[4] = (uint32_t)p[1];
+    w[5] = (uint32_t)p[2];
     return pass;
 }
 
@@ -525,11 +526,21 @@ __global__ void __launch_bounds__(512, 2)
     const uint32_t init_chi = cfg.chi2_cut == 0xFFFFFFFFu ? 0xFFFFFFFFu : cfg.chi2_cut + 1u;
     uint32_t n_rec = 0;    // entries of rl (uniform over the warp)
     uint32_t n_pass = 0;   // passing roads whose records this lane wrote, summed at exit
+    // Each lane forms one listed record into the warp's road slot (free
+    // between roads), then the warp stores the 6 * n_rec words with
+    // consecutive lanes on consecutive words, so that the records of
+    // consecutive roads go out as contiguous runs.
     auto flush = [&]() {
         __syncwarp();
+        uint32_t *stage = reinterpret_cast<uint32_t *>(&sm);
         if ((uint32_t)lane < n_rec &&
-            write_record(words, desc, rl.road[lane], rl.key[lane], F, q, cfg, out))
+            form_record(words, desc, rl.road[lane], rl.key[lane], F, q, cfg, stage + lane * 6))
             ++n_pass;
+        __syncwarp();
+        for (uint32_t e = (uint32_t)lane; e < n_rec * 6; e += 32) {
+            const uint32_t i = e / 6;
+            out[(size_t)rl.road[i] * 6 + (e - i * 6)] = stage[e];
+        }
         n_rec = 0;
         __syncwarp();
     };

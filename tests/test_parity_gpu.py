@@ -85,7 +85,7 @@ def test_uneven_batch_capped():
     key, rec = oracle_run(b.words, b.event_off, consts.F, consts.q, ocfg)
     st, got, _ = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "fused")
     assert_same(st, got, key, rec, "uneven")
-    assert np.mean(rec[:, 0] >> 24 & oracle.F_OVERFLOW > 0) > 0.5
+    assert np.mean(((rec[:, 0] >> 24) & oracle.F_OVERFLOW) > 0) > 0.5
 
 
 @pytest.mark.parametrize("sched", [(1, 1, 1, 1, 1), (4, 3, 7, 3, 100), (16, 1, 64, 32, 64),
@@ -100,6 +100,24 @@ def test_schedules_give_identical_results(sched):
     st, got, _ = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "fused",
                          sched=api.schedule(*sched))
     assert_same(st, got, key, rec, f"sched{sched}")
+
+
+@pytest.mark.parametrize("sched", [(1, 1, 16, 4, 4096), (1, 1, 16, 4, 4096, 1), (1, 1, 8, 1, 64),
+                                   (1, 1, 4, 3, 300, 1)])
+def test_record_lists_fill_and_flush(sched):
+    """One warp per SM, so that every warp finishes well over 32 roads: its
+    list of finished roads fills and is written out many times in the middle
+    of its work (also with two paired roads arriving at a nearly full list,
+    and with split roads retired into a full list)."""
+    from paper_1311_0380_gb300 import api
+    spec, consts, b = batch_for("scaled", 300, consts_for(512))
+    assert b.total_roads > 152 * 64
+    cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb)
+    key, rec = oracle_run(b.words, b.event_off, consts.F, consts.q, ocfg)
+    st, got, counts = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "fused",
+                              sched=api.schedule(*sched))
+    assert_same(st, got, key, rec, f"sched{sched}")
+    assert int(counts[3]) == int(np.sum(((rec[:, 0] >> 24) & oracle.F_PASS) > 0))
 
 
 def test_schedule_limits_are_checked():
@@ -363,4 +381,4 @@ def test_uneven_full_size_65536_events_sampled():
     road_pos = np.flatnonzero((b.words >> 30) == 2)[sample]
     want = oracle.run_roads(b.words, road_pos.astype(np.uint64), consts.F, consts.q, ocfg)
     assert np.array_equal(rec[sample], want)
-    assert np.mean((want[:, 0] >> 24) & oracle.F_OVERFLOW > 0) > 0.5   # mostly capped roads
+    assert np.mean(((want[:, 0] >> 24) & oracle.F_OVERFLOW) > 0) > 0.5   # mostly capped roads
