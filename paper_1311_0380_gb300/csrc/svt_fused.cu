@@ -54,8 +54,8 @@ struct RoadSmem {
     longlong2 A01[NR];              // prefix sums incl. q, rows 3, 4, per row of the chunk
     long long A5[NR];               // ... row 5
     uint32_t x[N_LAYERS * MH];      // hit coordinates [l][i] (x = 0 for an empty layer)
-    int32_t F[36];                  // F[s][m][k][l] at k*6+l
-    int32_t q[6];
+    int32_t F[36];                  // F[s][m][k][l] at k*6+l (chi rows k = 3..5 only)
+    int32_t q[6];                   // ... q[s][m][k] (k = 3..5 only)
     uint32_t n[N_LAYERS];           // n'_l = max(n_l, 1)
     uint32_t m[N_LAYERS];           // division magic of n'_l
     uint32_t off[N_LAYERS];         // index of the first hit of layer l in the road
@@ -164,14 +164,16 @@ __device__ __forceinline__ void road_setup(SM &sm, const uint32_t *__restrict__ 
                                            const int16_t *__restrict__ q, uint32_t sh,
                                            uint32_t xft, long long bias, const Lanes<W> &L) {
     constexpr uint32_t MH = SM::kMH;
-    constexpr int NFQ = (42 + W - 1) / W;   // passes over the 36 + 6 constants
+    // the chi rows k = 3..5 only (18 + 3 constants): the record's parameter
+    // rows are read from global memory by the lane that forms it
+    constexpr int NFQ = (21 + W - 1) / W;
     const uint32_t rw = D.a.x, packed = D.a.y, gl = L.gl;
     const size_t cs = (size_t)rd_sector(D.a.z) * 64 + g.mask;
     int32_t fv[NFQ];
 #pragma unroll
     for (int j = 0; j < NFQ; ++j) {
         const uint32_t e = gl + (uint32_t)W * j;
-        fv[j] = e < 36 ? __ldg(F + cs * 36 + e) : (e < 42 ? __ldg(q + cs * 6 + (e - 36)) : 0);
+        fv[j] = e < 18 ? __ldg(F + cs * 36 + 18 + e) : (e < 21 ? __ldg(q + cs * 6 + e - 15) : 0);
     }
     uint32_t hv[3];
 #pragma unroll
@@ -182,8 +184,8 @@ __device__ __forceinline__ void road_setup(SM &sm, const uint32_t *__restrict__ 
 #pragma unroll
     for (int j = 0; j < NFQ; ++j) {
         const uint32_t e = gl + (uint32_t)W * j;
-        if (e < 36) sm.F[e] = fv[j];
-        else if (e < 42) sm.q[e - 36] = fv[j];
+        if (e < 18) sm.F[18 + e] = fv[j];
+        else if (e < 21) sm.q[e - 15] = fv[j];
     }
     const uint32_t nl = gl < N_LAYERS ? nhit_of(packed, gl) : 0u;
     uint32_t incl = nl;   // inclusive prefix of the layer counts
