@@ -255,27 +255,33 @@ __global__ void __launch_bounds__(256, 8)
     }
 }
 
-// one block: loss = (sum of item partials in index order) / n, pairwise by blocks of 1024
+// one block: loss = (sum of the item partials) / n in a fixed order: thread
+// t sums items t, t + 1024, t + 2048, ... in that order (eight loads in
+// flight at a time), then the block sums the 1024 partials by a fixed tree
 __global__ void __launch_bounds__(1024)
     k_loss_final(const float *__restrict__ item_loss, const int32_t *__restrict__ n_items,
                  uint64_t n, float *loss) {
+    constexpr uint32_t B = 1024, U = 8;
     __shared__ float sm[32];
     wait_prior_grid();   // the item partials are complete (see launch_after)
     const uint32_t NI = (uint32_t)*n_items;
     float total = 0.f;
-    for (uint32_t c0 = 0; c0 < NI; c0 += 1024) {
-        float v = (c0 + threadIdx.x < NI) ? item_loss[c0 + threadIdx.x] : 0.f;
-        v = warp_sum(v);
-        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            float u = sm[threadIdx.x];
-            u = warp_sum(u);
-            if (threadIdx.x == 0) total += u;
-        }
-        __syncthreads();
+    uint32_t i = threadIdx.x;
+    for (; i + (U - 1) * B < NI; i += U * B) {
+        float v[U];
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) v[u] = item_loss[i + u * B];
+#pragma unroll
+        for (uint32_t u = 0; u < U; ++u) total += v[u];
     }
-    if (threadIdx.x == 0) *loss = n ? total / (float)n : 0.f;
+    for (; i < NI; i += B) total += item_loss[i];
+    total = warp_sum(total);
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = total;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        const float u = warp_sum(sm[threadIdx.x]);
+        if (threadIdx.x == 0) *loss = n ? u / (float)n : 0.f;
+    }
 }
 
 // per item: sum_t g_t x_t^T and sum_t g_t, where g comes from the loss
@@ -364,7 +370,15 @@ __global__ void k_grad_final(const float *__restrict__ item_grad,
     const uint32_t s = k / NPAR, j = k % NPAR;
     const uint32_t first = (uint32_t)sector_item[s], last = (uint32_t)sector_item[s + 1];
     float total = 0.f;
-    for (uint32_t m = first; m < last; ++m) total += item_grad[(size_t)m * NPAR + j];
+    uint32_t m = first;
+    for (; m + 8 <= last; m += 8) {   // eight loads in flight, added in index order
+        float v[8];
+#pragma unroll
+        for (uint32_t u = 0; u < 8; ++u) v[u] = item_grad[(size_t)(m + u) * NPAR + j];
+#pragma unroll
+        for (uint32_t u = 0; u < 8; ++u) total += v[u];
+    }
+    for (; m < last; ++m) total += item_grad[(size_t)m * NPAR + j];
     const float sc = scale * (scale_dev ? *scale_dev : 1.f);
     if (j < 36)
         dF[(size_t)s * 36 + j] = total * sc;
