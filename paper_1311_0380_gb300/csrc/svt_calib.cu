@@ -296,6 +296,9 @@ __global__ void k_grad_items(const float *__restrict__ x, const float *__restric
                              const float *__restrict__ q, const float *__restrict__ w,
                              float *item_grad, float *dx) {
     __shared__ float cs[8][48];
+    // per warp: the 32 lanes' partials, row stride NPAR + 1 (odd, so that both
+    // the row writes and the column reads are free of bank conflicts)
+    __shared__ float red_s[8][32 * (NPAR + 1)];
     allow_next_grid();   // the final reduction may be scheduled; it waits for this grid
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint32_t NI = (uint32_t)*n_items;
@@ -349,11 +352,17 @@ __global__ void k_grad_items(const float *__restrict__ x, const float *__restric
                 acc[36 + k] += g[k];
             }
         }
+        // the item's sums over the lanes: every lane writes its partials, then
+        // lane j adds column j (and j + 32) over the lanes in lane order
+        float *red = red_s[wib];
 #pragma unroll
-        for (int j = 0; j < NPAR; ++j) acc[j] = warp_sum(acc[j]);
-        if (lane == 0) {
-#pragma unroll
-            for (int j = 0; j < NPAR; ++j) item_grad[(size_t)i * NPAR + j] = acc[j];
+        for (int j = 0; j < NPAR; ++j) red[lane * (NPAR + 1) + j] = acc[j];
+        __syncwarp();
+        for (int j = lane; j < NPAR; j += 32) {
+            float total = 0.f;
+#pragma unroll 8
+            for (int m = 0; m < 32; ++m) total += red[m * (NPAR + 1) + j];
+            item_grad[(size_t)i * NPAR + j] = total;
         }
         __syncwarp();
     }
