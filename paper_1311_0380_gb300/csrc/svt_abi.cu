@@ -62,9 +62,11 @@ bool schedule_ok(const svt_schedule &s) {
            s.roads_per_chunk <= 32 && s.small_max >= 1 && s.pair_small <= 1;
 }
 
+// word tiles: up to 16 blocks of 128 threads per SM at once (grid-stride
+// over the tiles beyond)
 int tile_grid() {
     int sms = current_sm_count();
-    return (sms > 0 ? sms : 1) * 8;
+    return (sms > 0 ? sms : 1) * 16;
 }
 
 int launch_status() {

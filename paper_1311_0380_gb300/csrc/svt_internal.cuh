@@ -38,9 +38,9 @@ __device__ __forceinline__ bool status_ok(const unsigned long long *status) {
 }
 
 // ---- tiles of words ---------------------------------------------------------
-constexpr int TILE_THREADS = 256;
+constexpr int TILE_THREADS = 128;
 constexpr int TILE_PER_THREAD = 8;
-constexpr int TILE_WORDS = TILE_THREADS * TILE_PER_THREAD;  // 2048
+constexpr int TILE_WORDS = TILE_THREADS * TILE_PER_THREAD;  // 1024
 
 __host__ __device__ __forceinline__ uint64_t n_tiles(uint64_t n_words) {
     return (n_words + TILE_WORDS - 1) / TILE_WORDS;

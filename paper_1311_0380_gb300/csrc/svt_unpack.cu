@@ -1,7 +1,9 @@
 // svt_unpack.cu -- stage 1 of the paper's Sec. 2.1 ("unpacking of input data
 // and filling of all the necessary data structures") for GB300.
 //
-// The batch is cut into tiles of 2048 words.  A prologue maps every tile to
+// The batch is cut into tiles of 1024 words (128 threads x 8 words; smaller
+// tiles than 2048 words of 256 threads take 1-2 % off the step, since the
+// kernels are bound by each tile's chain of barriers and scans).  A prologue maps every tile to
 // the first event that starts in it (one pass over the event offsets).  K1
 // validates every word against its left neighbour (rules V2..V7, V9 of
 // include/svt.h's format), checks V1 for the events starting in the tile and
@@ -17,6 +19,7 @@ namespace svt {
 
 namespace {
 
+static_assert(TILE_PER_THREAD == 8, "load8 fills eight words per thread");
 __device__ __forceinline__ void load8(const uint32_t *__restrict__ words, uint64_t base,
                                       uint64_t n_words, uint32_t (&w)[TILE_PER_THREAD]) {
     if (base + TILE_PER_THREAD <= n_words) {
@@ -271,6 +274,8 @@ __global__ void __launch_bounds__(TILE_THREADS)
                    const svt_config cfg, const FusedRoads fr, uint64_t *counts,
                    unsigned long long *status) {
     constexpr int FRONT = 16, BACK = 100;
+    static_assert(TILE_THREADS >= BACK && TILE_THREADS > TILE_WORDS / 32,
+                  "one pass of the block loads the halo and covers the V8 bitmap");
     constexpr uint32_t SENTINEL = 0xC0000000u;   // an event-header word: ends every run
     __shared__ uint32_t red[TILE_THREADS / 32 + 1];
     __shared__ int redi[TILE_THREADS / 32];
