@@ -38,3 +38,15 @@ def test_version_and_workspace_sizes_need_no_gpu():
     assert L.svt_version() >= 10000
     assert L.svt_unpack_workspace_size(0) > 0
     assert L.svt_run_workspace_size(1 << 20, 1000, 50000, None) > 50000 * 20
+
+
+def test_autotune_cache_key_separates_flushed_and_back_to_back_timing():
+    """The schedule cache keys on the GPU, the workload shape and whether the
+    tuner timed every run after an L2 flush (host logic only)."""
+    from paper_1311_0380_gb300 import api, autotune
+    cfg = api.config(15, 15, 100, 4096, 5, 512)
+    a = autotune.signature(1 << 20, 3000, 191300, cfg)
+    b = autotune.signature(1 << 20, 3000, 191300, cfg, flushed=True)
+    assert a != b and a.endswith("|l0") and b.endswith("|l1")
+    assert autotune.signature((1 << 20) + 5, 3000, 191300, cfg) == a   # same powers of two
+    assert autotune.signature(1 << 21, 3000, 191300, cfg) != a
