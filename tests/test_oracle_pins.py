@@ -217,7 +217,8 @@ def test_validation_cases():
     data = json.load(open(os.path.join(GOLDEN, "validation_cases.json")))
     for case in data["cases"]:
         words = tokens_to_words(case["words"])
-        key = oracle.validate(words, np.array(case["offsets"], np.uint64), case["n_sectors"])
+        key = oracle.validate(words, np.array(case["offsets"], np.uint64), case["n_sectors"],
+                              xft_pairs=case.get("xft_pairs", 0))
         got = oracle.decode_key(key)
         exp = None if case["expect"] is None else tuple(case["expect"])
         assert got == exp, case["name"]
