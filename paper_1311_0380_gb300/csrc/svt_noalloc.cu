@@ -6,8 +6,10 @@
 // and failure modes) once data taking has started, or a host program that
 // links this library without a device allocator of its own.  For them this
 // entry point takes its scratch from one fixed array that lives in the
-// library itself: every GPU that loads the library holds the array until the
-// process exits, and every call on that GPU shares it.
+// library itself.  The array is reserved on a device when this code is
+// loaded there -- under CUDA's default lazy module loading, at the first
+// svt_run_noalloc call on that device -- and held until the process exits;
+// every call on that device shares it.
 #include <mutex>
 
 #include "svt_kernels.cuh"
@@ -21,23 +23,27 @@ constexpr size_t kScratchBytes = (size_t)32 << 20;   // 32 MiB per device
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
-void *g_scratch_ptr[kMaxDevices];
-int g_scratch_rc[kMaxDevices];
-std::once_flag g_scratch_once[kMaxDevices];
+void *g_scratch_ptr[kMaxDevices];   // null until a lookup on that device succeeds
+std::mutex g_scratch_mu;
 
-// Device address of the scratch on the current device, looked up once per
-// device (the first call on a device does this set-up).
+// Device address of the scratch on the current device.  Only a successful
+// lookup is kept: a failed one (for example a first call made while the
+// stream is being captured, when the module cannot be loaded) leaves the
+// slot empty, clears the error and is tried again on the next call.
 int scratch_address(void **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SVT_ERR_CUDA;
-    std::call_once(g_scratch_once[dev], [dev] {
+    std::lock_guard<std::mutex> g(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
         void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        g_scratch_ptr[dev] = e == cudaSuccess ? p : nullptr;
-        g_scratch_rc[dev] = e == cudaSuccess ? SVT_OK : SVT_ERR_CUDA;
-    });
+        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return SVT_ERR_CUDA;
+        }
+        g_scratch_ptr[dev] = p;
+    }
     *out = g_scratch_ptr[dev];
-    return g_scratch_rc[dev];
+    return SVT_OK;
 }
 
 }  // namespace

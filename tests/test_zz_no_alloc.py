@@ -3,13 +3,15 @@ memory (a front-end that only gets device pointers from the GPU's owner, a
 real-time loop that must not allocate once data taking has started, a host
 program without a device allocator): its scratch is a fixed array inside the
 library.  Its records, status and counts must equal svt_run's on the same
-input, on two calls in a row (the array keeps the previous call's contents).
+input, on two calls in a row (the array keeps the previous call's contents),
+and its records must equal the oracle's.
 
 Kept in a file of its own that pytest collects last.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_1311_0380_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -57,6 +59,10 @@ def test_noalloc_matches_svt_run_on_two_calls_in_a_row():
         assert np.array_equal(got[1], ref[1])
         assert np.array_equal(got[2], ref[2])
         assert np.array_equal(got[3], ref[3])
+        key, want = oracle.run(batch.words, batch.event_off, consts.F, consts.q,
+                               oracle.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5,
+                                             spec.n_sectors), omp=True)
+        assert key == oracle.KEY_OK and np.array_equal(got[1], want)
 
 
 def test_noalloc_refuses_a_batch_larger_than_its_scratch():
