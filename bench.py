@@ -46,6 +46,7 @@ ISSUE_PEAK_GINST = N_SM * 4 * SM_MAX_GHZ
 FIT_KERNEL_SRC = [os.path.join(ROOT, "paper_1311_0380_gb300", "csrc", f)
                   for f in ("svt_fused.cu", "svt_kernels.cuh")]
 TRAFFIC_NOTE = os.path.join(ROOT, "profiles", "fit_persistent_scaled3000.md")
+UNEVEN_NOTE = os.path.join(ROOT, "profiles", "fit_persistent_uneven512.md")
 
 
 def parse_args():
@@ -64,6 +65,8 @@ def parse_args():
     ap.add_argument("--serve-short", action="store_true",
                     help="serve 30k and 100k events instead of 10 s at 30 kHz and 1M at 300 kHz")
     ap.add_argument("--no-calib", action="store_true", help="skip the FP32 calibration measurement")
+    ap.add_argument("--no-uneven", action="store_true",
+                    help="skip the full-size uneven workload (65536 events per launch)")
     ap.add_argument("--no-tune", action="store_true", help="use the default schedule")
     ap.add_argument("--sweep", action="store_true",
                     help="latency against the number of fits for the paper-shape workload "
@@ -123,12 +126,12 @@ def file_sha(paths):
     return h.hexdigest()[:16]
 
 
-def recorded_profile(key):
-    """A figure of the fit kernel from the committed ncu summary (`key: value
+def recorded_profile(key, note=TRAFFIC_NOTE):
+    """A figure of the fit kernel from a committed ncu summary (`key: value
     kernel_sha: sha`), or None when the summary is absent or the kernel source
     changed since."""
     try:
-        text = open(TRAFFIC_NOTE).read()
+        text = open(note).read()
     except OSError:
         return None
     m = re.search(key + r":\s*([0-9.eE+]+)\s+kernel_sha:\s*([0-9a-f]+)", text)
@@ -251,6 +254,27 @@ def cpu_baseline(spec, consts, batch, budget_s=12.0):
             "seconds": round(dt, 3)}
 
 
+def cpu_baseline_omp(spec, consts, batch):
+    """The same oracle with one event per OpenMP thread on every host core
+    (how the paper ran the event loop on the many-core coprocessor), over the
+    whole batch."""
+    import oracle
+    cfg = oracle.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, spec.n_sectors,
+                        int(spec.xft))
+    fits = int(batch.combinations(spec.max_comb).sum())
+    oracle.run(batch.words[: int(batch.event_off[min(50, batch.n_events)])],
+               batch.event_off[: min(50, batch.n_events) + 1], consts.F, consts.q, cfg, omp=True)
+    t0 = time.perf_counter()
+    key, _ = oracle.run(batch.words, batch.event_off, consts.F, consts.q, cfg, omp=True)
+    dt = time.perf_counter() - t0
+    assert key == oracle.KEY_OK
+    return {"value": fits / dt, "unit": UNIT, "cores": oracle.num_threads(),
+            "nproc": os.cpu_count(), "kind": "oracle",
+            "sample": f"all {batch.n_events} events ({fits} fits), C oracle, one event per "
+                      "OpenMP thread, one pass",
+            "seconds": round(dt, 3)}
+
+
 CALIB_TRACKS = 1 << 20
 
 
@@ -334,10 +358,15 @@ def serving(dev, short=False):
     log-uniform in 1..2048, 1-16 hits per layer, 4096 combinations per road at
     most) at 30 kHz and 300 kHz through the continuous-batching server
     (fused path, 4 slots, CUDA graphs), and the plain per-stage path served one
-    batch at a time at 30 kHz beside it.  Latency = submission to completion,
-    H2D and D2H included.  Each rate runs 10 s or 1M events, whichever comes
-    first (300,000 events at 30 kHz, 1,000,000 at 300 kHz); `short` runs
-    30,000 and 100,000."""
+    batch at a time at the same two rates beside it.  Latency = scheduled
+    arrival to delivery of the event's result, H2D and D2H included.  The fused
+    server runs 10 s or 1M events per rate, whichever comes first (300,000
+    events at 30 kHz, 1,000,000 at 300 kHz; `short` runs 30,000 and 100,000);
+    the plain server 30,000 events per rate.  Every row carries the server's
+    queue and batching counters and, from a host-side trace of every batch,
+    the longest wait of a batch's first event before dispatch; a further
+    300 kHz run with device timestamps gives the fraction of batches whose
+    device work overlaps another slot's."""
     from paper_1311_0380_gb300 import api, serve, synth
     consts = synth.make_constants(512)
     pool_b = synth.make_batch("uneven", 1024, consts, seed=synth.BASE_SEED + 4)
@@ -348,18 +377,42 @@ def serving(dev, short=False):
     dc = api.DeviceConstants.from_numpy(consts.F, consts.q, cfg, dev)
     out = {"events": "uneven-shaped, pool of 1024 distinct events cycled",
            "mean_words_per_event": float(len(pool_b.words) / pool_b.n_events),
-           "mean_fits_per_event": float(fits_ev.mean())}
+           "mean_fits_per_event": float(fits_ev.mean()),
+           "latency": "from each event's scheduled Poisson arrival to the delivery of its result"}
 
-    def run(srv, rate, n):
+    def run(srv, rate, n, device_times=False):
+        srv.reset_stats()
+        srv.trace_start(1 << 21, device_times=device_times)
         lat, wall = srv.bench_poisson(pool, pool_b.event_off, rate, n, seed=7)
+        tr = srv.trace_stop()
+        st = srv.stats()
         ok = lat != np.uint64(2 ** 64 - 1)
         us = lat[ok].astype(np.float64) / 1e3
         reps, rest = divmod(n, pool_b.n_events)
         fits = float(reps * fits_ev.sum() + fits_ev[:rest].sum())
-        return {"rate_hz": rate, "events": n, "failed": int((~ok).sum()),
-                "p50_us": float(np.percentile(us, 50)), "p99_us": float(np.percentile(us, 99)),
-                "p999_us": float(np.percentile(us, 99.9)), "events_per_s": n / wall,
-                "fits_per_s": fits / wall, "wall_s": wall}
+        nb = max(int(st["batches"]), 1)
+        row = {"rate_hz": rate, "events": n, "failed": int((~ok).sum()),
+               "p50_us": float(np.percentile(us, 50)), "p99_us": float(np.percentile(us, 99)),
+               "p999_us": float(np.percentile(us, 99.9)), "max_us": float(us.max()),
+               "events_per_s": n / wall, "fits_per_s": fits / wall, "wall_s": wall,
+               "kept_up": bool(n / wall >= 0.99 * rate),
+               "batches": int(st["batches"]), "events_per_batch": n / nb,
+               "max_batch_events": int(st["max_batch_events"]),
+               "max_queue_depth": int(st["max_queued"]),
+               "dispatch_us_per_batch": st["launch_ns"] / 1e3 / nb,
+               "deliver_us_per_batch": st["finish_ns"] / 1e3 / nb,
+               "events_over_1ms": int((us > 1000).sum())}
+        if len(tr):
+            wait = (tr["t_dispatch_ns"] - tr["t_first_arrive_ns"]) / 1e3
+            k = int(np.argmax(wait))
+            row["longest_wait_us"] = float(wait[k])
+            row["longest_wait_at_s"] = float((tr["t_dispatch_ns"][k] - tr["t_dispatch_ns"][0]) / 1e9)
+            row["queue_after_dispatch_max"] = int(tr["queued_after"].max())
+            if device_times:
+                dev_us = tr["dev_end_us"] - tr["dev_start_us"]
+                row["overlap_fraction"] = serve.overlap_fraction(tr)
+                row["device_us_per_batch_p50"] = float(np.percentile(dev_us, 50))
+        return row
 
     # one road per chunk of the fit's work queue; batches of up to four events
     # replay a second graph with one persistent block per SM
@@ -369,13 +422,15 @@ def serving(dev, short=False):
     out["fused_schedule"] = dict({f: getattr(sched, f) for f, _ in api.SvtSchedule._fields_},
                                  small_batch_events=4, small_blocks_per_sm=1)
     n30, n300 = (30000, 100000) if short else (300000, 1000000)
+    run(srv, 30e3, 3000)   # warm-up
     out["fused_graph_4slots"] = [run(srv, 30e3, n30), run(srv, 300e3, n300)]
-    st = srv.stats()
-    out["fused_graph_4slots_stats"] = {k: st[k] for k in ("batches", "h2d_bytes", "d2h_bytes")}
+    out["fused_300khz_device_trace"] = run(srv, 300e3, 100000, device_times=True)
     srv.close()
-    plain = serve.Server(dc, n_slots=1, max_words=1 << 20, max_events=64, max_roads=1 << 14,
-                         mode=1, max_combs=(1 << 14) * 4096)
-    out["plain_per_batch"] = [run(plain, 30e3, 300)]
+    # the plain per-stage path, one batch in flight at a time
+    plain = serve.Server(dc, n_slots=1, max_words=1 << 22, max_events=256, max_roads=1 << 17,
+                         mode=1, max_combs=(1 << 17) * 4096)
+    run(plain, 30e3, 300)   # warm-up
+    out["plain_per_batch"] = [run(plain, 30e3, 30000), run(plain, 300e3, 30000)]
     plain.close()
     return out
 
@@ -623,21 +678,93 @@ def end_to_end(args, spec, consts, dconst, sched, rank, world, dev, barrier):
         h2d += bi
         d2h += bo
         used.append(k)
-    st, _ = runner.wait()
+    st, rec = runner.wait()
     barrier()
-    assert st == api.N.STATUS_OK
-    last = runner.paths[(runner.i - 1) % runner.depth]
-    assert int(api.u64(last.counts)[2]) == slices[used[-1]][3]   # evaluated combinations
+    assert st == api.N.STATUS_OK and len(rec) == slices[used[-1]][2]
     total_ms = marks[0][0].elapsed_time(marks[-1][1])
     lat = [a.elapsed_time(b) * 1e3 for a, b in marks]
     job_ms, (job_fits,) = reduce_over_ranks(world, total_ms, [fits], dev)
     return {"value": job_fits / (job_ms / 1e3), "unit": UNIT,
             "h2d_bytes_per_step": int(h2d // steps), "d2h_bytes_per_step": int(d2h // steps),
             "p50_us": percentile(lat, 50), "p99_us": percentile(lat, 99),
-            "inputs": f"{E2E_POOL_SLICES} distinct {n_ev}-event batches "
-                      f"({4 * h_pool.numel() / 1e6:.0f} MB) cycled, copied from pinned host memory "
-                      "every step; copy-in, compute and copy-out of consecutive steps overlap",
+            "inputs": f"svt_run_host (C entry: H2D, fused path, D2H on one stream) on two "
+                      f"alternating streams; {E2E_POOL_SLICES} distinct {n_ev}-event batches "
+                      f"({4 * h_pool.numel() / 1e6:.0f} MB) cycled from pinned host memory, each "
+                      "step copying its own batch in and its records and status out",
             "ms_per_step": job_ms / steps, "steps": steps}
+
+
+UNEVEN_EVENTS = 65536
+
+
+def uneven_full(dev, flush, timer, steps=5, warmup=2):
+    """The uneven workload at its full size: 65536 events per launch (16
+    copies of a 4096-event draw; roads log-uniform in 1..2048, 1-16 hits per
+    layer, 4096 combinations per road at most), through the fused path
+    replayed from a CUDA graph, in the schedule the autotuner picks on the
+    4096-event draw (every run timed after an L2 flush), the L2 flushed
+    between steps as well."""
+    import torch
+    from paper_1311_0380_gb300 import api, autotune, synth
+    spec = synth.SPECS["uneven"]
+    consts = synth.make_constants(spec.n_sectors)
+    base = synth.make_batch(spec, TILE_DRAW, consts, seed=spec.seed)
+    b = synth.tile_batch(base, UNEVEN_EVENTS // TILE_DRAW)
+    cfg = api.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, spec.n_sectors)
+    dc = api.DeviceConstants.from_numpy(consts.F, consts.q, cfg, dev)
+    stream = torch.cuda.current_stream()
+    fp0 = api.FusedPath(len(base.words), base.n_events, base.total_roads, dc, None, dev)
+    w0, o0 = api.to_device_u32(base.words, dev), api.to_device_u64(base.event_off, dev)
+    sched, tune_ms = autotune.tuned_schedule(fp0, w0, len(base.words), o0, base.n_events,
+                                             cache=None, reps=2, flush=flush)
+    del fp0, w0, o0
+    n_words, n_events, R = len(b.words), b.n_events, b.total_roads
+    fp = api.FusedPath(n_words, n_events, R, dc, sched, dev)
+    d_words, d_off = api.to_device_u32(b.words, dev), api.to_device_u64(b.event_off, dev)
+    g = api.GraphPath(fp, d_words, d_off)
+    g.set_sizes(n_words, n_events)
+    for _ in range(warmup):
+        g.launch(stream)
+    torch.cuda.synchronize()
+    st, rec, counts = fp.result()
+    assert st == api.N.STATUS_OK and int(counts[0]) == R
+    fits = int(counts[2])
+    assert fits == int(b.combinations(spec.max_comb).sum())
+    blocks = rec.reshape(UNEVEN_EVENTS // TILE_DRAW, base.total_roads, 6)
+    assert all(np.array_equal(blocks[k], blocks[0]) for k in range(1, len(blocks)))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(i)
+        ev[i][0].record(stream)
+        g.launch(stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(c) for a, c in ev]
+    fit_ms = []
+    for i in range(2):
+        flush.fill_(i)
+        fp.run(d_words, n_words, d_off, n_events, timer=timer)
+        fit_ms.append(timer.fit_ms())
+    g.close()
+    step_s = statistics.mean(ms) / 1e3
+    fit_s = statistics.mean(fit_ms) / 1e3
+    out = {"workload": f"uneven-{UNEVEN_EVENTS}ev", "events": n_events, "roads": R,
+           "fits_per_step": fits, "steps": steps, "ms_per_step": step_s * 1e3,
+           "fits_per_s": fits / step_s, "events_per_s": n_events / step_s,
+           "fit_kernel_ms": fit_s * 1e3, "launch": "CUDA graph of the five-kernel sequence",
+           "schedule": {f: getattr(sched, f) for f, _ in api.SvtSchedule._fields_},
+           "tuned_on": f"{TILE_DRAW}-event draw, {tune_ms:.3f} ms per run",
+           "l2": "flushed between steps (256 MB write)",
+           "check": "status OK, evaluated combinations equal the closed form, all copies equal"}
+    ipf = recorded_profile("warp_instructions_per_fit_uneven", UNEVEN_NOTE)
+    if ipf is not None:
+        ach = ipf * fits / fit_s / 1e9
+        out.update({"warp_instructions_per_fit": ipf, "issue_ginst_s": ach,
+                    "issue_frac": ach / ISSUE_PEAK_GINST})
+    del fp, d_words, d_off
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -715,37 +842,55 @@ def main():
     value = job_fits / (total_ms / 1e3)
     clock_summary = clocks.summary()
 
-    # ---- roofline of the persistent fit kernel (ALU / issue bound).  The peak
-    # is derived from the unit counts and the clock; beside it, what this GPU
-    # measurably sustains (svt_pipe_peak: int32 3-input adds, multiply-adds,
-    # both, and the fp32 FMA stream that shows the schedulers' issue rate)
+    # ---- roofline of the persistent fit kernel.  It is bound by instruction
+    # issue: the headline fraction is its warp instructions per second (the
+    # instructions per combination from the committed ncu summary x the
+    # combinations of a step / the kernel's time) against 152 SMs x 4
+    # schedulers x 2.07 GHz.  Beside it: what the GPU measurably sustains
+    # (svt_pipe_peak: int32 3-input adds, multiply-adds, both, and the fp32
+    # FMA stream that shows the schedulers' issue rate), the algorithmic
+    # throughput in direct-form operations (57 per combination; the kernel
+    # shares partial sums and executes far fewer, so this is not a
+    # utilisation) and the HBM traffic against the measured copy bandwidth.
     pipe = {name: api.pipe_peak(mode)[0] for mode, name in
             ((0, "int32_add3"), (1, "int32_imad"), (2, "int32_add3_imad"), (3, "fp32_fma"))}
     issue_measured = pipe["fp32_fma"] / 32 / 1e9
     fit_mean_s = statistics.mean(fit_ms) / 1e3
     profiled = args.workload == "scaled" and args.events == 3000
-    achieved = fits_per_step * OPS_PER_FIT / fit_mean_s / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
-                "frac": achieved / ALU_PEAK_TOPS,
-                # the ncu figures were taken on the scaled workload at 3000 events
-                "traffic": recorded_traffic() if profiled else None,
-                "kernel": "k_fit_persistent", "ops_per_fit": OPS_PER_FIT,
-                "fit_kernel_ms": statistics.mean(fit_ms),
-                "peak_source": "derived: 152 SM x 128 int32 lanes x 2.07 GHz",
-                "measured_tlanes_per_s": {k: v / 1e12 for k, v in pipe.items()}}
-    # the kernel's own bound: warp instructions it issues (per combination,
-    # from the committed ncu summary) against the schedulers' issue rate
+    algorithmic_tops = fits_per_step * OPS_PER_FIT / fit_mean_s / 1e12
+    traffic = recorded_traffic() if profiled else None
     ipf = recorded_profile("warp_instructions_per_fit") if profiled else None
+    hbm_peak = measured_hbm_peak()
     if ipf is not None:
         ach = ipf * fits_per_step / fit_mean_s / 1e9
-        roofline["issue"] = {
-            "warp_instructions_per_fit": ipf, "achieved_ginst_s": ach,
-            "peak_ginst_s": ISSUE_PEAK_GINST, "frac": ach / ISSUE_PEAK_GINST,
-            "peak_source": "derived: 152 SM x 4 schedulers x 2.07 GHz",
-            "measured_peak_ginst_s": issue_measured, "frac_of_measured": ach / issue_measured,
-            "measured_source": "svt_pipe_peak fp32 FMA stream / 32 lanes"}
+        roofline = {"bound": "alu", "achieved": ach, "peak": ISSUE_PEAK_GINST,
+                    "unit": "G warp-instructions/s", "frac": ach / ISSUE_PEAK_GINST,
+                    "peak_source": "derived: 152 SM x 4 schedulers x 2.07 GHz (issue rate)",
+                    "warp_instructions_per_fit": ipf,
+                    "frac_of_measured_issue": ach / issue_measured}
     else:
-        roofline["issue"] = None
+        # no ncu figure for this kernel source and workload: the direct-form
+        # algorithmic rate against the int32 unit count, labelled as such
+        roofline = {"bound": "alu", "achieved": algorithmic_tops, "peak": ALU_PEAK_TOPS,
+                    "unit": "Tops/s", "frac": algorithmic_tops / ALU_PEAK_TOPS,
+                    "peak_source": "derived: 152 SM x 128 int32 lanes x 2.07 GHz; achieved = "
+                                   "57 direct-form ops per combination, not a utilisation"}
+    roofline.update({
+        "traffic": traffic, "kernel": "k_fit_persistent", "fit_kernel_ms": fit_mean_s * 1e3,
+        "algorithmic_tops": algorithmic_tops, "ops_per_fit": OPS_PER_FIT,
+        "measured_issue_ginst_s": issue_measured,
+        "measured_int32_add3_tlanes_s": pipe["int32_add3"] / 1e12,
+        "measured_int32_imad_tlanes_s": pipe["int32_imad"] / 1e12,
+        "measured_int32_mixed_tlanes_s": pipe["int32_add3_imad"] / 1e12,
+        "measured_fp32_fma_tlanes_s": pipe["fp32_fma"] / 1e12,
+        "hbm_gbs": (traffic / fit_mean_s / 1e9) if traffic else None,
+        "hbm_frac": (traffic / fit_mean_s / 1e9 / hbm_peak) if traffic else None,
+        "hbm_peak_gbs": hbm_peak})
+
+    # ---- the uneven workload at its full size (65536 events per launch)
+    uneven = None
+    if rank == 0 and not args.no_uneven and args.workload == "scaled":
+        uneven = uneven_full(dev, flush, timer)
 
     # ---- end to end from pinned host memory (fused, copies overlapped with compute)
     e2e = None
@@ -810,9 +955,10 @@ def main():
     if rank == 0 and not args.no_calib:
         calib_out = calibration(dev)
 
-    cpu = None
+    cpu = cpu_omp = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(spec, consts, batch)
+        cpu_omp = cpu_baseline_omp(spec, consts, batch)
 
     if rank == 0:
         line = {
@@ -831,6 +977,7 @@ def main():
             "latency_us": {"p50": percentile([m * 1e3 for m in step_ms], 50),
                            "p99": percentile([m * 1e3 for m in step_ms], 99)},
             "e2e": e2e, "plain": plain, "roofline": roofline, "cpu_baseline": cpu,
+            "cpu_baseline_omp": cpu_omp, "uneven": uneven,
             "serving": serve_out,
             "calibration": calib_out,
             "clocks": clock_summary,

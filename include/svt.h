@@ -368,6 +368,39 @@ int svt_graph_launch(svt_graph graph, void *stream);
 int svt_graph_destroy(svt_graph graph);
 
 /* ======================================================================
+ * End to end from host memory: the batch's words and offsets copied in, the
+ * fused path, the records and the status copied out -- every step enqueued
+ * on `stream`, in that order (the trigger node's "data in -> GPU -> data
+ * out" loop of Sec. 3 and Sec. 4.2 as one call).
+ *   h_words[n_words], h_event_off[n_events+1]  host input; pinned memory
+ *                      makes the copies asynchronous (pageable memory is
+ *                      copied before the call returns)
+ *   d_F, d_q, cfg, road_cap, sched   as for svt_run
+ *   h_out[6*road_cap]  host, out: the records (valid once the stream has
+ *                      completed the call's work)
+ *   h_status[1]        host, out: the validation key, likewise
+ *   n_records          host, out (may be NULL): records written to h_out,
+ *                      the road count the event headers state (read on the
+ *                      host before the call returns), at most road_cap
+ *   d_workspace        svt_run_host_workspace_size(n_words, n_events,
+ *                      road_cap, sched) bytes of device memory, 256-byte
+ *                      aligned; it holds the batch's device copies and
+ *                      svt_run's workspace
+ * The host buffers and the workspace must stay untouched until the stream
+ * has completed the call.  To overlap one batch's copies with another's
+ * compute, alternate two streams, each with its own workspace and host
+ * buffers.  Errors: SVT_ERR_BAD_ARG (null pointers, sizes over the limits
+ * of svt_run, a workspace too small or misaligned), else as svt_run.
+ * ====================================================================== */
+size_t svt_run_host_workspace_size(uint64_t max_words, uint64_t max_events, uint64_t road_cap,
+                                   const svt_schedule *sched);
+int svt_run_host(const uint32_t *h_words, uint64_t n_words, const uint64_t *h_event_off,
+                 uint64_t n_events, const int16_t *d_F, const int16_t *d_q, const svt_config *cfg,
+                 uint64_t road_cap, uint32_t *h_out, uint64_t *h_status, uint64_t *n_records,
+                 void *d_workspace, size_t workspace_bytes, const svt_schedule *sched,
+                 void *stream);
+
+/* ======================================================================
  * svt_run without a workspace argument.  The paper has no counterpart: this
  * is for callers of this library that cannot allocate device memory at all
  * -- a front-end process that only receives device pointers from whatever
@@ -376,12 +409,16 @@ int svt_graph_destroy(svt_graph graph);
  * linked without a device allocator of its own.
  *
  * The scratch is one fixed array inside the library, SVT_NOALLOC_SCRATCH_BYTES
- * (32 MiB) on every GPU that loads the library, held until the process exits.
+ * (32 MiB) per GPU.  It is reserved on a GPU when the library's code is
+ * loaded there -- under CUDA's default lazy module loading, at the first
+ * svt_run_noalloc call on that GPU -- and held until the process exits.
  * A batch whose svt_run_workspace_size(n_words, n_events, road_cap, sched)
  * exceeds it is refused with SVT_ERR_OOM before anything is enqueued (32 MiB
  * covers, e.g., a 3000-event batch of 3.5 million words and 190 thousand
- * roads).  The first call on a device looks up the array's device address;
- * make that first call before any stream capture.  Every call on a device
+ * roads).  The first call on a device looks up the array's device address
+ * (only a successful lookup is kept; a failed one returns SVT_ERR_CUDA and
+ * is retried by the next call); make that first call before any stream
+ * capture.  Every call on a device
  * shares the array and it keeps the last call's contents; each call
  * re-initialises everything it reads, but calls whose work overlaps on the
  * GPU (different streams, or different host threads) race on it: issue them
@@ -427,7 +464,10 @@ int svt_host_free(void *host);
  * whose status reports a data error is re-run event by event, so a corrupt
  * event fails alone.  The library allocates no device or pinned memory here:
  * the caller passes both (svt_server_sizes).  Results carry the latency from
- * submission to the moment the dispatcher sees the batch complete.
+ * submission to the moment the event's records are in the caller's buffer.
+ * Per batch the dispatcher issues one copy per contiguous run of event words,
+ * one copy of the sizes and offsets, the graph replay and one copy back of
+ * the status, the event table and the records.
  * ====================================================================== */
 typedef struct {
     uint32_t n_slots;            /* batches in flight, 1..16 */
@@ -458,7 +498,27 @@ typedef struct {
 typedef struct {
     uint64_t batches, events_done, events_failed, retried_batches, rejected, queued;
     uint64_t h2d_bytes, d2h_bytes;
+    uint64_t max_queued;        /* most events waiting when a batch was taken */
+    uint64_t max_batch_events;  /* most events in one batch */
+    uint64_t launch_ns;         /* dispatcher time spent enqueueing batches */
+    uint64_t finish_ns;         /* dispatcher time spent delivering results */
 } svt_server_stats;
+
+/* One served batch, as recorded by svt_server_trace.  Host times are
+ * steady-clock nanoseconds (the clock of svt_event_result.t_arrive_ns);
+ * device times are microseconds since the trace started, from timing events
+ * recorded on the slot's stream before its first copy and after its last
+ * one (so two slots' intervals that overlap show batches in flight on the
+ * device together). */
+typedef struct {
+    uint32_t slot, n_events;
+    uint32_t n_roads, queued_after;   /* events still waiting once the batch was taken */
+    int64_t t_first_arrive_ns;        /* earliest arrival among the batch's events */
+    int64_t t_dispatch_ns;            /* the dispatcher took the events */
+    int64_t t_enqueued_ns;            /* every copy and launch of the batch enqueued */
+    int64_t t_done_ns;                /* the dispatcher saw the batch complete */
+    float dev_start_us, dev_end_us;   /* -1 when a timestamp could not be read */
+} svt_batch_trace;
 
 typedef struct svt_server_s *svt_server;
 
@@ -481,15 +541,30 @@ int svt_server_submit(svt_server server, const uint32_t *h_words, uint32_t n_wor
 int svt_server_poll(svt_server server, svt_event_result *out, uint32_t max_results,
                     uint32_t *n_out, uint32_t wait_us);
 int svt_server_stats_get(svt_server server, svt_server_stats *out);
+/* Zeroes the counters (the queue length is always the current one). */
+int svt_server_stats_reset(svt_server server);
+/* Starts recording one svt_batch_trace per completed batch into the caller's
+ * host array buf[cap] (from its first entry; batches beyond cap are not
+ * recorded); buf = NULL stops.  With device_times each batch also records
+ * two timing events on its stream (a few microseconds of latency per batch);
+ * without, dev_start_us and dev_end_us are -1.  Read the entries after
+ * stopping the trace, or once the server is idle: svt_server_trace_count
+ * gives how many were written. */
+int svt_server_trace(svt_server server, svt_batch_trace *buf, uint64_t cap, uint32_t device_times);
+int svt_server_trace_count(svt_server server, uint64_t *n);
 /* Stops the dispatcher after the batches in flight; undelivered events are dropped. */
 int svt_server_destroy(svt_server server);
-/* Poisson arrivals at rate_hz of n_events events taken in turn from a pool
- * (words h_pool in pinned memory, pool_off[n_pool + 1] word offsets);
- * lat_ns[i] = latency of event i (UINT64_MAX if it failed); *wall_s = time
- * from the first arrival to the last completion. */
+/* Poisson arrivals at rate_hz of n_events events, event i being pool event
+ * i mod n_pool (words h_pool in pinned memory, pool_off[n_pool + 1] word
+ * offsets).  h_records (may be NULL): event i's records go to
+ * h_records + 6 * rec_off[i] (rec_off[n_events] road offsets).  lat_ns[i] =
+ * latency of event i from its scheduled arrival time to the delivery of its
+ * result (UINT64_MAX if it failed); *wall_s = time from the first arrival to
+ * the last completion. */
 int svt_server_bench_poisson(svt_server server, const uint32_t *h_pool, const uint64_t *pool_off,
                              uint32_t n_pool, double rate_hz, uint64_t n_events, uint64_t seed,
-                             uint64_t *lat_ns, double *wall_s);
+                             uint32_t *h_records, const uint64_t *rec_off, uint64_t *lat_ns,
+                             double *wall_s);
 
 /* ======================================================================
  * FP32 calibration relaxation.  The fit of Sec. 2 without the integer shift

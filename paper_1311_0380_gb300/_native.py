@@ -56,7 +56,16 @@ class SvtEventResult(ctypes.Structure):
 class SvtServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ("batches", "events_done", "events_failed", "retried_batches", "rejected", "queued",
-                 "h2d_bytes", "d2h_bytes")]
+                 "h2d_bytes", "d2h_bytes", "max_queued", "max_batch_events", "launch_ns",
+                 "finish_ns")]
+
+
+class SvtBatchTrace(ctypes.Structure):
+    _fields_ = [("slot", ctypes.c_uint32), ("n_events", ctypes.c_uint32),
+                ("n_roads", ctypes.c_uint32), ("queued_after", ctypes.c_uint32),
+                ("t_first_arrive_ns", ctypes.c_int64), ("t_dispatch_ns", ctypes.c_int64),
+                ("t_enqueued_ns", ctypes.c_int64), ("t_done_ns", ctypes.c_int64),
+                ("dev_start_us", ctypes.c_float), ("dev_end_us", ctypes.c_float)]
 
 
 class SvtBest(ctypes.Structure):
@@ -101,6 +110,9 @@ SIGNATURES = {
     "svt_graph_destroy": (ctypes.c_int, [_vp]),
     "svt_host_alloc": (ctypes.c_int, [_sz, ctypes.POINTER(_vp), ctypes.POINTER(_vp)]),
     "svt_host_free": (ctypes.c_int, [_vp]),
+    "svt_run_host_workspace_size": (_sz, [_u64, _u64, _u64, _schp]),
+    "svt_run_host": (ctypes.c_int, [_vp, _u64, _vp, _u64, _vp, _vp, _cfgp, _u64, _vp, _vp,
+                                    ctypes.POINTER(_u64), _vp, _sz, _schp, _vp]),
     "svt_run_noalloc_scratch_bytes": (_sz, []),
     "svt_run_noalloc": (ctypes.c_int, [_vp, _u64, _vp, _u64, _vp, _vp, _cfgp, _u64, _vp, _vp, _vp,
                                        _vp, _schp, _vp]),
@@ -115,9 +127,12 @@ SIGNATURES = {
     "svt_server_poll": (ctypes.c_int, [_vp, ctypes.POINTER(SvtEventResult), _u32,
                                        ctypes.POINTER(_u32), _u32]),
     "svt_server_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(SvtServerStats)]),
+    "svt_server_stats_reset": (ctypes.c_int, [_vp]),
+    "svt_server_trace": (ctypes.c_int, [_vp, _vp, _u64, _u32]),
+    "svt_server_trace_count": (ctypes.c_int, [_vp, ctypes.POINTER(_u64)]),
     "svt_server_destroy": (ctypes.c_int, [_vp]),
     "svt_server_bench_poisson": (ctypes.c_int, [_vp, _vp, _vp, _u32, ctypes.c_double, _u64, _u64,
-                                                _vp, ctypes.POINTER(ctypes.c_double)]),
+                                                _vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)]),
     "svt_calib_index_size": (_sz, [_u64, _u32]),
     "svt_calib_index": (ctypes.c_int, [_vp, _u64, _u32, _vp, _sz, _vp, _vp, _vp]),
     "svt_calib_gather": (ctypes.c_int, [_vp, _u32, _vp, _u64, _vp, _vp]),

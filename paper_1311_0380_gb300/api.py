@@ -269,6 +269,43 @@ class FusedPath:
         return status, rec, counts
 
 
+class GraphPath:
+    """svt_graph_* over a FusedPath's buffers: the fused launch sequence
+    captured once with the batch sizes read on the device, then replayed for
+    every batch whose words and offsets sit in `words` / `event_off`."""
+
+    def __init__(self, path: FusedPath, words, event_off):
+        c = path.consts
+        self.path = path
+        self.sizes = torch.zeros(2, dtype=torch.int64, device=path.out.device)
+        self._keep = (words, event_off)
+        h = ctypes.c_void_p()
+        N.check(N.load().svt_graph_create(
+            _p(words), path.max_words, _p(event_off), path.max_events, _p(self.sizes), _p(c.F),
+            _p(c.q), ctypes.byref(c.cfg), path.road_cap, _p(path.out), _p(path.event_road),
+            _p(path.counts), _p(path.status), _p(path.workspace), path.workspace.numel(),
+            ctypes.byref(path.sched) if path.sched is not None else None, ctypes.byref(h)),
+            "svt_graph_create")
+        self.handle = h
+
+    def set_sizes(self, n_words: int, n_events: int):
+        self.sizes.copy_(torch.tensor([int(n_words), int(n_events)], dtype=torch.int64))
+
+    def launch(self, stream=None):
+        N.check(N.load().svt_graph_launch(self.handle, _stream(stream)), "svt_graph_launch")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.load().svt_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
 class PlainPath:
     """Buffers of the plain per-stage path."""
 
@@ -340,69 +377,80 @@ class PlainPath:
         return status, rec, R
 
 
+def svt_run_host_workspace_size(max_words, max_events, road_cap, sched=None) -> int:
+    return N.load().svt_run_host_workspace_size(max_words, max_events, road_cap,
+                                                ctypes.byref(sched) if sched is not None else None)
+
+
+def svt_run_host(h_words, n_words, h_event_off, n_events, F, q, cfg, road_cap, h_out, h_status,
+                 workspace, sched=None, stream=None) -> int:
+    """svt_run_host: copy in, fused path, copy out, all on `stream`; returns
+    the number of records that land in h_out (pinned host tensors)."""
+    n = ctypes.c_uint64()
+    N.check(N.load().svt_run_host(_p(h_words), n_words, _p(h_event_off), n_events, _p(F), _p(q),
+                                  ctypes.byref(cfg), road_cap, _p(h_out), _p(h_status),
+                                  ctypes.byref(n), _p(workspace), workspace.numel(),
+                                  ctypes.byref(sched) if sched is not None else None,
+                                  _stream(stream)), "svt_run_host")
+    return int(n.value)
+
+
 class StreamingRunner:
-    """A stream of batches from pinned host memory through the fused path with
-    the copies overlapped: while step i computes, step i+1's words and
-    offsets are copied in and step i-1's records are copied out.  Each step
-    still carries its own H2D copy and D2H read.  `depth` device sets (words,
-    offsets, workspace, records) alternate; copy-in, compute and copy-out run
-    on three streams ordered by events."""
+    """A stream of batches from pinned host memory through svt_run_host (copy
+    in, fused path, copy out as one library call per batch).  `depth` sets of
+    (CUDA stream, device workspace, pinned outputs) take the batches in turn,
+    so one batch's copies overlap another's compute; each batch still carries
+    its own H2D copy and D2H read.  A set's outputs are overwritten `depth`
+    batches later."""
 
     def __init__(self, max_words, max_events, road_cap, consts: DeviceConstants, sched=None,
                  device="cuda", depth: int = 2):
         self.depth = int(depth)
-        self.paths = [FusedPath(max_words, max_events, road_cap, consts, sched, device)
-                      for _ in range(self.depth)]
-        self.d_words = [torch.empty(max(int(max_words), 4), dtype=torch.int32, device=device)
-                        for _ in range(self.depth)]
-        self.d_off = [torch.empty(int(max_events) + 1, dtype=torch.int64, device=device)
-                      for _ in range(self.depth)]
-        self.h_out = [torch.empty(max(int(road_cap), 1) * 6, dtype=torch.int32, pin_memory=True)
+        self.consts, self.sched = consts, sched
+        self.max_words, self.max_events = int(max_words), int(max_events)
+        self.road_cap = int(road_cap)
+        ws = svt_run_host_workspace_size(self.max_words, self.max_events, self.road_cap, sched)
+        self.workspace = [torch.empty(ws, dtype=torch.uint8, device=device)
+                          for _ in range(self.depth)]
+        self.streams = [torch.cuda.Stream(device=device) for _ in range(self.depth)]
+        self.h_out = [torch.empty(max(self.road_cap, 1) * 6, dtype=torch.int32, pin_memory=True)
                       for _ in range(self.depth)]
         self.h_status = [torch.empty(1, dtype=torch.int64, pin_memory=True) for _ in range(self.depth)]
-        self.s_in, self.s_run, self.s_out = (torch.cuda.Stream(device=device) for _ in range(3))
-        self.ev_in = [torch.cuda.Event() for _ in range(self.depth)]
-        self.ev_run = [torch.cuda.Event() for _ in range(self.depth)]
-        self.used = [False] * self.depth
         self.n_out = [0] * self.depth
         self.i = 0
 
-    def submit(self, h_words, h_event_off, n_roads, marks=None):
-        """Enqueue one step; `marks` = (start, end) torch events recorded before
-        its copy-in and after its copy-out.  Returns the bytes (h2d, d2h)."""
+    def submit(self, h_words, h_event_off, n_roads=None, marks=None):
+        """Enqueue one batch; `marks` = (start, end) torch events recorded on the
+        batch's stream before its copy-in and after its copy-out.  Returns the
+        bytes (h2d, d2h)."""
         k = self.i % self.depth
         n_words, n_events = h_words.numel(), h_event_off.numel() - 1
-        path = self.paths[k]
-        n_out = min(int(n_roads), path.road_cap) * 6
-        with torch.cuda.stream(self.s_in):
-            if self.used[k]:   # step i - depth has finished reading this set
-                self.s_in.wait_event(self.ev_run[k])
-            if marks is not None:
-                marks[0].record(self.s_in)
-            self.d_words[k][:n_words].copy_(h_words, non_blocking=True)
-            self.d_off[k][: n_events + 1].copy_(h_event_off, non_blocking=True)
-            self.ev_in[k].record(self.s_in)
-        with torch.cuda.stream(self.s_run):
-            self.s_run.wait_event(self.ev_in[k])
-            path.run(self.d_words[k], n_words, self.d_off[k], n_events, stream=self.s_run)
-            self.ev_run[k].record(self.s_run)
-        with torch.cuda.stream(self.s_out):
-            self.s_out.wait_event(self.ev_run[k])
-            self.h_out[k][:n_out].copy_(path.out[:n_out], non_blocking=True)
-            self.h_status[k].copy_(path.status, non_blocking=True)
-            if marks is not None:
-                marks[1].record(self.s_out)
-        self.used[k] = True
-        self.n_out[k] = n_out
+        if n_words > self.max_words or n_events > self.max_events:
+            raise N.SvtError("batch larger than the buffers")
+        st = self.streams[k]
+        if marks is not None:
+            marks[0].record(st)
+        c = self.consts
+        n_rec = svt_run_host(h_words, n_words, h_event_off, n_events, c.F, c.q, c.cfg,
+                             self.road_cap, self.h_out[k], self.h_status[k], self.workspace[k],
+                             self.sched, st)
+        if marks is not None:
+            marks[1].record(st)
+        self.n_out[k] = n_rec
         self.i += 1
-        return 4 * n_words + 8 * (n_events + 1), 4 * n_out + 8
+        return 4 * n_words + 8 * (n_events + 1), 24 * n_rec + 8
 
     def wait(self):
-        """(status key, records [R, 6] uint32) of the last submitted step."""
-        self.s_out.synchronize()
+        """(status key, records [R, 6] uint32) of the last submitted batch."""
+        for st in self.streams:
+            st.synchronize()
         k = (self.i - 1) % self.depth
+        return self.result(k)
+
+    def result(self, k):
+        """(status key, records) held by set k (after wait)."""
         status = int(self.h_status[k].numpy().view(np.uint64)[0])
-        rec = self.h_out[k][: self.n_out[k]].numpy().view(np.uint32).reshape(-1, 6)
+        rec = self.h_out[k][: 6 * self.n_out[k]].numpy().view(np.uint32).reshape(-1, 6)
         return status, rec
 
 

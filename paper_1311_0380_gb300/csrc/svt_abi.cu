@@ -205,6 +205,7 @@ int svt_unpack(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_even
                uint32_t *d_road_word, uint32_t *d_road_nhit, uint32_t *d_event_road,
                uint64_t *d_n_roads, uint64_t *d_status, void *d_workspace,
                size_t workspace_bytes, void *stream) {
+    const NvtxRange range("svt_unpack");
     if (!d_event_off || !d_event_road || !d_n_roads || !d_status || !d_workspace)
         return SVT_ERR_BAD_ARG;
     if (n_words > 0 && (!d_words || !aligned16(d_words))) return SVT_ERR_BAD_ARG;
@@ -240,6 +241,7 @@ int svt_combine(const uint32_t *d_road_nhit, const uint64_t *d_n_roads, uint64_t
                 uint64_t *d_comb_off, uint32_t *d_comb_road, uint32_t *d_comb_hits,
                 uint64_t *d_n_combs, uint64_t *d_status, void *d_workspace,
                 size_t workspace_bytes, void *stream) {
+    const NvtxRange range("svt_combine");
     if (!config_ok(cfg)) return SVT_ERR_BAD_CONFIG;
     if (!d_n_roads || !d_comb_off || !d_n_combs || !d_status || !d_workspace) return SVT_ERR_BAD_ARG;
     if (road_cap > 0 && (!d_road_nhit || !d_road_flags)) return SVT_ERR_BAD_ARG;
@@ -262,6 +264,7 @@ int svt_fit(const uint32_t *d_words, const uint32_t *d_road_word, const uint32_t
             const uint32_t *d_comb_road, const uint32_t *d_comb_hits, const uint64_t *d_n_combs,
             uint64_t comb_cap, const int16_t *d_F, const int16_t *d_q, const svt_config *cfg,
             uint32_t *d_fit_chi2, int32_t *d_fit_par, const uint64_t *d_status, void *stream) {
+    const NvtxRange range("svt_fit");
     if (!config_ok(cfg)) return SVT_ERR_BAD_CONFIG;
     if (!d_n_combs || !d_F || !d_q || !d_status) return SVT_ERR_BAD_ARG;
     if (comb_cap > 0 && (!d_words || !d_road_word || !d_road_nhit || !d_comb_road ||
@@ -278,6 +281,7 @@ int svt_select(const uint32_t *d_fit_chi2, const int32_t *d_fit_par, uint64_t co
                const uint64_t *d_comb_off, const uint32_t *d_road_flags,
                const uint64_t *d_n_roads, uint64_t road_cap, const svt_config *cfg,
                svt_best *d_best, const uint64_t *d_status, void *stream) {
+    const NvtxRange range("svt_select");
     if (!config_ok(cfg)) return SVT_ERR_BAD_CONFIG;
     if (!d_comb_off || !d_n_roads || !d_status) return SVT_ERR_BAD_ARG;
     if (road_cap > 0 && (!d_road_flags || !d_best)) return SVT_ERR_BAD_ARG;
@@ -291,6 +295,7 @@ int svt_select(const uint32_t *d_fit_chi2, const int32_t *d_fit_par, uint64_t co
 int svt_format(const svt_best *d_best, const uint32_t *d_words, const uint32_t *d_road_word,
                const uint64_t *d_n_roads, uint64_t road_cap, uint32_t *d_out,
                const uint64_t *d_status, void *stream) {
+    const NvtxRange range("svt_format");
     if (!d_n_roads || !d_status) return SVT_ERR_BAD_ARG;
     if (road_cap > 0 && (!d_best || !d_words || !d_road_word || !d_out)) return SVT_ERR_BAD_ARG;
     launch_format(d_best, d_words, d_road_word, d_n_roads, road_cap, d_out,
@@ -341,13 +346,18 @@ int run_impl(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_
                      (uint32_t *)(w.work + 1)};
     const FusedRoads fr{w.desc, w.key, bl, sc.rows_per_item, sc.small_max};
 
-    launch_prologue(w.dims, n_words, n_events, d_sizes, d_event_off, w.first_ev, status, counts, 4,
-                    w.work, 2, grid, st);
-    launch_unpack_count(d_words, d_event_off, w.dims, w.first_ev, n_words, cfg->n_sectors,
-                        w.tile_roads, status, grid, st);
-    launch_scan_tiles(w.tile_roads, w.dims, nullptr, counts + 0, event_road, status, st);
-    launch_unpack_roads(d_words, d_event_off, w.dims, w.first_ev, n_words, w.tile_roads, road_cap,
-                        nullptr, nullptr, event_road, *cfg, fr, counts, status, grid, st);
+    const NvtxRange range("svt_run");
+    {
+        const NvtxRange stage("svt_run: unpack");
+        launch_prologue(w.dims, n_words, n_events, d_sizes, d_event_off, w.first_ev, status, counts, 4,
+                        w.work, 2, grid, st);
+        launch_unpack_count(d_words, d_event_off, w.dims, w.first_ev, n_words, cfg->n_sectors,
+                            w.tile_roads, status, grid, st);
+        launch_scan_tiles(w.tile_roads, w.dims, nullptr, counts + 0, event_road, status, st);
+        launch_unpack_roads(d_words, d_event_off, w.dims, w.first_ev, n_words, w.tile_roads, road_cap,
+                            nullptr, nullptr, event_road, *cfg, fr, counts, status, grid, st);
+    }
+    const NvtxRange fit_range("svt_run: combine, fit, cut, select, format");
     if (timer && cudaEventRecord(timer->start, st) != cudaSuccess) return SVT_ERR_CUDA;
     if (launch_fit_persistent(d_words, d_event_off, w.dims, event_road, w.desc, counts, road_cap,
                               d_F, d_q, *cfg, fr, sc.roads_per_chunk, sc.pair_small != 0, d_out,
@@ -547,6 +557,80 @@ done:
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return rc;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Device buffers of svt_run_host: the batch's words and offsets, the status,
+// the records, then svt_run's own workspace.
+struct HostRunWs {
+    uint32_t *words;
+    uint64_t *off, *status;
+    uint32_t *out;
+    void *run;
+    size_t run_bytes, bytes;
+};
+HostRunWs carve_host_run(void *base, uint64_t n_words, uint64_t n_events, uint64_t road_cap,
+                         const svt_schedule *sched) {
+    Carver c(base);
+    HostRunWs w;
+    w.words = c.take<uint32_t>(n_words + 4);
+    w.off = c.take<uint64_t>(n_events + 1);
+    w.status = c.take<uint64_t>(1);
+    w.out = c.take<uint32_t>(6 * (road_cap ? road_cap : 1));
+    w.run_bytes = svt_run_workspace_size(n_words, n_events, road_cap, sched);
+    w.run = c.take<char>(w.run_bytes);
+    w.bytes = c.size();
+    return w;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t svt_run_host_workspace_size(uint64_t max_words, uint64_t max_events, uint64_t road_cap,
+                                   const svt_schedule *sched) {
+    return carve_host_run(nullptr, max_words, max_events, road_cap, sched).bytes;
+}
+
+int svt_run_host(const uint32_t *h_words, uint64_t n_words, const uint64_t *h_event_off,
+                 uint64_t n_events, const int16_t *d_F, const int16_t *d_q, const svt_config *cfg,
+                 uint64_t road_cap, uint32_t *h_out, uint64_t *h_status, uint64_t *n_records,
+                 void *d_workspace, size_t workspace_bytes, const svt_schedule *sched,
+                 void *stream) {
+    if (!h_event_off || !h_status || !d_workspace || (n_words > 0 && !h_words) ||
+        (road_cap > 0 && !h_out))
+        return SVT_ERR_BAD_ARG;
+    if (n_words >= (1ull << 32) || n_events >= (1ull << 31) || road_cap >= (1ull << 31))
+        return SVT_ERR_BAD_ARG;
+    if ((uintptr_t)d_workspace & 255u) return SVT_ERR_BAD_ARG;
+    const HostRunWs w = carve_host_run(d_workspace, n_words, n_events, road_cap, sched);
+    if (workspace_bytes < w.bytes) return SVT_ERR_BAD_ARG;
+    // records to bring back: the road count the event headers state, at most
+    // road_cap (for a valid batch this is R; for an invalid one the status
+    // says so and the records are unspecified)
+    uint64_t R = 0;
+    for (uint64_t e = 0; e < n_events; ++e) {
+        const uint64_t s = h_event_off[e];
+        if (s < n_words) R += h_words[s] & 0xFFFu;
+    }
+    R = R < road_cap ? R : road_cap;
+    if (n_records) *n_records = R;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((n_words && cudaMemcpyAsync(w.words, h_words, n_words * 4, cudaMemcpyHostToDevice, st) !=
+                        cudaSuccess) ||
+        cudaMemcpyAsync(w.off, h_event_off, (n_events + 1) * 8, cudaMemcpyHostToDevice, st) !=
+            cudaSuccess)
+        return SVT_ERR_CUDA;
+    const int rc = svt_run(w.words, n_words, w.off, n_events, d_F, d_q, cfg, road_cap, w.out,
+                           nullptr, nullptr, w.status, w.run, w.run_bytes, sched, nullptr, stream);
+    if (rc != SVT_OK) return rc;
+    if ((R && cudaMemcpyAsync(h_out, w.out, R * 24, cudaMemcpyDeviceToHost, st) != cudaSuccess) ||
+        cudaMemcpyAsync(h_status, w.status, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return SVT_ERR_CUDA;
+    return SVT_OK;
 }
 
 int svt_host_alloc(size_t bytes, void **host, void **device) {

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/svt.h"
@@ -162,6 +163,15 @@ __device__ __forceinline__ void road_split(const RoadShape &s, uint32_t &split, 
 __host__ __device__ __forceinline__ size_t align_up(size_t v, size_t a) {
     return (v + a - 1) / a * a;
 }
+
+// A named NVTX range over the host-side enqueue of one stage (shown by the
+// Nsight tools on the CPU timeline; a no-op when no tool is attached).
+struct NvtxRange {
+    __host__ explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    __host__ ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 struct Carver {
     char *base;

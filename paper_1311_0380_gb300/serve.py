@@ -66,17 +66,50 @@ class Server:
         N.check(N.load().svt_server_stats_get(self.handle, ctypes.byref(st)), "svt_server_stats_get")
         return {f: getattr(st, f) for f, _ in N.SvtServerStats._fields_}
 
+    def reset_stats(self):
+        N.check(N.load().svt_server_stats_reset(self.handle), "svt_server_stats_reset")
+
+    def trace_start(self, cap: int = 1 << 20, device_times: bool = True):
+        """Record one entry per completed batch (up to cap) until trace_stop;
+        device_times adds each batch's device interval (two timing events)."""
+        self._trace = (N.SvtBatchTrace * cap)()
+        N.check(N.load().svt_server_trace(self.handle, ctypes.cast(self._trace, ctypes.c_void_p),
+                                          cap, int(device_times)), "svt_server_trace")
+
+    def trace_stop(self) -> np.ndarray:
+        """Stops the trace; returns its entries as a structured array."""
+        L = N.load()
+        n = ctypes.c_uint64()
+        N.check(L.svt_server_trace(self.handle, None, 0, 0), "svt_server_trace")
+        N.check(L.svt_server_trace_count(self.handle, ctypes.byref(n)), "svt_server_trace_count")
+        buf = getattr(self, "_trace", None)
+        self._trace = None
+        if buf is None:
+            return np.zeros(0, dtype=TRACE_DTYPE)
+        raw = np.frombuffer(buf, dtype=TRACE_DTYPE)
+        return raw[:min(int(n.value), len(raw))].copy()
+
     def bench_poisson(self, h_pool: torch.Tensor, pool_off: np.ndarray, rate_hz: float,
-                      n_events: int, seed: int = 1):
-        """Poisson arrivals from a pinned pool of events; returns (latencies in
-        ns as uint64, wall seconds)."""
+                      n_events: int, seed: int = 1, records: np.ndarray | None = None,
+                      rec_off: np.ndarray | None = None):
+        """Poisson arrivals from a pinned pool of events (event i is pool event
+        i mod pool size); returns (latencies in ns from each scheduled arrival
+        as uint64, wall seconds).  records / rec_off: event i's records land at
+        records[rec_off[i]:] (rows of 6 words)."""
         off = np.ascontiguousarray(pool_off, np.uint64)
         lat = np.zeros(n_events, np.uint64)
         wall = ctypes.c_double()
+        rp = ro = None
+        if records is not None:
+            assert records.dtype == np.uint32 and records.flags.c_contiguous
+            ro_arr = np.ascontiguousarray(rec_off, np.uint64)
+            assert len(ro_arr) >= n_events
+            rp = records.ctypes.data_as(ctypes.c_void_p)
+            ro = ro_arr.ctypes.data_as(ctypes.c_void_p)
         rc = N.load().svt_server_bench_poisson(
             self.handle, ctypes.c_void_p(h_pool.data_ptr()), off.ctypes.data_as(ctypes.c_void_p),
-            len(off) - 1, float(rate_hz), n_events, seed, lat.ctypes.data_as(ctypes.c_void_p),
-            ctypes.byref(wall))
+            len(off) - 1, float(rate_hz), n_events, seed, rp, ro,
+            lat.ctypes.data_as(ctypes.c_void_p), ctypes.byref(wall))
         N.check(rc, "svt_server_bench_poisson")
         return lat, wall.value
 
@@ -90,6 +123,31 @@ class Server:
             self.close()
         except Exception:  # noqa: BLE001
             pass
+
+
+TRACE_DTYPE = np.dtype([("slot", np.uint32), ("n_events", np.uint32), ("n_roads", np.uint32),
+                        ("queued_after", np.uint32), ("t_first_arrive_ns", np.int64),
+                        ("t_dispatch_ns", np.int64), ("t_enqueued_ns", np.int64),
+                        ("t_done_ns", np.int64), ("dev_start_us", np.float32),
+                        ("dev_end_us", np.float32)])
+
+
+def overlap_fraction(trace: np.ndarray) -> float:
+    """Fraction of traced batches whose device interval (first copy in to last
+    copy out) overlaps the interval of a batch in another slot."""
+    t = trace[(trace["dev_start_us"] >= 0) & (trace["dev_end_us"] >= 0)]
+    if len(t) < 2:
+        return 0.0
+    order = np.argsort(t["dev_start_us"], kind="stable")
+    a, z, s = t["dev_start_us"][order], t["dev_end_us"][order], t["slot"][order]
+    hit = np.zeros(len(t), bool)
+    for i in range(len(t)):
+        j = i + 1
+        while j < len(t) and a[j] < z[i]:
+            if s[j] != s[i]:
+                hit[i] = hit[j] = True
+            j += 1
+    return float(hit.mean())
 
 
 def pinned_pool(words: np.ndarray) -> torch.Tensor:

@@ -130,8 +130,10 @@ def test_autotune_with_l2_flush(tmp_path):
 
 
 def test_streaming_runner_overlapped_steps_are_exact():
-    """Copies and compute of consecutive steps overlap on three streams; the
-    records of each step still equal the oracle's for that step's batch."""
+    """Batches go through svt_run_host (copy in, fused path, copy out in one
+    library call) on two alternating streams, so copies and compute of
+    consecutive steps overlap; the records of each step still equal the
+    oracle's for that step's batch."""
     import torch
     from paper_1311_0380_gb300 import api
     consts = synth.make_constants(512)
@@ -150,8 +152,39 @@ def test_streaming_runner_overlapped_steps_are_exact():
     st, rec = runner.wait()
     assert st == oracle.KEY_OK and np.array_equal(rec, want[order[-1]])
     # the other set holds the step before
-    k_prev = (runner.i - 2) % runner.depth
-    n = batches[order[-2]].total_roads
-    prev = runner.h_out[k_prev][: 6 * n].numpy().view(np.uint32).reshape(-1, 6)
-    assert np.array_equal(prev, want[order[-2]])
-    assert int(runner.h_status[k_prev].numpy().view(np.uint64)[0]) == oracle.KEY_OK
+    st_prev, prev = runner.result((runner.i - 2) % runner.depth)
+    assert st_prev == oracle.KEY_OK and np.array_equal(prev, want[order[-2]])
+
+
+def test_run_host_single_call_matches_oracle_and_reports_bad_data():
+    """svt_run_host on one stream: the records equal the oracle's; a corrupt
+    batch returns the oracle's status key; a workspace sized for a smaller
+    batch is refused."""
+    import torch
+    from paper_1311_0380_gb300 import api
+    consts = synth.make_constants(512)
+    spec = synth.SPECS["uneven"]
+    b = synth.make_batch(spec, 5, consts, seed=77)
+    cfg = api.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, 512)
+    ocfg = oracle.config(15, 15, consts.chi2_cut_99, spec.max_comb, 5, 512)
+    dc = api.DeviceConstants.from_numpy(consts.F, consts.q, cfg)
+    hw, ho = api.HostRunner.pin_batch(b.words, b.event_off)
+    R = b.total_roads
+    ws = torch.empty(api.svt_run_host_workspace_size(len(b.words), b.n_events, R), dtype=torch.uint8,
+                     device="cuda")
+    h_out = torch.empty(R * 6, dtype=torch.int32, pin_memory=True)
+    h_st = torch.empty(1, dtype=torch.int64, pin_memory=True)
+    n = api.svt_run_host(hw, len(b.words), ho, b.n_events, dc.F, dc.q, cfg, R, h_out, h_st, ws)
+    torch.cuda.synchronize()
+    key, want = oracle.run(b.words, b.event_off, consts.F, consts.q, ocfg, omp=True)
+    assert n == R and int(h_st.numpy().view(np.uint64)[0]) == key == oracle.KEY_OK
+    assert np.array_equal(h_out.numpy().view(np.uint32).reshape(-1, 6), want)
+    w2 = b.words.copy()
+    w2[int(b.event_off[2]) + 1] = np.uint32(1 << 30)          # a type-1 word
+    hw2, _ = api.HostRunner.pin_batch(w2, b.event_off)
+    api.svt_run_host(hw2, len(w2), ho, b.n_events, dc.F, dc.q, cfg, R, h_out, h_st, ws)
+    torch.cuda.synchronize()
+    assert int(h_st.numpy().view(np.uint64)[0]) == oracle.validate(w2, b.event_off, 512)
+    with pytest.raises(api.N.SvtError, match="BAD_ARG"):
+        api.svt_run_host(hw, len(b.words), ho, b.n_events, dc.F, dc.q, cfg, R, h_out, h_st,
+                         ws[: ws.numel() // 2])

@@ -151,3 +151,51 @@ def test_poisson_driver_delivers_every_event():
     assert np.all(lat > 0) and wall > 0
     assert srv.stats()["events_done"] == 3000
     srv.close()
+
+
+def test_poisson_stream_at_30khz_matches_oracle():
+    """20,000 events shaped like the uneven workload arrive as a Poisson stream
+    at 30 kHz through the server in its benchmark configuration; every served
+    event's records equal the oracle's for that event."""
+    from paper_1311_0380_gb300 import api, serve
+    consts = synth.make_constants(512)
+    pool_b = synth.make_batch("uneven", 384, consts, seed=synth.BASE_SEED + 40)
+    ocfg = oracle.config(15, 15, consts.chi2_cut_99, 4096, 5, 512)
+    want, nr = oracle_per_event(pool_b.words, pool_b.event_off, consts, ocfg)
+    pool = serve.pinned_pool(pool_b.words)
+    srv, _ = make_server(consts, 0, max_words=1 << 22, max_events=256, max_roads=1 << 17,
+                         sched=api.schedule(8, 0, 16, 1, 4096, 0), small_batch_events=4,
+                         small_blocks_per_sm=1)
+    n = 20000
+    k = np.arange(n) % len(nr)
+    rec_off = np.zeros(n + 1, np.uint64)
+    rec_off[1:] = np.cumsum(nr[k])
+    rec = np.full((int(rec_off[-1]) + 1, 6), 0xDEADBEEF, np.uint32)
+    lat, wall = srv.bench_poisson(pool, pool_b.event_off, 30e3, n, seed=11, records=rec,
+                                  rec_off=rec_off)
+    assert np.all(lat != np.uint64(2 ** 64 - 1)) and wall > 0
+    expect = np.concatenate([want[i] for i in k])
+    assert np.array_equal(rec[:-1], expect)
+    assert srv.stats()["events_failed"] == 0
+    srv.close()
+
+
+def test_slots_overlap_on_the_device():
+    """Events submitted back to back are spread over the slots, and the traced
+    device intervals (first copy in to last copy out) of batches in different
+    slots overlap: their work is in flight on the GPU at the same time."""
+    from paper_1311_0380_gb300 import serve
+    consts, words, off = mixed_events()
+    pool = serve.pinned_pool(words)
+    srv, _ = make_server(consts, 0, max_events=4)
+    srv.trace_start(4096)
+    E = len(off) - 1
+    for e in range(E):
+        assert srv.submit(pool[int(off[e]):int(off[e + 1])], e) == 0
+    got = collect(srv, E)
+    assert len(got) == E
+    tr = srv.trace_stop()
+    assert len(tr) == srv.stats()["batches"] and len(set(tr["slot"].tolist())) > 1
+    assert np.all(tr["dev_end_us"] >= tr["dev_start_us"]) and np.all(tr["dev_start_us"] >= 0)
+    assert serve.overlap_fraction(tr) > 0.5
+    srv.close()
