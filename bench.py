@@ -288,12 +288,14 @@ def calibration(dev, reps=20):
 
 def calibration_one(dev, n_tracks, reps):
     """The FP32 relaxation on n_tracks generated tracks over 512 sectors: the
-    forward y = F[s] x + q[s], the loss, and the hand-written backward of the
-    loss (dL/dF, dL/dq), each timed with CUDA events over `reps` calls with
-    the L2 flushed (by a 256 MB read) before each, every call replayed from a
-    one-call CUDA graph.  Algorithmic bytes per track: the forward reads
-    x (24 B) and writes y (24 B); the loss and its backward read x and the
-    true parameters (36 B)."""
+    forward y = F[s] x + q[s], the loss alone, the loss and its gradient in
+    one fused pass (what autograd runs), the scaling of that gradient by the
+    upstream one, and the separate backward pass (svt_calib_loss_backward),
+    each timed with CUDA events over `reps` calls with the L2 flushed (by a
+    256 MB read) before each, every call replayed from a one-call CUDA graph.
+    Algorithmic bytes per track: the forward reads x (24 B) and writes y
+    (24 B); the loss, the fused pass and the backward read x and the true
+    parameters (36 B)."""
     import torch
     from paper_1311_0380_gb300 import calib, synth
     consts = synth.make_constants(512)
@@ -336,20 +338,49 @@ def calibration_one(dev, n_tracks, reps):
         def save_for_backward(self, *t):
             self.saved_tensors = t
 
-    ctx_f, ctx_l = _Ctx(), _Ctx()
+        def mark_non_differentiable(self, *t):
+            pass
+
+    ctx_f, ctx_l, ctx_g, ctx_u = _Ctx(), _Ctx(), _Ctx(), _Ctx()
+    ctx_l.needs_input_grad = (False, False, False)   # the loss alone
+    ctx_g.needs_input_grad = (True, True, False)     # the loss and its gradient in one pass
     g1 = torch.ones((), device=dev)
     with torch.no_grad():
         t_fwd = timed(lambda: calib.FitFP32.forward(ctx_f, F, q, data))
         t_loss = timed(lambda: calib.CalibLoss.forward(ctx_l, F, q, data))
-        t_bwd = timed(lambda: calib.CalibLoss.backward(ctx_l, g1))
+        t_lg = timed(lambda: calib.CalibLoss.forward(ctx_g, F, q, data))
+        ctx_y = _Ctx()
+        t_lgy = timed(lambda: calib.CalibLossFit.forward(ctx_y, F, q, data))
+        t_scale = timed(lambda: calib.CalibLoss.backward(ctx_g, g1))
+        calib.CalibLossUnfused.forward(ctx_u, F, q, data)
+        t_bwd = timed(lambda: calib.CalibLossUnfused.backward(ctx_u, g1))
     loss = calib.calib_loss(F, q, data)
     n = n_tracks
     out = {"tracks": n, "sectors": 512, "loss_value": float(loss.item()), "peak_gbs": peak,
            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
-    for name, ms, bpt in (("forward", t_fwd, 48), ("loss", t_loss, 36), ("loss_backward", t_bwd, 36)):
+    for name, ms, bpt in (("forward", t_fwd, 48), ("loss", t_loss, 36),
+                          ("loss_and_grad", t_lg, 36), ("loss_backward", t_bwd, 36)):
         gbs = n * bpt / (ms / 1e3) / 1e9
         out[name] = {"us": ms * 1e3, "bytes_per_track": bpt, "achieved_gbs": gbs,
                      "frac": gbs / peak, "tracks_per_s": n / (ms / 1e3)}
+    out["grad_scale_us"] = t_scale * 1e3
+    gbs = n * 60 / (t_lgy / 1e3) / 1e9
+    out["loss_grad_and_fit"] = {"us": t_lgy * 1e3, "bytes_per_track": 60, "achieved_gbs": gbs,
+                                "frac": gbs / peak}
+    # a calibration step from one pass: the fitted parameters, the loss and
+    # its gradient (x and theta read, y written: 60 B per track), then the
+    # scaling by the upstream gradient
+    ms = t_lgy + t_scale
+    gbs = n * 60 / (ms / 1e3) / 1e9
+    out["step_one_pass"] = {"us": ms * 1e3, "bytes_per_track": 60, "achieved_gbs": gbs,
+                            "frac": gbs / peak}
+    # a calibration step as the autograd graph runs it, with the fitted
+    # parameters also produced: forward y, the fused loss and gradient, and
+    # the scaling by the upstream gradient (84 algorithmic bytes per track)
+    ms = t_fwd + t_lg + t_scale
+    gbs = n * 84 / (ms / 1e3) / 1e9
+    out["step_forward_loss_grad"] = {"us": ms * 1e3, "bytes_per_track": 84, "achieved_gbs": gbs,
+                                     "frac": gbs / peak}
     return out
 
 

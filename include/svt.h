@@ -593,7 +593,8 @@ int svt_calib_index(const int32_t *d_sector, uint64_t n_tracks, uint32_t n_secto
 int svt_calib_gather(const float *d_src, uint32_t width, const int32_t *d_perm, uint64_t n,
                      float *d_dst, void *stream);
 
-/* Workspace bytes of the loss and backward calls. */
+/* Workspace bytes of the loss and backward calls (zero-fill it once after
+ * allocating it: see svt_calib_loss_grad). */
 size_t svt_calib_workspace_size(uint64_t n_tracks, uint32_t n_sectors);
 
 /* y = F[s] x + q[s] for sector-ordered tracks. */
@@ -606,12 +607,35 @@ int svt_calib_loss(const float *d_x, const float *d_theta, const float *d_w, uin
                    uint32_t n_sectors, const void *d_index, const float *d_F, const float *d_q,
                    float *d_loss, void *d_workspace, size_t workspace_bytes, void *stream);
 
-/* d_dF = g dL/dF, d_dq = g dL/dq with g = *d_grad_loss (NULL: g = 1). */
+/* d_dF = g dL/dF, d_dq = g dL/dq with g = *d_grad_loss (NULL: g = 1): the
+ * pass of svt_calib_loss_grad with its loss kept in the workspace. */
 int svt_calib_loss_backward(const float *d_x, const float *d_theta, const float *d_w,
                             uint64_t n_tracks, uint32_t n_sectors, const void *d_index,
                             const float *d_F, const float *d_q, const float *d_grad_loss,
                             float *d_dF, float *d_dq, void *d_workspace, size_t workspace_bytes,
                             void *stream);
+
+/* The loss and its gradient in one pass over the tracks (x and theta read
+ * once): d_loss[0] = L, d_dF = dL/dF, d_dq = dL/dq and, when d_y is not NULL,
+ * d_y = F[s] x + q[s] as svt_calib_forward writes it.  The final sums are
+ * made by the warps that complete each sector and the batch (atomic tickets
+ * in the workspace; nothing waits), in a fixed order, so repeated calls give
+ * identical bits.  Sectors without tracks get zero gradients.  The tickets
+ * live in the workspace, which must be zero-filled once after it is
+ * allocated; every call of svt_calib_loss_grad or svt_calib_loss_backward
+ * leaves them at zero again. */
+int svt_calib_loss_grad(const float *d_x, const float *d_theta, const float *d_w,
+                        uint64_t n_tracks, uint32_t n_sectors, const void *d_index,
+                        const float *d_F, const float *d_q, float *d_loss, float *d_dF,
+                        float *d_dq, float *d_y, void *d_workspace, size_t workspace_bytes,
+                        void *stream);
+
+/* d_out_dF = (*d_scale) d_dF and d_out_dq = (*d_scale) d_dq (n_sectors
+ * sectors; the outputs may alias the inputs): the chain rule's last step when
+ * the gradient of L was formed by svt_calib_loss_grad before the upstream
+ * gradient was known. */
+int svt_calib_grad_scale(const float *d_scale, const float *d_dF, const float *d_dq,
+                         uint32_t n_sectors, float *d_out_dF, float *d_out_dq, void *stream);
 
 /* Backward of y = F[s] x + q[s] from d_grad_y [N][6]: d_dF[s] = sum_t g_t x_t^T,
  * d_dq[s] = sum_t g_t and, when d_dx is not NULL, d_dx_t = F[s]^T g_t. */

@@ -143,6 +143,9 @@ SIGNATURES = {
                                                _vp, _vp, _sz, _vp]),
     "svt_calib_backward": (ctypes.c_int, [_vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
                                           _vp]),
+    "svt_calib_loss_grad": (ctypes.c_int, [_vp, _vp, _vp, _u64, _u32, _vp, _vp, _vp, _vp, _vp, _vp,
+                                           _vp, _vp, _sz, _vp]),
+    "svt_calib_grad_scale": (ctypes.c_int, [_vp, _vp, _vp, _u32, _vp, _vp, _vp]),
 }
 
 _lib = None

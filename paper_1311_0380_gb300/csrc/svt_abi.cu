@@ -145,7 +145,8 @@ CalibIndex carve_calib_index(const void *base, uint64_t n, uint32_t S) {
     return x;
 }
 struct CalibWs {
-    float *item_loss, *item_grad;
+    float *item_loss, *item_grad, *sector_loss, *loss;
+    unsigned int *tickets;
     size_t bytes;
 };
 CalibWs carve_calib_ws(void *base, uint64_t n, uint32_t S) {
@@ -154,6 +155,9 @@ CalibWs carve_calib_ws(void *base, uint64_t n, uint32_t S) {
     const uint32_t mi = calib_max_items(n, S);
     w.item_loss = c.take<float>(mi);
     w.item_grad = c.take<float>((size_t)mi * 42);
+    w.sector_loss = c.take<float>(S);
+    w.loss = c.take<float>(1);
+    w.tickets = c.take<unsigned int>(S + 1);
     w.bytes = c.size();
     return w;
 }
@@ -745,10 +749,40 @@ int svt_calib_loss_backward(const float *d_x, const float *d_theta, const float 
     CalibWs w = carve_calib_ws(d_workspace, n_tracks, n_sectors);
     if (workspace_bytes < w.bytes) return SVT_ERR_BAD_ARG;
     CalibIndex x = carve_calib_index(d_index, n_tracks, n_sectors);
-    const float scale = n_tracks ? 2.0f / (float)n_tracks : 0.f;
-    launch_calib_grad(0, d_x, d_theta, nullptr, x.item_sector, x.item_start, x.sector_off,
-                      x.sector_item, x.n_items, x.max_items, n_sectors, d_F, d_q, d_w, d_grad_loss, scale,
-                      w.item_grad, d_dF, d_dq, nullptr, tile_grid(), (cudaStream_t)stream);
+    // the fused pass, its loss kept in the workspace
+    launch_calib_loss_grad(d_x, d_theta, x.item_sector, x.item_start, x.sector_off,
+                           x.sector_item, x.n_items, n_sectors, n_tracks, d_F, d_q, d_w,
+                           d_grad_loss, w.item_loss, w.item_grad, w.sector_loss, w.tickets,
+                           w.loss, d_dF, d_dq, nullptr, current_sm_count(), (cudaStream_t)stream);
+    return launch_status();
+}
+
+int svt_calib_loss_grad(const float *d_x, const float *d_theta, const float *d_w,
+                        uint64_t n_tracks, uint32_t n_sectors, const void *d_index,
+                        const float *d_F, const float *d_q, float *d_loss, float *d_dF,
+                        float *d_dq, float *d_y, void *d_workspace, size_t workspace_bytes,
+                        void *stream) {
+    if (!calib_sizes_ok(n_tracks, n_sectors) || !d_index || !d_F || !d_q || !d_w || !d_loss ||
+        !d_dF || !d_dq || !d_workspace)
+        return SVT_ERR_BAD_ARG;
+    if (n_tracks > 0 && (!d_x || !d_theta || ((uintptr_t)d_x & 7u) || ((uintptr_t)d_y & 7u)))
+        return SVT_ERR_BAD_ARG;
+    CalibWs w = carve_calib_ws(d_workspace, n_tracks, n_sectors);
+    if (workspace_bytes < w.bytes) return SVT_ERR_BAD_ARG;
+    CalibIndex x = carve_calib_index(d_index, n_tracks, n_sectors);
+    launch_calib_loss_grad(d_x, d_theta, x.item_sector, x.item_start, x.sector_off,
+                           x.sector_item, x.n_items, n_sectors, n_tracks, d_F, d_q, d_w, nullptr,
+                           w.item_loss, w.item_grad, w.sector_loss, w.tickets, d_loss, d_dF, d_dq,
+                           d_y, current_sm_count(), (cudaStream_t)stream);
+    return launch_status();
+}
+
+int svt_calib_grad_scale(const float *d_scale, const float *d_dF, const float *d_dq,
+                         uint32_t n_sectors, float *d_out_dF, float *d_out_dq, void *stream) {
+    if (!d_scale || !d_dF || !d_dq || !d_out_dF || !d_out_dq || n_sectors < 1 || n_sectors > 512)
+        return SVT_ERR_BAD_ARG;
+    launch_calib_grad_scale(d_scale, d_dF, d_dq, n_sectors, d_out_dF, d_out_dq,
+                            (cudaStream_t)stream);
     return launch_status();
 }
 
@@ -765,9 +799,9 @@ int svt_calib_backward(const float *d_x, const float *d_grad_y, uint64_t n_track
     CalibWs w = carve_calib_ws(d_workspace, n_tracks, n_sectors);
     if (workspace_bytes < w.bytes) return SVT_ERR_BAD_ARG;
     CalibIndex x = carve_calib_index(d_index, n_tracks, n_sectors);
-    launch_calib_grad(1, d_x, nullptr, d_grad_y, x.item_sector, x.item_start, x.sector_off,
-                      x.sector_item, x.n_items, x.max_items, n_sectors, d_F, nullptr, nullptr, nullptr, 1.0f,
-                      w.item_grad, d_dF, d_dq, d_dx, tile_grid(), (cudaStream_t)stream);
+    launch_calib_grad(d_x, d_grad_y, x.item_sector, x.item_start, x.sector_off, x.sector_item,
+                      x.n_items, x.max_items, n_sectors, d_F, w.item_grad, d_dF, d_dq, d_dx,
+                      tile_grid(), (cudaStream_t)stream);
     return launch_status();
 }
 

@@ -7,9 +7,12 @@
 //
 // Tracks are first sorted by sector (stable counting sort on the device);
 // every kernel then works on "items" of at most CALIB_CHUNK consecutive tracks
-// of one sector, one warp per item.  Reductions are two-level and in a fixed
-// order (lanes -> shuffle tree -> items in index order), so results are
-// bitwise reproducible run to run.
+// of one sector: the forward, the loss alone and the general backward take
+// one warp per item, the fused loss-and-gradient pass a contiguous run of
+// items per warp with its final sums made by the warps that complete each
+// sector (atomic tickets, no waiting).  Every reduction runs in a fixed order
+// (lanes, then items or segments in index order), so results are bitwise
+// reproducible run to run.
 #include "svt_kernels.cuh"
 
 namespace svt {
@@ -19,6 +22,7 @@ namespace {
 constexpr int CALIB_CHUNK = 256;          // tracks per item (8 per lane)
 constexpr int SORT_TILE = 1024;           // tracks per histogram tile
 constexpr int NPAR = 42;                  // 36 entries of F[s] + 6 of q[s]
+
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -284,16 +288,13 @@ __global__ void __launch_bounds__(1024)
     }
 }
 
-// per item: sum_t g_t x_t^T and sum_t g_t, where g comes from the loss
-// (mode 0, without the 2/N factor) or from grad_y (mode 1); also dx (mode 1).
-template <int MODE>
-__global__ void k_grad_items(const float *__restrict__ x, const float *__restrict__ theta,
-                             const float *__restrict__ grad_y,
+// per item of the general backward: sum_t g_t x_t^T and sum_t g_t with g
+// from grad_y, and dx_t = F[s]^T g_t when dx is given
+__global__ void k_grad_items(const float *__restrict__ x, const float *__restrict__ grad_y,
                              const int32_t *__restrict__ item_sector,
                              const int32_t *__restrict__ item_start,
                              const int32_t *__restrict__ sector_off,
                              const int32_t *__restrict__ n_items, const float *__restrict__ F,
-                             const float *__restrict__ q, const float *__restrict__ w,
                              float *item_grad, float *dx) {
     __shared__ float cs[8][48];
     // per warp: the 32 lanes' partials, row stride NPAR + 1 (odd, so that both
@@ -304,7 +305,7 @@ __global__ void k_grad_items(const float *__restrict__ x, const float *__restric
     const uint32_t NI = (uint32_t)*n_items;
     for (uint32_t i = blockIdx.x * (blockDim.x >> 5) + wib; i < NI; i += gridDim.x * (blockDim.x >> 5)) {
         const Item it = item_of(item_sector, item_start, sector_off, i);
-        load_consts(cs[wib], F, q, it.s, lane);
+        load_consts(cs[wib], F, nullptr, it.s, lane);
         float acc[NPAR];
 #pragma unroll
         for (int j = 0; j < NPAR; ++j) acc[j] = 0.f;
@@ -314,16 +315,7 @@ __global__ void k_grad_items(const float *__restrict__ x, const float *__restric
 #pragma unroll 2
         for (uint32_t t = it.start + lane; t < it.end; t += 32) {
             float xv[6], g[6];
-            if (MODE == 0) {
-                float yv[6];
-                eval_track(cs[wib], x, t, xv, yv);
-                g[0] = w[0] * (yv[0] - theta[(size_t)t * 3 + 0]);
-                g[1] = w[1] * (yv[1] - theta[(size_t)t * 3 + 1]);
-                g[2] = w[2] * (yv[2] - theta[(size_t)t * 3 + 2]);
-                g[3] = yv[3];
-                g[4] = yv[4];
-                g[5] = yv[5];
-            } else {
+            {
                 const float2 *xp = reinterpret_cast<const float2 *>(x + (size_t)t * 6);
                 const float2 *gp = reinterpret_cast<const float2 *>(grad_y + (size_t)t * 6);
                 float2 a = xp[0], b = xp[1], d = xp[2];
@@ -395,6 +387,253 @@ __global__ void k_grad_final(const float *__restrict__ item_grad,
         dq[(size_t)s * 6 + (j - 36)] = total * sc;
 }
 
+// ---- the loss and its gradient in one pass --------------------------------------
+constexpr int LG_BT = 4;   // tracks per lane whose loads are in flight together
+
+// The loss and its gradient in one pass over the tracks.  Warp w of the grid
+// takes the contiguous items [w per, (w + 1) per) (per = ceil(items /
+// warps)); their sectors and first tracks are looked up together, one item
+// per lane, before any of them is used.  Every lane loads LG_BT of its tracks
+// (x and theta; the index is clamped to the last track, so the loads need
+// only the item's first track) before using any of them, while the item's
+// end and, for a new sector, its constants are fetched, then adds its tracks'
+// loss terms and the 42 products g x^T, g (g = dL/dy up to the factor 2/N)
+// in track order for as long as consecutive items belong to one sector; with
+// WY it also writes each track's y = F x + q.  When the sector changes, or
+// the warp's items end, the lanes' partials are summed through shared memory
+// (four runs of eight lanes in lane order, then the runs in a fixed tree)
+// into the slot of the segment's first item.  The final sums need no second
+// launch: after writing a segment the warp adds the segment's item count to
+// its sector's ticket (atomicAdd after a fence); the warp that completes the
+// sector's count sums the sector's segments in warp order -- their slots
+// follow from `per` alone --, writes dF[s], dq[s] and the sector's loss,
+// then adds the sector's item count to the batch's ticket; the warp that
+// completes that count sums the sector losses in sector order.  Nothing waits
+// on another warp, and for a given grid every sum runs in a fixed order, so
+// repeated calls give identical bits.  Sectors without tracks get zero
+// gradients.  The tickets (tickets[0..S]) must be zero at entry; every warp
+// that completes one sets it back to zero, so a call leaves them ready for
+// the next.
+template <bool WY>
+__global__ void __launch_bounds__(256, 2)
+    k_loss_grad(const float *__restrict__ x, const float *__restrict__ theta,
+                const int32_t *__restrict__ item_sector, const int32_t *__restrict__ item_start,
+                const int32_t *__restrict__ sector_off, const int32_t *__restrict__ sector_item,
+                const int32_t *__restrict__ n_items, uint32_t S, uint64_t n,
+                const float *__restrict__ F, const float *__restrict__ q,
+                const float *__restrict__ w, const float *__restrict__ scale_dev,
+                float *item_loss, float *item_grad, float *sector_loss, unsigned int *tickets,
+                float *loss, float *dF, float *dq, float *y) {
+    constexpr int TPL = CALIB_CHUNK / 32;   // tracks per lane and item
+    // per warp: F[s] and q[s] as six rows of eight floats (F[r][0..5], q[r], 0)
+    __shared__ __align__(16) float cs[8][48];
+    __shared__ float red_s[8][32 * (NPAR + 1)];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + wib, nw = gridDim.x * (blockDim.x >> 5);
+    const uint32_t NI = (uint32_t)*n_items;
+    const float scale = (n ? 2.0f / (float)n : 0.f) * (scale_dev ? *scale_dev : 1.f);
+    for (uint32_t s = gw; s < S; s += nw) {
+        if (sector_item[s + 1] != sector_item[s]) continue;
+        for (int j = lane; j < NPAR; j += 32) {
+            if (j < 36)
+                dF[(size_t)s * 36 + j] = 0.f;
+            else
+                dq[(size_t)s * 6 + (j - 36)] = 0.f;
+        }
+    }
+    if (NI == 0) {
+        if (gw == 0 && lane == 0) *loss = 0.f;
+        return;
+    }
+    const uint32_t per = (NI + nw - 1) / nw;
+    const uint32_t i0 = gw * per, i1 = min(i0 + per, NI);
+    if (i0 >= i1) return;
+    const float w0 = w[0], w1 = w[1], w2 = w[2];
+    const uint32_t last_track = (uint32_t)n - 1;
+    float acc[NPAR];
+    float lacc = 0.f;
+#pragma unroll
+    for (int j = 0; j < NPAR; ++j) acc[j] = 0.f;
+    uint32_t seg = i0;   // first item of the current segment
+    float *c = cs[wib];
+    for (uint32_t base = i0; base < i1; base += 32) {
+        // the next 32 items' sector, first track and end, one item per lane
+        const uint32_t cnt = min(32u, i1 - base);
+        uint32_t m_s = 0, m_start = 0, m_end = 0;
+        if ((uint32_t)lane < cnt) {
+            m_s = (uint32_t)__ldg(item_sector + base + lane);
+            m_start = (uint32_t)__ldg(item_start + base + lane);
+            m_end = min(m_start + (uint32_t)CALIB_CHUNK, (uint32_t)__ldg(sector_off + m_s + 1));
+        }
+        const uint32_t after = base + cnt < i1 ? (uint32_t)__ldg(item_sector + base + cnt) : ~0u;
+        for (uint32_t k = 0; k < cnt; ++k) {
+            const uint32_t i = base + k;
+            const uint32_t is = __shfl_sync(0xffffffffu, m_s, (int)k);
+            const uint32_t start = __shfl_sync(0xffffffffu, m_start, (int)k);
+#pragma unroll 1
+            for (int h = 0; h < TPL; h += LG_BT) {
+                float xv[LG_BT][6], th[LG_BT][3];
+#pragma unroll
+                for (int kk = 0; kk < LG_BT; ++kk) {
+                    const uint32_t t = min(start + (uint32_t)lane + 32u * (h + kk), last_track);
+                    const float2 *xp = reinterpret_cast<const float2 *>(x + (size_t)t * 6);
+                    const float2 a = __ldg(xp), b = __ldg(xp + 1), d = __ldg(xp + 2);
+                    xv[kk][0] = a.x; xv[kk][1] = a.y; xv[kk][2] = b.x;
+                    xv[kk][3] = b.y; xv[kk][4] = d.x; xv[kk][5] = d.y;
+                    th[kk][0] = __ldg(theta + (size_t)t * 3 + 0);
+                    th[kk][1] = __ldg(theta + (size_t)t * 3 + 1);
+                    th[kk][2] = __ldg(theta + (size_t)t * 3 + 2);
+                }
+                const uint32_t iend = __shfl_sync(0xffffffffu, m_end, (int)k);
+                if (h == 0 && i == seg) {
+                    // a new segment's constants, fetched while the tracks are in flight
+                    for (int j = lane; j < 48; j += 32) {
+                        const int r = j >> 3, l = j & 7;
+                        c[j] = l < 6 ? __ldg(F + (size_t)is * 36 + r * 6 + l)
+                                     : (l == 6 ? __ldg(q + (size_t)is * 6 + r) : 0.f);
+                    }
+                    __syncwarp();
+                }
+#pragma unroll
+                for (int kk = 0; kk < LG_BT; ++kk) {
+                    const uint32_t t = start + (uint32_t)lane + 32u * (h + kk);
+                    if (t >= iend) continue;
+                    float g[6];
+#pragma unroll
+                    for (int r = 0; r < 6; ++r) {
+                        const float4 u = *reinterpret_cast<const float4 *>(c + r * 8);
+                        const float4 v = *reinterpret_cast<const float4 *>(c + r * 8 + 4);
+                        float e = v.z;
+                        e = fmaf(u.x, xv[kk][0], e);
+                        e = fmaf(u.y, xv[kk][1], e);
+                        e = fmaf(u.z, xv[kk][2], e);
+                        e = fmaf(u.w, xv[kk][3], e);
+                        e = fmaf(v.x, xv[kk][4], e);
+                        e = fmaf(v.y, xv[kk][5], e);
+                        g[r] = e;
+                    }
+                    if (WY) {
+                        float2 *yp = reinterpret_cast<float2 *>(y + (size_t)t * 6);
+                        yp[0] = make_float2(g[0], g[1]);
+                        yp[1] = make_float2(g[2], g[3]);
+                        yp[2] = make_float2(g[4], g[5]);
+                    }
+                    const float r0 = g[0] - th[kk][0], r1 = g[1] - th[kk][1], r2 = g[2] - th[kk][2];
+                    lacc += w0 * r0 * r0 + w1 * r1 * r1 + w2 * r2 * r2 + g[3] * g[3] +
+                            g[4] * g[4] + g[5] * g[5];
+                    g[0] = w0 * r0;
+                    g[1] = w1 * r1;
+                    g[2] = w2 * r2;
+#pragma unroll
+                    for (int r = 0; r < 6; ++r) {
+#pragma unroll
+                        for (int l = 0; l < 6; ++l) acc[r * 6 + l] = fmaf(g[r], xv[kk][l], acc[r * 6 + l]);
+                        acc[36 + r] += g[r];
+                    }
+                }
+            }
+            // does the segment end with this item?
+            const uint32_t next_s = __shfl_sync(0xffffffffu, m_s, (int)min(k + 1, 31u));
+            if (i + 1 != i1 && (k + 1 < cnt ? next_s : after) == is) continue;
+            // the segment's sums over the lanes into its first item's slot: four
+            // runs of eight lanes in lane order, then the runs in a fixed tree
+            {
+                float *red = red_s[wib];
+#pragma unroll
+                for (int j = 0; j < NPAR; ++j) red[lane * (NPAR + 1) + j] = acc[j];
+                __syncwarp();
+                for (int j = lane; j < NPAR; j += 32) {
+                    float part[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        float v = red[(8 * u) * (NPAR + 1) + j];
+#pragma unroll
+                        for (int m = 1; m < 8; ++m) v += red[(8 * u + m) * (NPAR + 1) + j];
+                        part[u] = v;
+                    }
+                    item_grad[(size_t)seg * NPAR + j] = (part[0] + part[1]) + (part[2] + part[3]);
+                }
+                const float lt = warp_sum(lacc);
+                if (lane == 0) item_loss[seg] = lt;
+                __syncwarp();
+            }
+            const uint32_t seg_items = i + 1 - seg;
+            seg = i + 1;
+            lacc = 0.f;
+#pragma unroll
+            for (int j = 0; j < NPAR; ++j) acc[j] = 0.f;
+            // the sector's ticket
+            const uint32_t a = (uint32_t)sector_item[is], b = (uint32_t)sector_item[is + 1];
+            __threadfence();
+            unsigned int last = 0;
+            if (lane == 0) last = atomicAdd(&tickets[is], seg_items) + seg_items == b - a;
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (!last) continue;
+            __threadfence();
+            if (lane == 0) tickets[is] = 0u;   // ready for the next call
+            // the sector's segments: one per warp whose items meet [a, b), in warp order
+            const uint32_t wa = a / per, wz = (b - 1) / per;
+            for (int j = lane; j < NPAR; j += 32) {
+                float total = 0.f;
+                uint32_t v = wa;
+                for (; v + 8 <= wz + 1; v += 8) {   // eight loads in flight, added in order
+                    float u8[8];
+#pragma unroll
+                    for (uint32_t u = 0; u < 8; ++u)
+                        u8[u] = __ldcg(item_grad + (size_t)max(a, (v + u) * per) * NPAR + j);
+#pragma unroll
+                    for (uint32_t u = 0; u < 8; ++u) total += u8[u];
+                }
+                for (; v <= wz; ++v) total += __ldcg(item_grad + (size_t)max(a, v * per) * NPAR + j);
+                if (j < 36)
+                    dF[(size_t)is * 36 + j] = total * scale;
+                else
+                    dq[(size_t)is * 6 + (j - 36)] = total * scale;
+            }
+            float sl = 0.f;
+            for (uint32_t v = wa + (uint32_t)lane; v <= wz; v += 32)
+                sl += __ldcg(item_loss + max(a, v * per));
+            sl = warp_sum(sl);
+            if (lane == 0) sector_loss[is] = sl;
+            __syncwarp();
+            // the batch's ticket counts the items of summed sectors
+            __threadfence();
+            unsigned int fin = 0;
+            if (lane == 0) fin = atomicAdd(&tickets[S], b - a) + (b - a) == NI;
+            fin = __shfl_sync(0xffffffffu, fin, 0);
+            if (fin) {
+                __threadfence();
+                if (lane == 0) tickets[S] = 0u;   // ready for the next call
+                float tl[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {   // S <= 512: every sector loss in flight at once
+                    const uint32_t s2 = (uint32_t)lane + 32u * u;
+                    tl[u] = (s2 < S && sector_item[s2 + 1] != sector_item[s2])
+                                ? __ldcg(sector_loss + s2)
+                                : 0.f;
+                }
+                float t = 0.f;
+#pragma unroll
+                for (int u = 0; u < 16; ++u) t += tl[u];
+                t = warp_sum(t);
+                if (lane == 0) *loss = t / (float)n;
+            }
+        }
+    }
+}
+
+// out_F = g dF, out_q = g dq over S sectors, one launch
+__global__ void k_grad_scale(const float *__restrict__ g, const float *__restrict__ dF,
+                             const float *__restrict__ dq, uint32_t S, float *out_F,
+                             float *out_q) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    const float v = *g;
+    if (k < S * 36)
+        out_F[k] = dF[k] * v;
+    else if (k < S * NPAR)
+        out_q[k - S * 36] = dq[k - S * 36] * v;
+}
+
 }  // namespace
 
 // ---- launchers used by svt_abi.cu -------------------------------------------------
@@ -444,22 +683,42 @@ void launch_calib_loss(const float *x, const float *theta, const int32_t *item_s
     launch_after(k_loss_final, 1, 1024, 0, st, item_loss, n_items, n, loss);
 }
 
-void launch_calib_grad(int mode, const float *x, const float *theta, const float *grad_y,
-                       const int32_t *item_sector, const int32_t *item_start,
-                       const int32_t *sector_off, const int32_t *sector_item,
-                       const int32_t *n_items, uint32_t max_items, uint32_t S, const float *F,
-                       const float *q, const float *w, const float *scale_dev, float scale,
-                       float *item_grad, float *dF, float *dq, float *dx, int grid,
-                       cudaStream_t st) {
-    const int g = (int)min((uint32_t)grid, (max_items + 7) / 8 + 1);
-    if (mode == 0)
-        k_grad_items<0><<<g, 256, 0, st>>>(x, theta, grad_y, item_sector, item_start, sector_off,
-                                          n_items, F, q, w, item_grad, dx);
+void launch_calib_loss_grad(const float *x, const float *theta, const int32_t *item_sector,
+                            const int32_t *item_start, const int32_t *sector_off,
+                            const int32_t *sector_item, const int32_t *n_items, uint32_t S,
+                            uint64_t n, const float *F, const float *q, const float *w,
+                            const float *scale_dev, float *item_loss, float *item_grad,
+                            float *sector_loss, unsigned int *tickets, float *loss, float *dF,
+                            float *dq, float *y, int sms, cudaStream_t st) {
+    // two resident blocks of 8 warps per SM, each warp a contiguous run of items
+    const int g = max(sms, 1) * 2;
+    if (y)
+        k_loss_grad<true><<<g, 256, 0, st>>>(x, theta, item_sector, item_start, sector_off,
+                                             sector_item, n_items, S, n, F, q, w, scale_dev,
+                                             item_loss, item_grad, sector_loss, tickets, loss, dF,
+                                             dq, y);
     else
-        k_grad_items<1><<<g, 256, 0, st>>>(x, theta, grad_y, item_sector, item_start, sector_off,
-                                          n_items, F, q, w, item_grad, dx);
+        k_loss_grad<false><<<g, 256, 0, st>>>(x, theta, item_sector, item_start, sector_off,
+                                              sector_item, n_items, S, n, F, q, w, scale_dev,
+                                              item_loss, item_grad, sector_loss, tickets, loss,
+                                              dF, dq, y);
+}
+
+void launch_calib_grad_scale(const float *g, const float *dF, const float *dq, uint32_t S,
+                             float *out_F, float *out_q, cudaStream_t st) {
+    k_grad_scale<<<(S * NPAR + 255) / 256, 256, 0, st>>>(g, dF, dq, S, out_F, out_q);
+}
+
+void launch_calib_grad(const float *x, const float *grad_y, const int32_t *item_sector,
+                       const int32_t *item_start, const int32_t *sector_off,
+                       const int32_t *sector_item, const int32_t *n_items, uint32_t max_items,
+                       uint32_t S, const float *F, float *item_grad, float *dF, float *dq,
+                       float *dx, int grid, cudaStream_t st) {
+    const int g = (int)min((uint32_t)grid, (max_items + 7) / 8 + 1);
+    k_grad_items<<<g, 256, 0, st>>>(x, grad_y, item_sector, item_start, sector_off, n_items, F,
+                                    item_grad, dx);
     launch_after(k_grad_final, (S * NPAR + 255) / 256, 256, 0, st, item_grad, sector_item, S,
-                 scale_dev, scale, dF, dq);
+                 (const float *)nullptr, 1.0f, dF, dq);
 }
 
 }  // namespace svt

@@ -271,12 +271,19 @@ void launch_calib_loss(const float *x, const float *theta, const int32_t *item_s
                        const int32_t *n_items, uint32_t max_items, uint64_t n, const float *F,
                        const float *q, const float *w, float *item_loss, float *loss, int grid,
                        cudaStream_t st);
-void launch_calib_grad(int mode, const float *x, const float *theta, const float *grad_y,
-                       const int32_t *item_sector, const int32_t *item_start,
-                       const int32_t *sector_off, const int32_t *sector_item,
-                       const int32_t *n_items, uint32_t max_items, uint32_t S, const float *F,
-                       const float *q, const float *w, const float *scale_dev, float scale,
-                       float *item_grad, float *dF, float *dq, float *dx, int grid,
-                       cudaStream_t st);
+void launch_calib_loss_grad(const float *x, const float *theta, const int32_t *item_sector,
+                            const int32_t *item_start, const int32_t *sector_off,
+                            const int32_t *sector_item, const int32_t *n_items, uint32_t S,
+                            uint64_t n, const float *F, const float *q, const float *w,
+                            const float *scale_dev, float *item_loss, float *item_grad,
+                            float *sector_loss, unsigned int *tickets, float *loss, float *dF,
+                            float *dq, float *y, int sms, cudaStream_t st);
+void launch_calib_grad_scale(const float *g, const float *dF, const float *dq, uint32_t S,
+                             float *out_F, float *out_q, cudaStream_t st);
+void launch_calib_grad(const float *x, const float *grad_y, const int32_t *item_sector,
+                       const int32_t *item_start, const int32_t *sector_off,
+                       const int32_t *sector_item, const int32_t *n_items, uint32_t max_items,
+                       uint32_t S, const float *F, float *item_grad, float *dF, float *dq,
+                       float *dx, int grid, cudaStream_t st);
 
 }  // namespace svt

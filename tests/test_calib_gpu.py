@@ -138,3 +138,85 @@ def test_calibration_descent_reduces_loss():
         loss.backward()
         opt.step()
     assert calib.calib_loss(F, q, data).item() < 0.7 * first
+
+
+def test_fused_and_unfused_paths_empty_sectors_and_upstream_scale():
+    """The fused loss-and-gradient pass and the separate backward pass both
+    match the FP64 gradient; sectors without tracks get exactly zero; an
+    upstream gradient of 3 scales the result; the loss without a gradient
+    request uses the loss-only pass and gives the same value."""
+    import torch
+    from paper_1311_0380_gb300 import calib
+    S = 64
+    cs = make(20000, S, seed=21)
+    sector = (cs.sector % 41).astype(np.int32)          # sectors 41..63 stay empty
+    data = calib.CalibData(cs.x, sector, cs.theta, S, cs.weight)
+    rF, rq = ref.grad(cs.x, sector, cs.theta, cs.weight, cs.F0, cs.q0)
+    L64 = ref.loss(cs.x, sector, cs.theta, cs.weight, cs.F0, cs.q0)
+    for fused in (True, False):
+        F = torch.tensor(cs.F0, device="cuda", requires_grad=True)
+        q = torch.tensor(cs.q0, device="cuda", requires_grad=True)
+        loss = calib.calib_loss(F, q, data, fused=fused)
+        assert abs(loss.item() - L64) <= REL * abs(L64)
+        (3.0 * loss).backward()
+        gF, gq = F.grad.cpu().numpy(), q.grad.cpu().numpy()
+        check_grad(gF / 3.0, gq / 3.0, rF, rq)
+        assert np.all(gF[41:] == 0) and np.all(gq[41:] == 0)
+    with torch.no_grad():
+        F = torch.tensor(cs.F0, device="cuda")
+        q = torch.tensor(cs.q0, device="cuda")
+        l0 = calib.calib_loss(F, q, data).item()
+    assert abs(l0 - L64) <= REL * abs(L64)
+
+
+def test_fused_pass_on_one_track_and_on_no_tracks():
+    import torch
+    from paper_1311_0380_gb300 import calib
+    S = 4
+    cs = make(2000, S, seed=23)
+    for n in (1, 0):
+        data = calib.CalibData(cs.x[:n], cs.sector[:n], cs.theta[:n], S, cs.weight)
+        F = torch.tensor(cs.F0, device="cuda", requires_grad=True)
+        q = torch.tensor(cs.q0, device="cuda", requires_grad=True)
+        loss = calib.calib_loss(F, q, data)
+        loss.backward()
+        if n == 0:
+            assert loss.item() == 0.0
+            assert np.all(F.grad.cpu().numpy() == 0) and np.all(q.grad.cpu().numpy() == 0)
+        else:
+            L64 = ref.loss(cs.x[:n], cs.sector[:n], cs.theta[:n], cs.weight, cs.F0, cs.q0)
+            assert abs(loss.item() - L64) <= REL * abs(L64)
+            rF, rq = ref.grad(cs.x[:n], cs.sector[:n], cs.theta[:n], cs.weight, cs.F0, cs.q0)
+            check_grad(F.grad.cpu().numpy(), q.grad.cpu().numpy(), rF, rq)
+
+
+def test_loss_and_fit_in_one_pass_match_the_separate_calls():
+    """calib_loss_and_fit gives the fitted parameters bit for bit as the
+    forward kernel writes them, the same loss and gradient as calib_loss, and
+    repeated calls on one CalibData (whose workspace keeps the pass's
+    tickets) give identical bits."""
+    import torch
+    from paper_1311_0380_gb300 import calib
+    S = 32
+    cs = make(60000, S, seed=31)
+    data = calib.CalibData(cs.x, cs.sector, cs.theta, S, cs.weight)
+    runs = []
+    for _ in range(3):
+        F = torch.tensor(cs.F0, device="cuda", requires_grad=True)
+        q = torch.tensor(cs.q0, device="cuda", requires_grad=True)
+        loss, y = calib.calib_loss_and_fit(F, q, data)
+        loss.backward()
+        runs.append((loss.item(), y.cpu().numpy(), F.grad.cpu().numpy(), q.grad.cpu().numpy()))
+    for r in runs[1:]:
+        assert r[0] == runs[0][0]
+        assert all(np.array_equal(a, b) for a, b in zip(r[1:], runs[0][1:]))
+    F = torch.tensor(cs.F0, device="cuda", requires_grad=True)
+    q = torch.tensor(cs.q0, device="cuda", requires_grad=True)
+    y_ref = calib.fit_fp32(F, q, data).detach().cpu().numpy()
+    assert np.array_equal(runs[0][1], y_ref)
+    loss = calib.calib_loss(F, q, data)
+    loss.backward()
+    assert loss.item() == runs[0][0]
+    assert np.array_equal(F.grad.cpu().numpy(), runs[0][2])
+    rF, rq = ref.grad(cs.x, cs.sector, cs.theta, cs.weight, cs.F0, cs.q0)
+    check_grad(runs[0][2], runs[0][3], rF, rq)
