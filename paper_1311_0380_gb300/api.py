@@ -454,8 +454,8 @@ class StreamingRunner:
         return status, rec
 
 
-FUSED_LAUNCHES_PER_RUN = 5   # prologue, unpack_count, scan, unpack_roads, fit
-PLAIN_LAUNCHES_PER_RUN = 13  # unpack (5), combine (5), fit, select, format
+FUSED_LAUNCHES_PER_RUN = 3   # prologue, unpack_roads (one pass over the tiles), fit
+PLAIN_LAUNCHES_PER_RUN = 11  # unpack (3), combine (5), fit, select, format
 
 
 class HostRunner:

@@ -79,7 +79,8 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 // Workspace layout of svt_unpack.
 struct UnpackWs {
     Dims *dims;
-    uint32_t *tile_roads;
+    unsigned long long *tile_state;   // road counts the tiles publish (look-back)
+    uint32_t *tile_ticket;            // next tile to take
     uint32_t *first_ev;
     size_t bytes;
 };
@@ -87,7 +88,8 @@ UnpackWs carve_unpack(void *base, uint64_t max_words) {
     Carver c(base);
     UnpackWs w;
     w.dims = c.take<Dims>(1);
-    w.tile_roads = c.take<uint32_t>(n_tiles(max_words) + 1);
+    w.tile_state = c.take<unsigned long long>(n_tiles(max_words) + 1);
+    w.tile_ticket = c.take<uint32_t>(1);
     w.first_ev = c.take<uint32_t>(n_tiles(max_words) + 1);
     w.bytes = c.size();
     return w;
@@ -98,7 +100,8 @@ struct RunWs {
     Dims *dims;
     uint64_t *counts;
     uint64_t *work;   // [0] split-road reservation, [1] the fit kernel's two queue counters
-    uint32_t *tile_roads, *first_ev;
+    unsigned long long *tile_state;   // road counts the tiles publish (look-back)
+    uint32_t *tile_ticket, *first_ev;
     RoadDesc *desc;
     uint32_t *big_road, *big_item_off, *big_pending;
     unsigned long long *key;
@@ -112,7 +115,8 @@ RunWs carve_run(void *base, uint64_t max_words, uint64_t max_events, uint64_t ro
     w.dims = c.take<Dims>(1);
     w.counts = c.take<uint64_t>(4);
     w.work = c.take<uint64_t>(2);
-    w.tile_roads = c.take<uint32_t>(T + 1);
+    w.tile_state = c.take<unsigned long long>(T + 1);
+    w.tile_ticket = c.take<uint32_t>(1);
     w.first_ev = c.take<uint32_t>(T + 1);
     w.desc = c.take<RoadDesc>(road_cap);
     w.big_road = c.take<uint32_t>(road_cap);
@@ -224,14 +228,11 @@ int svt_unpack(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_even
     const int grid = tile_grid();
     svt_config cfg{15, 15, 0, 1, 0, n_sectors, xft_pairs};
     launch_prologue(w.dims, n_words, n_events, nullptr, d_event_off, w.first_ev, status, d_n_roads,
-                    1, nullptr, 0, grid, st);
-    launch_unpack_count(d_words, d_event_off, w.dims, w.first_ev, n_words, n_sectors, w.tile_roads,
-                        status, grid, st);
-    launch_scan_tiles(w.tile_roads, w.dims, nullptr, d_n_roads, d_event_road, status, st);
+                    1, nullptr, 0, w.tile_state, w.tile_ticket, grid, st);
     const FusedRoads none{nullptr, nullptr, BigList{}, 1, 0};
-    launch_unpack_roads(d_words, d_event_off, w.dims, w.first_ev, n_words, w.tile_roads, road_cap,
-                        d_road_word, d_road_nhit, d_event_road, cfg, none, nullptr, status, grid,
-                        st);
+    launch_unpack_roads(d_words, d_event_off, w.dims, w.first_ev, n_words, w.tile_state,
+                        w.tile_ticket, d_n_roads, road_cap, d_road_word, d_road_nhit, d_event_road,
+                        cfg, none, nullptr, status, grid, st);
     launch_unpack_events(d_words, d_event_off, w.dims, n_events, d_event_road, status, grid, st);
     return launch_status();
 }
@@ -354,12 +355,10 @@ int run_impl(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_
     {
         const NvtxRange stage("svt_run: unpack");
         launch_prologue(w.dims, n_words, n_events, d_sizes, d_event_off, w.first_ev, status, counts, 4,
-                        w.work, 2, grid, st);
-        launch_unpack_count(d_words, d_event_off, w.dims, w.first_ev, n_words, cfg->n_sectors,
-                            w.tile_roads, status, grid, st);
-        launch_scan_tiles(w.tile_roads, w.dims, nullptr, counts + 0, event_road, status, st);
-        launch_unpack_roads(d_words, d_event_off, w.dims, w.first_ev, n_words, w.tile_roads, road_cap,
-                            nullptr, nullptr, event_road, *cfg, fr, counts, status, grid, st);
+                        w.work, 2, w.tile_state, w.tile_ticket, grid, st);
+        launch_unpack_roads(d_words, d_event_off, w.dims, w.first_ev, n_words, w.tile_state,
+                            w.tile_ticket, counts + 0, road_cap, nullptr, nullptr, event_road,
+                            *cfg, fr, counts, status, grid, st);
     }
     const NvtxRange fit_range("svt_run: combine, fit, cut, select, format");
     if (timer && cudaEventRecord(timer->start, st) != cudaSuccess) return SVT_ERR_CUDA;
@@ -685,7 +684,8 @@ int svt_calib_index(const int32_t *d_sector, uint64_t n_tracks, uint32_t n_secto
     if (index_bytes < x.bytes) return SVT_ERR_BAD_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     unsigned long long *status = (unsigned long long *)d_status;
-    launch_prologue(nullptr, 0, 0, nullptr, nullptr, nullptr, status, nullptr, 0, nullptr, 0, 1, st);
+    launch_prologue(nullptr, 0, 0, nullptr, nullptr, nullptr, status, nullptr, 0, nullptr, 0,
+                    nullptr, nullptr, 1, st);
     if (cudaMemsetAsync(x.sector_off, 0, sizeof(int32_t) * (n_sectors + 1), st) != cudaSuccess ||
         cudaMemsetAsync(x.sector_item, 0, sizeof(int32_t) * (n_sectors + 1), st) != cudaSuccess ||
         cudaMemsetAsync(x.n_items, 0, sizeof(int32_t), st) != cudaSuccess)

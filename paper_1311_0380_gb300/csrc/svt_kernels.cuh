@@ -159,28 +159,23 @@ __device__ __forceinline__ uint32_t road_big_items(const RoadDesc &d, const Fuse
 // Prologue: batch sizes (from `sizes` on the device when given, bounded by
 // n_words / n_events), status reset, counts[0..n_counts) and zero[0..n_zero)
 // cleared and, when first_ev is given, first_ev[t] = the first event whose
-// offset is at or after word tile t's start, for t = 0..T.  Only block 0
-// writes the sizes and the status; no block reports anything.
+// offset is at or after word tile t's start, for t = 0..T, and the tiles'
+// published road counts (tile_state[0..T)) and the tile counter cleared.
+// Only block 0 writes the sizes and the status; no block reports anything.
 void launch_prologue(Dims *dims, uint64_t n_words, uint64_t n_events, const uint64_t *sizes,
                      const uint64_t *event_off, uint32_t *first_ev, unsigned long long *status,
-                     uint64_t *counts, int n_counts, uint64_t *zero, int n_zero, int grid,
+                     uint64_t *counts, int n_counts, uint64_t *zero, int n_zero,
+                     unsigned long long *tile_state, uint32_t *tile_ticket, int grid,
                      cudaStream_t st);
-// K1: per-word validation (rules V1..V7, V9) and road headers per tile.
-void launch_unpack_count(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
-                         const uint32_t *first_ev, uint64_t max_words, uint32_t n_sectors,
-                         uint32_t *tile_roads, unsigned long long *status, int grid,
-                         cudaStream_t st);
-// Exclusive scan, in place, of a[0..n) where n = *n_dev, or the number of
-// word tiles when n_dev is NULL; writes the total to a[n] and, when given, to
-// *total64 and to event_road[n_events].  A total of 2^32 or more lowers the
-// status to (0, OOM).
-void launch_scan_tiles(uint32_t *a, const Dims *dims, const uint64_t *n_dev, uint64_t *total64,
-                       uint32_t *event_road, unsigned long long *status, cudaStream_t st);
-// K2: road extraction: road_word, road_nhit (either may be null), rule V8,
-// event_road of events starting in each tile; with fr.desc also the road
-// descriptors, the split-road list and the evaluated combinations (counts[2]).
+// The one pass over the word tiles: per-word validation (rules V1..V9),
+// global road indices (block scan plus a look-back over the counts earlier
+// tiles publish), road_word, road_nhit (either may be null), event_road of
+// the events starting in each tile and of n_events (the road count R, also
+// written to *total64); with fr.desc also the road descriptors, the split-road
+// list and the evaluated combinations (counts[2]).
 void launch_unpack_roads(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
-                         const uint32_t *first_ev, uint64_t max_words, const uint32_t *tile_roads,
+                         const uint32_t *first_ev, uint64_t max_words,
+                         unsigned long long *tile_state, uint32_t *tile_ticket, uint64_t *total64,
                          uint64_t road_cap, uint32_t *road_word, uint32_t *road_nhit,
                          uint32_t *event_road, const svt_config cfg, const FusedRoads fr,
                          uint64_t *counts, unsigned long long *status, int grid, cudaStream_t st);

@@ -4,15 +4,16 @@
 // The batch is cut into tiles of 1024 words (128 threads x 8 words; smaller
 // tiles than 2048 words of 256 threads take 1-2 % off the step, since the
 // kernels are bound by each tile's chain of barriers and scans).  A prologue maps every tile to
-// the first event that starts in it (one pass over the event offsets).  K1
-// validates every word against its left neighbour (rules V2..V7, V9 of
-// include/svt.h's format), checks V1 for the events starting in the tile and
-// counts road headers per tile; a single-block scan turns the counts into
-// each tile's first road index; K2 then gives every road header its global
-// index (block scan), records where it sits, counts its hits (rule V8, hits
-// per layer) and, for the fused path, sizes its work and appends split roads
-// to the work list.  The offsets and V10 are checked per event afterwards.
-// Loads are vectorised (2 x 16 B per thread, coalesced across the warp).
+// the first event that starts in it (one pass over the event offsets).  One
+// pass over the tiles then validates every word against its left neighbour
+// (rules V2..V7, V9 of include/svt.h's format), checks V1 for the events
+// starting in the tile, gives every road header its global index (a block
+// scan, plus the road count of the tiles before, found by looking back over
+// the counts that earlier tiles publish), records where it sits, counts its
+// hits (rule V8, hits per layer) and, for the fused path, sizes its work and
+// appends split roads to the work list.  The offsets and V10 are checked per
+// event afterwards.  Loads are vectorised (2 x 16 B per thread, coalesced
+// across the warp).
 #include "svt_kernels.cuh"
 
 namespace svt {
@@ -69,7 +70,8 @@ __device__ __forceinline__ uint64_t warp_lower_bound64(const uint64_t *__restric
 __global__ void k_prologue(Dims *dims, uint64_t n_words, uint64_t n_events,
                            const uint64_t *sizes, const uint64_t *__restrict__ event_off,
                            uint32_t *first_ev, unsigned long long *status, uint64_t *counts,
-                           int n_counts, uint64_t *zero, int n_zero) {
+                           int n_counts, uint64_t *zero, int n_zero,
+                           unsigned long long *tile_state, uint32_t *tile_ticket) {
     // first of its sequence: launched in stream order after whatever came
     // before, so only the next kernel is let in early
     allow_next_grid();
@@ -93,6 +95,10 @@ __global__ void k_prologue(Dims *dims, uint64_t n_words, uint64_t n_events,
     if (zero && tid < (uint64_t)n_zero) zero[tid] = 0;
     if (!first_ev) return;
     const uint64_t T = n_tiles(n_words);
+    // nothing published and no tile taken yet
+    if (tile_ticket && tid == 0) *tile_ticket = 0;
+    if (tile_state)
+        for (uint64_t t = tid; t < T; t += stride) tile_state[t] = 0ull;
     for (uint64_t e = tid; e <= n_events; e += stride) {
         const uint64_t t0 = e > 0 ? min(__ldg(event_off + e - 1), n_words) / TILE_WORDS + 1 : 0;
         const uint64_t t1 = e < n_events ? min(__ldg(event_off + e), n_words) / TILE_WORDS : T;
@@ -107,116 +113,65 @@ __device__ __forceinline__ void tile_events(const uint32_t *__restrict__ first_e
     e_hi = max(e_lo, min((uint64_t)__ldg(first_ev + t + 1), n_events));
 }
 
-__global__ void __launch_bounds__(TILE_THREADS)
-    k_unpack_count(const uint32_t *__restrict__ words, const uint64_t *__restrict__ event_off,
-                   const Dims *__restrict__ dims, const uint32_t *__restrict__ first_ev,
-                   uint32_t n_sectors, uint32_t *tile_roads, unsigned long long *status) {
-    __shared__ uint32_t red[TILE_THREADS / 32 + 1];
-    wait_prior_grid();
-    allow_next_grid();
-    const uint64_t n_words = dims->n_words, n_events = dims->n_events;
-    const uint64_t T = n_tiles(n_words);
-    for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
-        const uint64_t tile_start = t * TILE_WORDS, tile_end = min(tile_start + TILE_WORDS, n_words);
-        const uint64_t base = tile_start + (uint64_t)threadIdx.x * TILE_PER_THREAD;
-        uint64_t e_lo, e_hi;
-        tile_events(first_ev, t, n_events, e_lo, e_hi);
-        uint32_t w[TILE_PER_THREAD];
-        load8(words, base, n_words, w);
-        uint32_t prev = __shfl_up_sync(0xffffffffu, w[TILE_PER_THREAD - 1], 1);
-        if ((threadIdx.x & 31) == 0) prev = (base > 0 && base - 1 < n_words) ? __ldg(words + base - 1) : 0u;
-        uint32_t cnt = 0;   // road headers (low 16 bits) and event headers (high 16 bits)
-#pragma unroll
-        for (int j = 0; j < TILE_PER_THREAD; ++j) {
-            const uint64_t i = base + j;
-            if (i >= n_words) break;
-            const uint32_t x = w[j];
-            const uint32_t p = (j == 0) ? prev : w[j - 1];
-            const uint32_t ty = w_type(x);
-            if (ty == TYPE_ROAD) {
-                cnt += 1;
-                if (rd_sector(x) >= n_sectors) report(status, i, SVT_ERR_BAD_SECTOR);     // V9
-            } else if (ty == TYPE_BAD) {
-                report(status, i, SVT_ERR_BAD_TYPE);                                    // V3
-            } else if (ty == TYPE_EVENT) {
-                cnt += 1u << 16;   // V2 (an event header must start an event): below
-            } else {
-                // V4 and V7 also fire on an event's first word, where V1 already
-                // reports the same word with the smallest code, so the key is unchanged.
-                if (i > 0 && w_type(p) == TYPE_EVENT) report(status, i, SVT_ERR_BAD_TYPE);   // V4
-                if (hit_reserved(x) != 0) report(status, i, SVT_ERR_BAD_RESERVED);           // V5
-                if (hit_layer(x) > 5) report(status, i, SVT_ERR_BAD_LAYER);                  // V6
-                if (i > 0 && w_type(p) == TYPE_HIT && hit_layer(p) > hit_layer(x))
-                    report(status, i, SVT_ERR_UNSORTED);                                     // V7
-            }
-        }
-        // V1: the events starting in this tile start with an event header
-        int v1_bad = 0;
-        for (uint64_t e = e_lo + threadIdx.x; e < e_hi; e += TILE_THREADS) {
-            const uint64_t s0 = __ldg(event_off + e);
-            if (s0 >= tile_start && s0 < tile_end && w_type(__ldg(words + s0)) != TYPE_EVENT) {
-                report(status, s0, SVT_ERR_BAD_TYPE);                                   // V1
-                v1_bad = 1;
-            }
-        }
-        uint32_t total;
-        block_exclusive_scan<uint32_t>(cnt, red, &total);
-        v1_bad = __syncthreads_or(v1_bad);
-        // V2: every event-header word must sit at an event offset.  When the
-        // tile holds as many headers as events start in it and all of those
-        // start with a header (V1), the headers are exactly those starts;
-        // otherwise every header of the tile is looked up.
-        if ((total >> 16) != e_hi - e_lo || v1_bad) {   // (rare: the batch is invalid)
-            const int lane = threadIdx.x & 31;
-            for (int j = 0; j < TILE_PER_THREAD; ++j) {
-                const bool ev = base + j < n_words && w_type(__ldg(words + base + j)) == TYPE_EVENT;
-                uint32_t bal = __ballot_sync(0xffffffffu, ev);
-                while (bal) {
-                    const int src = __ffs(bal) - 1;
-                    const uint64_t i = __shfl_sync(0xffffffffu, base + j, src);
-                    const uint64_t e = warp_lower_bound64(event_off, n_events, i, lane);
-                    const bool start = e < n_events && __ldg(event_off + e) == i;
-                    if (lane == src && !start) report(status, i, SVT_ERR_BAD_TYPE);
-                    bal &= bal - 1;
-                }
-            }
-        }
-        if (threadIdx.x == 0) tile_roads[t] = total & 0xFFFFu;
-    }
+// ---- road indices across tiles: one pass with look-back --------------------------
+// Every tile publishes its road count in tile_state[t] as soon as its block
+// has counted (kind TILE_AGGREGATE), and its inclusive prefix -- the roads of
+// tiles 0..t -- once it knows the tiles before it (kind TILE_INCLUSIVE; tile 0
+// publishes that at once).  Words: kind in bits [63:62], count in [39:0];
+// zero means nothing published yet.
+constexpr unsigned long long TILE_AGGREGATE = 1, TILE_INCLUSIVE = 2;
+constexpr unsigned long long TILE_COUNT_MASK = (1ull << 40) - 1;
+constexpr uint32_t LOOK_BACK_SPINS = 1u << 20;   // bounded wait, then SVT_ERR_TIMEOUT
+
+__device__ __forceinline__ void publish_tile(unsigned long long *p, unsigned long long kind,
+                                             unsigned long long v) {
+    const unsigned long long x = (kind << 62) | (v & TILE_COUNT_MASK);
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(x) : "memory");
+}
+__device__ __forceinline__ unsigned long long peek_tile(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
 
-__global__ void __launch_bounds__(1024)
-    k_scan_tiles(uint32_t *a, const Dims *__restrict__ dims, const uint64_t *n_dev,
-                 uint64_t *total64, uint32_t *event_road, unsigned long long *status) {
-    __shared__ uint32_t sm[33];
-    wait_prior_grid();
-    allow_next_grid();
-    const uint64_t n = n_dev ? *n_dev : n_tiles(dims->n_words);
-    uint64_t carry = 0;
-    for (uint64_t c0 = 0; c0 < n; c0 += 4096) {
-        const uint64_t i0 = c0 + (uint64_t)threadIdx.x * 4;
-        uint32_t v[4], s = 0;
+// Roads in the tiles before tile t (t >= 1), by one warp: lane k reads tile
+// hi - k of a window of 32 tiles, newest first; the sum runs over the window's
+// tiles up to the newest one whose inclusive count is out (that one
+// included), else over the whole window and on to the next.  A tile that has
+// published nothing yet is re-read after a short sleep; it belongs to a block
+// that took its tile earlier and is running, so it publishes soon.  After
+// LOOK_BACK_SPINS rounds the wait gives up with SVT_ERR_TIMEOUT (the batch's
+// status is then an error and its outputs are not used).
+__device__ unsigned long long tiles_before(const unsigned long long *state, uint64_t t, int lane,
+                                           unsigned long long *status) {
+    unsigned long long excl = 0;
+    uint32_t spins = 0;
+    for (int64_t hi = (int64_t)t - 1; hi >= 0; hi -= 32) {
+        const int64_t idx = hi - lane;
+        // before tile 0 there is nothing: read as an inclusive count of zero
+        unsigned long long v = idx >= 0 ? peek_tile(state + idx) : (TILE_INCLUSIVE << 62);
+        for (;;) {
+            const uint32_t incl = __ballot_sync(0xffffffffu, (v >> 62) == TILE_INCLUSIVE);
+            const uint32_t stop = incl ? (uint32_t)(__ffs(incl) - 1) : 31u;
+            const uint32_t need = stop == 31u ? 0xffffffffu : ((2u << stop) - 1u);
+            const uint32_t missing = __ballot_sync(0xffffffffu, (v >> 62) == 0) & need;
+            if (!missing) {
+                unsigned long long x = (uint32_t)lane <= stop ? (v & TILE_COUNT_MASK) : 0ull;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            v[k] = (i0 + k < n) ? a[i0 + k] : 0u;
-            s += v[k];
+                for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+                excl += x;
+                if (incl) return excl;
+                break;
+            }
+            if (++spins > LOOK_BACK_SPINS) {
+                if (lane == 0) report(status, 0, SVT_ERR_TIMEOUT);
+                return excl;
+            }
+            __nanosleep(64);
+            if ((missing >> lane) & 1u) v = peek_tile(state + idx);
         }
-        uint32_t tot;
-        uint32_t ex = block_exclusive_scan<uint32_t>(s, sm, &tot);
-        uint64_t run = carry + ex;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (i0 + k < n) a[i0 + k] = (uint32_t)run;
-            run += v[k];
-        }
-        carry += tot;
     }
-    if (threadIdx.x == 0) {
-        a[n] = (uint32_t)carry;
-        if (carry > 0xFFFFFFFFull) report(status, 0, SVT_ERR_OOM);
-        if (total64) *total64 = carry;
-        if (event_road) event_road[dims->n_events] = (uint32_t)carry;
-    }
+    return excl;
 }
 
 // Largest v over the lower threads of the block (-1 when there are none);
@@ -269,10 +224,10 @@ __device__ __forceinline__ int block_exclusive_max(int v, int *smem) {
 __global__ void __launch_bounds__(TILE_THREADS)
     k_unpack_roads(const uint32_t *__restrict__ words, const uint64_t *__restrict__ event_off,
                    const Dims *__restrict__ dims, const uint32_t *__restrict__ first_ev,
-                   const uint32_t *__restrict__ tile_roads, uint64_t road_cap,
-                   uint32_t *road_word, uint32_t *road_nhit, uint32_t *event_road,
-                   const svt_config cfg, const FusedRoads fr, uint64_t *counts,
-                   unsigned long long *status) {
+                   unsigned long long *tile_state, uint32_t *tile_ticket, uint64_t *total64,
+                   uint64_t road_cap, uint32_t *road_word, uint32_t *road_nhit,
+                   uint32_t *event_road, const svt_config cfg, const FusedRoads fr,
+                   uint64_t *counts, unsigned long long *status) {
     constexpr int FRONT = 16, BACK = 100;
     static_assert(TILE_THREADS >= BACK && TILE_THREADS > TILE_WORDS / 32,
                   "one pass of the block loads the halo and covers the V8 bitmap");
@@ -290,12 +245,20 @@ __global__ void __launch_bounds__(TILE_THREADS)
     __shared__ unsigned long long big_base;
     __shared__ unsigned long long tile_comb;   // evaluated combinations of the tile
     __shared__ uint32_t same_bits[1 + TILE_WORDS / 32];   // V8 bitmap, see below
+    __shared__ uint32_t tile_s;                            // the tile this block took
+    __shared__ unsigned long long base_s;                  // roads before the tile
     wait_prior_grid();
     allow_next_grid();
     if (threadIdx.x == 0) tile_comb = 0;   // visible after the tile loop's first barrier
     const uint64_t n_words = dims->n_words, n_events = dims->n_events;
     const uint64_t T = n_tiles(n_words);
-    for (uint64_t t = blockIdx.x; t < T; t += gridDim.x) {
+    // tiles are taken in increasing order from a counter, so the tiles before
+    // the one a block holds belong to blocks that are already running
+    for (;;) {
+        if (threadIdx.x == 0) tile_s = atomicAdd(tile_ticket, 1u);
+        __syncthreads();
+        const uint64_t t = tile_s;
+        if (t >= T) break;
         const uint64_t tile_start = t * TILE_WORDS;
         const uint64_t tile_end = min(tile_start + TILE_WORDS, n_words);
         const int tile_len = (int)(tile_end - tile_start);
@@ -303,13 +266,14 @@ __global__ void __launch_bounds__(TILE_THREADS)
         if (threadIdx.x == 0) last_nonhit = -1;
         uint32_t w[TILE_PER_THREAD];
         load8(words, base, n_words, w);
-        uint32_t nh = 0;
+        uint32_t nh = 0;   // road headers (low 16 bits) and event headers (high 16 bits)
 #pragma unroll
         for (int j = 0; j < TILE_PER_THREAD; ++j) {
             const int p = threadIdx.x * TILE_PER_THREAD + j;
             const bool in = p < tile_len;
             sw[FRONT + p] = in ? w[j] : SENTINEL;
             nh += (in && w_type(w[j]) == TYPE_ROAD) ? 1u : 0u;
+            nh += (in && w_type(w[j]) == TYPE_EVENT) ? 1u << 16 : 0u;
         }
         if (threadIdx.x < FRONT) {
             const int64_t k = (int64_t)tile_start - FRONT + threadIdx.x;
@@ -319,9 +283,66 @@ __global__ void __launch_bounds__(TILE_THREADS)
             const uint64_t k = tile_end + threadIdx.x;
             sw[FRONT + TILE_WORDS + threadIdx.x] = k < n_words ? __ldg(words + k) : SENTINEL;
         }
-        uint32_t n_roads_tile;
-        const uint32_t ex = block_exclusive_scan<uint32_t>(nh, red, &n_roads_tile);   // syncs
-        const uint64_t tile_base = tile_roads[t];
+        uint32_t n_heads_tile;
+        const uint32_t ex = block_exclusive_scan<uint32_t>(nh, red, &n_heads_tile) & 0xFFFFu;   // syncs
+        const uint32_t n_roads_tile = n_heads_tile & 0xFFFFu;
+        // the tile's road count for the tiles after it, before anything else
+        if (threadIdx.x == 0)
+            publish_tile(tile_state + t, t == 0 ? TILE_INCLUSIVE : TILE_AGGREGATE, n_roads_tile);
+        // per-word rules V3..V7 and V9 against the word before (the staged
+        // front halo holds the previous tile's last word; tile 0 has none)
+        uint64_t e_lo, e_hi;
+        tile_events(first_ev, t, n_events, e_lo, e_hi);
+#pragma unroll
+        for (int j = 0; j < TILE_PER_THREAD; ++j) {
+            const int p = threadIdx.x * TILE_PER_THREAD + j;
+            if (p >= tile_len) break;
+            const uint64_t i = tile_start + p;
+            const uint32_t x = w[j], pw = sw[FRONT + p - 1];
+            const uint32_t ty = w_type(x);
+            if (ty == TYPE_ROAD) {
+                if (rd_sector(x) >= cfg.n_sectors) report(status, i, SVT_ERR_BAD_SECTOR);   // V9
+            } else if (ty == TYPE_BAD) {
+                report(status, i, SVT_ERR_BAD_TYPE);                                      // V3
+            } else if (ty == TYPE_HIT) {
+                // V4 and V7 also fire on an event's first word, where V1 already
+                // reports the same word with the smallest code, so the key is unchanged.
+                if (i > 0 && w_type(pw) == TYPE_EVENT) report(status, i, SVT_ERR_BAD_TYPE);  // V4
+                if (hit_reserved(x) != 0) report(status, i, SVT_ERR_BAD_RESERVED);          // V5
+                if (hit_layer(x) > 5) report(status, i, SVT_ERR_BAD_LAYER);                 // V6
+                if (i > 0 && w_type(pw) == TYPE_HIT && hit_layer(pw) > hit_layer(x))
+                    report(status, i, SVT_ERR_UNSORTED);                                    // V7
+            }
+        }
+        // V1: the events starting in this tile start with an event header
+        int v1_bad = 0;
+        for (uint64_t e = e_lo + threadIdx.x; e < e_hi; e += TILE_THREADS) {
+            const uint64_t s0 = __ldg(event_off + e);
+            if (s0 >= tile_start && s0 < tile_end && w_type(__ldg(words + s0)) != TYPE_EVENT) {
+                report(status, s0, SVT_ERR_BAD_TYPE);                                   // V1
+                v1_bad = 1;
+            }
+        }
+        v1_bad = __syncthreads_or(v1_bad);
+        // V2: every event-header word must sit at an event offset.  When the
+        // tile holds as many headers as events start in it and all of those
+        // start with a header (V1), the headers are exactly those starts;
+        // otherwise every header of the tile is looked up.
+        if ((n_heads_tile >> 16) != e_hi - e_lo || v1_bad) {   // (rare: the batch is invalid)
+            const int lane = threadIdx.x & 31;
+            for (int j = 0; j < TILE_PER_THREAD; ++j) {
+                const bool ev = base + j < n_words && w_type(w[j]) == TYPE_EVENT;
+                uint32_t bal = __ballot_sync(0xffffffffu, ev);
+                while (bal) {
+                    const int src = __ffs(bal) - 1;
+                    const uint64_t i = __shfl_sync(0xffffffffu, base + j, src);
+                    const uint64_t e = warp_lower_bound64(event_off, n_events, i, lane);
+                    const bool start = e < n_events && __ldg(event_off + e) == i;
+                    if (lane == src && !start) report(status, i, SVT_ERR_BAD_TYPE);
+                    bal &= bal - 1;
+                }
+            }
+        }
         // road headers: positions; counters cleared
         {
             uint32_t r = ex;
@@ -454,7 +475,25 @@ __global__ void __launch_bounds__(TILE_THREADS)
                 }
             }
         }
+        // the roads of the tiles before this one (the last warp, while the
+        // first may still be counting the hits past the tile's end); then the
+        // tile's inclusive count for the tiles after it
+        if (threadIdx.x >= TILE_THREADS - 32) {
+            const int lane = threadIdx.x & 31;
+            const unsigned long long before = t ? tiles_before(tile_state, t, lane, status) : 0ull;
+            if (lane == 0) {
+                if (t) publish_tile(tile_state + t, TILE_INCLUSIVE, before + n_roads_tile);
+                base_s = before;
+                if (t + 1 == T) {   // the last tile: the batch's road count
+                    const unsigned long long R = before + n_roads_tile;
+                    if (R > 0xFFFFFFFFull) report(status, 0, SVT_ERR_OOM);
+                    if (total64) *total64 = R;
+                    if (event_road) event_road[n_events] = (uint32_t)R;
+                }
+            }
+        }
         __syncthreads();
+        const uint64_t tile_base = base_s;
         // one thread per road of the tile; for the fused path cnt[rl] then
         // holds the road's work items (0 unless it is split)
         uint32_t items_sum = 0, big_sum = 0;
@@ -490,8 +529,6 @@ __global__ void __launch_bounds__(TILE_THREADS)
         }
         // first road of every event that starts inside this tile: the number
         // of road headers before the event's first word
-        uint64_t e_lo, e_hi;
-        tile_events(first_ev, t, n_events, e_lo, e_hi);
         for (uint64_t e = e_lo + threadIdx.x; e < e_hi; e += TILE_THREADS) {
             const uint64_t s0 = __ldg(event_off + e);
             if (s0 >= tile_start && s0 < tile_end) {
@@ -551,6 +588,8 @@ __global__ void __launch_bounds__(TILE_THREADS)
         }
         __syncthreads();
     }
+    // an empty batch has no last tile to write the road count of
+    if (T == 0 && blockIdx.x == 0 && threadIdx.x == 0 && event_road) event_road[n_events] = 0;
 }
 
 __global__ void k_unpack_events(const uint32_t *__restrict__ words,
@@ -569,42 +608,30 @@ __global__ void k_unpack_events(const uint32_t *__restrict__ words,
 
 void launch_prologue(Dims *dims, uint64_t n_words, uint64_t n_events, const uint64_t *sizes,
                      const uint64_t *event_off, uint32_t *first_ev, unsigned long long *status,
-                     uint64_t *counts, int n_counts, uint64_t *zero, int n_zero, int grid,
+                     uint64_t *counts, int n_counts, uint64_t *zero, int n_zero,
+                     unsigned long long *tile_state, uint32_t *tile_ticket, int grid,
                      cudaStream_t st) {
     uint64_t g = first_ev ? (n_events + 1 + 255) / 256 : 1;
+    const uint64_t gt = tile_state ? (n_tiles(n_words) + 255) / 256 : 1;
+    if (gt > g) g = gt;
     if (g > (uint64_t)grid) g = (uint64_t)grid;
     if (g < 1) g = 1;
     k_prologue<<<(int)g, 256, 0, st>>>(dims, n_words, n_events, sizes, event_off, first_ev, status,
-                                       counts, n_counts, zero, n_zero);
-}
-
-void launch_unpack_count(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
-                         const uint32_t *first_ev, uint64_t max_words, uint32_t n_sectors,
-                         uint32_t *tile_roads, unsigned long long *status, int grid,
-                         cudaStream_t st) {
-    uint64_t T = n_tiles(max_words);
-    int g = (int)(T < (uint64_t)grid ? T : (uint64_t)grid);
-    if (g > 0)
-        launch_after(k_unpack_count, g, TILE_THREADS, 0, st, words, event_off, dims, first_ev,
-                     n_sectors, tile_roads, status);
-}
-
-void launch_scan_tiles(uint32_t *a, const Dims *dims, const uint64_t *n_dev, uint64_t *total64,
-                       uint32_t *event_road, unsigned long long *status, cudaStream_t st) {
-    launch_after(k_scan_tiles, 1, 1024, 0, st, a, dims, n_dev, total64, event_road, status);
+                                       counts, n_counts, zero, n_zero, tile_state, tile_ticket);
 }
 
 void launch_unpack_roads(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
-                         const uint32_t *first_ev, uint64_t max_words, const uint32_t *tile_roads,
+                         const uint32_t *first_ev, uint64_t max_words,
+                         unsigned long long *tile_state, uint32_t *tile_ticket, uint64_t *total64,
                          uint64_t road_cap, uint32_t *road_word, uint32_t *road_nhit,
                          uint32_t *event_road, const svt_config cfg, const FusedRoads fr,
                          uint64_t *counts, unsigned long long *status, int grid, cudaStream_t st) {
     uint64_t T = n_tiles(max_words);
     int g = (int)(T < (uint64_t)grid ? T : (uint64_t)grid);
-    if (g > 0)
-        launch_after(k_unpack_roads, g, TILE_THREADS, 0, st, words, event_off, dims, first_ev,
-                     tile_roads, road_cap, road_word, road_nhit, event_road, cfg, fr, counts,
-                     status);
+    if (g < 1) g = 1;   // an empty batch still writes its road count
+    launch_after(k_unpack_roads, g, TILE_THREADS, 0, st, words, event_off, dims, first_ev,
+                 tile_state, tile_ticket, total64, road_cap, road_word, road_nhit, event_road, cfg,
+                 fr, counts, status);
 }
 
 void launch_unpack_events(const uint32_t *words, const uint64_t *event_off, const Dims *dims,
