@@ -44,7 +44,7 @@ ALU_PEAK_TOPS = N_SM * LANES_PER_SM * SM_MAX_GHZ * 1e9 / 1e12
 ISSUE_PEAK_GINST = N_SM * 4 * SM_MAX_GHZ
 # the fit kernel and the road descriptors that shape its work
 FIT_KERNEL_SRC = [os.path.join(ROOT, "paper_1311_0380_gb300", "csrc", f)
-                  for f in ("svt_fused.cu", "svt_kernels.cuh")]
+                  for f in ("svt_fused.cu", "svt_roads.cuh")]
 TRAFFIC_NOTE = os.path.join(ROOT, "profiles", "fit_persistent_scaled3000.md")
 UNEVEN_NOTE = os.path.join(ROOT, "profiles", "fit_persistent_uneven512.md")
 
