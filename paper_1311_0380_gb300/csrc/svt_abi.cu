@@ -59,7 +59,7 @@ svt_schedule resolve(const svt_schedule *s) {
 bool schedule_ok(const svt_schedule &s) {
     return s.warps_per_block >= 1 && s.warps_per_block <= 16 && s.blocks_per_sm <= 32 &&
            s.rows_per_item >= 1 && s.rows_per_item <= 64 && s.roads_per_chunk >= 1 &&
-           s.roads_per_chunk <= 32 && s.small_max >= 1 && s.pair_small <= 1;
+           s.roads_per_chunk <= 32 && s.small_max >= 1 && s.pair_small <= 2;
 }
 
 // word tiles: up to 16 blocks of 128 threads per SM at once (grid-stride
@@ -363,7 +363,8 @@ int run_impl(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_
     const NvtxRange fit_range("svt_run: combine, fit, cut, select, format");
     if (timer && cudaEventRecord(timer->start, st) != cudaSuccess) return SVT_ERR_CUDA;
     if (launch_fit_persistent(d_words, d_event_off, w.dims, event_road, w.desc, counts, road_cap,
-                              d_F, d_q, *cfg, fr, sc.roads_per_chunk, sc.pair_small != 0, d_out,
+                              d_F, d_q, *cfg, fr, sc.roads_per_chunk,
+                              sc.pair_small == 2 ? 4u : (sc.pair_small == 1 ? 2u : 1u), d_out,
                               status, (int)sc.warps_per_block, sms * bps, st) != cudaSuccess)
         return SVT_ERR_CUDA;
     if (timer) {
@@ -525,10 +526,11 @@ int svt_autotune(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_ev
                     if ((rc = trial(svt_schedule{w, 0, r, c, m, 0})) != SVT_OK) goto done;
     {
         const svt_schedule base = top_s[0];
-        for (uint32_t c : {2u, 4u, 8u})
-            if ((rc = trial(svt_schedule{base.warps_per_block, 0, base.rows_per_item, c,
-                                         base.small_max, 1})) != SVT_OK)
-                goto done;
+        for (uint32_t g : {1u, 2u})
+            for (uint32_t c : {2u, 4u, 8u})
+                if ((rc = trial(svt_schedule{base.warps_per_block, 0, base.rows_per_item,
+                                             g == 2 ? 2 * c : c, base.small_max, g})) != SVT_OK)
+                    goto done;
     }
     {
         // fewer resident blocks: small batches leave most warps idle and

@@ -19,9 +19,9 @@
 //     counter; the road of an item is found by a 32-way warp search of the
 //     short list of split roads).  Then warps take chunks of consecutive
 //     roads (one coalesced load of their 32-byte descriptors) and fit every
-//     remaining road whole, one warp per road; with the PAIR instance two
+//     remaining road whole, one warp per road; with the grouped instances two
 //     consecutive SMALL roads of the same geometry go to the two halves of a
-//     warp instead.
+//     warp instead, or four TINY ones to its four quarters.
 //   * Each lane visits its combinations in increasing c within a column (or
 //     within its block of rows of a column), so a strict '<' keeps the
 //     smallest index among equal chi2; across columns, row blocks, lanes and
@@ -62,11 +62,15 @@ struct RoadSmem {
     static constexpr uint32_t kMH = MH, kNR = NR;
 };
 // one road per warp; or two roads marked SMALL, one per half warp, each in
-// half of the same space
+// half of the same space; or four roads marked TINY, one per quarter warp,
+// each in a quarter of it
 using WarpSmem = RoadSmem<MAX_HITS, 32, ROWS_MAX>;
 using HalfSmem = RoadSmem<8, 16, 16>;
+using QuarterSmem = RoadSmem<2, 16, 8>;
 static_assert(2 * sizeof(HalfSmem) <= sizeof(WarpSmem), "two half slots fit in a warp slot");
+static_assert(4 * sizeof(QuarterSmem) <= sizeof(WarpSmem), "four quarter slots fit in a warp slot");
 static_assert(sizeof(HalfSmem) % 16 == 0, "half slots keep 16-byte alignment");
+static_assert(sizeof(QuarterSmem) % 16 == 0, "quarter slots keep 16-byte alignment");
 static_assert(sizeof(WarpSmem) % 16 == 0, "warp slots keep 16-byte alignment");
 static_assert(sizeof(WarpSmem) >= 32 * 6 * sizeof(uint32_t), "a road slot holds 32 records");
 
@@ -77,7 +81,7 @@ struct RecordList {
     unsigned long long key[32];   // best key (UINT64_MAX: none passed)
     uint32_t road[32];
 };
-constexpr uint32_t GEO_SMALL = 1u << 28;
+constexpr uint32_t GEO_SMALL = 1u << 28, GEO_TINY = 1u << 29;
 
 // The W lanes (the warp, or one half of it) that fit one road.  Every
 // warp-synchronous step of the per-road code names only these lanes, so the
@@ -91,7 +95,8 @@ template <int W>
 __device__ __forceinline__ Lanes<W> lanes_of(int lane) {
     Lanes<W> L;
     L.gl = (uint32_t)lane & (uint32_t)(W - 1);
-    L.mask = W == 32 ? 0xffffffffu : (0xFFFFu << ((uint32_t)lane & 16u));
+    L.mask = W == 32 ? 0xffffffffu
+                     : (((1u << W) - 1u) << ((uint32_t)lane & (uint32_t)(32 - W)));
     return L;
 }
 
@@ -242,8 +247,9 @@ __device__ __forceinline__ void road_setup(SM &sm, const uint32_t *__restrict__ 
     __syncwarp(L.mask);
     // S[b'] = bias + sum over the suffix layers below the top one, b' < NBp
     // (< 32; <= 16 for a SMALL road)
-    if (gl < g.NBp) {
-        uint32_t rem = gl;
+    // (NBp <= W for whole and half warps; a quarter warp takes two passes)
+    for (uint32_t bp = gl; bp < g.NBp; bp += (uint32_t)W) {
+        uint32_t rem = bp;
         long long S3 = bias, S4 = bias, S5 = bias;
 #pragma unroll
         for (int l = N_LAYERS - 1; l >= 1; --l) {
@@ -258,8 +264,8 @@ __device__ __forceinline__ void road_setup(SM &sm, const uint32_t *__restrict__ 
                 S5 += sm.T[l * MH + i][1].x;
             }
         }
-        sm.S01[gl] = make_longlong2(S3, S4);
-        sm.S5[gl] = S5;
+        sm.S01[bp] = make_longlong2(S3, S4);
+        sm.S5[bp] = S5;
     }
     __syncwarp(L.mask);
 }
@@ -401,6 +407,42 @@ __device__ __forceinline__ unsigned long long fit_road(SM &sm, const uint32_t *_
     return eval_rows<GUARDED, W>(sm, g, 0, g.NA, qsh, init_chi, L);
 }
 
+// The split of a TINY road for a quarter warp: the shortest suffix of at
+// least 8 columns (every layer has one or two hits, so it has exactly 8 when
+// the road has 8 or more combinations), one column per lane in a single pass.
+// The combination index c = row * NB + column is the same whatever the split,
+// so the key is re-expressed in the descriptor's split afterwards (see
+// quarter_key).
+__device__ __forceinline__ void quarter_geometry(Geo &g, uint32_t packed, uint32_t xft) {
+    const RoadShape s = road_shape(packed, xft);
+    uint32_t nb = 1, top = 0, NB = (uint32_t)s.C;
+    bool found = false;
+#pragma unroll
+    for (int l = N_LAYERS - 1; l >= 0; --l) {
+        nb *= s.n[l];
+        if (!found && nb >= 8u) {
+            top = (uint32_t)l;
+            NB = nb;
+            found = true;
+        }
+    }
+    g.split = top;
+    g.NBp = NB / s.n[top];
+    g.NB = NB;
+    g.NA = g.C_eval ? (g.C_eval + NB - 1) / NB : 0u;
+}
+
+// A key of the quarter split, (chi2, row, column), in the descriptor's split.
+__device__ __forceinline__ unsigned long long quarter_key(unsigned long long best,
+                                                          uint32_t NB_quarter,
+                                                          uint32_t NB_desc) {
+    if (best == ~0ull) return best;
+    const uint32_t low = (uint32_t)best;
+    const uint32_t c = (low >> 9) * NB_quarter + (low & 511u);
+    const uint32_t row = c / NB_desc;
+    return (best & 0xFFFFFFFF00000000ull) | (row << 9) | (c - row * NB_desc);
+}
+
 __device__ __forceinline__ RoadDesc shfl_desc(const uint4 &da, const uint4 &db, uint32_t src) {
     RoadDesc D;
     D.a.x = __shfl_sync(0xffffffffu, da.x, src);
@@ -494,11 +536,13 @@ __device__ __forceinline__ bool form_record(const uint32_t *__restrict__ words,
     return pass;
 }
 
-// K4: persistent fit / cut / select / format.  PAIR: two consecutive SMALL
-// roads of one chunk with the same geometry go to the two halves of the warp
-// (a separate instance, so that warps never switch between the two code
-// paths unless pairing was asked for).
-template <bool GUARDED, bool PAIR>
+// K4: persistent fit / cut / select / format.  GROUP 2: two consecutive SMALL
+// roads of one chunk with the same geometry go to the two halves of the warp;
+// GROUP 4: four consecutive TINY roads of the same geometry go to its four
+// quarters (else two SMALL roads to its halves, as with GROUP 2).  Each is a
+// separate instance, so that warps never switch between the code paths
+// unless grouping was asked for.
+template <bool GUARDED, int GROUP>
 __global__ void __launch_bounds__(512, 2)
     k_fit_persistent(const uint32_t *__restrict__ words, const uint64_t *__restrict__ event_off,
                      const Dims *__restrict__ dims, const uint32_t *__restrict__ event_road,
@@ -604,8 +648,42 @@ __global__ void __launch_bounds__(512, 2)
                 ++jj;
                 continue;
             }
-            if (n_rec > 30) flush();   // room for two more
-            if constexpr (PAIR) {
+            if (n_rec > 32 - GROUP) flush();   // room for GROUP more
+            if constexpr (GROUP == 4) {
+                // four TINY roads with the same hits per layer and the same
+                // number of combinations to evaluate, so that the quarters
+                // run their loops in step
+                if ((D.b.x & GEO_TINY) && jj + 3 < n) {
+                    // lane k holds road c0 + k: one vote over the next four
+                    const bool same = (db.x & GEO_TINY) && da.y == D.a.y && da.w == D.a.w;
+                    const uint32_t votes = __ballot_sync(0xffffffffu, same);
+                    if (((votes >> jj) & 15u) == 15u) {
+                        const uint32_t qt = (uint32_t)lane >> 3;   // this lane's quarter and road
+                        QuarterSmem &qs = reinterpret_cast<QuarterSmem *>(&sm)[qt];
+                        const RoadDesc Dq = shfl_desc(da, db, jj + qt);
+                        const Lanes<8> LQ = lanes_of<8>(lane);
+                        Geo g = geo_of(Dq);
+                        unsigned long long best = ~0ull;
+                        if (g.C_eval) {
+                            quarter_geometry(g, Dq.a.y, cfg.xft_pairs);
+                            road_setup<8>(qs, words, Dq, g, F, q, sh, cfg.xft_pairs,
+                                          kColBias<GUARDED>, LQ);
+                            best = quarter_key(
+                                eval_rows<GUARDED, 8>(qs, g, 0, g.NA, qsh, init_chi, LQ), g.NB,
+                                Dq.b.y);
+                        }
+                        if ((lane & 7) == 0) {
+                            rl.key[n_rec + qt] = best;
+                            rl.road[n_rec + qt] = c0 + jj + qt;
+                        }
+                        n_rec += 4;
+                        jj += 4;
+                        __syncwarp();
+                        continue;
+                    }
+                }
+            }
+            if constexpr (GROUP >= 2) {
                 // two SMALL roads of the same geometry (split, NBp, ntop and NA),
                 // so that the two halves run their loops in step
                 if ((D.b.x & GEO_SMALL) && jj + 1 < n) {
@@ -661,10 +739,12 @@ int fit_persistent_blocks_per_sm(int warps_per_block) {
             n = 0;
         occ = n < occ ? n : occ;
     };
-    one(k_fit_persistent<true, false>);
-    one(k_fit_persistent<false, false>);
-    one(k_fit_persistent<true, true>);
-    one(k_fit_persistent<false, true>);
+    one(k_fit_persistent<true, 1>);
+    one(k_fit_persistent<false, 1>);
+    one(k_fit_persistent<true, 2>);
+    one(k_fit_persistent<false, 2>);
+    one(k_fit_persistent<true, 4>);
+    one(k_fit_persistent<false, 4>);
     return occ;
 }
 
@@ -672,7 +752,7 @@ cudaError_t launch_fit_persistent(const uint32_t *words, const uint64_t *event_o
                                   const Dims *dims, const uint32_t *event_road,
                                   const RoadDesc *desc, uint64_t *counts, uint64_t road_cap,
                                   const int16_t *F, const int16_t *q, const svt_config cfg,
-                                  const FusedRoads fr, uint32_t roads_per_chunk, bool pair_small,
+                                  const FusedRoads fr, uint32_t roads_per_chunk, uint32_t group,
                                   uint32_t *out, unsigned long long *status,
                                   int warps_per_block, int grid, cudaStream_t st) {
     const size_t smem = fit_smem_bytes(warps_per_block);
@@ -682,10 +762,15 @@ cudaError_t launch_fit_persistent(const uint32_t *words, const uint64_t *event_o
                      event_road, desc, counts, road_cap, F, q, cfg, fr, roads_per_chunk, out,
                      status);
     };
-    if (guarded)
-        pair_small ? launch(k_fit_persistent<true, true>) : launch(k_fit_persistent<true, false>);
-    else
-        pair_small ? launch(k_fit_persistent<false, true>) : launch(k_fit_persistent<false, false>);
+    if (guarded) {
+        if (group == 4) launch(k_fit_persistent<true, 4>);
+        else if (group == 2) launch(k_fit_persistent<true, 2>);
+        else launch(k_fit_persistent<true, 1>);
+    } else {
+        if (group == 4) launch(k_fit_persistent<false, 4>);
+        else if (group == 2) launch(k_fit_persistent<false, 2>);
+        else launch(k_fit_persistent<false, 1>);
+    }
     return cudaGetLastError();
 }
 

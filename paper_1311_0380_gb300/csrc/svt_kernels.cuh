@@ -111,7 +111,7 @@ cudaError_t launch_fit_persistent(const uint32_t *words, const uint64_t *event_o
                                   const Dims *dims, const uint32_t *event_road,
                                   const RoadDesc *desc, uint64_t *counts, uint64_t road_cap,
                                   const int16_t *F, const int16_t *q, const svt_config cfg,
-                                  const FusedRoads fr, uint32_t roads_per_chunk, bool pair_small,
+                                  const FusedRoads fr, uint32_t roads_per_chunk, uint32_t group,
                                   uint32_t *out, unsigned long long *status,
                                   int warps_per_block, int grid, cudaStream_t st);
 int fit_persistent_blocks_per_sm(int warps_per_block);

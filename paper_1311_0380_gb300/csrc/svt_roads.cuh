@@ -16,7 +16,9 @@ namespace svt {
 //       below the top suffix layer, NB = ntop * NBp), [12:8] ntop, [18:13] layer
 //       mask, [25:19] total hits, [26] OVERFLOW, [27] BAD_PATTERN, [28] SMALL:
 //       at most 8 hits on every layer, NBp <= 16 and NA <= 16, so that half a
-//       warp can fit the road (the fit kernel pairs such roads).
+//       warp can fit the road (the fit kernel pairs such roads), [29] TINY: at
+//       most 2 hits on every layer, NBp <= 16 and NA <= 8, so that a quarter
+//       of a warp can fit it (the fit kernel can group four such roads).
 struct RoadDesc {
     uint4 a, b;
 };
@@ -71,12 +73,15 @@ __device__ __forceinline__ RoadDesc make_road_desc(uint32_t rw, uint32_t packed,
         if ((uint32_t)l == split) ntop = s.n[l];
     }
     const uint32_t NA = C_eval ? (C_eval + NB - 1) / NB : 0u;
-    bool small = NBp <= 16u && NA <= 16u;
+    bool small = NBp <= 16u && NA <= 16u, tiny = NBp <= 16u && NA <= 8u;
 #pragma unroll
-    for (int l = 0; l < N_LAYERS; ++l) small = small && nhit_of(packed, l) <= 8u;
+    for (int l = 0; l < N_LAYERS; ++l) {
+        small = small && nhit_of(packed, l) <= 8u;
+        tiny = tiny && nhit_of(packed, l) <= 2u;
+    }
     const uint32_t geo = split | (NBp << 3) | (ntop << 8) | (s.mask << 13) | (s.total_hits << 19) |
                          ((!bad && C > cfg.max_comb) ? (1u << 26) : 0u) | (bad ? (1u << 27) : 0u) |
-                         (small ? (1u << 28) : 0u);
+                         (small ? (1u << 28) : 0u) | (tiny ? (1u << 29) : 0u);
     RoadDesc d;
     d.a = make_uint4(rw, packed, hw, C_eval);
     d.b = make_uint4(geo, NB, NA, 0u);

@@ -35,7 +35,7 @@ def consts_for(S):
     return CONSTS[S]
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
 def test_small_batch(path):
     spec, consts, b = batch_for("small", 100, consts_for(64))
     cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb, n_sectors=64)
@@ -73,10 +73,37 @@ def test_paper_shape_3000_events():
     assert int(b.combinations().sum()) == 2048 * 3000
     cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb)
     key, rec = oracle_run(b.words, b.event_off, consts.F, consts.q, ocfg)
-    for path in ("fused", "plain", "fused_pair"):
+    for path in ("fused", "plain", "fused_pair", "fused_quad"):
         st, got, _ = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, path,
                              comb_cap=2048 * 3000)
         assert_same(st, got, key, rec, "paper/" + path)
+
+
+@pytest.mark.parametrize("group", [1, 2])
+def test_grouped_roads_in_mixed_shapes(group):
+    """Events of the paper's shape (runs of identical tiny roads), of the
+    small workload (tiny roads of mixed geometry) and of the scaled workload
+    (mostly larger roads) interleaved in one batch: with pairs (group 1) or
+    also quads (group 2) the chunks mix quads, pairs and whole-warp roads,
+    and every record equals the oracle's."""
+    from paper_1311_0380_gb300 import api
+    consts = consts_for(512)
+    parts = [synth.make_batch(name, n, consts, seed=70 + i)
+             for i, (name, n) in enumerate((("paper", 40), ("small", 60), ("scaled", 30)))]
+    events = []
+    for bt in parts:
+        for e in range(bt.n_events):
+            events.append(bt.words[int(bt.event_off[e]):int(bt.event_off[e + 1])])
+    order = np.random.default_rng(5).permutation(len(events))
+    words = np.concatenate([events[i] for i in order]).astype(np.uint32)
+    off = np.zeros(len(events) + 1, np.uint64)
+    off[1:] = np.cumsum([len(events[i]) for i in order])
+    cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=262144)
+    key, rec = oracle_run(words, off, consts.F, consts.q, ocfg)
+    for chunk in (4, 8, 13):
+        st, got, _ = gpu_run(words, off, consts.F, consts.q, cfg, "fused",
+                             sched=api.schedule(8, 0, 16, chunk, 4096, group))
+        assert_same(st, got, key, rec, f"group{group}/chunk{chunk}")
 
 
 def test_uneven_batch_capped():
@@ -91,7 +118,9 @@ def test_uneven_batch_capped():
 @pytest.mark.parametrize("sched", [(1, 1, 1, 1, 1), (4, 3, 7, 3, 100), (16, 1, 64, 32, 64),
                                    (8, 4, 32, 8, 1 << 30), (2, 8, 2, 2, 33), (8, 0, 16, 4, 4096),
                                    (8, 0, 16, 4, 4096, 1), (4, 3, 7, 3, 100, 1),
-                                   (16, 1, 64, 32, 64, 1), (2, 8, 2, 2, 33, 1), (1, 1, 1, 2, 1, 1)])
+                                   (16, 1, 64, 32, 64, 1), (2, 8, 2, 2, 33, 1), (1, 1, 1, 2, 1, 1),
+                                   (8, 0, 16, 8, 4096, 2), (4, 3, 7, 5, 100, 2),
+                                   (1, 1, 1, 4, 1, 2)])
 def test_schedules_give_identical_results(sched):
     from paper_1311_0380_gb300 import api
     spec, consts, b = batch_for("scaled", 60, consts_for(512))
@@ -103,7 +132,8 @@ def test_schedules_give_identical_results(sched):
 
 
 @pytest.mark.parametrize("sched", [(1, 1, 16, 4, 4096), (1, 1, 16, 4, 4096, 1), (1, 1, 8, 1, 64),
-                                   (1, 1, 4, 3, 300, 1)])
+                                   (1, 1, 4, 3, 300, 1), (1, 1, 16, 8, 4096, 2),
+                                   (1, 1, 4, 5, 300, 2)])
 def test_record_lists_fill_and_flush(sched):
     """One warp per SM, so that every warp finishes well over 32 roads: its
     list of finished roads fills and is written out many times in the middle
@@ -124,7 +154,7 @@ def test_schedule_limits_are_checked():
     from paper_1311_0380_gb300 import api
     spec, consts, b = batch_for("scaled", 4, consts_for(512))
     cfg, _ = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb)
-    for bad in (api.schedule(pair_small=2), api.schedule(warps_per_block=17),
+    for bad in (api.schedule(pair_small=3), api.schedule(warps_per_block=17),
                 api.schedule(roads_per_chunk=33), api.schedule(rows_per_item=65)):
         with pytest.raises(RuntimeError, match="BAD_ARG"):
             gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "fused", sched=bad)
@@ -180,7 +210,7 @@ def test_plain_fit_tiles_over_many_and_few_roads():
     assert_same(st, got, key, rec, "plain tiles")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
 def test_empty_batch_and_events_without_roads(path):
     F, q = random_consts(4, 1)
     cfg, ocfg = cfg_pair(n_sectors=4)
@@ -194,7 +224,7 @@ def test_empty_batch_and_events_without_roads(path):
     assert_same(st, got, key, rec, "no roads")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
 def test_missing_layers_patterns_and_no_hits(path):
     rng = np.random.default_rng(3)
     F, q = random_consts(8, 2, scale=3000)
@@ -214,7 +244,7 @@ def test_missing_layers_patterns_and_no_hits(path):
         assert_same(st, got, key, rec, f"min_layers{min_layers}")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
 def test_ties_and_extreme_constants(path):
     rng = np.random.default_rng(4)
     S = 2
@@ -236,7 +266,7 @@ def test_ties_and_extreme_constants(path):
             assert_same(st, got, key, rec, f"cut{cut} os{oshift} qs{qshift}")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
 def test_chi_components_at_the_clamp_boundary(path):
     """chi components straddling +-32767 / +-32768 (the clamp of Eq. 2's
     chi-square), with cuts just below, at and above 32767^2: the range test of
@@ -270,7 +300,7 @@ def test_chi_components_at_the_clamp_boundary(path):
     assert 0 < n_pass[0] < n_pass[1] < n_pass[2] < n_pass[3]   # each cut decides roads
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
 def test_maximum_hits_per_layer(path):
     # 16 hits in every layer: 16^6 combinations, capped
     rng = np.random.default_rng(6)
@@ -311,7 +341,7 @@ def test_uncapped_giant_road_fused():
     assert_same(st, got, key, rec, "giant")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
 def test_validation_cases_match_oracle(path):
     from test_oracle_pins import tokens_to_words
     data = json.load(open(os.path.join(GOLDEN, "validation_cases.json")))
