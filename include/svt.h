@@ -605,7 +605,9 @@ int svt_calib_forward(const float *d_x, uint64_t n_tracks, uint32_t n_sectors,
                       const void *d_index, const float *d_F, const float *d_q, float *d_y,
                       void *stream);
 
-/* d_loss[0] = L for sector-ordered tracks. */
+/* d_loss[0] = L for sector-ordered tracks (staged in shared memory by bulk
+ * copies, as in svt_calib_loss_grad, when d_x and d_theta start on 16-byte
+ * boundaries). */
 int svt_calib_loss(const float *d_x, const float *d_theta, const float *d_w, uint64_t n_tracks,
                    uint32_t n_sectors, const void *d_index, const float *d_F, const float *d_q,
                    float *d_loss, void *d_workspace, size_t workspace_bytes, void *stream);
@@ -620,13 +622,18 @@ int svt_calib_loss_backward(const float *d_x, const float *d_theta, const float 
 
 /* The loss and its gradient in one pass over the tracks (x and theta read
  * once): d_loss[0] = L, d_dF = dL/dF, d_dq = dL/dq and, when d_y is not NULL,
- * d_y = F[s] x + q[s] as svt_calib_forward writes it.  The final sums are
- * made by the warps that complete each sector and the batch (atomic tickets
- * in the workspace; nothing waits), in a fixed order, so repeated calls give
- * identical bits.  Sectors without tracks get zero gradients.  The tickets
- * live in the workspace, which must be zero-filled once after it is
- * allocated; every call of svt_calib_loss_grad or svt_calib_loss_backward
- * leaves them at zero again. */
+ * d_y = F[s] x + q[s] as svt_calib_forward writes it.  Every sum runs in a
+ * fixed order for a given device, so repeated calls give identical bits.
+ * Sectors without tracks get zero gradients.  When d_x and d_theta start on
+ * 16-byte boundaries, each item's tracks are staged in shared memory by
+ * bulk copies (the bulk-copy unit's alignment rule) and the final sums are
+ * made by a second kernel chained by programmatic dependent launch; a staged
+ * copy that does not land within the pass's bounded wait makes *d_loss NaN.
+ * Otherwise every lane loads its own tracks and the final sums are made by
+ * the warps that complete each sector and the batch (atomic tickets in the
+ * workspace; nothing waits).  Both give the same y.  The workspace must be
+ * zero-filled once after it is allocated; every call of svt_calib_loss_grad
+ * or svt_calib_loss_backward leaves its tickets and flag at zero again. */
 int svt_calib_loss_grad(const float *d_x, const float *d_theta, const float *d_w,
                         uint64_t n_tracks, uint32_t n_sectors, const void *d_index,
                         const float *d_F, const float *d_q, float *d_loss, float *d_dF,

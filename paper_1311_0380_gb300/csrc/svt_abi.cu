@@ -161,7 +161,7 @@ CalibWs carve_calib_ws(void *base, uint64_t n, uint32_t S) {
     w.item_grad = c.take<float>((size_t)mi * 42);
     w.sector_loss = c.take<float>(S);
     w.loss = c.take<float>(1);
-    w.tickets = c.take<unsigned int>(S + 1);
+    w.tickets = c.take<unsigned int>(S + 2);   // per sector, the batch, a copy-wait flag
     w.bytes = c.size();
     return w;
 }
@@ -733,8 +733,9 @@ int svt_calib_loss(const float *d_x, const float *d_theta, const float *d_w, uin
     CalibWs w = carve_calib_ws(d_workspace, n_tracks, n_sectors);
     if (workspace_bytes < w.bytes) return SVT_ERR_BAD_ARG;
     CalibIndex x = carve_calib_index(d_index, n_tracks, n_sectors);
-    launch_calib_loss(d_x, d_theta, x.item_sector, x.item_start, x.sector_off, x.n_items,
-                      x.max_items, n_tracks, d_F, d_q, d_w, w.item_loss, d_loss, tile_grid(),
+    launch_calib_loss(d_x, d_theta, x.item_sector, x.item_start, x.sector_off, x.sector_item,
+                      x.n_items, x.max_items, n_sectors, n_tracks, d_F, d_q, d_w, w.item_loss,
+                      w.tickets + n_sectors + 1, d_loss, current_sm_count(), tile_grid(),
                       (cudaStream_t)stream);
     return launch_status();
 }

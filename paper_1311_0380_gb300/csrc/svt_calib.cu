@@ -13,6 +13,8 @@
 // sector (atomic tickets, no waiting).  Every reduction runs in a fixed order
 // (lanes, then items or segments in index order), so results are bitwise
 // reproducible run to run.
+#include <mutex>
+
 #include "svt_kernels.cuh"
 
 namespace svt {
@@ -622,6 +624,417 @@ __global__ void __launch_bounds__(256, 2)
     }
 }
 
+// ---- the fused pass with its tracks staged by the bulk-copy unit ------------------
+// The loss and its gradient as k_loss_grad computes them, in two kernels
+// chained by programmatic dependent launch, for x and theta that start on a
+// 16-byte boundary (the launcher takes k_loss_grad otherwise).
+//
+// k_loss_grad_bulk takes the track loads off the lanes: the x and theta rows
+// of each item are copied to the warp's shared-memory buffers by one
+// cp.async.bulk per array (completion counted on an mbarrier per buffer),
+// NBUF - 1 items ahead of the item the warp adds up, so that every warp
+// always has an item's bytes in flight while it computes.  A bulk copy moves
+// 16-byte aligned spans of a multiple of 16 bytes, hence the copied range
+// [lo, hi) is the item's track range widened to multiples of four tracks
+// (4 x 24 bytes of x, 4 x 12 of theta) and cut at the last multiple of four
+// at or below n, so no byte past either array is read; the at most three
+// tracks past that cut are read from global memory by their lanes.  The end
+// of item i is the first track of item i + 1 (the items tile the sorted
+// tracks), n for the last item.  The I items are cut into runs for the first
+// W warps (W the smaller of I and the grid's warps) that differ by one item
+// at most (CalibRuns), so that every SM gets work.  Each warp writes one
+// partial per segment (a run of its items in one sector) into the slot of
+// the segment's first item, as k_loss_grad does, and takes no ticket.
+//
+// k_lg_final, once the first kernel has completed, sums each sector's
+// segment partials in warp order (one thread per sector and entry, every
+// sector including those without tracks) and, in its last block, the
+// sectors' losses in a fixed tree.  Every sum runs in a fixed order for a
+// given grid, so repeated calls give identical bits.  (Taking the final sums
+// in the first kernel by tickets, as k_loss_grad does, put a chain of
+// fences, atomics and loads after the last warp's compute that took longer
+// than the dependent launch.)
+//
+// Every wait on a copy is bounded; a copy that does not land within the
+// bound sets the flag word the launcher passes (the workspace's tickets[S +
+// 1]), and k_lg_final then writes a NaN loss and clears it.
+constexpr int ST_TRACKS = CALIB_CHUNK + 4;                 // an item with its widening
+constexpr uint32_t ST_XBYTES = ST_TRACKS * 24u;            // x rows of a buffer
+constexpr uint32_t ST_BUF = ST_TRACKS * 36u;               // x rows, then theta rows
+constexpr uint32_t BULK_WAIT_SPINS = 1u << 20;
+static_assert(ST_XBYTES % 16 == 0 && ST_BUF % 16 == 0, "bulk copy spans");
+static_assert(32 * (NPAR + 1) * 4 <= (int)ST_XBYTES, "the lane sums reuse an x buffer");
+
+// the cut of I items into runs for the first W = min(warps, I) warps: the
+// first I mod W warps take one item more than the others (no division in
+// first(); warp_of() divides by a 32-bit value)
+struct CalibRuns {
+    uint32_t nwe, qi, rq;
+    __device__ __forceinline__ CalibRuns(uint32_t warps, uint32_t items) {
+        nwe = max(1u, min(warps, items));
+        qi = items / nwe;
+        rq = items % nwe;
+    }
+    __device__ __forceinline__ uint32_t first(uint32_t v) const { return v * qi + min(v, rq); }
+    __device__ __forceinline__ uint32_t warp_of(uint32_t i) const {   // the run holding item i
+        const uint32_t big = rq * (qi + 1);
+        return i < big ? i / (qi + 1) : rq + (i - big) / qi;
+    }
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *m, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(m)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+// generic-proxy accesses of shared memory before this point are ordered
+// before later bulk-copy (async-proxy) writes
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *m, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(m)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void *dst, const void *src, uint32_t bytes,
+                                              uint64_t *m) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(m))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(m)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// false when the phase did not complete within the bound
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, uint32_t parity) {
+    for (uint32_t k = 0; k < BULK_WAIT_SPINS; ++k)
+        if (mbar_try_wait(m, parity)) return true;
+    return false;
+}
+
+// F[s] (rows of six) and q[s] as six rows of eight floats, entries lane and
+// lane + 32 of the 48
+__device__ __forceinline__ void fetch_consts(const float *__restrict__ F,
+                                             const float *__restrict__ q, uint32_t s, int lane,
+                                             float &k0, float &k1) {
+    auto one = [&](int j) {
+        const int r = j >> 3, l = j & 7;
+        return l < 6 ? __ldg(F + (size_t)s * 36 + r * 6 + l)
+                     : (l == 6 ? __ldg(q + (size_t)s * 6 + r) : 0.f);
+    };
+    k0 = one(lane);
+    k1 = lane < 16 ? one(lane + 32) : 0.f;
+}
+
+template <bool WY, bool GRAD, int WARPS, int NBUF>
+__global__ void __launch_bounds__(WARPS * 32, 1)
+    k_loss_grad_bulk(const float *__restrict__ x, const float *__restrict__ theta,
+                     const int32_t *__restrict__ item_sector,
+                     const int32_t *__restrict__ item_start, const int32_t *__restrict__ n_items,
+                     uint64_t n, const float *__restrict__ F, const float *__restrict__ q,
+                     const float *__restrict__ w, float *item_loss, float *item_grad,
+                     unsigned int *flag, float *y) {
+    constexpr int TPL = CALIB_CHUNK / 32;   // tracks per lane and item
+    extern __shared__ __align__(128) unsigned char st_buf[];
+    __shared__ __align__(16) float cs[WARPS][48];
+    __shared__ __align__(8) uint64_t bars[WARPS][NBUF];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t gw = blockIdx.x * WARPS + wib, nw = gridDim.x * WARPS;
+    allow_next_grid();   // k_lg_final's blocks may take SMs as this grid's blocks leave
+    const uint32_t NI = (uint32_t)*n_items;
+    if (NI == 0) return;
+    const CalibRuns runs(nw, NI);
+    if (gw >= runs.nwe) return;
+    const uint32_t i0 = runs.first(gw), i1 = runs.first(gw + 1);
+    unsigned char *wbuf = st_buf + (size_t)wib * NBUF * ST_BUF;
+    uint64_t *mb = bars[wib];
+    if (lane == 0) {
+#pragma unroll
+        for (int b = 0; b < NBUF; ++b) mbar_init(&mb[b], 1);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    const float w0 = w[0], w1 = w[1], w2 = w[2];
+    const uint32_t n32 = (uint32_t)n, n4 = n32 & ~3u;
+    // sector, first track and end of 32 items, one per lane: the current
+    // batch [base, base + 32) and the next
+    uint32_t base = i0;
+    uint32_t c_s = 0, c_st = 0, c_en = 0, x_s = 0, x_st = 0, x_en = 0;
+    auto fetch = [&](uint32_t b0, uint32_t &ms, uint32_t &mst, uint32_t &men) {
+        const uint32_t i = b0 + (uint32_t)lane;
+        ms = mst = men = 0;
+        if (i < i1) {
+            ms = (uint32_t)__ldg(item_sector + i);
+            mst = (uint32_t)__ldg(item_start + i);
+            men = i + 1 < NI ? (uint32_t)__ldg(item_start + i + 1) : n32;
+        }
+    };
+    auto info = [&](uint32_t j, uint32_t &s, uint32_t &st, uint32_t &en) {
+        const uint32_t d = j - base;   // below 64
+        const int src = (int)(d & 31u);
+        const uint32_t a0 = __shfl_sync(0xffffffffu, c_s, src), b0 = __shfl_sync(0xffffffffu, x_s, src);
+        const uint32_t a1 = __shfl_sync(0xffffffffu, c_st, src), b1 = __shfl_sync(0xffffffffu, x_st, src);
+        const uint32_t a2 = __shfl_sync(0xffffffffu, c_en, src), b2 = __shfl_sync(0xffffffffu, x_en, src);
+        s = d < 32 ? a0 : b0;
+        st = d < 32 ? a1 : b1;
+        en = d < 32 ? a2 : b2;
+    };
+    auto span = [&](uint32_t st, uint32_t en, uint32_t &lo, uint32_t &hi) {
+        lo = st & ~3u;
+        hi = max(lo, min((en + 3u) & ~3u, n4));
+    };
+    // copy item j's rows into buffer b (every lane's reads of b are done)
+    auto issue = [&](uint32_t j, int b) {
+        uint32_t s, st, en, lo, hi;
+        info(j, s, st, en);
+        span(st, en, lo, hi);
+        __syncwarp();
+        if (lane == 0) {
+            unsigned char *d = wbuf + (size_t)b * ST_BUF;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&mb[b], (hi - lo) * 36u);
+            if (hi > lo) {
+                bulk_copy_g2s(d, x + (size_t)lo * 6, (hi - lo) * 24u, &mb[b]);
+                bulk_copy_g2s(d + ST_XBYTES, theta + (size_t)lo * 3, (hi - lo) * 12u, &mb[b]);
+            }
+        }
+    };
+    fetch(base, c_s, c_st, c_en);
+    fetch(base + 32, x_s, x_st, x_en);
+#pragma unroll
+    for (int b = 0; b < NBUF - 1; ++b)
+        if (i0 + (uint32_t)b < i1) issue(i0 + (uint32_t)b, b);
+    float k0, k1;   // the constants of the next segment, fetched one item ahead
+    {
+        uint32_t s, st, en;
+        info(i0, s, st, en);
+        fetch_consts(F, q, s, lane, k0, k1);
+    }
+    // per lane: acc[6k + l] = sum r_k x_l, acc[36 + k] = sum r_k with
+    // r = y - theta in rows 0..2 and r = y in rows 3..5 (the weights w_k of
+    // rows 0..2 are applied once, at the segment's end), l3[k] = sum r_k^2
+    // for k < 3 and l3[3] = sum over rows 3..5
+    float acc[NPAR], l3[4];
+#pragma unroll
+    for (int j = 0; j < NPAR; ++j) acc[j] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) l3[k] = 0.f;
+    uint32_t seg = i0, phase = 0u, bad = 0u, ever_bad = 0u;
+    float *c = cs[wib];
+    int b = 0;   // buffer of item i
+    for (uint32_t i = i0; i < i1; ++i) {
+        if (i - base >= 32u) {   // the next batch of lookups
+            base += 32;
+            c_s = x_s; c_st = x_st; c_en = x_en;
+            fetch(base + 32, x_s, x_st, x_en);
+        }
+        uint32_t is, start, iend;
+        info(i, is, start, iend);
+        if (i + NBUF - 1 < i1) issue(i + NBUF - 1, (b + NBUF - 1) % NBUF);
+        if (i == seg) {   // a new segment's constants
+            __syncwarp();
+            c[lane] = k0;
+            if (lane < 16) c[lane + 32] = k1;
+            __syncwarp();
+        }
+        uint32_t nxt_s = ~0u;
+        if (i + 1 < i1) {
+            uint32_t st2, en2;
+            info(i + 1, nxt_s, st2, en2);
+            if (nxt_s != is) fetch_consts(F, q, nxt_s, lane, k0, k1);
+        }
+        uint32_t lo, hi;
+        span(start, iend, lo, hi);
+        if (!mbar_wait_bounded(&mb[b], (phase >> b) & 1u)) bad = 1u;
+        phase ^= 1u << b;
+        const float *xs = reinterpret_cast<const float *>(wbuf + (size_t)b * ST_BUF);
+        const float *ts = reinterpret_cast<const float *>(wbuf + (size_t)b * ST_BUF + ST_XBYTES);
+        float cr[6][8];   // the segment's constants, in registers for the item
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+            const float4 p = *reinterpret_cast<const float4 *>(c + r * 8);
+            const float4 v = *reinterpret_cast<const float4 *>(c + r * 8 + 4);
+            cr[r][0] = p.x; cr[r][1] = p.y; cr[r][2] = p.z; cr[r][3] = p.w;
+            cr[r][4] = v.x; cr[r][5] = v.y; cr[r][6] = v.z; cr[r][7] = 0.f;
+        }
+#pragma unroll 2
+        for (int u = 0; u < TPL; ++u) {
+            const uint32_t t = start + (uint32_t)lane + 32u * (uint32_t)u;
+            if (t >= iend) break;
+            float xv[6], th[3];
+            if (t < hi) {
+                const float2 *xp = reinterpret_cast<const float2 *>(xs + (size_t)(t - lo) * 6);
+                const float2 a = xp[0], bb = xp[1], d = xp[2];
+                xv[0] = a.x; xv[1] = a.y; xv[2] = bb.x; xv[3] = bb.y; xv[4] = d.x; xv[5] = d.y;
+                const float *tp = ts + (size_t)(t - lo) * 3;
+                th[0] = tp[0]; th[1] = tp[1]; th[2] = tp[2];
+            } else {   // past the last multiple of four tracks
+#pragma unroll
+                for (int l = 0; l < 6; ++l) xv[l] = __ldg(x + (size_t)t * 6 + l);
+#pragma unroll
+                for (int l = 0; l < 3; ++l) th[l] = __ldg(theta + (size_t)t * 3 + l);
+            }
+            float g[6];
+#pragma unroll
+            for (int r = 0; r < 6; ++r) {
+                float e = cr[r][6];
+                e = fmaf(cr[r][0], xv[0], e);
+                e = fmaf(cr[r][1], xv[1], e);
+                e = fmaf(cr[r][2], xv[2], e);
+                e = fmaf(cr[r][3], xv[3], e);
+                e = fmaf(cr[r][4], xv[4], e);
+                e = fmaf(cr[r][5], xv[5], e);
+                g[r] = e;
+            }
+            if (WY) {
+                float2 *yp = reinterpret_cast<float2 *>(y + (size_t)t * 6);
+                yp[0] = make_float2(g[0], g[1]);
+                yp[1] = make_float2(g[2], g[3]);
+                yp[2] = make_float2(g[4], g[5]);
+            }
+            g[0] -= th[0];
+            g[1] -= th[1];
+            g[2] -= th[2];
+            l3[0] = fmaf(g[0], g[0], l3[0]);
+            l3[1] = fmaf(g[1], g[1], l3[1]);
+            l3[2] = fmaf(g[2], g[2], l3[2]);
+            l3[3] = fmaf(g[3], g[3], l3[3]);
+            l3[3] = fmaf(g[4], g[4], l3[3]);
+            l3[3] = fmaf(g[5], g[5], l3[3]);
+            if (GRAD) {
+#pragma unroll
+                for (int r = 0; r < 6; ++r) {
+#pragma unroll
+                    for (int l = 0; l < 6; ++l) acc[r * 6 + l] = fmaf(g[r], xv[l], acc[r * 6 + l]);
+                    acc[36 + r] += g[r];
+                }
+            }
+        }
+        const int bi = b;
+        b = b + 1 == NBUF ? 0 : b + 1;
+        // does the segment end with this item?
+        if (i + 1 != i1 && nxt_s == is) continue;
+        {   // the segment's sums over the lanes, through item i's x buffer
+#pragma unroll
+            for (int l = 0; l < 6; ++l) {
+                acc[l] *= w0;
+                acc[6 + l] *= w1;
+                acc[12 + l] *= w2;
+            }
+            acc[36] *= w0;
+            acc[37] *= w1;
+            acc[38] *= w2;
+            const float lacc = fmaf(w0, l3[0], fmaf(w1, l3[1], fmaf(w2, l3[2], l3[3])));
+            if (GRAD) {
+                float *red = reinterpret_cast<float *>(wbuf + (size_t)bi * ST_BUF);
+                __syncwarp();
+#pragma unroll
+                for (int j = 0; j < NPAR; ++j) red[lane * (NPAR + 1) + j] = acc[j];
+                __syncwarp();
+                for (int j = lane; j < NPAR; j += 32) {
+                    float part[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        float v = red[(8 * u) * (NPAR + 1) + j];
+#pragma unroll
+                        for (int m = 1; m < 8; ++m) v += red[(8 * u + m) * (NPAR + 1) + j];
+                        part[u] = v;
+                    }
+                    item_grad[(size_t)seg * NPAR + j] = (part[0] + part[1]) + (part[2] + part[3]);
+                }
+            }
+            const float lt = warp_sum(lacc);
+            if (lane == 0) item_loss[seg] = lt;
+            __syncwarp();
+        }
+        seg = i + 1;
+#pragma unroll
+        for (int j = 0; j < NPAR; ++j) acc[j] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) l3[k] = 0.f;
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(flag, 1u);
+        ever_bad |= bad;
+        bad = 0u;
+    }
+    // after a wait that gave up, wait (bounded again) for the last copy into
+    // each buffer before the block's shared memory is released
+    if (ever_bad) {
+#pragma unroll
+        for (int bb = 0; bb < NBUF; ++bb) mbar_wait_bounded(&mb[bb], ((phase >> bb) & 1u) ^ 1u);
+    }
+}
+
+
+// the final sums of the staged pass (see above): blocks [0, ncol) one thread
+// per (sector, entry) (ncol = 0: the loss alone), block ncol the loss; nw =
+// the first kernel's warps
+constexpr int LGF_THREADS = 512;
+__global__ void __launch_bounds__(LGF_THREADS)
+    k_lg_final(const float *__restrict__ item_grad, const float *__restrict__ item_loss,
+               const int32_t *__restrict__ sector_item, const int32_t *__restrict__ n_items,
+               uint32_t S, uint64_t n, uint32_t nw, uint32_t ncol,
+               const float *__restrict__ scale_dev, unsigned int *flag, float *loss, float *dF,
+               float *dq) {
+    wait_prior_grid();
+    const uint32_t NI = (uint32_t)*n_items;
+    const float scale = (n ? 2.0f / (float)n : 0.f) * (scale_dev ? *scale_dev : 1.f);
+    const CalibRuns runs(nw, NI);
+    auto first = [&](uint32_t v) { return runs.first(v); };
+    auto warp_of = [&](uint32_t i) { return runs.warp_of(i); };
+    if (blockIdx.x < ncol) {
+        const uint32_t k = blockIdx.x * LGF_THREADS + threadIdx.x;
+        if (k >= S * NPAR) return;
+        const uint32_t s = k / NPAR, j = k % NPAR;
+        const uint32_t a = (uint32_t)sector_item[s], e = (uint32_t)sector_item[s + 1];
+        float total = 0.f;
+        if (e > a) {
+            const uint32_t wa = warp_of(a), wz = warp_of(e - 1);
+#pragma unroll 4
+            for (uint32_t v = wa; v <= wz; ++v) total += item_grad[(size_t)max(a, first(v)) * NPAR + j];
+        }
+        if (j < 36)
+            dF[(size_t)s * 36 + j] = total * scale;
+        else
+            dq[(size_t)s * 6 + (j - 36)] = total * scale;
+        return;
+    }
+    __shared__ float red[LGF_THREADS];
+    float sl = 0.f;
+    for (uint32_t s = threadIdx.x; s < S; s += LGF_THREADS) {
+        const uint32_t a = (uint32_t)sector_item[s], e = (uint32_t)sector_item[s + 1];
+        if (e > a) {
+            const uint32_t wa = warp_of(a), wz = warp_of(e - 1);
+            for (uint32_t v = wa; v <= wz; ++v) sl += item_loss[max(a, first(v))];
+        }
+    }
+    red[threadIdx.x] = sl;
+    __syncthreads();
+    for (uint32_t w = LGF_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const unsigned int f = *flag;
+        if (f) *flag = 0u;
+        *loss = n == 0 ? 0.f : (f ? __int_as_float(0x7fc00000) : red[0] / (float)n);
+    }
+}
+
 // out_F = g dF, out_q = g dq over S sectors, one launch
 __global__ void k_grad_scale(const float *__restrict__ g, const float *__restrict__ dF,
                              const float *__restrict__ dq, uint32_t S, float *out_F,
@@ -637,6 +1050,82 @@ __global__ void k_grad_scale(const float *__restrict__ g, const float *__restric
 }  // namespace
 
 // ---- launchers used by svt_abi.cu -------------------------------------------------
+// the staged pass's blocks: 12 warps without y (more warps to hide the
+// per-warp latency), 8 with y (whose stores favour fewer warps), two
+// buffers per warp each
+constexpr int LGB_NBUF = 2, LGB_WARPS_NOY = 12, LGB_WARPS_Y = 8;
+
+size_t calib_bulk_smem(int warps) { return (size_t)warps * LGB_NBUF * ST_BUF; }
+
+// the staged pass's three instances: loss and gradient, the same with y,
+// the loss alone
+enum { LGB_GRAD = 0, LGB_GRAD_Y = 1, LGB_LOSS = 2 };
+constexpr int lgb_warps(int kind) { return kind == LGB_GRAD_Y ? LGB_WARPS_Y : LGB_WARPS_NOY; }
+
+// resident blocks per SM of each instance on the current device (0: it
+// cannot be launched, the register-staged kernels are taken); the first call
+// on a device raises the kernels' dynamic shared-memory limit
+const int *calib_bulk_blocks_per_sm() {
+    constexpr int MAXD = 64;
+    static std::once_flag once[MAXD];
+    static int per_sm[MAXD][3];
+    static const int none[3] = {0, 0, 0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAXD) return none;
+    std::call_once(once[dev], [dev] {
+        auto one = [&](auto kernel, int warps) {
+            const int smem = (int)calib_bulk_smem(warps);
+            int k = 0;
+            if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+                    cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, kernel, warps * 32, smem) !=
+                    cudaSuccess)
+                k = 0;
+            return k;
+        };
+        per_sm[dev][LGB_GRAD] =
+            one(k_loss_grad_bulk<false, true, LGB_WARPS_NOY, LGB_NBUF>, LGB_WARPS_NOY);
+        per_sm[dev][LGB_GRAD_Y] =
+            one(k_loss_grad_bulk<true, true, LGB_WARPS_Y, LGB_NBUF>, LGB_WARPS_Y);
+        per_sm[dev][LGB_LOSS] =
+            one(k_loss_grad_bulk<false, false, LGB_WARPS_NOY, LGB_NBUF>, LGB_WARPS_NOY);
+        (void)cudaGetLastError();
+    });
+    return per_sm[dev];
+}
+
+// the staged pass when x and theta are 16-byte aligned and it can be
+// launched; false: the caller takes the register-staged kernels
+bool launch_loss_grad_bulk(int kind, const float *x, const float *theta,
+                           const int32_t *item_sector, const int32_t *item_start,
+                           const int32_t *sector_item, const int32_t *n_items, uint32_t S,
+                           uint64_t n, const float *F, const float *q, const float *w,
+                           const float *scale_dev, float *item_loss, float *item_grad,
+                           unsigned int *flag, float *loss, float *dF, float *dq, float *y,
+                           int sms, cudaStream_t st) {
+    if ((((uintptr_t)x | (uintptr_t)theta) & 15u) != 0) return false;
+    const int per_sm = calib_bulk_blocks_per_sm()[kind];
+    if (per_sm <= 0) return false;
+    const int g = max(sms, 1) * per_sm, warps = lgb_warps(kind);
+    const size_t smem = calib_bulk_smem(warps);
+    if (kind == LGB_GRAD_Y)
+        k_loss_grad_bulk<true, true, LGB_WARPS_Y, LGB_NBUF><<<g, warps * 32, smem, st>>>(
+            x, theta, item_sector, item_start, n_items, n, F, q, w, item_loss, item_grad, flag, y);
+    else if (kind == LGB_GRAD)
+        k_loss_grad_bulk<false, true, LGB_WARPS_NOY, LGB_NBUF><<<g, warps * 32, smem, st>>>(
+            x, theta, item_sector, item_start, n_items, n, F, q, w, item_loss, item_grad, flag,
+            nullptr);
+    else
+        k_loss_grad_bulk<false, false, LGB_WARPS_NOY, LGB_NBUF><<<g, warps * 32, smem, st>>>(
+            x, theta, item_sector, item_start, n_items, n, F, q, w, item_loss, item_grad, flag,
+            nullptr);
+    const uint32_t ncol = kind == LGB_LOSS ? 0u : (S * NPAR + LGF_THREADS - 1) / LGF_THREADS;
+    launch_after(k_lg_final, ncol + 1, LGF_THREADS, 0, st, (const float *)item_grad,
+                 (const float *)item_loss, sector_item, n_items, S, n, (uint32_t)(g * warps), ncol,
+                 scale_dev, flag, loss, dF, dq);
+    return true;
+}
+
 uint32_t calib_max_items(uint64_t n, uint32_t S) {
     return (uint32_t)((n + CALIB_CHUNK - 1) / CALIB_CHUNK + S);
 }
@@ -672,9 +1161,14 @@ void launch_calib_forward(const float *x, const int32_t *item_sector, const int3
 
 void launch_calib_loss(const float *x, const float *theta, const int32_t *item_sector,
                        const int32_t *item_start, const int32_t *sector_off,
-                       const int32_t *n_items, uint32_t max_items, uint64_t n, const float *F,
-                       const float *q, const float *w, float *item_loss, float *loss, int grid,
+                       const int32_t *sector_item, const int32_t *n_items, uint32_t max_items,
+                       uint32_t S, uint64_t n, const float *F, const float *q, const float *w,
+                       float *item_loss, unsigned int *flag, float *loss, int sms, int grid,
                        cudaStream_t st) {
+    if (launch_loss_grad_bulk(LGB_LOSS, x, theta, item_sector, item_start, sector_item, n_items,
+                              S, n, F, q, w, nullptr, item_loss, nullptr, flag, loss, nullptr,
+                              nullptr, nullptr, sms, st))
+        return;
     // one warp per item (8 per block); the block scheduler keeps the SMs full
     const int g = (int)((max_items + 7) / 8 + 1);
     (void)grid;
@@ -690,6 +1184,10 @@ void launch_calib_loss_grad(const float *x, const float *theta, const int32_t *i
                             const float *scale_dev, float *item_loss, float *item_grad,
                             float *sector_loss, unsigned int *tickets, float *loss, float *dF,
                             float *dq, float *y, int sms, cudaStream_t st) {
+    if (launch_loss_grad_bulk(y ? LGB_GRAD_Y : LGB_GRAD, x, theta, item_sector, item_start,
+                              sector_item, n_items, S, n, F, q, w, scale_dev, item_loss,
+                              item_grad, tickets + S + 1, loss, dF, dq, y, sms, st))
+        return;
     // two resident blocks of 8 warps per SM, each warp a contiguous run of items
     const int g = max(sms, 1) * 2;
     if (y)

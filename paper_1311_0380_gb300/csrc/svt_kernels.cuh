@@ -156,8 +156,9 @@ void launch_calib_forward(const float *x, const int32_t *item_sector, const int3
                           const float *F, const float *q, float *y, int grid, cudaStream_t st);
 void launch_calib_loss(const float *x, const float *theta, const int32_t *item_sector,
                        const int32_t *item_start, const int32_t *sector_off,
-                       const int32_t *n_items, uint32_t max_items, uint64_t n, const float *F,
-                       const float *q, const float *w, float *item_loss, float *loss, int grid,
+                       const int32_t *sector_item, const int32_t *n_items, uint32_t max_items,
+                       uint32_t S, uint64_t n, const float *F, const float *q, const float *w,
+                       float *item_loss, unsigned int *flag, float *loss, int sms, int grid,
                        cudaStream_t st);
 void launch_calib_loss_grad(const float *x, const float *theta, const int32_t *item_sector,
                             const int32_t *item_start, const int32_t *sector_off,

@@ -220,3 +220,64 @@ def test_loss_and_fit_in_one_pass_match_the_separate_calls():
     assert np.array_equal(F.grad.cpu().numpy(), runs[0][2])
     rF, rq = ref.grad(cs.x, cs.sector, cs.theta, cs.weight, cs.F0, cs.q0)
     check_grad(runs[0][2], runs[0][3], rF, rq)
+
+
+@pytest.mark.parametrize("n", [1, 3, 5, 7, 1029, 4099, 70001])
+def test_staged_and_register_passes_on_ragged_sizes(n):
+    """The fused pass stages each item's tracks in shared memory by bulk
+    copies when x and theta start on 16-byte boundaries (copies widened to
+    multiples of four tracks and cut below n; the last tracks past the cut
+    read directly; final sums in a second, dependent kernel), and loads them
+    per lane otherwise (final sums by tickets).  Both match the FP64 loss and
+    gradient, give exactly zero for sectors without tracks, write the same y
+    bit for bit, and leave the workspace's tickets and flag at zero, for
+    sizes that are not multiples of four, with sectors of one to a few
+    tracks."""
+    import torch
+    from paper_1311_0380_gb300 import _native as N, calib
+    from paper_1311_0380_gb300.api import _p, _stream
+    S = 16
+    cs = make(max(n, 8), S, seed=n)
+    x, theta = cs.x[:n], cs.theta[:n]
+    sector = (cs.sector[:n] % 11).astype(np.int32)       # sectors 11, 14, 15 stay empty
+    if n > 40:
+        sector[-3:] = 12                                 # sectors of three and five tracks
+        sector[:5] = 13
+    data = calib.CalibData(x, sector, theta, S, cs.weight)
+    F = torch.tensor(cs.F0, device="cuda", dtype=torch.float32)
+    q = torch.tensor(cs.q0, device="cuda", dtype=torch.float32)
+    L = N.load()
+    L64 = ref.loss(x, sector, theta, cs.weight, cs.F0, cs.q0)
+    rF, rq = ref.grad(x, sector, theta, cs.weight, cs.F0, cs.q0)
+    # the same sorted tracks off 16-byte boundaries (x keeps the 8 bytes its
+    # pair loads need)
+    xu = torch.zeros(n * 6 + 4, dtype=torch.float32, device="cuda")
+    tu = torch.zeros(n * 3 + 4, dtype=torch.float32, device="cuda")
+    xu[2:2 + n * 6] = data.x[:n].reshape(-1)
+    tu[1:1 + n * 3] = data.theta[:n].reshape(-1)
+    ys = []
+    for xp, tp in ((data.x.data_ptr(), data.theta.data_ptr()),
+                   (xu.data_ptr() + 8, tu.data_ptr() + 4)):
+        assert ((xp | tp) % 16 == 0) == (xp == data.x.data_ptr())
+        loss = torch.empty(1, dtype=torch.float32, device="cuda")
+        dF = torch.empty_like(F)
+        dq = torch.empty_like(q)
+        y = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+        N.check(L.svt_calib_loss_grad(xp, tp, _p(data.w), n, S, _p(data.index), _p(F), _p(q),
+                                      _p(loss), _p(dF), _p(dq), _p(y), _p(data.workspace),
+                                      data.workspace.numel(), _stream(None)),
+                "svt_calib_loss_grad")
+        torch.cuda.synchronize()
+        assert abs(loss.item() - L64) <= REL * abs(L64)
+        check_grad(dF.cpu().numpy(), dq.cpu().numpy(), rF, rq)
+        empty = np.setdiff1d(np.arange(S), sector)
+        assert np.all(dF.cpu().numpy()[empty] == 0) and np.all(dq.cpu().numpy()[empty] == 0)
+        ys.append(y.cpu().numpy())
+        lo = torch.empty(1, dtype=torch.float32, device="cuda")   # the loss alone
+        N.check(L.svt_calib_loss(xp, tp, _p(data.w), n, S, _p(data.index), _p(F), _p(q),
+                                 _p(lo), _p(data.workspace), data.workspace.numel(),
+                                 _stream(None)), "svt_calib_loss")
+        assert abs(lo.item() - L64) <= REL * abs(L64)
+        tail = ((S + 2) * 4 + 255) // 256 * 256           # the tickets and the flag, last
+        assert not data.workspace[-tail:].any()
+    assert np.array_equal(ys[0], ys[1])
