@@ -1013,25 +1013,29 @@ __global__ void __launch_bounds__(LGF_THREADS)
             dq[(size_t)s * 6 + (j - 36)] = total * scale;
         return;
     }
-    __shared__ float red[LGF_THREADS];
+    // the loss: each thread its sectors' segment losses in order, then the
+    // threads' sums by a fixed shuffle tree per warp and over the warps
+    __shared__ float wsum[LGF_THREADS / 32];
     float sl = 0.f;
     for (uint32_t s = threadIdx.x; s < S; s += LGF_THREADS) {
         const uint32_t a = (uint32_t)sector_item[s], e = (uint32_t)sector_item[s + 1];
         if (e > a) {
             const uint32_t wa = warp_of(a), wz = warp_of(e - 1);
+#pragma unroll 4
             for (uint32_t v = wa; v <= wz; ++v) sl += item_loss[max(a, first(v))];
         }
     }
-    red[threadIdx.x] = sl;
+    sl = warp_sum(sl);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = sl;
     __syncthreads();
-    for (uint32_t w = LGF_THREADS / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const unsigned int f = *flag;
-        if (f) *flag = 0u;
-        *loss = n == 0 ? 0.f : (f ? __int_as_float(0x7fc00000) : red[0] / (float)n);
+    if (threadIdx.x < 32) {
+        float t = threadIdx.x < LGF_THREADS / 32 ? wsum[threadIdx.x] : 0.f;
+        t = warp_sum(t);
+        if (threadIdx.x == 0) {
+            const unsigned int f = *flag;
+            if (f) *flag = 0u;
+            *loss = n == 0 ? 0.f : (f ? __int_as_float(0x7fc00000) : t / (float)n);
+        }
     }
 }
 

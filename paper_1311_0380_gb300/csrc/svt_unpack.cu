@@ -1,5 +1,6 @@
-// svt_unpack.cu -- stage 1 of the paper's Sec. 2.1 ("unpacking of input data
-// and filling of all the necessary data structures") for GB300.
+// svt_unpack.cu -- stage 1 of the paper's Sec. 2.1 for GB300: the input
+// words are parsed and the per-road structures the later stages read are
+// built.
 //
 // The batch is cut into tiles of 1024 words (128 threads x 8 words; smaller
 // tiles than 2048 words of 256 threads take 1-2 % off the step, since the
