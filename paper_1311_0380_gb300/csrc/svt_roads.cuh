@@ -92,13 +92,14 @@ __device__ __forceinline__ RoadDesc make_road_desc(uint32_t rw, uint32_t packed,
 // split roads with one 64-bit atomic on `reserve` ((items << 32) | roads), so
 // road slots and item ranges are reserved together and item_off increases
 // with the slot; the fit kernel's work queues are counters[0] (items) and
-// counters[1] (roads).
+// counters[1] (chunks of roads; past each warp's first chunk where the fit
+// kernel hands those out statically).
 struct BigList {
     uint32_t *road;                // split road of each slot
     uint32_t *item_off;            // its first work item
     uint32_t *pending;             // its items not yet finished
     unsigned long long *reserve;   // (items << 32) | roads appended so far
-    uint32_t *counters;            // [0] items taken, [1] roads taken
+    uint32_t *counters;            // [0] items, [1] chunks taken from the queues
 };
 
 // Fused-path outputs of the road extraction (desc == nullptr: plain path).
