@@ -281,3 +281,39 @@ def test_staged_and_register_passes_on_ragged_sizes(n):
         tail = ((S + 2) * 4 + 255) // 256 * 256           # the tickets and the flag, last
         assert not data.workspace[-tail:].any()
     assert np.array_equal(ys[0], ys[1])
+
+
+def _calib_flag_offset(n, S):
+    """Byte offset of the staged pass's copy-wait flag in the workspace:
+    item losses, item partials (42 per item), sector losses, the loss, then
+    the tickets (S per sector, the batch's, the flag), each at a multiple of
+    256 bytes."""
+    items = (n + 255) // 256 + S
+    off = 0
+    for count in (items, items * 42, S, 1):
+        off = (off + 255) // 256 * 256 + 4 * count
+    return (off + 255) // 256 * 256 + 4 * (S + 1)
+
+
+def test_staged_pass_reports_a_failed_copy_wait_as_nan():
+    """A copy wait that gives up sets the workspace's flag; the final kernel
+    then writes a NaN loss and clears the flag.  The flag is set here from
+    the host (no copy is made to fail), so the next call is clean again."""
+    import torch
+    from paper_1311_0380_gb300 import calib
+    S = 8
+    cs = make(5000, S, seed=41)
+    data = calib.CalibData(cs.x, cs.sector, cs.theta, S, cs.weight)
+    F = torch.tensor(cs.F0, device="cuda", requires_grad=True)
+    q = torch.tensor(cs.q0, device="cuda", requires_grad=True)
+    off = _calib_flag_offset(data.n, S)
+    assert data.workspace.numel() >= off + 4
+    flag = data.workspace[off:off + 4]
+    assert not flag.any()
+    flag.copy_(torch.tensor([1, 0, 0, 0], dtype=torch.uint8, device="cuda"))
+    loss = calib.calib_loss(F, q, data)
+    assert np.isnan(loss.item())
+    assert not flag.any()                                  # cleared by the call
+    L64 = ref.loss(cs.x, cs.sector, cs.theta, cs.weight, cs.F0, cs.q0)
+    loss = calib.calib_loss(F, q, data)
+    assert abs(loss.item() - L64) <= REL * abs(L64)
