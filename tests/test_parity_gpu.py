@@ -185,7 +185,8 @@ def test_plain_fit_tiles_over_many_and_few_roads():
     tile spans at most 64 roads and reads them directly otherwise: runs of
     one-combination roads (direct), of 2048-combination roads (one road per
     tile), of 48-combination roads (about 43 per tile) and a mix, with
-    missing layers and random constants, against the oracle."""
+    missing layers and random constants, against the oracle, with
+    capacities that leave a ragged last tile."""
     rng = np.random.default_rng(11)
     S = 8
     F, q = random_consts(S, 12)
@@ -206,8 +207,14 @@ def test_plain_fit_tiles_over_many_and_few_roads():
     cfg, ocfg = cfg_pair(15, 15, 3 * 12000 ** 2, 4096, 3, S)
     key, rec = oracle_run(w, off, F, q, ocfg)
     assert key == oracle.KEY_OK
-    st, got, _ = gpu_run(w, off, F, q, cfg, "plain", comb_cap=len(roads) * 4096)
-    assert_same(st, got, key, rec, "plain tiles")
+    # capacities above, at and just past the combination count (a ragged
+    # last tile)
+    n_comb = int(sum(np.prod([max(sum(1 for h in hits if h[0] == l), 1) for l in range(6)])
+                     for _, _, hits in roads))
+    for cap in (len(roads) * 4096, len(roads) * 4096 + 1, n_comb + 3 - (n_comb + 3) % 4,
+                n_comb):
+        st, got, _ = gpu_run(w, off, F, q, cfg, "plain", comb_cap=cap)
+        assert_same(st, got, key, rec, f"plain tiles, capacity {cap}")
 
 
 @pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
