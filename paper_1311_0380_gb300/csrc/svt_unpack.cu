@@ -222,7 +222,7 @@ __device__ __forceinline__ int block_exclusive_max(int v, int *smem) {
 //  * one thread per road then writes the road's outputs; for the fused path
 //    the tile's split roads are appended to the work list at a range that
 //    one atomic reserves for the whole tile.
-__global__ void __launch_bounds__(TILE_THREADS)
+__global__ void __launch_bounds__(TILE_THREADS, 9)
     k_unpack_roads(const uint32_t *__restrict__ words, const uint64_t *__restrict__ event_off,
                    const Dims *__restrict__ dims, const uint32_t *__restrict__ first_ev,
                    unsigned long long *tile_state, uint32_t *tile_ticket, uint64_t *total64,
@@ -243,6 +243,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
     __shared__ uint32_t cnt45[TILE_WORDS];
     __shared__ uint16_t hdr_pos[TILE_WORDS];          // tile position of each road header
     __shared__ int last_nonhit;
+    __shared__ int v1_flag;   // a V1 failure in the tile (read after the header barrier)
     __shared__ unsigned long long big_base;
     __shared__ unsigned long long tile_comb;   // evaluated combinations of the tile
     __shared__ uint32_t same_bits[1 + TILE_WORDS / 32];   // V8 bitmap, see below
@@ -264,9 +265,18 @@ __global__ void __launch_bounds__(TILE_THREADS)
         const uint64_t tile_end = min(tile_start + TILE_WORDS, n_words);
         const int tile_len = (int)(tile_end - tile_start);
         const uint64_t base = tile_start + (uint64_t)threadIdx.x * TILE_PER_THREAD;
-        if (threadIdx.x == 0) last_nonhit = -1;
+        if (threadIdx.x == 0) {
+            last_nonhit = -1;
+            v1_flag = 0;
+        }
         uint32_t w[TILE_PER_THREAD];
         load8(words, base, n_words, w);
+        // the events that start in the tile and the first offset of this
+        // thread's first one, loaded while the block scans
+        uint64_t e_lo, e_hi;
+        tile_events(first_ev, t, n_events, e_lo, e_hi);
+        const uint64_t s0_first =
+            e_lo + threadIdx.x < e_hi ? __ldg(event_off + e_lo + threadIdx.x) : 0ull;
         uint32_t nh = 0;   // road headers (low 16 bits) and event headers (high 16 bits)
 #pragma unroll
         for (int j = 0; j < TILE_PER_THREAD; ++j) {
@@ -291,57 +301,57 @@ __global__ void __launch_bounds__(TILE_THREADS)
         if (threadIdx.x == 0)
             publish_tile(tile_state + t, t == 0 ? TILE_INCLUSIVE : TILE_AGGREGATE, n_roads_tile);
         // per-word rules V3..V7 and V9 against the word before (the staged
-        // front halo holds the previous tile's last word; tile 0 has none)
-        uint64_t e_lo, e_hi;
-        tile_events(first_ev, t, n_events, e_lo, e_hi);
+        // front halo holds the previous tile's last word; tile 0 has none).
+        // A branch-free filter first: a word is suspect when it is of the
+        // reserved type, a road header of a sector past n_sectors, or a hit
+        // with reserved bits, a layer above 5, an event header before it, or a
+        // hit of a higher layer before it.  Only warps with a suspect word run
+        // the rules one by one (which report the exact status keys).
+        bool suspect = false;
 #pragma unroll
         for (int j = 0; j < TILE_PER_THREAD; ++j) {
             const int p = threadIdx.x * TILE_PER_THREAD + j;
-            if (p >= tile_len) break;
-            const uint64_t i = tile_start + p;
             const uint32_t x = w[j], pw = sw[FRONT + p - 1];
-            const uint32_t ty = w_type(x);
-            if (ty == TYPE_ROAD) {
-                if (rd_sector(x) >= cfg.n_sectors) report(status, i, SVT_ERR_BAD_SECTOR);   // V9
-            } else if (ty == TYPE_BAD) {
-                report(status, i, SVT_ERR_BAD_TYPE);                                      // V3
-            } else if (ty == TYPE_HIT) {
-                // V4 and V7 also fire on an event's first word, where V1 already
-                // reports the same word with the smallest code, so the key is unchanged.
-                if (i > 0 && w_type(pw) == TYPE_EVENT) report(status, i, SVT_ERR_BAD_TYPE);  // V4
-                if (hit_reserved(x) != 0) report(status, i, SVT_ERR_BAD_RESERVED);          // V5
-                if (hit_layer(x) > 5) report(status, i, SVT_ERR_BAD_LAYER);                 // V6
-                if (i > 0 && w_type(pw) == TYPE_HIT && hit_layer(pw) > hit_layer(x))
-                    report(status, i, SVT_ERR_UNSORTED);                                    // V7
+            const uint32_t ty = x >> 30, pty = pw >> 30;
+            const bool hit_bad = x >= (6u << 27) || (x & 0x07FF8000u) != 0u || pty == TYPE_EVENT ||
+                                 (pty == TYPE_HIT && (pw & (7u << 27)) > (x & (7u << 27)));
+            const bool bad = ty == TYPE_HIT    ? hit_bad
+                             : ty == TYPE_ROAD ? rd_sector(x) >= cfg.n_sectors
+                                               : ty == TYPE_BAD;
+            suspect |= p < tile_len && bad;
+        }
+        if (__any_sync(0xffffffffu, suspect)) {
+#pragma unroll
+            for (int j = 0; j < TILE_PER_THREAD; ++j) {
+                const int p = threadIdx.x * TILE_PER_THREAD + j;
+                if (p >= tile_len) break;
+                const uint64_t i = tile_start + p;
+                const uint32_t x = w[j], pw = sw[FRONT + p - 1];
+                const uint32_t ty = w_type(x);
+                if (ty == TYPE_ROAD) {
+                    if (rd_sector(x) >= cfg.n_sectors) report(status, i, SVT_ERR_BAD_SECTOR);   // V9
+                } else if (ty == TYPE_BAD) {
+                    report(status, i, SVT_ERR_BAD_TYPE);                                      // V3
+                } else if (ty == TYPE_HIT) {
+                    // V4 and V7 also fire on an event's first word, where V1 already
+                    // reports the same word with the smallest code, so the key is unchanged.
+                    if (i > 0 && w_type(pw) == TYPE_EVENT) report(status, i, SVT_ERR_BAD_TYPE);  // V4
+                    if (hit_reserved(x) != 0) report(status, i, SVT_ERR_BAD_RESERVED);          // V5
+                    if (hit_layer(x) > 5) report(status, i, SVT_ERR_BAD_LAYER);                 // V6
+                    if (i > 0 && w_type(pw) == TYPE_HIT && hit_layer(pw) > hit_layer(x))
+                        report(status, i, SVT_ERR_UNSORTED);                                    // V7
+                }
             }
         }
         // V1: the events starting in this tile start with an event header
-        int v1_bad = 0;
+        // (their first words are staged; the outcome is read after the next
+        // barrier)
         for (uint64_t e = e_lo + threadIdx.x; e < e_hi; e += TILE_THREADS) {
-            const uint64_t s0 = __ldg(event_off + e);
-            if (s0 >= tile_start && s0 < tile_end && w_type(__ldg(words + s0)) != TYPE_EVENT) {
+            const uint64_t s0 = e == e_lo + threadIdx.x ? s0_first : __ldg(event_off + e);
+            if (s0 >= tile_start && s0 < tile_end &&
+                w_type(sw[FRONT + (int)(s0 - tile_start)]) != TYPE_EVENT) {
                 report(status, s0, SVT_ERR_BAD_TYPE);                                   // V1
-                v1_bad = 1;
-            }
-        }
-        v1_bad = __syncthreads_or(v1_bad);
-        // V2: every event-header word must sit at an event offset.  When the
-        // tile holds as many headers as events start in it and all of those
-        // start with a header (V1), the headers are exactly those starts;
-        // otherwise every header of the tile is looked up.
-        if ((n_heads_tile >> 16) != e_hi - e_lo || v1_bad) {   // (rare: the batch is invalid)
-            const int lane = threadIdx.x & 31;
-            for (int j = 0; j < TILE_PER_THREAD; ++j) {
-                const bool ev = base + j < n_words && w_type(w[j]) == TYPE_EVENT;
-                uint32_t bal = __ballot_sync(0xffffffffu, ev);
-                while (bal) {
-                    const int src = __ffs(bal) - 1;
-                    const uint64_t i = __shfl_sync(0xffffffffu, base + j, src);
-                    const uint64_t e = warp_lower_bound64(event_off, n_events, i, lane);
-                    const bool start = e < n_events && __ldg(event_off + e) == i;
-                    if (lane == src && !start) report(status, i, SVT_ERR_BAD_TYPE);
-                    bal &= bal - 1;
-                }
+                v1_flag = 1;
             }
         }
         // road headers: positions; counters cleared
@@ -359,6 +369,25 @@ __global__ void __launch_bounds__(TILE_THREADS)
             }
         }
         __syncthreads();
+        // V2: every event-header word must sit at an event offset.  When the
+        // tile holds as many headers as events start in it and all of those
+        // start with a header (V1), the headers are exactly those starts;
+        // otherwise every header of the tile is looked up.
+        if ((n_heads_tile >> 16) != e_hi - e_lo || v1_flag) {   // (rare: the batch is invalid)
+            const int lane = threadIdx.x & 31;
+            for (int j = 0; j < TILE_PER_THREAD; ++j) {
+                const bool ev = base + j < n_words && w_type(w[j]) == TYPE_EVENT;
+                uint32_t bal = __ballot_sync(0xffffffffu, ev);
+                while (bal) {
+                    const int src = __ffs(bal) - 1;
+                    const uint64_t i = __shfl_sync(0xffffffffu, base + j, src);
+                    const uint64_t e = warp_lower_bound64(event_off, n_events, i, lane);
+                    const bool start = e < n_events && __ldg(event_off + e) == i;
+                    if (lane == src && !start) report(status, i, SVT_ERR_BAD_TYPE);
+                    bal &= bal - 1;
+                }
+            }
+        }
         // hits: count into their road (one shared atomic per run of the
         // thread's words that belongs to one road), note the tile's last
         // non-hit word, and mark "same layer as the word before" for V8
@@ -432,11 +461,13 @@ __global__ void __launch_bounds__(TILE_THREADS)
         }
         __syncthreads();
         // V8: a hit whose 16 predecessors are hits of its layer is the 17th (or
-        // later) of a run, i.e. 16 consecutive "same" bits end at it.  Thread k
-        // looks at bitmap words k - 1 and k: bit i of X is position 32 (k - 2) + i,
-        // and after the four steps bit s of y says bits s .. s + 15 of X are set.
-        if (threadIdx.x >= 1 && threadIdx.x <= TILE_WORDS / 32) {
-            const int k = threadIdx.x;
+        // later) of a run, i.e. 16 consecutive "same" bits end at it.  Thread
+        // k - 1 (the first warp) looks at bitmap words k - 1 and k: bit i of X
+        // is position 32 (k - 2) + i, and after the four steps bit s of y says
+        // bits s .. s + 15 of X are set.
+        static_assert(TILE_WORDS / 32 == 32, "one warp covers the bitmap's words");
+        if (threadIdx.x < TILE_WORDS / 32) {
+            const int k = threadIdx.x + 1;
             const unsigned long long X =
                 (unsigned long long)same_bits[k - 1] | ((unsigned long long)same_bits[k] << 32);
             unsigned long long y = X & (X >> 1);
