@@ -49,8 +49,10 @@ __host__ __device__ __forceinline__ uint64_t n_tiles(uint64_t n_words) {
 
 // ---- block-wide exclusive scan (blockDim.x == TILE_THREADS) ----------------
 // Returns the exclusive prefix of `v` over the block and writes the block
-// total to *total.  `smem` holds TILE_THREADS/32 + 1 entries.
-template <typename T>
+// total to *total.  `smem` holds TILE_THREADS/32 + 1 entries.  With
+// END_SYNC false the closing barrier is left out: the caller then reaches
+// another barrier before `smem` is written again.
+template <typename T, bool END_SYNC = true>
 __device__ __forceinline__ T block_exclusive_scan(T v, T *smem, T *total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n_warps = blockDim.x >> 5;
@@ -76,7 +78,7 @@ __device__ __forceinline__ T block_exclusive_scan(T v, T *smem, T *total) {
     __syncthreads();
     T res = smem[warp] + x - v;
     *total = smem[n_warps];
-    __syncthreads();
+    if (END_SYNC) __syncthreads();
     return res;
 }
 

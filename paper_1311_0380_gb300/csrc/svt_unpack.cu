@@ -236,6 +236,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 12)
                   "one pass of the block loads the halo and covers the V8 bitmap");
     constexpr uint32_t SENTINEL = 0xC0000000u;   // an event-header word: ends every run
     __shared__ uint32_t red[TILE_THREADS / 32 + 1];
+    __shared__ unsigned long long red64[TILE_THREADS / 32 + 1];
     __shared__ int redi[TILE_THREADS / 32];
     __shared__ uint32_t sw[FRONT + TILE_WORDS + BACK];
     __shared__ uint32_t cnt[TILE_WORDS];              // per road of the tile: 5 bits per layer
@@ -258,9 +259,10 @@ __global__ void __launch_bounds__(TILE_THREADS, 12)
     const uint64_t T = n_tiles(n_words);
     // tiles are taken in increasing order from a counter, so the tiles before
     // the one a block holds belong to blocks that are already running
+    // (the next tile is taken by thread 0 before the barrier that ends a tile)
+    if (threadIdx.x == 0) tile_s = atomicAdd(tile_ticket, 1u);
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) tile_s = atomicAdd(tile_ticket, 1u);
-        __syncthreads();
         const uint64_t t = tile_s;
         if (t >= T) break;
         const uint64_t tile_start = t * TILE_WORDS;
@@ -297,7 +299,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 12)
             sw[FRONT + TILE_WORDS + threadIdx.x] = k < n_words ? __ldg(words + k) : SENTINEL;
         }
         uint32_t n_heads_tile;
-        const uint32_t ex = block_exclusive_scan<uint32_t>(nh, red, &n_heads_tile) & 0xFFFFu;   // syncs
+        // (no closing barrier: `red` is next written by the split-road scan,
+        // several barriers later)
+        const uint32_t ex = block_exclusive_scan<uint32_t, false>(nh, red, &n_heads_tile) & 0xFFFFu;
         const uint32_t n_roads_tile = n_heads_tile & 0xFFFFu;
         // the tile's road count for the tiles after it, before anything else
         if (threadIdx.x == 0)
@@ -588,8 +592,15 @@ __global__ void __launch_bounds__(TILE_THREADS, 12)
             if ((threadIdx.x & 31) == 0 && cw) atomicAdd(&tile_comb, cw);
             uint32_t it_total = 0, big_total = 0, it_ex = 0, big_ex = 0;
             if (__syncthreads_or(big_sum != 0)) {
-                it_ex = block_exclusive_scan<uint32_t>(items_sum, red, &it_total);
-                big_ex = block_exclusive_scan<uint32_t>(big_sum, red, &big_total);
+                // items and roads in one scan ((items << 32) | roads); its
+                // shared entries are read before the barrier below
+                unsigned long long tot64;
+                const unsigned long long ex64 = block_exclusive_scan<unsigned long long, false>(
+                    ((unsigned long long)items_sum << 32) | big_sum, red64, &tot64);
+                it_ex = (uint32_t)(ex64 >> 32);
+                big_ex = (uint32_t)ex64;
+                it_total = (uint32_t)(tot64 >> 32);
+                big_total = (uint32_t)tot64;
             }
             if (threadIdx.x == 0) {
                 const unsigned long long c_total = tile_comb;
@@ -620,6 +631,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 12)
                 }
             }
         }
+        if (threadIdx.x == 0) tile_s = atomicAdd(tile_ticket, 1u);   // every thread has read t
         __syncthreads();
     }
     // an empty batch has no last tile to write the road count of
