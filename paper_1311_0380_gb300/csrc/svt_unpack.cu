@@ -313,20 +313,30 @@ __global__ void __launch_bounds__(TILE_THREADS, 12)
         // with reserved bits, a layer above 5, an event header before it, or a
         // hit of a higher layer before it.  Only warps with a suspect word run
         // the rules one by one (which report the exact status keys).
-        bool suspect = false;
+        // Word types by value: hit < 2^30 <= reserved < 2^31 <= road < 3 2^30
+        // <= event header; a valid hit is below layer 6 (x < 6 2^27) with no
+        // reserved bit; the word before comes from registers (the first one
+        // from the staged front halo).
+        const uint32_t n_in = (uint32_t)max(0, min(TILE_PER_THREAD,
+                                                   tile_len - (int)threadIdx.x * TILE_PER_THREAD));
+        uint32_t suspect = 0;
+        {
+            uint32_t pw = sw[FRONT + threadIdx.x * TILE_PER_THREAD - 1];
 #pragma unroll
-        for (int j = 0; j < TILE_PER_THREAD; ++j) {
-            const int p = threadIdx.x * TILE_PER_THREAD + j;
-            const uint32_t x = w[j], pw = sw[FRONT + p - 1];
-            const uint32_t ty = x >> 30, pty = pw >> 30;
-            const bool hit_bad = x >= (6u << 27) || (x & 0x07FF8000u) != 0u || pty == TYPE_EVENT ||
-                                 (pty == TYPE_HIT && (pw & (7u << 27)) > (x & (7u << 27)));
-            const bool bad = ty == TYPE_HIT    ? hit_bad
-                             : ty == TYPE_ROAD ? rd_sector(x) >= cfg.n_sectors
-                                               : ty == TYPE_BAD;
-            suspect |= p < tile_len && bad;
+            for (int j = 0; j < TILE_PER_THREAD; ++j) {
+                const uint32_t x = w[j];
+                const uint32_t hit_bad = (x >= (6u << 27)) | ((x & 0x07FF8000u) != 0u) |
+                                         (pw >= (3u << 30)) |
+                                         ((pw < (1u << 30)) & ((pw >> 27) > (x >> 27)));
+                const uint32_t bad = x < (1u << 30)   ? hit_bad
+                                     : x < (2u << 30) ? 1u
+                                     : x < (3u << 30) ? (uint32_t)(rd_sector(x) >= cfg.n_sectors)
+                                                      : 0u;
+                suspect |= ((uint32_t)j < n_in ? bad : 0u);
+                pw = x;
+            }
         }
-        if (__any_sync(0xffffffffu, suspect)) {
+        if (__any_sync(0xffffffffu, suspect != 0u)) {
 #pragma unroll
             for (int j = 0; j < TILE_PER_THREAD; ++j) {
                 const int p = threadIdx.x * TILE_PER_THREAD + j;
@@ -360,18 +370,22 @@ __global__ void __launch_bounds__(TILE_THREADS, 12)
                 v1_flag = 1;
             }
         }
-        // road headers: positions; counters cleared
+        // road headers: positions; counters cleared (a loop over the set bits
+        // of this thread's header mask: headers are about one word in 18)
         {
-            uint32_t r = ex;
+            uint32_t hm = 0;
 #pragma unroll
-            for (int j = 0; j < TILE_PER_THREAD; ++j) {
-                const int p = threadIdx.x * TILE_PER_THREAD + j;
-                if (p < tile_len && w_type(w[j]) == TYPE_ROAD) {
-                    hdr_pos[r] = (uint16_t)p;
-                    cnt[r] = 0u;
-                    cnt45[r] = 0u;
-                    r += 1;
-                }
+            for (int j = 0; j < TILE_PER_THREAD; ++j)
+                hm |= (threadIdx.x * TILE_PER_THREAD + j < tile_len && w_type(w[j]) == TYPE_ROAD)
+                          ? 1u << j : 0u;
+            uint32_t r = ex;
+            while (hm) {
+                const int j = __ffs(hm) - 1;
+                hm &= hm - 1;
+                hdr_pos[r] = (uint16_t)(threadIdx.x * TILE_PER_THREAD + j);
+                cnt[r] = 0u;
+                cnt45[r] = 0u;
+                r += 1;
             }
         }
         __syncthreads();
@@ -421,31 +435,53 @@ __global__ void __launch_bounds__(TILE_THREADS, 12)
                 const int before = block_exclusive_max(mine, redi);
                 in_run = before >= 0 && (before & 1);
             }
+            if (!cfg.xft_pairs) {
+                // the same steps by word value (hit < 2^30, road in [2^31,
+                // 3 2^30)), without the pairing counts
 #pragma unroll
-            for (int j = 0; j < TILE_PER_THREAD; ++j) {
-                const int p = threadIdx.x * TILE_PER_THREAD + j;
-                const uint32_t x = w[j];
-                const bool in = p < tile_len;
-                const uint32_t ty = w_type(x);
-                if (in && ty == TYPE_HIT && w_type(prev) == TYPE_HIT && hit_layer(prev) == hit_layer(x))
-                    same |= 1u << j;
-                prev = x;
-                if (!in) continue;
-                if (ty == TYPE_ROAD) {
-                    if (acc && r >= 0) atomicAdd(&cnt[r], acc);
-                    if (acc45 && r >= 0) atomicAdd(&cnt45[r], acc45);
-                    acc = 0;
-                    acc45 = 0;
-                    r += 1;
+                for (int j = 0; j < TILE_PER_THREAD; ++j) {
+                    const uint32_t x = w[j];
+                    const bool in = (uint32_t)j < n_in;
+                    const bool hit = in && x < (1u << 30);
+                    // a hit whose predecessor has the same top five bits is a
+                    // hit of the same layer
+                    same |= (hit && ((prev ^ x) >> 27) == 0u) ? 1u << j : 0u;
+                    prev = x;
+                    if (in && x >= (2u << 30) && x < (3u << 30)) {
+                        if (acc && r >= 0) atomicAdd(&cnt[r], acc);
+                        acc = 0;
+                        r += 1;
+                    }
+                    if (in && !hit) my_last_nonhit = (int)threadIdx.x * TILE_PER_THREAD + j;
+                    acc += hit ? 1u << (5 * hit_layer(x)) : 0u;
                 }
-                if (ty != TYPE_HIT) {
-                    my_last_nonhit = p;
-                    in_run = ty == TYPE_ROAD;
-                    continue;
+            } else {
+#pragma unroll
+                for (int j = 0; j < TILE_PER_THREAD; ++j) {
+                    const int p = threadIdx.x * TILE_PER_THREAD + j;
+                    const uint32_t x = w[j];
+                    const bool in = p < tile_len;
+                    const uint32_t ty = w_type(x);
+                    if (in && ty == TYPE_HIT && w_type(prev) == TYPE_HIT && hit_layer(prev) == hit_layer(x))
+                        same |= 1u << j;
+                    prev = x;
+                    if (!in) continue;
+                    if (ty == TYPE_ROAD) {
+                        if (acc && r >= 0) atomicAdd(&cnt[r], acc);
+                        if (acc45 && r >= 0) atomicAdd(&cnt45[r], acc45);
+                        acc = 0;
+                        acc45 = 0;
+                        r += 1;
+                    }
+                    if (ty != TYPE_HIT) {
+                        my_last_nonhit = p;
+                        in_run = ty == TYPE_ROAD;
+                        continue;
+                    }
+                    acc += 1u << (5 * hit_layer(x));
+                    if (in_run)
+                        acc45 += (1u << 20) + (hit_layer(x) == 4 ? 1u : 0u) + (hit_layer(x) == 5 ? 1u << 10 : 0u);
                 }
-                acc += 1u << (5 * hit_layer(x));
-                if (cfg.xft_pairs && in_run)
-                    acc45 += (1u << 20) + (hit_layer(x) == 4 ? 1u : 0u) + (hit_layer(x) == 5 ? 1u << 10 : 0u);
             }
             if (acc && r >= 0) atomicAdd(&cnt[r], acc);
             if (acc45 && r >= 0) atomicAdd(&cnt45[r], acc45);
