@@ -503,8 +503,14 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}-{step_events}ev-slices", "events_per_step": step_events,
-                   "fits_per_step": fits / args.steps, "sectors": spec.n_sectors},
+        # the same workload as the GPU arm's line (its batch, its fits per
+        # batch); every timed step processes a sample of it
+        "config": {"workload": f"{args.workload}-{batch.n_events}ev", "events": batch.n_events,
+                   "roads": int(batch.total_roads),
+                   "fits_per_step": int(fits_ev.sum()), "sectors": spec.n_sectors,
+                   "max_comb": spec.max_comb,
+                   "sample_events_per_step": step_events,
+                   "sample_fits_per_step": fits / args.steps},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{step_events}-event slices of the {args.workload} workload per step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
