@@ -791,7 +791,7 @@ def uneven_full(dev, flush, timer, steps=5, warmup=2):
     out = {"workload": f"uneven-{UNEVEN_EVENTS}ev", "events": n_events, "roads": R,
            "fits_per_step": fits, "steps": steps, "ms_per_step": step_s * 1e3,
            "fits_per_s": fits / step_s, "events_per_s": n_events / step_s,
-           "fit_kernel_ms": fit_s * 1e3, "launch": "CUDA graph of the five-kernel sequence",
+           "fit_kernel_ms": fit_s * 1e3, "launch": "CUDA graph of the three-kernel sequence",
            "schedule": {f: getattr(sched, f) for f, _ in api.SvtSchedule._fields_},
            "tuned_on": f"{TILE_DRAW}-event draw, {tune_ms:.3f} ms per run",
            "l2": "flushed between steps (256 MB write)",
