@@ -278,6 +278,13 @@ def test_staged_and_register_passes_on_ragged_sizes(n):
                                  _p(lo), _p(data.workspace), data.workspace.numel(),
                                  _stream(None)), "svt_calib_loss")
         assert abs(lo.item() - L64) <= REL * abs(L64)
+        g = torch.tensor([2.5], dtype=torch.float32, device="cuda")   # the separate backward
+        bF, bq = torch.empty_like(F), torch.empty_like(q)
+        N.check(L.svt_calib_loss_backward(xp, tp, _p(data.w), n, S, _p(data.index), _p(F), _p(q),
+                                          _p(g), _p(bF), _p(bq), _p(data.workspace),
+                                          data.workspace.numel(), _stream(None)),
+                "svt_calib_loss_backward")
+        check_grad(bF.cpu().numpy() / 2.5, bq.cpu().numpy() / 2.5, rF, rq)
         tail = ((S + 2) * 4 + 255) // 256 * 256           # the tickets and the flag, last
         assert not data.workspace[-tail:].any()
     assert np.array_equal(ys[0], ys[1])
