@@ -570,23 +570,25 @@ def run_sweep(args):
         st, rec, _ = fp.result()
         assert st == api.N.STATUS_OK
         fused = [a.elapsed_time(b) * 1e3 for a, b in evs]
-        # fused, end to end
-        runner = api.HostRunner(fp, stream)
+        # fused, end to end through the library's one call (svt_run_host:
+        # copy-in, the fused path and copy-out enqueued by one C call), one
+        # batch in flight, timed from before its copy-in to after its copy-out
+        runner = api.StreamingRunner(n_words, n_ev, R, dconst, sched, dev, depth=1)
         h_w, h_o = api.HostRunner.pin_batch(words, off)
         for _ in range(3):
-            runner.submit(h_w, h_o, R)
+            runner.submit(h_w, h_o)
             runner.wait()
         e2e = []
         for _ in range(reps):
             a, b = ev_pair()
-            a.record(stream)
-            runner.submit(h_w, h_o, R)
-            b.record(stream)
-            runner.wait()
+            runner.submit(h_w, h_o, marks=(a, b))
+            zst_e2e, rec_e2e = runner.wait()
             e2e.append(a.elapsed_time(b) * 1e3)
+        assert zst_e2e == api.N.STATUS_OK and np.array_equal(rec_e2e, rec)
         # zero-copy: words and offsets stay in mapped host memory and the
         # kernels read them in place (the records go to device memory and are
-        # copied back, or are written straight into host memory)
+        # copied back, or are written straight into host memory; the status
+        # word is copied back either way)
         w_bytes = (4 * n_words + 255) // 256 * 256
         mh = api.MappedHost(w_bytes + 8 * (n_ev + 1) + 24 * max(R, 1))
         mh.view(np.uint32, 0, n_words)[:] = words
