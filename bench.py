@@ -80,6 +80,8 @@ def parse_args():
                     help="pair small roads on half warps (schedule field pair_small = 1)")
     ap.add_argument("--quad", action="store_true",
                     help="also group tiny roads four to a warp (pair_small = 2)")
+    ap.add_argument("--lanes", action="store_true",
+                    help="one tiny road per lane, 32 roads per chunk (pair_small = 3)")
     return ap.parse_args()
 
 
@@ -828,8 +830,8 @@ def main():
                      int(spec.xft))
     dconst = api.DeviceConstants.from_numpy(consts.F, consts.q, cfg, dev)
     n_words, n_events, R = len(batch.words), batch.n_events, batch.total_roads
-    sched = api.schedule(args.warps, args.bps, args.rows,
-                         pair_small=2 if args.quad else int(args.pair))
+    sched = api.schedule(args.warps, args.bps, args.rows, 32 if args.lanes else 0,
+                         pair_small=3 if args.lanes else 2 if args.quad else int(args.pair))
     fused = api.FusedPath(n_words, n_events, R, dconst, sched, dev)
     d_words = api.to_device_u32(batch.words, dev)
     d_off = api.to_device_u64(batch.event_off, dev)
@@ -837,7 +839,8 @@ def main():
     flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)   # 256 MB > 129 MB L2
     stream = torch.cuda.current_stream()
     tuned = None
-    if not args.no_tune and not (args.warps or args.rows or args.bps or args.pair or args.quad):
+    if not args.no_tune and not (args.warps or args.rows or args.bps or args.pair or args.quad
+                                 or args.lanes):
         from paper_1311_0380_gb300 import autotune
         # timed as the steps are: L2 overwritten before every run
         sch, tms = autotune.tuned_schedule(fused, d_words, n_words, d_off, n_events, cache=None,

@@ -141,6 +141,11 @@ typedef struct {
  *                    2: also four consecutive tiny roads (at most 2 hits per
  *                    layer, at most 8 rows and 16 suffix-table entries) of
  *                    the same geometry by the four quarters of one warp;
+ *                    3: every tiny road of a chunk by one lane of its own
+ *                    (lane k: the chunk's road k, any geometry), then the
+ *                    chunk's other roads one per warp; meant for 32 roads per
+ *                    chunk; needs d_F and d_q 4-byte aligned and at most 12
+ *                    warps per block (else BAD_ARG);
  *                    0 (default): one road per warp.  Grouping pays when most
  *                    roads are small and alike (the paper's fixed shape); on
  *                    mixed roads the warps keep switching between the code
@@ -335,8 +340,11 @@ int svt_run_sized(const uint32_t *d_words, uint64_t max_words, const uint64_t *d
  * schedule of {4, 8, 16} warps per block x {8, 16, 32, 64} rows per item x
  * {1, 2, 4, 8} roads per chunk x {1024, 4096, 16384} small_max (blocks per SM
  * as many as fit, no pairing), then the fastest of those with pair_small = 1
- * and {2, 4, 8} roads per chunk and with pair_small = 2 and {4, 8, 16} roads
- * per chunk, then the fastest so far with 1 and 2 blocks per SM, one warm-up and `reps` timed runs each (CUDA events on `stream`);
+ * and {2, 4, 8} roads per chunk, with pair_small = 2 and {4, 8, 16} roads
+ * per chunk and (for 4-byte aligned d_F and d_q) with pair_small = 3 and
+ * {16, 32} roads per chunk (8 warps per block where the fastest had 16), then
+ * the fastest so far with 1 and 2 blocks per SM, one warm-up and `reps` timed
+ * runs each (CUDA events on `stream`);
  * finally the four fastest of all these once more with 3 * reps runs each,
  * and returns the fastest of that pass and its mean time per run.
  *   d_flush, flush_bytes  device scratch (may be NULL with flush_bytes 0):

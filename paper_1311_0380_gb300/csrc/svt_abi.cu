@@ -59,7 +59,8 @@ svt_schedule resolve(const svt_schedule *s) {
 bool schedule_ok(const svt_schedule &s) {
     return s.warps_per_block >= 1 && s.warps_per_block <= 16 && s.blocks_per_sm <= 32 &&
            s.rows_per_item >= 1 && s.rows_per_item <= 64 && s.roads_per_chunk >= 1 &&
-           s.roads_per_chunk <= 32 && s.small_max >= 1 && s.pair_small <= 2;
+           s.roads_per_chunk <= 32 && s.small_max >= 1 && s.pair_small <= 3 &&
+           (s.pair_small != 3 || s.warps_per_block <= 12);
 }
 
 // word tiles: up to 16 blocks of 128 threads per SM at once (grid-stride
@@ -67,6 +68,11 @@ bool schedule_ok(const svt_schedule &s) {
 int tile_grid() {
     int sms = current_sm_count();
     return (sms > 0 ? sms : 1) * 16;
+}
+
+// warps' road grouping of the fit kernel for a schedule's pair_small
+uint32_t fit_group(uint32_t pair_small) {
+    return pair_small == 3 ? 32u : pair_small == 2 ? 4u : pair_small == 1 ? 2u : 1u;
 }
 
 int launch_status() {
@@ -336,6 +342,9 @@ int run_impl(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_
     if (n_words >= (1ull << 32) || n_events >= (1ull << 31) || road_cap >= (1ull << 31))
         return SVT_ERR_BAD_ARG;
     if ((uintptr_t)d_workspace & 255u) return SVT_ERR_BAD_ARG;
+    // one road per lane reads the constants as 32-bit pairs
+    if (fit_group(sc.pair_small) == 32 && (((uintptr_t)d_F | (uintptr_t)d_q) & 3u))
+        return SVT_ERR_BAD_ARG;
     RunWs w = carve_run(d_workspace, n_words, n_events, road_cap);
     if (workspace_bytes < w.bytes) return SVT_ERR_BAD_ARG;
     unsigned long long *status = (unsigned long long *)d_status;
@@ -344,7 +353,8 @@ int run_impl(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_
     const int grid = tile_grid();
     const int sms = current_sm_count();
     if (sms <= 0) return SVT_ERR_CUDA;
-    const int occ = fit_persistent_blocks_per_sm((int)sc.warps_per_block);
+    const int occ =
+        fit_persistent_blocks_per_sm((int)sc.warps_per_block, fit_group(sc.pair_small));
     if (occ <= 0) return SVT_ERR_CUDA;
     const int bps = (sc.blocks_per_sm == 0 || (int)sc.blocks_per_sm > occ) ? occ : (int)sc.blocks_per_sm;
     const BigList bl{w.big_road, w.big_item_off, w.big_pending, (unsigned long long *)w.work,
@@ -364,7 +374,7 @@ int run_impl(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_event_
     if (timer && cudaEventRecord(timer->start, st) != cudaSuccess) return SVT_ERR_CUDA;
     if (launch_fit_persistent(d_words, d_event_off, w.dims, event_road, w.desc, counts, road_cap,
                               d_F, d_q, *cfg, fr, sc.roads_per_chunk,
-                              sc.pair_small == 2 ? 4u : (sc.pair_small == 1 ? 2u : 1u), d_out,
+                              fit_group(sc.pair_small), d_out,
                               status, (int)sc.warps_per_block, sms * bps, st) != cudaSuccess)
         return SVT_ERR_CUDA;
     if (timer) {
@@ -530,6 +540,14 @@ int svt_autotune(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_ev
             for (uint32_t c : {2u, 4u, 8u})
                 if ((rc = trial(svt_schedule{base.warps_per_block, 0, base.rows_per_item,
                                              g == 2 ? 2 * c : c, base.small_max, g})) != SVT_OK)
+                    goto done;
+        // one tiny road per lane, 16 or 32 roads per chunk (constants that
+        // are not 4-byte aligned rule it out)
+        if (!(((uintptr_t)d_F | (uintptr_t)d_q) & 3u))
+            for (uint32_t c : {16u, 32u})
+                if ((rc = trial(svt_schedule{base.warps_per_block > 12 ? 8 : base.warps_per_block,
+                                             0, base.rows_per_item, c, base.small_max, 3})) !=
+                    SVT_OK)
                     goto done;
     }
     {

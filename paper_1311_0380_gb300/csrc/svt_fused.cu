@@ -21,7 +21,8 @@
 //     roads (one coalesced load of their 32-byte descriptors) and fit every
 //     remaining road whole, one warp per road; with the grouped instances two
 //     consecutive SMALL roads of the same geometry go to the two halves of a
-//     warp instead, or four TINY ones to its four quarters.
+//     warp instead, or four TINY ones to its four quarters, or every TINY road
+//     of the chunk to a lane of its own (see lane_fit).
 //   * Each lane visits its combinations in increasing c within a column (or
 //     within its block of rows of a column), so a strict '<' keeps the
 //     smallest index among equal chi2; across columns, row blocks, lanes and
@@ -73,6 +74,16 @@ static_assert(sizeof(HalfSmem) % 16 == 0, "half slots keep 16-byte alignment");
 static_assert(sizeof(QuarterSmem) % 16 == 0, "quarter slots keep 16-byte alignment");
 static_assert(sizeof(WarpSmem) % 16 == 0, "warp slots keep 16-byte alignment");
 static_assert(sizeof(WarpSmem) >= 32 * 6 * sizeof(uint32_t), "a road slot holds 32 records");
+
+// A warp's slot when each lane fits a TINY road alone (lane_fit): the lane's
+// column sums B_k(b), at most 8 columns, in column j of the tables.
+struct LaneTables {
+    longlong2 B01[8][32];   // B_3(b), B_4(b) of lane j at [b][j]
+    long long B5[8][32];    // B_5(b)
+};
+constexpr size_t SLOT_BYTES =
+    sizeof(WarpSmem) > sizeof(LaneTables) ? sizeof(WarpSmem) : sizeof(LaneTables);
+static_assert(SLOT_BYTES % 16 == 0, "slots keep 16-byte alignment");
 
 // Roads a warp has finished but whose records it has not yet written: when 31
 // or 32 are listed (and when the warp runs out of work) each lane writes one
@@ -457,6 +468,223 @@ __device__ __forceinline__ RoadDesc shfl_desc(const uint4 &da, const uint4 &db, 
     return D;
 }
 
+// One TINY road (at most two hits on every layer, so at most 64
+// combinations) fitted by one lane, and its record formed there.  The prefix
+// layers 0..2 index the rows a and the suffix layers 3..5 the columns b,
+// c = a * NB3 + b: the same combination index as in any other split, so the
+// lane visits the combinations in increasing c and a strict '<' keeps the
+// smallest c among equal chi2.  Every layer has radix 1 or 2, so the digits
+// of a row or a column are single bits, and a sum over the layers is the sum
+// of the first hits' terms plus, for every digit that is set, the layer's
+// difference between its second and its first hit.  The column sums (at most
+// 8) go to the lane's column of the slot's tables; each row's sums are formed
+// once in registers.  With track-trigger pairs layer 5 has radix 1 and its
+// hits' terms are added to those of their layer-4 partners, as in
+// road_setup.  The record is the one form_record writes: flags, the best c
+// and its chi2, and the three parameter rows (Eq. 1) of the best combination
+// formed in int64 from its hits' coordinates, which the lane still holds.
+struct LaneRecord {
+    uint32_t w[6];
+    bool pass;
+};
+template <bool GUARDED>
+__device__ __forceinline__ LaneRecord lane_fit(LaneTables &tb, const uint32_t *__restrict__ words,
+                                               const uint4 &da, const uint4 &db,
+                                               const int16_t *__restrict__ F,
+                                               const int16_t *__restrict__ q,
+                                               const svt_config &cfg, uint32_t sh, uint32_t qsh,
+                                               uint32_t init_chi, int lane) {
+    const uint32_t C_eval = da.w, packed = da.y, geo = db.x, xft = cfg.xft_pairs;
+    const size_t cs = (size_t)rd_sector(da.z) * 64 + ((geo >> 13) & 63u);
+    // The chi rows k = 3..5 of F as pairs of int16 (F[k][l], F[k][l+1]) for
+    // even l (row k starts at element (cs * 36 + 6 k), an even index, so each
+    // pair is 4-byte aligned), q_3, and the pair (q_4, q_5); two hit words per
+    // layer (the second repeats the first when the layer has one hit; a layer
+    // without hits reads the road's header word and takes x = 0).  Every load
+    // is issued before any is used.
+    const uint32_t *F32 = reinterpret_cast<const uint32_t *>(F + cs * 36);
+    const uint32_t *q32 = reinterpret_cast<const uint32_t *>(q + cs * 6);
+    uint32_t fp[9];
+#pragma unroll
+    for (int j = 0; j < 9; ++j) fp[j] = __ldg(F32 + 9 + j);
+    const uint32_t q23 = __ldg(q32 + 1), q45 = __ldg(q32 + 2);
+    uint32_t hw[N_LAYERS][2];
+    {
+        uint32_t off = da.x + 1;   // first hit word of layer l (hits are sorted by layer)
+#pragma unroll
+        for (int l = 0; l < N_LAYERS; ++l) {
+            const uint32_t nl = nhit_of(packed, l);
+            const uint32_t p0 = nl ? off : da.x;
+            hw[l][0] = __ldg(words + p0);
+            hw[l][1] = __ldg(words + (nl > 1u ? off + 1u : p0));
+            off += nl;
+        }
+    }
+    // the int16 at index j of a run of pairs (little-endian: the even element
+    // in the low half)
+    auto lo16 = [](uint32_t v) { return (int32_t)(int16_t)(v & 0xFFFFu); };
+    auto hi16 = [](uint32_t v) { return (int32_t)v >> 16; };
+    auto f_of = [&](int k, int l) -> int32_t {   // F[3 + k][l]
+        const uint32_t v = fp[(k * 6 + l) >> 1];
+        return (l & 1) ? hi16(v) : lo16(v);
+    };
+    // Every term is multiplied by P = 2^(32 - oshift) on its way into a 64-bit
+    // sum (one wide multiply-add).  A0 and B0 hold the first hits' terms (with
+    // q and the column bias); dA and dB the per-layer differences between a
+    // layer's second and first hit, F (x1 - x0), which fit in 32 bits.
+    const int32_t P = (int32_t)(1u << sh);
+    long long A0[3], B0[3];
+    int32_t dA[3][3], dB[3][3];
+    uint32_t beta[N_LAYERS];   // 1 when the layer's radix is 2
+    uint32_t xs[N_LAYERS];     // the layer's two coordinates, x0 | x1 << 16 (0: no hits)
+    A0[0] = (long long)hi16(q23) << qsh;
+    A0[1] = (long long)lo16(q45) << qsh;
+    A0[2] = (long long)hi16(q45) << qsh;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) B0[k] = kColBias<GUARDED>;
+    const uint32_t n5 = nhit_of(packed, N_LAYERS - 1);
+#pragma unroll
+    for (int l = 0; l < N_LAYERS; ++l) {
+        const uint32_t nl = nhit_of(packed, l);
+        const bool paired5 = xft && l == N_LAYERS - 1;
+        beta[l] = (nl == 2u && !paired5) ? 1u : 0u;
+        // with pairs, layer 4's entry i also carries layer 5's hit i
+        const bool fold = xft && l == N_LAYERS - 2;
+        const int32_t x0 = nl ? (int32_t)hit_coord(hw[l][0]) : 0;
+        const int32_t x1 = nl ? (int32_t)hit_coord(hw[l][1]) : 0;
+        xs[l] = (uint32_t)x0 | ((uint32_t)x1 << 16);
+        const int32_t y0 = (fold && n5) ? (int32_t)hit_coord(hw[N_LAYERS - 1][0]) : 0;
+        const int32_t y1 = (fold && n5) ? (int32_t)hit_coord(hw[N_LAYERS - 1][1]) : 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            // |F x| < 2^30: one product, or a pair's two, and their
+            // differences fit in 32 bits
+            int32_t t0 = 0, d = 0;
+            if (!paired5) {
+                const int32_t fl = f_of(k, l);
+                t0 = fl * x0;
+                d = fl * (x1 - x0);
+                if (fold) {
+                    const int32_t f5 = f_of(k, N_LAYERS - 1);
+                    t0 += f5 * y0;
+                    d += f5 * (y1 - y0);
+                }
+            }
+            if (l < 3) {
+                A0[k] += (long long)t0 * P;
+                dA[l][k] = d;
+            } else {
+                B0[k] += (long long)t0 * P;
+                dB[l - 3][k] = d;
+            }
+        }
+    }
+    const uint32_t nbB = beta[3] + beta[4] + beta[5], NB3 = 1u << nbB;
+    // column sums: column b's digits are bit b5 (layer 5), then layer 4, then layer 3
+#pragma unroll
+    for (uint32_t b = 0; b < 8u; ++b) {
+        if (b < NB3) {
+            const uint32_t d5 = b & beta[5], d4 = (b >> beta[5]) & beta[4],
+                           d3 = (b >> (beta[5] + beta[4])) & beta[3];
+            long long s[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                s[k] = B0[k];
+                s[k] += (long long)(d3 ? dB[0][k] : 0) * P;
+                s[k] += (long long)(d4 ? dB[1][k] : 0) * P;
+                s[k] += (long long)(d5 ? dB[2][k] : 0) * P;
+            }
+            tb.B01[b][lane] = make_longlong2(s[0], s[1]);
+            tb.B5[b][lane] = s[2];
+        }
+    }
+    uint32_t bchi = init_chi, bc = 0;
+    const uint32_t NA3 = 1u << (beta[0] + beta[1] + beta[2]);
+    for (uint32_t a = 0, c0 = 0; a < NA3 && c0 < C_eval; ++a, c0 += NB3) {
+        const uint32_t d2 = a & beta[2], d1 = (a >> beta[2]) & beta[1],
+                       d0 = (a >> (beta[2] + beta[1])) & beta[0];
+        long long A[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            A[k] = A0[k];
+            A[k] += (long long)(d0 ? dA[0][k] : 0) * P;
+            A[k] += (long long)(d1 ? dA[1][k] : 0) * P;
+            A[k] += (long long)(d2 ? dA[2][k] : 0) * P;
+        }
+        const uint32_t nbr = min(NB3, C_eval - c0);   // columns of this row to evaluate
+#pragma unroll
+        for (uint32_t b = 0; b < 8u; ++b) {
+            if (b < nbr) {
+                const longlong2 v01 = tb.B01[b][lane];
+                const long long v5 = tb.B5[b][lane];
+                const int32_t y3 = hi_word(A[0] + v01.x);
+                const int32_t y4 = hi_word(A[1] + v01.y);
+                const int32_t y5 = hi_word(A[2] + v5);
+                if (GUARDED) {   // as in eval_rows
+                    const uint32_t g3 = (uint32_t)y3, g4 = (uint32_t)y4, g5 = (uint32_t)y5;
+                    const uint32_t range = g3 | g4 | g5;
+                    const uint32_t chi2 = g3 * g3 + g4 * g4 + g5 * g5 + (3u << 30) -
+                                          ((g3 + g4 + g5) << 16);
+                    if (range < 65536u && chi2 < bchi) {
+                        bchi = chi2;
+                        bc = c0 + b;
+                    }
+                } else {
+                    const int32_t c3 = clamp_chi(y3), c4 = clamp_chi(y4), c5 = clamp_chi(y5);
+                    const uint32_t chi2 =
+                        (uint32_t)(c3 * c3) + (uint32_t)(c4 * c4) + (uint32_t)(c5 * c5);
+                    if (chi2 < bchi) {
+                        bchi = chi2;
+                        bc = c0 + b;
+                    }
+                }
+            }
+        }
+    }
+    // the record
+    LaneRecord rec;
+    rec.pass = C_eval > 0 && bchi != init_chi;
+    uint32_t flags = rec.pass ? SVT_FLAG_PASS : 0u;
+    if (((geo >> 19) & 127u) == 0) flags |= SVT_FLAG_NO_HITS;
+    if (geo & (1u << 27)) flags |= SVT_FLAG_BAD_PATTERN;
+    if (geo & (1u << 26)) flags |= SVT_FLAG_OVERFLOW;
+    rec.w[0] = rd_id(da.z) | (flags << 24);
+    rec.w[1] = rec.pass ? bc : 0xFFFFFFFFu;
+    rec.w[2] = rec.pass ? bchi : 0u;
+    rec.w[3] = rec.w[4] = rec.w[5] = 0u;
+    if (rec.pass) {
+        // the parameter rows k = 0..2 of F and q
+#pragma unroll
+        for (int j = 0; j < 9; ++j) fp[j] = __ldg(F32 + j);
+        const uint32_t q01 = __ldg(q32), q2x = __ldg(q32 + 1);
+        // the best combination's digits (with pairs, layer 5 takes layer 4's)
+        const uint32_t a = bc >> nbB, b = bc & (NB3 - 1u);
+        uint32_t d[N_LAYERS];
+        d[5] = b & beta[5];
+        d[4] = (b >> beta[5]) & beta[4];
+        d[3] = (b >> (beta[5] + beta[4])) & beta[3];
+        d[2] = a & beta[2];
+        d[1] = (a >> beta[2]) & beta[1];
+        d[0] = (a >> (beta[2] + beta[1])) & beta[0];
+        if (xft) d[5] = d[4];
+        int32_t x[N_LAYERS];
+#pragma unroll
+        for (int l = 0; l < N_LAYERS; ++l) x[l] = (int32_t)((xs[l] >> (16u * d[l])) & 0xFFFFu);
+        const int32_t qv[3] = {lo16(q01), hi16(q01), lo16(q2x)};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            long long acc = (long long)qv[k] * (1ll << cfg.qshift);
+#pragma unroll
+            for (int l = 0; l < N_LAYERS; ++l) {
+                const uint32_t v = fp[(k * 6 + l) >> 1];
+                acc += (long long)((l & 1) ? hi16(v) : lo16(v)) * (long long)x[l];
+            }
+            rec.w[3 + k] = (uint32_t)(int32_t)(acc >> cfg.oshift);   // floor
+        }
+    }
+    return rec;
+}
+
 // Record of road r from its best key (six words into w), formed by one lane
 // (the warps of the fit kernel hand their finished roads out one per lane,
 // see RecordList).
@@ -540,11 +768,18 @@ __device__ __forceinline__ bool form_record(const uint32_t *__restrict__ words,
 // K4: persistent fit / cut / select / format.  GROUP 2: two consecutive SMALL
 // roads of one chunk with the same geometry go to the two halves of the warp;
 // GROUP 4: four consecutive TINY roads of the same geometry go to its four
-// quarters (else two SMALL roads to its halves, as with GROUP 2).  Each is a
-// separate instance, so that warps never switch between the code paths
+// quarters (else two SMALL roads to its halves, as with GROUP 2); GROUP 32:
+// every TINY road of the chunk goes to a lane of its own (lane k: the chunk's
+// road k), then the warp fits the chunk's other roads one at a time.  Each is
+// a separate instance, so that warps never switch between the code paths
 // unless grouping was asked for.
+// (GROUP 32 keeps every load of a lane's road in flight at once with up to 85
+// registers a thread, blocks of at most 12 warps: 80 are used, three blocks of
+// 8 warps per SM; with 64, loads were serialised or spilled and with 128 only
+// 16 warps per SM were resident.  The others fit in 64, for two blocks of
+// 512 threads.)
 template <bool GUARDED, int GROUP>
-__global__ void __launch_bounds__(512, 2)
+__global__ void __launch_bounds__(GROUP == 32 ? 384 : 512, 2)
     k_fit_persistent(const uint32_t *__restrict__ words, const uint64_t *__restrict__ event_off,
                      const Dims *__restrict__ dims, const uint32_t *__restrict__ event_road,
                      const RoadDesc *__restrict__ desc, uint64_t *counts, uint64_t road_cap,
@@ -552,9 +787,9 @@ __global__ void __launch_bounds__(512, 2)
                      const svt_config cfg, const FusedRoads fr, uint32_t roads_per_chunk,
                      uint32_t *out, unsigned long long *status) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    WarpSmem &sm = reinterpret_cast<WarpSmem *>(smem_raw)[threadIdx.x >> 5];
+    WarpSmem &sm = *reinterpret_cast<WarpSmem *>(smem_raw + SLOT_BYTES * (threadIdx.x >> 5));
     RecordList &rl = reinterpret_cast<RecordList *>(
-        smem_raw + sizeof(WarpSmem) * (blockDim.x >> 5))[threadIdx.x >> 5];
+        smem_raw + SLOT_BYTES * (blockDim.x >> 5))[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const Lanes<32> LW = lanes_of<32>(lane);
     wait_prior_grid();   // road extraction has completed (see launch_after)
@@ -594,17 +829,18 @@ __global__ void __launch_bounds__(512, 2)
         __syncwarp();
     };
 
-    // With four tiny roads per warp (GROUP 4) a batch without split roads
-    // skips phase 1 and hands every warp its first chunk of phase 2
-    // statically (chunk = the warp's index in the grid), the rest through the
+    // With four tiny roads per warp (GROUP 4) or one per lane (GROUP 32) a
+    // batch without split roads skips phase 1 and hands every warp its first
+    // chunk of phase 2 statically (warp w of block b takes chunk
+    // w * gridDim.x + b, so that a batch of fewer chunks than warps spreads
+    // over the SMs), the rest through the
     // counter counted from nw: the grid's warps then start without queueing
     // on one address, which for chunks this short is a large part of the
     // kernel (the paper's shape, 3000 events: 43 -> 37 us).  Otherwise every
     // claim goes through the counters (static first claims made the scaled
     // shape 6 % slower).
-    const uint32_t gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const uint32_t nw = gridDim.x * (blockDim.x >> 5);
-    const bool static_first = GROUP == 4 && n_items == 0;
+    const bool static_first = (GROUP == 4 || GROUP == 32) && n_items == 0;
 
     // phase 1: items of split roads
     while (!static_first) {
@@ -645,7 +881,7 @@ __global__ void __launch_bounds__(512, 2)
     // phase 2: chunks of consecutive roads, each fitted whole by this warp,
     // or two SMALL roads side by side by its two halves
     for (bool first = true;; first = false) {
-        uint32_t k = gw;   // chunk index
+        uint32_t k = (threadIdx.x >> 5) * gridDim.x + blockIdx.x;   // chunk index
         if (!(first && static_first)) {
             if (lane == 0) k = atomicAdd(bl.counters + 1, 1u) + (static_first ? nw : 0u);
             k = __shfl_sync(0xffffffffu, k, 0);
@@ -658,78 +894,123 @@ __global__ void __launch_bounds__(512, 2)
             da = __ldg(&desc[c0 + lane].a);
             db = __ldg(&desc[c0 + lane].b);
         }
-        for (uint32_t jj = 0; jj < n;) {
-            const RoadDesc D = shfl_desc(da, db, jj);
-            if (D.a.w > fr.small_max) {   // split road: done in phase 1
-                ++jj;
-                continue;
+        if constexpr (GROUP == 32) {
+            // the chunk's TINY roads one per lane, their records formed by
+            // their lanes and stored at once as runs of consecutive words ...
+            const bool mine = (uint32_t)lane < n && (db.x & GEO_TINY) && da.w <= fr.small_max;
+            const uint32_t lm = __ballot_sync(0xffffffffu, mine);
+            if (lm) {
+                LaneRecord rec;
+                if (mine)
+                    rec = lane_fit<GUARDED>(*reinterpret_cast<LaneTables *>(&sm), words, da, db, F,
+                                            q, cfg, sh, qsh, init_chi, lane);
+                __syncwarp();
+                uint32_t *stage = reinterpret_cast<uint32_t *>(&sm);
+                if (mine) {
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) stage[lane * 6 + j] = rec.w[j];
+                    n_pass += rec.pass ? 1u : 0u;
+                }
+                __syncwarp();
+                for (uint32_t e = (uint32_t)lane; e < n * 6; e += 32) {
+                    const uint32_t i = e / 6;
+                    if ((lm >> i) & 1u) out[(size_t)(c0 + i) * 6 + (e - i * 6)] = stage[e];
+                }
+                __syncwarp();
             }
-            if (n_rec > 32 - GROUP) flush();   // room for GROUP more
-            if constexpr (GROUP == 4) {
-                // four TINY roads with the same hits per layer and the same
-                // number of combinations to evaluate, so that the quarters
-                // run their loops in step
-                if ((D.b.x & GEO_TINY) && jj + 3 < n) {
-                    // lane k holds road c0 + k: one vote over the next four
-                    const bool same = (db.x & GEO_TINY) && da.y == D.a.y && da.w == D.a.w;
-                    const uint32_t votes = __ballot_sync(0xffffffffu, same);
-                    if (((votes >> jj) & 15u) == 15u) {
-                        const uint32_t qt = (uint32_t)lane >> 3;   // this lane's quarter and road
-                        QuarterSmem &qs = reinterpret_cast<QuarterSmem *>(&sm)[qt];
-                        const RoadDesc Dq = shfl_desc(da, db, jj + qt);
-                        const Lanes<8> LQ = lanes_of<8>(lane);
-                        Geo g = geo_of(Dq);
-                        unsigned long long best = ~0ull;
-                        if (g.C_eval) {
-                            quarter_geometry(g, Dq.a.y, cfg.xft_pairs);
-                            road_setup<8>(qs, words, Dq, g, F, q, sh, cfg.xft_pairs,
-                                          kColBias<GUARDED>, LQ);
-                            best = quarter_key(
-                                eval_rows<GUARDED, 8>(qs, g, 0, g.NA, qsh, init_chi, LQ), g.NB,
-                                Dq.b.y);
+            // ... then the others (not split) one per warp
+            uint32_t rest =
+                __ballot_sync(0xffffffffu, (uint32_t)lane < n && !mine && da.w <= fr.small_max);
+            while (rest) {
+                const uint32_t jj = (uint32_t)__ffs(rest) - 1u;
+                rest &= rest - 1u;
+                const RoadDesc D = shfl_desc(da, db, jj);
+                if (n_rec == 32) flush();
+                const unsigned long long best =
+                    fit_road<GUARDED, 32>(sm, words, D, F, q, cfg, sh, qsh, init_chi, LW);
+                if (lane == 0) {
+                    rl.key[n_rec] = best;
+                    rl.road[n_rec] = c0 + jj;
+                }
+                n_rec += 1;
+                __syncwarp();
+            }
+        } else {
+            for (uint32_t jj = 0; jj < n;) {
+                const RoadDesc D = shfl_desc(da, db, jj);
+                if (D.a.w > fr.small_max) {   // split road: done in phase 1
+                    ++jj;
+                    continue;
+                }
+                if (n_rec > 32 - GROUP) flush();   // room for GROUP more
+                if constexpr (GROUP == 4) {
+                    // four TINY roads with the same hits per layer and the same
+                    // number of combinations to evaluate, so that the quarters
+                    // run their loops in step
+                    if ((D.b.x & GEO_TINY) && jj + 3 < n) {
+                        // lane k holds road c0 + k: one vote over the next four
+                        const bool same = (db.x & GEO_TINY) && da.y == D.a.y && da.w == D.a.w;
+                        const uint32_t votes = __ballot_sync(0xffffffffu, same);
+                        if (((votes >> jj) & 15u) == 15u) {
+                            // this lane's quarter and road
+                            const uint32_t qt = (uint32_t)lane >> 3;
+                            QuarterSmem &qs = reinterpret_cast<QuarterSmem *>(&sm)[qt];
+                            const RoadDesc Dq = shfl_desc(da, db, jj + qt);
+                            const Lanes<8> LQ = lanes_of<8>(lane);
+                            Geo g = geo_of(Dq);
+                            unsigned long long best = ~0ull;
+                            if (g.C_eval) {
+                                quarter_geometry(g, Dq.a.y, cfg.xft_pairs);
+                                road_setup<8>(qs, words, Dq, g, F, q, sh, cfg.xft_pairs,
+                                              kColBias<GUARDED>, LQ);
+                                best = quarter_key(
+                                    eval_rows<GUARDED, 8>(qs, g, 0, g.NA, qsh, init_chi, LQ), g.NB,
+                                    Dq.b.y);
+                            }
+                            if ((lane & 7) == 0) {
+                                rl.key[n_rec + qt] = best;
+                                rl.road[n_rec + qt] = c0 + jj + qt;
+                            }
+                            n_rec += 4;
+                            jj += 4;
+                            __syncwarp();
+                            continue;
                         }
-                        if ((lane & 7) == 0) {
-                            rl.key[n_rec + qt] = best;
-                            rl.road[n_rec + qt] = c0 + jj + qt;
-                        }
-                        n_rec += 4;
-                        jj += 4;
-                        __syncwarp();
-                        continue;
                     }
                 }
-            }
-            if constexpr (GROUP >= 2) {
-                // two SMALL roads of the same geometry (split, NBp, ntop and NA),
-                // so that the two halves run their loops in step
-                if ((D.b.x & GEO_SMALL) && jj + 1 < n) {
-                    const RoadDesc D2 = shfl_desc(da, db, jj + 1);
-                    if ((D2.b.x & GEO_SMALL) && ((D.b.x ^ D2.b.x) & 0x1FFFu) == 0 &&
-                        D.b.z == D2.b.z && D2.a.w <= fr.small_max) {
-                        const uint32_t h = (uint32_t)lane >> 4;   // this lane's half and road
-                        HalfSmem &hs = reinterpret_cast<HalfSmem *>(&sm)[h];
-                        const unsigned long long best = fit_road<GUARDED, 16>(
-                            hs, words, h ? D2 : D, F, q, cfg, sh, qsh, init_chi, lanes_of<16>(lane));
-                        if ((lane & 15) == 0) {
-                            rl.key[n_rec + h] = best;
-                            rl.road[n_rec + h] = c0 + jj + h;
+                if constexpr (GROUP >= 2) {
+                    // two SMALL roads of the same geometry (split, NBp, ntop and NA),
+                    // so that the two halves run their loops in step
+                    if ((D.b.x & GEO_SMALL) && jj + 1 < n) {
+                        const RoadDesc D2 = shfl_desc(da, db, jj + 1);
+                        if ((D2.b.x & GEO_SMALL) && ((D.b.x ^ D2.b.x) & 0x1FFFu) == 0 &&
+                            D.b.z == D2.b.z && D2.a.w <= fr.small_max) {
+                            const uint32_t h = (uint32_t)lane >> 4;   // this lane's half and road
+                            HalfSmem &hs = reinterpret_cast<HalfSmem *>(&sm)[h];
+                            const unsigned long long best = fit_road<GUARDED, 16>(
+                                hs, words, h ? D2 : D, F, q, cfg, sh, qsh, init_chi,
+                                lanes_of<16>(lane));
+                            if ((lane & 15) == 0) {
+                                rl.key[n_rec + h] = best;
+                                rl.road[n_rec + h] = c0 + jj + h;
+                            }
+                            n_rec += 2;
+                            jj += 2;
+                            __syncwarp();
+                            continue;
                         }
-                        n_rec += 2;
-                        jj += 2;
-                        __syncwarp();
-                        continue;
                     }
                 }
+                const unsigned long long best =
+                    fit_road<GUARDED, 32>(sm, words, D, F, q, cfg, sh, qsh, init_chi, LW);
+                if (lane == 0) {
+                    rl.key[n_rec] = best;
+                    rl.road[n_rec] = c0 + jj;
+                }
+                n_rec += 1;
+                jj += 1;
+                __syncwarp();
             }
-            const unsigned long long best =
-                fit_road<GUARDED, 32>(sm, words, D, F, q, cfg, sh, qsh, init_chi, LW);
-            if (lane == 0) {
-                rl.key[n_rec] = best;
-                rl.road[n_rec] = c0 + jj;
-            }
-            n_rec += 1;
-            jj += 1;
-            __syncwarp();
         }
     }
     flush();
@@ -741,10 +1022,10 @@ __global__ void __launch_bounds__(512, 2)
 }  // namespace
 
 size_t fit_smem_bytes(int warps_per_block) {
-    return (sizeof(WarpSmem) + sizeof(RecordList)) * (size_t)warps_per_block;
+    return (SLOT_BYTES + sizeof(RecordList)) * (size_t)warps_per_block;
 }
 
-int fit_persistent_blocks_per_sm(int warps_per_block) {
+int fit_persistent_blocks_per_sm(int warps_per_block, uint32_t group) {
     const size_t smem = fit_smem_bytes(warps_per_block);
     int occ = 1 << 30;
     auto one = [&](auto kernel) {
@@ -755,12 +1036,20 @@ int fit_persistent_blocks_per_sm(int warps_per_block) {
             n = 0;
         occ = n < occ ? n : occ;
     };
-    one(k_fit_persistent<true, 1>);
-    one(k_fit_persistent<false, 1>);
-    one(k_fit_persistent<true, 2>);
-    one(k_fit_persistent<false, 2>);
-    one(k_fit_persistent<true, 4>);
-    one(k_fit_persistent<false, 4>);
+    // both instances of the group (the chi2 cut picks one at launch)
+    if (group == 32) {
+        one(k_fit_persistent<true, 32>);
+        one(k_fit_persistent<false, 32>);
+    } else if (group == 4) {
+        one(k_fit_persistent<true, 4>);
+        one(k_fit_persistent<false, 4>);
+    } else if (group == 2) {
+        one(k_fit_persistent<true, 2>);
+        one(k_fit_persistent<false, 2>);
+    } else {
+        one(k_fit_persistent<true, 1>);
+        one(k_fit_persistent<false, 1>);
+    }
     return occ;
 }
 
@@ -779,11 +1068,13 @@ cudaError_t launch_fit_persistent(const uint32_t *words, const uint64_t *event_o
                      status);
     };
     if (guarded) {
-        if (group == 4) launch(k_fit_persistent<true, 4>);
+        if (group == 32) launch(k_fit_persistent<true, 32>);
+        else if (group == 4) launch(k_fit_persistent<true, 4>);
         else if (group == 2) launch(k_fit_persistent<true, 2>);
         else launch(k_fit_persistent<true, 1>);
     } else {
-        if (group == 4) launch(k_fit_persistent<false, 4>);
+        if (group == 32) launch(k_fit_persistent<false, 32>);
+        else if (group == 4) launch(k_fit_persistent<false, 4>);
         else if (group == 2) launch(k_fit_persistent<false, 2>);
         else launch(k_fit_persistent<false, 1>);
     }

@@ -114,7 +114,9 @@ cudaError_t launch_fit_persistent(const uint32_t *words, const uint64_t *event_o
                                   const FusedRoads fr, uint32_t roads_per_chunk, uint32_t group,
                                   uint32_t *out, unsigned long long *status,
                                   int warps_per_block, int grid, cudaStream_t st);
-int fit_persistent_blocks_per_sm(int warps_per_block);
+// persistent blocks of the fit kernel per SM for a block size and a road
+// grouping (1, 2, 4 or 32; both chi2-cut instances of it)
+int fit_persistent_blocks_per_sm(int warps_per_block, uint32_t group);
 size_t fit_smem_bytes(int warps_per_block);
 
 // ---- plain path (svt_plain.cu) --------------------------------------------------

@@ -26,14 +26,16 @@ def gpu_run(words, event_off, F, q, cfg, path="fused", sched=None, road_cap=None
     if road_cap is None:
         road_cap = max(api.roads_in(words, event_off), 1)
     consts = api.DeviceConstants.from_numpy(F, q, cfg)
-    if path in ("fused_pair", "fused_quad"):
+    if path in ("fused_pair", "fused_quad", "fused_lanes"):
         # the fused path with pairing of small roads (chunks of 8 roads unless
         # the test gives its own schedule); fused_quad also groups four tiny
-        # roads per warp
+        # roads per warp; fused_lanes fits every tiny road on a lane of its
+        # own (chunks of 32 roads)
         s = sched if sched is not None else api.schedule()
+        lanes = path == "fused_lanes"
         sched = api.schedule(s.warps_per_block, s.blocks_per_sm, s.rows_per_item,
-                             s.roads_per_chunk or 8, s.small_max,
-                             2 if path == "fused_quad" else 1)
+                             s.roads_per_chunk or (32 if lanes else 8), s.small_max,
+                             3 if lanes else 2 if path == "fused_quad" else 1)
         path = "fused"
     dw = api.to_device_u32(words if n_words else np.zeros(4, np.uint32))
     de = api.to_device_u64(event_off)

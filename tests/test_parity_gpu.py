@@ -35,7 +35,7 @@ def consts_for(S):
     return CONSTS[S]
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad", "fused_lanes"])
 def test_small_batch(path):
     spec, consts, b = batch_for("small", 100, consts_for(64))
     cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb, n_sectors=64)
@@ -73,19 +73,21 @@ def test_paper_shape_3000_events():
     assert int(b.combinations().sum()) == 2048 * 3000
     cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb)
     key, rec = oracle_run(b.words, b.event_off, consts.F, consts.q, ocfg)
-    for path in ("fused", "plain", "fused_pair", "fused_quad"):
+    for path in ("fused", "plain", "fused_pair", "fused_quad", "fused_lanes"):
         st, got, _ = gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, path,
                              comb_cap=2048 * 3000)
         assert_same(st, got, key, rec, "paper/" + path)
 
 
-@pytest.mark.parametrize("group", [1, 2])
+@pytest.mark.parametrize("group", [1, 2, 3])
 def test_grouped_roads_in_mixed_shapes(group):
     """Events of the paper's shape (runs of identical tiny roads), of the
     small workload (tiny roads of mixed geometry) and of the scaled workload
     (mostly larger roads) interleaved in one batch: with pairs (group 1) or
-    also quads (group 2) the chunks mix quads, pairs and whole-warp roads,
-    and every record equals the oracle's."""
+    also quads (group 2) the chunks mix quads, pairs and whole-warp roads;
+    with one tiny road per lane (group 3) lanes of different geometry run
+    side by side and the chunk's other roads follow one per warp.  Every
+    record equals the oracle's."""
     from paper_1311_0380_gb300 import api
     consts = consts_for(512)
     parts = [synth.make_batch(name, n, consts, seed=70 + i)
@@ -100,7 +102,7 @@ def test_grouped_roads_in_mixed_shapes(group):
     off[1:] = np.cumsum([len(events[i]) for i in order])
     cfg, ocfg = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=262144)
     key, rec = oracle_run(words, off, consts.F, consts.q, ocfg)
-    for chunk in (4, 8, 13):
+    for chunk in ((4, 13, 32) if group == 3 else (4, 8, 13)):
         st, got, _ = gpu_run(words, off, consts.F, consts.q, cfg, "fused",
                              sched=api.schedule(8, 0, 16, chunk, 4096, group))
         assert_same(st, got, key, rec, f"group{group}/chunk{chunk}")
@@ -120,7 +122,9 @@ def test_uneven_batch_capped():
                                    (8, 0, 16, 4, 4096, 1), (4, 3, 7, 3, 100, 1),
                                    (16, 1, 64, 32, 64, 1), (2, 8, 2, 2, 33, 1), (1, 1, 1, 2, 1, 1),
                                    (8, 0, 16, 8, 4096, 2), (4, 3, 7, 5, 100, 2),
-                                   (1, 1, 1, 4, 1, 2)])
+                                   (1, 1, 1, 4, 1, 2), (8, 0, 16, 32, 4096, 3),
+                                   (4, 3, 7, 13, 100, 3), (1, 1, 1, 32, 1, 3),
+                                   (12, 1, 64, 1, 64, 3)])
 def test_schedules_give_identical_results(sched):
     from paper_1311_0380_gb300 import api
     spec, consts, b = batch_for("scaled", 60, consts_for(512))
@@ -133,7 +137,8 @@ def test_schedules_give_identical_results(sched):
 
 @pytest.mark.parametrize("sched", [(1, 1, 16, 4, 4096), (1, 1, 16, 4, 4096, 1), (1, 1, 8, 1, 64),
                                    (1, 1, 4, 3, 300, 1), (1, 1, 16, 8, 4096, 2),
-                                   (1, 1, 4, 5, 300, 2)])
+                                   (1, 1, 4, 5, 300, 2), (1, 1, 16, 32, 4096, 3),
+                                   (1, 1, 4, 7, 300, 3)])
 def test_record_lists_fill_and_flush(sched):
     """One warp per SM, so that every warp finishes well over 32 roads: its
     list of finished roads fills and is written out many times in the middle
@@ -154,10 +159,31 @@ def test_schedule_limits_are_checked():
     from paper_1311_0380_gb300 import api
     spec, consts, b = batch_for("scaled", 4, consts_for(512))
     cfg, _ = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb)
-    for bad in (api.schedule(pair_small=3), api.schedule(warps_per_block=17),
+    for bad in (api.schedule(pair_small=4), api.schedule(warps_per_block=17),
+                api.schedule(warps_per_block=13, pair_small=3),
                 api.schedule(roads_per_chunk=33), api.schedule(rows_per_item=65)):
         with pytest.raises(RuntimeError, match="BAD_ARG"):
             gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "fused", sched=bad)
+    # one road per lane reads the constants as 32-bit pairs: constants that
+    # start 2 bytes past an alignment boundary are refused before any launch
+    import torch
+    dc = api.DeviceConstants.from_numpy(consts.F, consts.q, cfg)
+    F2 = torch.empty(dc.F.numel() + 2, dtype=torch.int16, device=dc.F.device)
+    F2[1:1 + dc.F.numel()].copy_(dc.F.reshape(-1))
+    q2 = torch.empty(dc.q.numel() + 2, dtype=torch.int16, device=dc.q.device)
+    q2[1:1 + dc.q.numel()].copy_(dc.q.reshape(-1))
+    R = api.roads_in(b.words, b.event_off)
+    fp = api.FusedPath(len(b.words), b.n_events, R, dc)
+    dw, de = api.to_device_u32(b.words), api.to_device_u64(b.event_off)
+    for Fp, qp in ((F2[1:], dc.q), (dc.F, q2[1:])):
+        with pytest.raises(RuntimeError, match="BAD_ARG"):
+            api.svt_run(dw, len(b.words), de, b.n_events, Fp, qp, cfg, R, fp.out, fp.event_road,
+                        fp.counts, fp.status, fp.workspace, sched=api.schedule(pair_small=3))
+    # ... and the same buffers aligned run
+    api.svt_run(dw, len(b.words), de, b.n_events, dc.F, dc.q, cfg, R, fp.out, fp.event_road,
+                fp.counts, fp.status, fp.workspace, sched=api.schedule(pair_small=3))
+    torch.cuda.synchronize()
+    assert int(api.u64(fp.status)[0]) == api.N.STATUS_OK
 
 
 # ----------------------------------------------------------------------------- edge cases
@@ -217,7 +243,7 @@ def test_plain_fit_tiles_over_many_and_few_roads():
         assert_same(st, got, key, rec, f"plain tiles, capacity {cap}")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad", "fused_lanes"])
 def test_empty_batch_and_events_without_roads(path):
     F, q = random_consts(4, 1)
     cfg, ocfg = cfg_pair(n_sectors=4)
@@ -231,7 +257,7 @@ def test_empty_batch_and_events_without_roads(path):
     assert_same(st, got, key, rec, "no roads")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad", "fused_lanes"])
 def test_missing_layers_patterns_and_no_hits(path):
     rng = np.random.default_rng(3)
     F, q = random_consts(8, 2, scale=3000)
@@ -251,7 +277,7 @@ def test_missing_layers_patterns_and_no_hits(path):
         assert_same(st, got, key, rec, f"min_layers{min_layers}")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad", "fused_lanes"])
 def test_ties_and_extreme_constants(path):
     rng = np.random.default_rng(4)
     S = 2
@@ -273,7 +299,7 @@ def test_ties_and_extreme_constants(path):
             assert_same(st, got, key, rec, f"cut{cut} os{oshift} qs{qshift}")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad", "fused_lanes"])
 def test_chi_components_at_the_clamp_boundary(path):
     """chi components straddling +-32767 / +-32768 (the clamp of Eq. 2's
     chi-square), with cuts just below, at and above 32767^2: the range test of
@@ -307,7 +333,7 @@ def test_chi_components_at_the_clamp_boundary(path):
     assert 0 < n_pass[0] < n_pass[1] < n_pass[2] < n_pass[3]   # each cut decides roads
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad", "fused_lanes"])
 def test_maximum_hits_per_layer(path):
     # 16 hits in every layer: 16^6 combinations, capped
     rng = np.random.default_rng(6)
@@ -348,7 +374,7 @@ def test_uncapped_giant_road_fused():
     assert_same(st, got, key, rec, "giant")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad", "fused_lanes"])
 def test_validation_cases_match_oracle(path):
     from test_oracle_pins import tokens_to_words
     data = json.load(open(os.path.join(GOLDEN, "validation_cases.json")))

@@ -19,7 +19,7 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad", "fused_lanes"])
 @pytest.mark.parametrize("xft", [1, 0])
 def test_paired_batch(path, xft):
     spec, consts, b = batch_for("xft", 200)
@@ -35,7 +35,7 @@ def test_paired_batch(path, xft):
         assert int(extra[2]) == fits   # evaluated combinations
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad", "fused_lanes"])
 def test_paired_batch_split_roads_and_caps(path):
     """Caps and split roads (small_max) under pairing."""
     from paper_1311_0380_gb300 import api
@@ -49,7 +49,7 @@ def test_paired_batch_split_roads_and_caps(path):
         assert_same(st, got, key, rec, f"cap {max_comb}")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad", "fused_lanes"])
 def test_unpaired_road_is_reported(path):
     spec, consts, b = batch_for("xft", 40)
     w = b.words.copy()
@@ -74,7 +74,7 @@ def test_unpaired_road_is_reported(path):
     assert_same(st0, got0, key0, rec0, "pairing off")
 
 
-@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad"])
+@pytest.mark.parametrize("path", ["fused", "plain", "fused_pair", "fused_quad", "fused_lanes"])
 def test_hand_written_pairing_cases(path):
     ev = ["E:1:3",
           "R:0:1", "H:0:5", "H:1:5", "H:2:5", "H:3:5", "H:4:1", "H:4:2", "H:5:9", "H:5:8",
