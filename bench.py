@@ -81,7 +81,9 @@ def parse_args():
     ap.add_argument("--quad", action="store_true",
                     help="also group tiny roads four to a warp (pair_small = 2)")
     ap.add_argument("--lanes", action="store_true",
-                    help="one tiny road per lane, 32 roads per chunk (pair_small = 3)")
+                    help="tiny roads on lanes of their own, 32 roads per chunk unless --chunk "
+                         "says otherwise (pair_small = 3)")
+    ap.add_argument("--chunk", type=int, default=0, help="roads per chunk of the schedule")
     return ap.parse_args()
 
 
@@ -830,7 +832,8 @@ def main():
                      int(spec.xft))
     dconst = api.DeviceConstants.from_numpy(consts.F, consts.q, cfg, dev)
     n_words, n_events, R = len(batch.words), batch.n_events, batch.total_roads
-    sched = api.schedule(args.warps, args.bps, args.rows, 32 if args.lanes else 0,
+    sched = api.schedule(args.warps, args.bps, args.rows,
+                         args.chunk or (32 if args.lanes else 0),
                          pair_small=3 if args.lanes else 2 if args.quad else int(args.pair))
     fused = api.FusedPath(n_words, n_events, R, dconst, sched, dev)
     d_words = api.to_device_u32(batch.words, dev)
@@ -840,7 +843,7 @@ def main():
     stream = torch.cuda.current_stream()
     tuned = None
     if not args.no_tune and not (args.warps or args.rows or args.bps or args.pair or args.quad
-                                 or args.lanes):
+                                 or args.lanes or args.chunk):
         from paper_1311_0380_gb300 import autotune
         # timed as the steps are: L2 overwritten before every run
         sch, tms = autotune.tuned_schedule(fused, d_words, n_words, d_off, n_events, cache=None,

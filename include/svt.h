@@ -141,10 +141,12 @@ typedef struct {
  *                    2: also four consecutive tiny roads (at most 2 hits per
  *                    layer, at most 8 rows and 16 suffix-table entries) of
  *                    the same geometry by the four quarters of one warp;
- *                    3: every tiny road of a chunk by one lane of its own
- *                    (lane k: the chunk's road k, any geometry), then the
- *                    chunk's other roads one per warp; meant for 32 roads per
- *                    chunk; needs d_F and d_q 4-byte aligned and at most 12
+ *                    3: every tiny road of a chunk by lanes of its own (any
+ *                    geometry): one lane a road with more than 16 roads per
+ *                    chunk, two with 9..16, four with at most 8 (each lane
+ *                    then takes every second or fourth row of the road's
+ *                    combinations), then the chunk's other roads one per
+ *                    warp; needs d_F and d_q 4-byte aligned and at most 12
  *                    warps per block (else BAD_ARG);
  *                    0 (default): one road per warp.  Grouping pays when most
  *                    roads are small and alike (the paper's fixed shape); on
@@ -342,7 +344,7 @@ int svt_run_sized(const uint32_t *d_words, uint64_t max_words, const uint64_t *d
  * as many as fit, no pairing), then the fastest of those with pair_small = 1
  * and {2, 4, 8} roads per chunk, with pair_small = 2 and {4, 8, 16} roads
  * per chunk and (for 4-byte aligned d_F and d_q) with pair_small = 3 and
- * {16, 32} roads per chunk (8 warps per block where the fastest had 16), then
+ * {8, 16, 32} roads per chunk (8 warps per block where the fastest had 16), then
  * the fastest so far with 1 and 2 blocks per SM, one warm-up and `reps` timed
  * runs each (CUDA events on `stream`);
  * finally the four fastest of all these once more with 3 * reps runs each,

@@ -541,10 +541,10 @@ int svt_autotune(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_ev
                 if ((rc = trial(svt_schedule{base.warps_per_block, 0, base.rows_per_item,
                                              g == 2 ? 2 * c : c, base.small_max, g})) != SVT_OK)
                     goto done;
-        // one tiny road per lane, 16 or 32 roads per chunk (constants that
-        // are not 4-byte aligned rule it out)
+        // tiny roads on 1, 2 or 4 lanes each: 32, 16 or 8 roads per chunk
+        // (constants that are not 4-byte aligned rule it out)
         if (!(((uintptr_t)d_F | (uintptr_t)d_q) & 3u))
-            for (uint32_t c : {16u, 32u})
+            for (uint32_t c : {8u, 16u, 32u})
                 if ((rc = trial(svt_schedule{base.warps_per_block > 12 ? 8 : base.warps_per_block,
                                              0, base.rows_per_item, c, base.small_max, 3})) !=
                     SVT_OK)

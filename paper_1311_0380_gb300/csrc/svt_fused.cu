@@ -480,9 +480,13 @@ __device__ __forceinline__ RoadDesc shfl_desc(const uint4 &da, const uint4 &db, 
 // 8) go to the lane's column of the slot's tables; each row's sums are formed
 // once in registers.  With track-trigger pairs layer 5 has radix 1 and its
 // hits' terms are added to those of their layer-4 partners, as in
-// road_setup.  The record is the one form_record writes: flags, the best c
-// and its chi2, and the three parameter rows (Eq. 1) of the best combination
-// formed in int64 from its hits' coordinates, which the lane still holds.
+// road_setup.  With L > 1 lanes to a road (lanes sub = 0..L-1 of a group of
+// L consecutive lanes) each lane takes the rows a = sub mod L and the group
+// merges its (chi2, c) keys; every lane of the group builds the same column
+// sums in its own column.  The record is the one form_record writes: flags,
+// the best c and its chi2, and the three parameter rows (Eq. 1) of the best
+// combination formed in int64 from its hits' coordinates, which the lanes
+// still hold.
 struct LaneRecord {
     uint32_t w[6];
     bool pass;
@@ -493,7 +497,8 @@ __device__ __forceinline__ LaneRecord lane_fit(LaneTables &tb, const uint32_t *_
                                                const int16_t *__restrict__ F,
                                                const int16_t *__restrict__ q,
                                                const svt_config &cfg, uint32_t sh, uint32_t qsh,
-                                               uint32_t init_chi, int lane) {
+                                               uint32_t init_chi, int lane, uint32_t L,
+                                               uint32_t group_mask) {
     const uint32_t C_eval = da.w, packed = da.y, geo = db.x, xft = cfg.xft_pairs;
     const size_t cs = (size_t)rd_sector(da.z) * 64 + ((geo >> 13) & 63u);
     // The chi rows k = 3..5 of F as pairs of int16 (F[k][l], F[k][l+1]) for
@@ -599,8 +604,8 @@ __device__ __forceinline__ LaneRecord lane_fit(LaneTables &tb, const uint32_t *_
         }
     }
     uint32_t bchi = init_chi, bc = 0;
-    const uint32_t NA3 = 1u << (beta[0] + beta[1] + beta[2]);
-    for (uint32_t a = 0, c0 = 0; a < NA3 && c0 < C_eval; ++a, c0 += NB3) {
+    const uint32_t NA3 = 1u << (beta[0] + beta[1] + beta[2]), sub = (uint32_t)lane & (L - 1u);
+    for (uint32_t a = sub, c0 = sub * NB3; a < NA3 && c0 < C_eval; a += L, c0 += L * NB3) {
         const uint32_t d2 = a & beta[2], d1 = (a >> beta[2]) & beta[1],
                        d0 = (a >> (beta[2] + beta[1])) & beta[0];
         long long A[3];
@@ -641,9 +646,17 @@ __device__ __forceinline__ LaneRecord lane_fit(LaneTables &tb, const uint32_t *_
             }
         }
     }
+    // the group's best: smallest chi2, then smallest c
+    unsigned long long key = bchi != init_chi ? ((unsigned long long)bchi << 32) | bc : ~0ull;
+    for (uint32_t d = 1; d < L; d <<= 1) {
+        const unsigned long long o = __shfl_xor_sync(group_mask, key, d);
+        key = o < key ? o : key;
+    }
+    bchi = (uint32_t)(key >> 32);
+    bc = (uint32_t)key;
     // the record
     LaneRecord rec;
-    rec.pass = C_eval > 0 && bchi != init_chi;
+    rec.pass = C_eval > 0 && key != ~0ull;
     uint32_t flags = rec.pass ? SVT_FLAG_PASS : 0u;
     if (((geo >> 19) & 127u) == 0) flags |= SVT_FLAG_NO_HITS;
     if (geo & (1u << 27)) flags |= SVT_FLAG_BAD_PATTERN;
@@ -808,6 +821,9 @@ __global__ void __launch_bounds__(GROUP == 32 ? 384 : 512, 2)
     const uint32_t R = (uint32_t)R64;
     const uint32_t sh = 32u - cfg.oshift, qsh = cfg.qshift + sh;
     const uint32_t init_chi = cfg.chi2_cut == 0xFFFFFFFFu ? 0xFFFFFFFFu : cfg.chi2_cut + 1u;
+    // GROUP 32: lanes to a tiny road, so that chunks of 32, 16 or at most 8
+    // roads fill the warp
+    const uint32_t L = GROUP != 32 ? 1u : roads_per_chunk > 16 ? 1u : roads_per_chunk > 8 ? 2u : 4u;
     uint32_t n_rec = 0;    // entries of rl (uniform over the warp)
     uint32_t n_pass = 0;   // passing roads whose records this lane wrote, summed at exit
     // Each lane forms one listed record into the warp's road slot (free
@@ -889,42 +905,46 @@ __global__ void __launch_bounds__(GROUP == 32 ? 384 : 512, 2)
         if ((uint64_t)k * roads_per_chunk >= R) break;
         const uint32_t c0 = k * roads_per_chunk;
         const uint32_t n = min(roads_per_chunk, R - c0);
+        // this lane's road of the chunk (GROUP 32: L lanes to a road)
+        const uint32_t jr = (uint32_t)lane / L;
         uint4 da = make_uint4(0, 0, 0, 0), db = make_uint4(0, 0, 0, 0);
-        if ((uint32_t)lane < n) {
-            da = __ldg(&desc[c0 + lane].a);
-            db = __ldg(&desc[c0 + lane].b);
+        if (jr < n) {
+            da = __ldg(&desc[c0 + jr].a);
+            db = __ldg(&desc[c0 + jr].b);
         }
         if constexpr (GROUP == 32) {
-            // the chunk's TINY roads one per lane, their records formed by
-            // their lanes and stored at once as runs of consecutive words ...
-            const bool mine = (uint32_t)lane < n && (db.x & GEO_TINY) && da.w <= fr.small_max;
+            // the chunk's TINY roads, L lanes each, their records formed by
+            // their first lanes and stored at once as runs of consecutive
+            // words ...
+            const bool mine = jr < n && (db.x & GEO_TINY) && da.w <= fr.small_max;
             const uint32_t lm = __ballot_sync(0xffffffffu, mine);
+            const bool first_lane = ((uint32_t)lane & (L - 1u)) == 0;
             if (lm) {
                 LaneRecord rec;
                 if (mine)
                     rec = lane_fit<GUARDED>(*reinterpret_cast<LaneTables *>(&sm), words, da, db, F,
-                                            q, cfg, sh, qsh, init_chi, lane);
+                                            q, cfg, sh, qsh, init_chi, lane, L, lm);
                 __syncwarp();
                 uint32_t *stage = reinterpret_cast<uint32_t *>(&sm);
-                if (mine) {
+                if (mine && first_lane) {
 #pragma unroll
-                    for (int j = 0; j < 6; ++j) stage[lane * 6 + j] = rec.w[j];
+                    for (int j = 0; j < 6; ++j) stage[jr * 6 + j] = rec.w[j];
                     n_pass += rec.pass ? 1u : 0u;
                 }
                 __syncwarp();
                 for (uint32_t e = (uint32_t)lane; e < n * 6; e += 32) {
                     const uint32_t i = e / 6;
-                    if ((lm >> i) & 1u) out[(size_t)(c0 + i) * 6 + (e - i * 6)] = stage[e];
+                    if ((lm >> (i * L)) & 1u) out[(size_t)(c0 + i) * 6 + (e - i * 6)] = stage[e];
                 }
                 __syncwarp();
             }
             // ... then the others (not split) one per warp
-            uint32_t rest =
-                __ballot_sync(0xffffffffu, (uint32_t)lane < n && !mine && da.w <= fr.small_max);
+            uint32_t rest = __ballot_sync(0xffffffffu,
+                                          first_lane && jr < n && !mine && da.w <= fr.small_max);
             while (rest) {
-                const uint32_t jj = (uint32_t)__ffs(rest) - 1u;
+                const uint32_t src = (uint32_t)__ffs(rest) - 1u, jj = src / L;
                 rest &= rest - 1u;
-                const RoadDesc D = shfl_desc(da, db, jj);
+                const RoadDesc D = shfl_desc(da, db, src);
                 if (n_rec == 32) flush();
                 const unsigned long long best =
                     fit_road<GUARDED, 32>(sm, words, D, F, q, cfg, sh, qsh, init_chi, LW);
