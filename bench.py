@@ -67,6 +67,8 @@ def parse_args():
     ap.add_argument("--no-calib", action="store_true", help="skip the FP32 calibration measurement")
     ap.add_argument("--no-uneven", action="store_true",
                     help="skip the full-size uneven workload (65536 events per launch)")
+    ap.add_argument("--no-batch-sweep", action="store_true",
+                    help="skip the scaled workload's batch sizes (1, 10, 100, 1000, 3000 events)")
     ap.add_argument("--no-tune", action="store_true", help="use the default schedule")
     ap.add_argument("--sweep", action="store_true",
                     help="latency against the number of fits for the paper-shape workload "
@@ -742,6 +744,123 @@ def end_to_end(args, spec, consts, dconst, sched, rank, world, dev, barrier):
 UNEVEN_EVENTS = 65536
 
 
+SCALED_BATCH_SIZES = (1, 10, 100, 1000, 3000)
+
+
+def scaled_batch_sweep(spec, batch, dconst, dev, flush, reps=20, warmup=3):
+    """The scaled workload's batch sizes (the first 1, 10, 100, 1000 and all
+    3000 events of the headline batch), each with the schedule the autotuner
+    picks for it, the fused path beside the plain per-stage path, L2
+    overwritten before every timed run.  Per size: latency with inputs
+    resident in HBM (both paths), and end to end from pinned host memory,
+    each run copying its batch in and its records and status back: the fused
+    path through its one C call (svt_run_host), and both paths through the
+    same Python runner (torch copies around the path's calls), so that the
+    fused-vs-plain comparison carries the same host overhead on both sides.
+    Every size checks that both paths give the same records."""
+    import torch
+    from paper_1311_0380_gb300 import api, autotune
+    stream = torch.cuda.current_stream()
+    road_end = np.concatenate([[0], np.cumsum(batch.n_roads)])
+    fits_road = np.concatenate([[0], np.cumsum(batch.combinations(spec.max_comb))])
+
+    def stats(us):
+        return {"mean": statistics.mean(us), "p50": percentile(us, 50), "p99": percentile(us, 99)}
+
+    def timed(run, on=None):
+        """Latency (us) of `reps` runs, each after an L2 overwrite; events on
+        the stream `on` (default: the current one)."""
+        st = on if on is not None else stream
+        for _ in range(warmup):
+            run(None)
+        torch.cuda.synchronize()
+        us = []
+        for i in range(reps):
+            flush.fill_(i)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            run((a, b, st))
+            b.synchronize()
+            us.append(a.elapsed_time(b) * 1e3)
+        return us
+
+    rows = []
+    for n_ev in SCALED_BATCH_SIZES:
+        n_words = int(batch.event_off[n_ev])
+        words, off = batch.words[:n_words], batch.event_off[: n_ev + 1].copy()
+        R = int(road_end[n_ev])
+        fits = int(fits_road[R])
+        d_w, d_o = api.to_device_u32(words, dev), api.to_device_u64(off, dev)
+        fp = api.FusedPath(n_words, n_ev, R, dconst, None, dev)
+        sched, _ = autotune.tuned_schedule(fp, d_w, n_words, d_o, n_ev, cache=None, flush=flush,
+                                           reps=2)
+        fp.sched = sched
+
+        def fused_run(m):
+            if m:
+                m[0].record(m[2])
+            fp.run(d_w, n_words, d_o, n_ev)
+            if m:
+                m[1].record(m[2])
+        fused_us = timed(fused_run)
+        fst, frec, _ = fp.result()
+        pp = api.PlainPath(n_words, n_ev, R, fits, dconst, dev)
+
+        def plain_run(m):
+            if m:
+                m[0].record(m[2])
+            pp.run(d_w, n_words, d_o, n_ev)
+            if m:
+                m[1].record(m[2])
+        plain_us = timed(plain_run)
+        pst, prec, _ = pp.result()
+        assert fst == api.N.STATUS_OK and pst == api.N.STATUS_OK and np.array_equal(frec, prec), \
+            f"fused and plain paths differ at {n_ev} events"
+        # end to end
+        h_w, h_o = api.HostRunner.pin_batch(words, off)
+        sr = api.StreamingRunner(n_words, n_ev, R, dconst, sched, dev, depth=1)
+
+        def c_entry(m):
+            sr.submit(h_w, h_o, marks=(m[0], m[1]) if m else None)
+            sr.wait()
+        e2e_us = timed(c_entry, sr.streams[0])
+        est, erec = sr.wait()
+        assert est == api.N.STATUS_OK and np.array_equal(erec, frec)
+        py = {}
+        for name, path in (("fused", fp), ("plain", pp)):
+            hr = api.HostRunner(path, stream)
+
+            def py_run(m, hr=hr):
+                if m:
+                    m[0].record(m[2])
+                hr.submit(h_w, h_o, R)
+                if m:
+                    m[1].record(m[2])
+                hr.wait()
+            py[name] = timed(py_run)
+            pst2, prec2 = hr.wait()
+            assert pst2 == api.N.STATUS_OK and np.array_equal(prec2, frec)
+        rows.append({
+            "events": n_ev, "roads": R, "fits": fits,
+            "h2d_bytes": 4 * n_words + 8 * (n_ev + 1), "d2h_bytes": 24 * R + 8,
+            "schedule": {f: getattr(sched, f) for f, _ in api.SvtSchedule._fields_},
+            "fused_us": stats(fused_us), "plain_us": stats(plain_us),
+            "fused_e2e_us": stats(e2e_us),
+            "fused_e2e_python_us": stats(py["fused"]), "plain_e2e_python_us": stats(py["plain"]),
+            "fused_fits_per_s": fits / (statistics.mean(fused_us) / 1e6),
+            "fused_events_per_s": n_ev / (statistics.mean(fused_us) / 1e6),
+            "fused_e2e_events_per_s": n_ev / (statistics.mean(e2e_us) / 1e6),
+            "plain_fits_per_s": fits / (statistics.mean(plain_us) / 1e6)})
+        del pp, fp, sr
+    return {"workload": "scaled, first N events of the headline batch",
+            "timing": "CUDA events; 256 MB written before every run (L2 cold); "
+                      f"{reps} runs per size after {warmup} warm-up",
+            "e2e": "fused_e2e: svt_run_host (one C call: H2D, fused path, D2H on one stream); "
+                   "*_e2e_python: the same copies as torch copies around the path's calls "
+                   "from Python (one svt_run, or the five per-stage calls)",
+            "rows": rows}
+
+
 def uneven_full(dev, flush, timer, steps=5, warmup=2):
     """The uneven workload at its full size: 65536 events per launch (16
     copies of a 4096-event draw; roads log-uniform in 1..2048, 1-16 hits per
@@ -995,6 +1114,11 @@ def main():
             plain["e2e_p99_us"] = percentile(lat, 99)
         del pp
 
+    # ---- the scaled workload's batch sizes, fused beside plain
+    batch_sweep = None
+    if rank == 0 and not args.no_batch_sweep and args.workload == "scaled" and n_events >= 3000:
+        batch_sweep = scaled_batch_sweep(spec, batch, dconst, dev, flush)
+
     serve_out = None
     if rank == 0 and not args.no_serve:
         serve_out = serving(dev, args.serve_short)
@@ -1025,7 +1149,7 @@ def main():
             "latency_us": {"p50": percentile([m * 1e3 for m in step_ms], 50),
                            "p99": percentile([m * 1e3 for m in step_ms], 99)},
             "e2e": e2e, "plain": plain, "roofline": roofline, "cpu_baseline": cpu,
-            "cpu_baseline_omp": cpu_omp, "uneven": uneven,
+            "cpu_baseline_omp": cpu_omp, "uneven": uneven, "batch_sizes": batch_sweep,
             "serving": serve_out,
             "calibration": calib_out,
             "clocks": clock_summary,
