@@ -481,7 +481,7 @@ __device__ __forceinline__ RoadDesc shfl_desc(const uint4 &da, const uint4 &db, 
 // once in registers.  With track-trigger pairs layer 5 has radix 1 and its
 // hits' terms are added to those of their layer-4 partners, as in
 // road_setup.  With L > 1 lanes to a road (lanes sub = 0..L-1 of a group of
-// L consecutive lanes) each lane takes the rows a = sub mod L and the group
+// L consecutive lanes) each lane takes the rows a = sub (mod L) and the group
 // merges its (chi2, c) keys; every lane of the group builds the same column
 // sums in its own column.  The record is the one form_record writes: flags,
 // the best c and its chi2, and the three parameter rows (Eq. 1) of the best
@@ -503,7 +503,7 @@ __device__ __forceinline__ LaneRecord lane_fit(LaneTables &tb, const uint32_t *_
     const size_t cs = (size_t)rd_sector(da.z) * 64 + ((geo >> 13) & 63u);
     // The chi rows k = 3..5 of F as pairs of int16 (F[k][l], F[k][l+1]) for
     // even l (row k starts at element (cs * 36 + 6 k), an even index, so each
-    // pair is 4-byte aligned), q_3, and the pair (q_4, q_5); two hit words per
+    // pair is 4-byte aligned), the pairs (q_2, q_3), (q_4, q_5); two hit words per
     // layer (the second repeats the first when the layer has one hit; a layer
     // without hits reads the road's header word and takes x = 0).  Every load
     // is issued before any is used.
