@@ -153,6 +153,37 @@ def recorded_traffic():
     return recorded_profile("traffic_bytes_per_launch")
 
 
+def recorded_schedule(note=TRAFFIC_NOTE):
+    """The schedule the committed ncu figures were taken with
+    (`profiled_schedule: field=value ... kernel_sha: sha`), or None."""
+    try:
+        text = open(note).read()
+    except OSError:
+        return None
+    m = re.search(r"profiled_schedule:\s*((?:\w+=\d+\s+)+)kernel_sha:\s*([0-9a-f]+)", text)
+    if not m or m.group(2) != file_sha(FIT_KERNEL_SRC):
+        return None
+    return {k: int(v) for k, v in (kv.split("=") for kv in m.group(1).split())}
+
+
+def same_work_split(a, b, max_comb):
+    """Whether two schedules give the fit kernel the same work units, so that
+    its instructions per combination agree: the same roads per chunk and
+    grouping, and -- where roads are split at all (small_max below the
+    workload's cap) -- the same split threshold and rows per item."""
+    if a is None or b is None:
+        return False
+    defaults = {"warps_per_block": 8, "rows_per_item": 16, "roads_per_chunk": 4,
+                "small_max": 4096}   # what zero fields of a schedule mean
+
+    def key(s):
+        s = {f: (v or defaults.get(f, v)) for f, v in s.items()}
+        split = s["small_max"] < max_comb
+        return (s["roads_per_chunk"], s["pair_small"], s["rows_per_item"] if split else None,
+                s["small_max"] if split else None)
+    return key(a) == key(b)
+
+
 class ClockSampler:
     """nvidia-smi samples during the timed region."""
 
@@ -924,8 +955,11 @@ def uneven_full(dev, flush, timer, steps=5, warmup=2):
     ipf = recorded_profile("warp_instructions_per_fit_uneven", UNEVEN_NOTE)
     if ipf is not None:
         ach = ipf * fits / fit_s / 1e9
+        prof_sched = recorded_schedule(UNEVEN_NOTE)
         out.update({"warp_instructions_per_fit": ipf, "issue_ginst_s": ach,
-                    "issue_frac": ach / ISSUE_PEAK_GINST})
+                    "issue_frac": ach / ISSUE_PEAK_GINST, "ipf_schedule": prof_sched,
+                    "ipf_schedule_matches": same_work_split(out["schedule"], prof_sched,
+                                                            spec.max_comb)})
     del fp, d_words, d_off
     torch.cuda.empty_cache()
     return out
@@ -1030,11 +1064,20 @@ def main():
     hbm_peak = measured_hbm_peak()
     if ipf is not None:
         ach = ipf * fits_per_step / fit_mean_s / 1e9
+        prof_sched = recorded_schedule()
+        run_sched = {f: getattr(fused.sched, f) for f, _ in api.SvtSchedule._fields_} \
+            if fused.sched is not None else None
         roofline = {"bound": "alu", "achieved": ach, "peak": ISSUE_PEAK_GINST,
                     "unit": "G warp-instructions/s", "frac": ach / ISSUE_PEAK_GINST,
                     "peak_source": "derived: 152 SM x 4 schedulers x 2.07 GHz (issue rate)",
                     "warp_instructions_per_fit": ipf,
-                    "frac_of_measured_issue": ach / issue_measured}
+                    "frac_of_measured_issue": ach / issue_measured,
+                    # the schedule of the ncu figure, and whether the timed
+                    # schedule splits the work the same way (else the
+                    # instructions per combination are those of the other)
+                    "ipf_schedule": prof_sched,
+                    "ipf_schedule_matches": same_work_split(run_sched, prof_sched,
+                                                            spec.max_comb)}
     else:
         # no ncu figure for this kernel source and workload: the direct-form
         # algorithmic rate against the int32 unit count, labelled as such

@@ -129,7 +129,9 @@ typedef struct {
  *   warps_per_block  warps of one persistent block (1..16, default 8)
  *   blocks_per_sm    persistent blocks per SM (default: as many as fit)
  *   rows_per_item    rows of the (prefix x suffix) combination grid in one
- *                    work item of a split road (1..64, default 16)
+ *                    work item of a split road (1..1024, default 16; each
+ *                    item repeats its road's set-up, so longer items cost
+ *                    less set-up and balance the work less finely)
  *   roads_per_chunk  consecutive roads a warp takes at once (1..32, default 4)
  *   small_max        roads with more evaluated combinations than this are
  *                    split into work items; the others are fitted whole by
@@ -341,7 +343,8 @@ int svt_run_sized(const uint32_t *d_words, uint64_t max_words, const uint64_t *d
 /* Schedule autotuner: runs svt_run on one device-resident batch for every
  * schedule of {4, 8, 16} warps per block x {8, 16, 32, 64} rows per item x
  * {1, 2, 4, 8} roads per chunk x {1024, 4096, 16384} small_max (blocks per SM
- * as many as fit, no pairing), then the fastest of those with pair_small = 1
+ * as many as fit, no pairing), then the fastest of those with 2 and 4 times
+ * its rows per item, then the fastest so far with pair_small = 1
  * and {2, 4, 8} roads per chunk, with pair_small = 2 and {4, 8, 16} roads
  * per chunk and (for 4-byte aligned d_F and d_q) with pair_small = 3 and
  * {8, 16, 32} roads per chunk (8 warps per block where the fastest had 16), then

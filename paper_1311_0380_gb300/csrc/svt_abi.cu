@@ -58,7 +58,7 @@ svt_schedule resolve(const svt_schedule *s) {
 
 bool schedule_ok(const svt_schedule &s) {
     return s.warps_per_block >= 1 && s.warps_per_block <= 16 && s.blocks_per_sm <= 32 &&
-           s.rows_per_item >= 1 && s.rows_per_item <= 64 && s.roads_per_chunk >= 1 &&
+           s.rows_per_item >= 1 && s.rows_per_item <= 1024 && s.roads_per_chunk >= 1 &&
            s.roads_per_chunk <= 32 && s.small_max >= 1 && s.pair_small <= 3 &&
            (s.pair_small != 3 || s.warps_per_block <= 12);
 }
@@ -534,6 +534,15 @@ int svt_autotune(const uint32_t *d_words, uint64_t n_words, const uint64_t *d_ev
             for (uint32_t c : kChunk)
                 for (uint32_t m : kSmall)
                     if ((rc = trial(svt_schedule{w, 0, r, c, m, 0})) != SVT_OK) goto done;
+    {
+        // longer items of split roads (each item repeats its road's set-up)
+        const svt_schedule base = top_s[0];
+        for (uint32_t f : {2u, 4u}) {
+            svt_schedule sc = base;
+            sc.rows_per_item = base.rows_per_item * f;
+            if ((rc = trial(sc)) != SVT_OK) goto done;
+        }
+    }
     {
         const svt_schedule base = top_s[0];
         for (uint32_t g : {1u, 2u})

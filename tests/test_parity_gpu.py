@@ -124,7 +124,8 @@ def test_uneven_batch_capped():
                                    (8, 0, 16, 8, 4096, 2), (4, 3, 7, 5, 100, 2),
                                    (1, 1, 1, 4, 1, 2), (8, 0, 16, 32, 4096, 3),
                                    (4, 3, 7, 13, 100, 3), (1, 1, 1, 32, 1, 3),
-                                   (12, 1, 64, 1, 64, 3)])
+                                   (12, 1, 64, 1, 64, 3), (8, 0, 256, 4, 1024),
+                                   (4, 3, 1000, 3, 100), (2, 1, 129, 2, 64, 1)])
 def test_schedules_give_identical_results(sched):
     from paper_1311_0380_gb300 import api
     spec, consts, b = batch_for("scaled", 60, consts_for(512))
@@ -161,7 +162,7 @@ def test_schedule_limits_are_checked():
     cfg, _ = cfg_pair(chi2_cut=consts.chi2_cut_99, max_comb=spec.max_comb)
     for bad in (api.schedule(pair_small=4), api.schedule(warps_per_block=17),
                 api.schedule(warps_per_block=13, pair_small=3),
-                api.schedule(roads_per_chunk=33), api.schedule(rows_per_item=65)):
+                api.schedule(roads_per_chunk=33), api.schedule(rows_per_item=1025)):
         with pytest.raises(RuntimeError, match="BAD_ARG"):
             gpu_run(b.words, b.event_off, consts.F, consts.q, cfg, "fused", sched=bad)
     # one road per lane reads the constants as 32-bit pairs: constants that
