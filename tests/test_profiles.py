@@ -33,3 +33,28 @@ def test_recorded_figures_are_plausible():
     assert 0.5 < ipf_uneven < ipf < 4.0
     # the kernel reads the words and descriptors once: tens of MB, not GB
     assert 1e7 < traffic < 1e8
+
+
+def test_work_split_comparison():
+    """Schedules that hand the fit kernel the same work units compare equal:
+    zero fields mean the defaults, and the split threshold and rows per item
+    only count where roads are split at all."""
+    import bench
+    default = {"warps_per_block": 8, "blocks_per_sm": 0, "rows_per_item": 16,
+               "roads_per_chunk": 4, "small_max": 4096, "pair_small": 0}
+    zeros = {k: 0 for k in default}
+    assert bench.same_work_split(zeros, default, 262144)
+    # warps per block and blocks per SM do not change the work units
+    assert bench.same_work_split(dict(default, warps_per_block=16, blocks_per_sm=2), default,
+                                 262144)
+    # with split roads the rows per item and the threshold count ...
+    assert not bench.same_work_split(dict(default, rows_per_item=256), default, 262144)
+    assert not bench.same_work_split(dict(default, small_max=1024), default, 262144)
+    # ... without them (every road within the threshold) they do not
+    assert bench.same_work_split(dict(default, rows_per_item=256, small_max=16384), default, 4096)
+    assert not bench.same_work_split(dict(default, roads_per_chunk=2), default, 4096)
+    assert not bench.same_work_split(dict(default, pair_small=3), default, 4096)
+    assert not bench.same_work_split(None, default, 4096)
+    # the recorded schedules parse
+    assert bench.recorded_schedule()["rows_per_item"] >= 1
+    assert bench.recorded_schedule(bench.UNEVEN_NOTE)["roads_per_chunk"] >= 1
