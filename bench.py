@@ -776,11 +776,14 @@ UNEVEN_EVENTS = 65536
 
 
 SCALED_BATCH_SIZES = (1, 10, 100, 1000, 3000)
+PAPER_BATCH_SIZES = (1, 100, 1000, 3000)
 
 
-def scaled_batch_sweep(spec, batch, dconst, dev, flush, reps=20, warmup=3):
-    """The scaled workload's batch sizes (the first 1, 10, 100, 1000 and all
-    3000 events of the headline batch), each with the schedule the autotuner
+def batch_size_sweep(spec, batch, dconst, dev, flush, sizes=SCALED_BATCH_SIZES,
+                     label="scaled, first N events of the headline batch", reps=20, warmup=3):
+    """A workload's batch sizes (the first N events of one batch; for the
+    scaled workload 1, 10, 100, 1000 and all 3000 events of the headline
+    batch, for the paper's shape 1, 100, 1000 and 3000), each with the schedule the autotuner
     picks for it, the fused path beside the plain per-stage path, L2
     overwritten before every timed run.  Per size: latency with inputs
     resident in HBM (both paths), and end to end from pinned host memory,
@@ -816,7 +819,7 @@ def scaled_batch_sweep(spec, batch, dconst, dev, flush, reps=20, warmup=3):
         return us
 
     rows = []
-    for n_ev in SCALED_BATCH_SIZES:
+    for n_ev in sizes:
         n_words = int(batch.event_off[n_ev])
         words, off = batch.words[:n_words], batch.event_off[: n_ev + 1].copy()
         R = int(road_end[n_ev])
@@ -883,7 +886,7 @@ def scaled_batch_sweep(spec, batch, dconst, dev, flush, reps=20, warmup=3):
             "fused_e2e_events_per_s": n_ev / (statistics.mean(e2e_us) / 1e6),
             "plain_fits_per_s": fits / (statistics.mean(plain_us) / 1e6)})
         del pp, fp, sr
-    return {"workload": "scaled, first N events of the headline batch",
+    return {"workload": label,
             "timing": "CUDA events; 256 MB written before every run (L2 cold); "
                       f"{reps} runs per size after {warmup} warm-up",
             "e2e": "fused_e2e: svt_run_host (one C call: H2D, fused path, D2H on one stream); "
@@ -1157,10 +1160,20 @@ def main():
             plain["e2e_p99_us"] = percentile(lat, 99)
         del pp
 
-    # ---- the scaled workload's batch sizes, fused beside plain
-    batch_sweep = None
+    # ---- the scaled workload's batch sizes, fused beside plain, and those of
+    # the paper's shape (events of 32 roads x 2^6 combinations, its Sec. 4.1)
+    batch_sweep = paper_sweep = None
     if rank == 0 and not args.no_batch_sweep and args.workload == "scaled" and n_events >= 3000:
-        batch_sweep = scaled_batch_sweep(spec, batch, dconst, dev, flush)
+        batch_sweep = batch_size_sweep(spec, batch, dconst, dev, flush)
+        from paper_1311_0380_gb300 import synth
+        pspec = synth.SPECS["paper"]
+        pconsts = synth.make_constants(pspec.n_sectors)
+        pcfg = api.config(15, 15, pconsts.chi2_cut_99, pspec.max_comb, 5, pspec.n_sectors)
+        pdconst = api.DeviceConstants.from_numpy(pconsts.F, pconsts.q, pcfg, dev)
+        pbatch = synth.make_batch(pspec, max(PAPER_BATCH_SIZES), pconsts)
+        paper_sweep = batch_size_sweep(pspec, pbatch, pdconst, dev, flush, PAPER_BATCH_SIZES,
+                                       "paper shape (32 roads of 64 combinations an event), "
+                                       "first N events of a 3000-event batch")
 
     serve_out = None
     if rank == 0 and not args.no_serve:
@@ -1193,6 +1206,7 @@ def main():
                            "p99": percentile([m * 1e3 for m in step_ms], 99)},
             "e2e": e2e, "plain": plain, "roofline": roofline, "cpu_baseline": cpu,
             "cpu_baseline_omp": cpu_omp, "uneven": uneven, "batch_sizes": batch_sweep,
+            "paper_batch_sizes": paper_sweep,
             "serving": serve_out,
             "calibration": calib_out,
             "clocks": clock_summary,
